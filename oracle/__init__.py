@@ -1,0 +1,180 @@
+"""CPU oracle for the halo-finding path (3D FoF, 6D FoF hierarchy, unbinding, halo properties).
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline may import this package. The product path (``paper_2412_18629_gb300``) never does.
+
+The arithmetic lives in ``rs_oracle.cpp`` (plain C++17, built with -ffp-contract=off); this
+module compiles it with g++ on first use and wraps it with ctypes. Every function takes and
+returns NumPy arrays on the host.
+
+Parity status per function (what pins each one to something other than itself is listed in the
+tests named here):
+* fof3d_brute / fof3d_grid: brute force vs grid, SciPy k-d tree components, lattice, periodic
+  and exact-distance special cases (tests/test_oracle_fof3d.py).
+* cro_sum: exactly rounded sums (math.fsum) within the recursive-summation bound, hand-derived
+  order-sensitive cases (tests/test_oracle_cro.py).
+* split_node / hierarchy: invariants (linked fraction, subsets, disjointness, sizes), exact
+  velocity-scaling invariance, two-blob special cases (tests/test_oracle_hierarchy.py).
+* unbind: two-body, centre-of-sphere and cube closed forms, Plummer and uniform-sphere profiles,
+  bound/unbound limits (tests/test_oracle_unbind.py).
+* props: lattice moments and inertia in closed form, centre wrapping (tests/test_oracle_props.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rs_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle_rs.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+          "-pthread"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library with g++ (no-op when it is newer than its source)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["g++", *CFLAGS, _SRC, "-o", tmp], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64, i32, f32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_double
+        lib.or_fof3d_brute.argtypes = [i64, P, P, f32, f32, P]
+        lib.or_fof3d_grid.argtypes = [i64, P, P, f32, f32, P]
+        lib.or_cro_sum.argtypes = [P, i64]
+        lib.or_cro_sum.restype = f64
+        lib.or_split_node.argtypes = [i64, P, P, i32, i32, P, P, P]
+        lib.or_hierarchy.argtypes = [i64, P, P, P, P, f32, i32, i32, i32, i32,
+                                     ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.or_hierarchy.restype = P
+        lib.or_hierarchy_copy.argtypes = [P, P, P, P, P, P, P, P]
+        lib.or_hierarchy_free.argtypes = [P]
+        lib.or_unbind.argtypes = [i64, P, P, P, P, f32, f32, f64, f64, i32, i32, i32, i32,
+                                  P, P, P, P, P]
+        lib.or_props.argtypes = [i64, P, P, P, P, P, P, f32, f64, i64, i32, P]
+        _lib = lib
+        return lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _threads(threads):
+    return int(threads) if threads else (os.cpu_count() or 1)
+
+
+def fof3d_brute(pos, ids, box, ll):
+    pos, ids = _c(pos, np.float32), _c(ids, np.int64)
+    out = np.empty(len(ids), np.int64)
+    rc = _load().or_fof3d_brute(len(ids), _p(pos), _p(ids), box, ll, _p(out))
+    assert rc == 0
+    return out
+
+
+def fof3d_grid(pos, ids, box, ll):
+    pos, ids = _c(pos, np.float32), _c(ids, np.int64)
+    out = np.empty(len(ids), np.int64)
+    rc = _load().or_fof3d_grid(len(ids), _p(pos), _p(ids), box, ll, _p(out))
+    assert rc == 0
+    return out
+
+
+def fof3d(pos, ids, box, ll):
+    """3D FoF labels (smallest id of each particle's group)."""
+    return fof3d_brute(pos, ids, box, ll) if len(ids) <= 2048 else fof3d_grid(pos, ids, box, ll)
+
+
+def cro_sum(a):
+    a = _c(a, np.float64)
+    return float(_load().or_cro_sum(_p(a), len(a)))
+
+
+def split_node(u, v, f_num=7, f_den=10):
+    """One 6D FoF level on a single node: (inv_sx2, inv_sv2, l2, nn2[g], comp[g])."""
+    u, v = _c(u, np.float32), _c(v, np.float32)
+    g = len(u)
+    scal = np.empty(3, np.float32)
+    nn2 = np.empty(g, np.float32)
+    comp = np.empty(g, np.int64)
+    rc = _load().or_split_node(g, _p(u), _p(v), f_num, f_den, _p(scal), _p(nn2), _p(comp))
+    assert rc == 0
+    return float(scal[0]), float(scal[1]), float(scal[2]), nn2, comp
+
+
+def hierarchy(pos, vel, ids, fof_label, box, f_num=7, f_den=10, min_size=10, threads=None):
+    """6D FoF hierarchy. Returns a dict of node arrays, member CSR and per-particle deepest node."""
+    pos, vel = _c(pos, np.float32), _c(vel, np.float32)
+    ids, lab = _c(ids, np.int64), _c(fof_label, np.int64)
+    lib = _load()
+    nn, nm = ctypes.c_int64(0), ctypes.c_int64(0)
+    h = lib.or_hierarchy(len(ids), _p(pos), _p(vel), _p(ids), _p(lab), box, f_num, f_den,
+                         min_size, _threads(threads), ctypes.byref(nn), ctypes.byref(nm))
+    assert h
+    try:
+        n_nodes, n_mem = nn.value, nm.value
+        out = {
+            "parent": np.empty(n_nodes, np.int64), "level": np.empty(n_nodes, np.int32),
+            "min_id": np.empty(n_nodes, np.int64), "size": np.empty(n_nodes, np.int64),
+            "member_off": np.empty(n_nodes + 1, np.int64),
+            "member_idx": np.empty(n_mem, np.int64), "deepest": np.empty(len(ids), np.int64),
+        }
+        rc = lib.or_hierarchy_copy(h, *(_p(out[k]) for k in (
+            "parent", "level", "min_id", "size", "member_off", "member_idx", "deepest")))
+        assert rc == 0
+    finally:
+        lib.or_hierarchy_free(h)
+    return out
+
+
+def unbind(member_off, member_idx, pos, vel, box, eps, G, m, min_size=10, bf_num=1, bf_den=2,
+           threads=None, want_phi=True):
+    """Potential (float64 per member), bound flags, and per-node n_bound / is_halo / m_bound."""
+    off, idx = _c(member_off, np.int64), _c(member_idx, np.int64)
+    pos, vel = _c(pos, np.float32), _c(vel, np.float32)
+    n_nodes, n_mem = len(off) - 1, int(off[-1]) if len(off) else 0
+    phi = np.empty(n_mem, np.float64) if want_phi else None
+    bound = np.empty(n_mem, np.uint8)
+    nb = np.empty(n_nodes, np.int64)
+    halo = np.empty(n_nodes, np.uint8)
+    mb = np.empty(n_nodes, np.float64)
+    rc = _load().or_unbind(n_nodes, _p(off), _p(idx), _p(pos), _p(vel), box, eps, G, m,
+                           min_size, bf_num, bf_den, _threads(threads), _p(phi), _p(bound),
+                           _p(nb), _p(halo), _p(mb))
+    assert rc == 0
+    return {"phi": phi, "bound": bound, "n_bound": nb, "is_halo": halo, "m_bound": mb}
+
+
+def props(member_off, member_idx, pos, vel, bound, is_halo, box, m, n_total, threads=None):
+    """Halo properties: float64 [n_nodes][20] (layout in rs_oracle.cpp, or_props)."""
+    off, idx = _c(member_off, np.int64), _c(member_idx, np.int64)
+    pos, vel = _c(pos, np.float32), _c(vel, np.float32)
+    bound, is_halo = _c(bound, np.uint8), _c(is_halo, np.uint8)
+    out = np.empty((len(off) - 1, 20), np.float64)
+    rc = _load().or_props(len(off) - 1, _p(off), _p(idx), _p(pos), _p(vel), _p(bound),
+                          _p(is_halo), box, m, n_total, _threads(threads), _p(out))
+    assert rc == 0
+    return out

@@ -1,0 +1,552 @@
+// Oracle for the halo-finding path: a plain, slow, single-node-at-a-time CPU restatement of
+// 3D friends-of-friends, the recursive 6D phase-space FoF hierarchy, potential-based unbinding
+// and halo properties.
+//
+// TEST INFRASTRUCTURE ONLY. Nothing on the product path calls this code: only the tests, the
+// smoke check and the benchmark's CPU-baseline leg load it. It shares no code, header, table or
+// helper with the CUDA library.
+//
+// What the paper fixes: each process runs 3D FoF on its particles, then finds subhalos inside
+// every FoF halo from 6D phase-space information (Section "Parallelization"), and the halo
+// catalogue carries extra properties such as the inertia tensor (Summary). The linking length
+// b = 0.28, the 6D metric |dx|^2/sx^2 + |dv|^2/sv^2, the linked fraction f = 0.7 with recursion,
+// the 0.5 bound-fraction threshold and the 10-particle minimum are Rockstar's parameters
+// (Behroozi et al. 2013, cited in the Summary). Every rounding-level choice below (operation
+// order, <= vs <, the canonical FP64 reduction order) is a reading this implementation fixes so
+// that a GPU implementation can reproduce it bit for bit.
+//
+// Build: g++ -std=c++17 -O2 -ffp-contract=off -fno-fast-math -fPIC -shared -pthread
+// (-ffp-contract=off matters on aarch64, where GCC contracts a*b+c into FMA by default.)
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Periodic minimum-image difference of two float32 coordinates (3D FoF, Section
+// "Parallelization"): d = b - a rounded to float32; if d > L/2 subtract L, else if d < -L/2 add L.
+// IEEE round-to-nearest commutes with negation, so wrap(b - a) == -wrap(a - b) exactly.
+inline float wrap_diff(float a, float b, float L, float hL) {
+  float d = b - a;
+  if (d > hL) {
+    d = d - L;
+  } else if (d < -hL) {
+    d = d + L;
+  }
+  return d;
+}
+
+// Squared distance, float32, left to right, no fused multiply-add: (dx*dx + dy*dy) + dz*dz.
+inline float sq3(float dx, float dy, float dz) {
+  float a = dx * dx;
+  float b = dy * dy;
+  float c = dz * dz;
+  float s = a + b;
+  return s + c;
+}
+
+// Plain union-find with path halving; roots are the smallest index of their set.
+struct UnionFind {
+  std::vector<int64_t> p;
+  explicit UnionFind(int64_t n) : p(n) { std::iota(p.begin(), p.end(), int64_t(0)); }
+  int64_t find(int64_t x) {
+    while (p[x] != x) {
+      p[x] = p[p[x]];
+      x = p[x];
+    }
+    return x;
+  }
+  void unite(int64_t a, int64_t b) {
+    a = find(a);
+    b = find(b);
+    if (a == b) return;
+    if (a < b) p[b] = a; else p[a] = b;
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Canonical reduction order (CRO) for every FP64 sum of the path. For a[0..m):
+//   chunks of 1024 consecutive terms; inside chunk c, lane l (0..31) sums a[1024c + l + 32k]
+//   for k = 0..31 in order, starting from 0.0; lanes are then combined by halving,
+//   s[l] = s[l] + s[l + off] for off = 16, 8, 4, 2, 1; the chunk total is s[0]. Chunk totals
+//   are combined by a pairwise tree, t'[k] = t[2k] + t[2k+1], an odd last element carried up.
+// An empty sequence sums to 0.0.
+template <class Term>
+double cro_sum(int64_t m, Term term) {
+  if (m <= 0) return 0.0;
+  const int64_t chunks = (m + 1023) / 1024;
+  std::vector<double> t(chunks);
+  for (int64_t c = 0; c < chunks; ++c) {
+    double s[32];
+    for (int l = 0; l < 32; ++l) {
+      double acc = 0.0;
+      for (int k = 0; k < 32; ++k) {
+        const int64_t idx = c * 1024 + l + 32 * k;
+        if (idx < m) acc = acc + term(idx);
+      }
+      s[l] = acc;
+    }
+    for (int off = 16; off >= 1; off >>= 1)
+      for (int l = 0; l < off; ++l) s[l] = s[l] + s[l + off];
+    t[c] = s[0];
+  }
+  while (t.size() > 1) {
+    std::vector<double> nt;
+    nt.reserve((t.size() + 1) / 2);
+    for (size_t k = 0; 2 * k + 1 < t.size(); ++k) nt.push_back(t[2 * k] + t[2 * k + 1]);
+    if (t.size() % 2 == 1) nt.push_back(t.back());
+    t.swap(nt);
+  }
+  return t[0];
+}
+
+// Run f(i) for i in [0, count) on up to `threads` std::threads (static interleaved split).
+template <class F>
+void parallel_for(int64_t count, int threads, F f) {
+  if (threads <= 1 || count <= 1) {
+    for (int64_t i = 0; i < count; ++i) f(i);
+    return;
+  }
+  const int nt = int(std::min<int64_t>(threads, count));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([=]() {
+      for (int64_t i = t; i < count; i += nt) f(i);
+    });
+  for (auto& th : pool) th.join();
+}
+
+// ---------------------------------------------------------------------------------------------
+// 3D FoF link predicate: i ~ j iff the float32 periodic squared distance is <= ll^2 (float32).
+inline bool fof_linked(const float* pos, int64_t i, int64_t j, float L, float hL, float ll2) {
+  const float dx = wrap_diff(pos[3 * i + 0], pos[3 * j + 0], L, hL);
+  const float dy = wrap_diff(pos[3 * i + 1], pos[3 * j + 1], L, hL);
+  const float dz = wrap_diff(pos[3 * i + 2], pos[3 * j + 2], L, hL);
+  return sq3(dx, dy, dz) <= ll2;
+}
+
+// Labels = smallest id in each connected component of the link graph.
+void labels_from_uf(int64_t n, const int64_t* ids, UnionFind& uf, int64_t* labels) {
+  std::vector<int64_t> min_id(n, INT64_MAX);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t r = uf.find(i);
+    min_id[r] = std::min(min_id[r], ids[i]);
+  }
+  for (int64_t i = 0; i < n; ++i) labels[i] = min_id[uf.find(i)];
+}
+
+// ---------------------------------------------------------------------------------------------
+// 6D phase-space hierarchy (Section "Parallelization": subhalo finding per FoF halo from 6D
+// phase-space information).
+struct Node {
+  int64_t parent;
+  int32_t level;
+  int64_t min_id;
+  int64_t size;
+  int64_t off;  // into the member list
+};
+
+struct Hierarchy {
+  int64_t n = 0;
+  std::vector<Node> nodes;
+  std::vector<int64_t> members;  // particle indices; each node's members in ascending id order
+  std::vector<int64_t> deepest;  // per particle: deepest node holding it, -1 if none
+};
+
+// Positions of a node's members relative to its reference member (the smallest id), float32.
+void unwrap_node(const float* pos, const int64_t* mem, int64_t g, float L, std::vector<float>& u) {
+  const float hL = 0.5f * L;
+  const int64_t r = mem[0];
+  u.resize(3 * g);
+  for (int64_t a = 0; a < g; ++a)
+    for (int d = 0; d < 3; ++d) u[3 * a + d] = wrap_diff(pos[3 * r + d], pos[3 * mem[a] + d], L, hL);
+}
+
+// Total (3-dimension) variance of a float32 [g][3] array from CRO FP64 moments:
+// mean_d = S_d / g; var = ((Q_0/g - mean_0^2) + (Q_1/g - mean_1^2)) + (Q_2/g - mean_2^2).
+double total_variance(const float* a, int64_t g) {
+  double var = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double s = cro_sum(g, [&](int64_t i) { return double(a[3 * i + d]); });
+    const double q = cro_sum(g, [&](int64_t i) { return double(a[3 * i + d]) * double(a[3 * i + d]); });
+    const double mean = s / double(g);
+    const double term = q / double(g) - mean * mean;
+    var = (d == 0) ? term : var + term;
+  }
+  return var;
+}
+
+inline float inv_or_zero(double var) { return var > 0.0 ? float(1.0 / var) : 0.0f; }
+
+// 6D squared distance, float32, no FMA:
+// fl(fl(|du|^2) * inv_sx2) + fl(fl(|dv|^2) * inv_sv2), |d|^2 = (dx*dx + dy*dy) + dz*dz.
+inline float d6(const float* u, const float* v, int64_t i, int64_t j, float isx, float isv) {
+  const float rx = sq3(u[3 * j] - u[3 * i], u[3 * j + 1] - u[3 * i + 1], u[3 * j + 2] - u[3 * i + 2]);
+  const float rv = sq3(v[3 * j] - v[3 * i], v[3 * j + 1] - v[3 * i + 1], v[3 * j + 2] - v[3 * i + 2]);
+  const float a = rx * isx;
+  const float b = rv * isv;
+  return a + b;
+}
+
+struct SplitResult {
+  float inv_sx2 = 0.f, inv_sv2 = 0.f, l2 = 0.f;
+  std::vector<float> nn2;
+  std::vector<int64_t> comp;  // per member: smallest member position of its 6D component
+};
+
+// One level of 6D FoF on a node whose members (ascending id) have unwrapped positions u and
+// velocities v: sigma from CRO moments, nearest-neighbour distances, the adaptive link length
+// (the k-th smallest nn2 with k = ceil(f g) - 1), and the components of the link graph.
+void split_node(const float* u, const float* v, int64_t g, int32_t f_num, int32_t f_den,
+                SplitResult& out) {
+  out.inv_sx2 = inv_or_zero(total_variance(u, g));
+  out.inv_sv2 = inv_or_zero(total_variance(v, g));
+  out.nn2.assign(g, INFINITY);
+  for (int64_t i = 0; i < g; ++i) {
+    float best = INFINITY;
+    for (int64_t j = 0; j < g; ++j) {
+      if (j == i) continue;
+      const float d = d6(u, v, i, j, out.inv_sx2, out.inv_sv2);
+      if (d < best) best = d;
+    }
+    out.nn2[i] = best;
+  }
+  const int64_t k = (int64_t(f_num) * g + f_den - 1) / f_den - 1;
+  std::vector<float> sorted(out.nn2);
+  std::nth_element(sorted.begin(), sorted.begin() + k, sorted.end());
+  out.l2 = sorted[k];
+  UnionFind uf(g);
+  for (int64_t i = 0; i < g; ++i)
+    for (int64_t j = i + 1; j < g; ++j)
+      if (d6(u, v, i, j, out.inv_sx2, out.inv_sv2) <= out.l2) uf.unite(i, j);
+  out.comp.resize(g);
+  for (int64_t i = 0; i < g; ++i) out.comp[i] = uf.find(i);
+}
+
+// Children of a split node: components with at least min_size members and fewer than g.
+// Returned in ascending order of their smallest member (hence of their min id); each child's
+// member positions ascend.
+std::vector<std::vector<int64_t>> children_of(const SplitResult& s, int64_t g, int32_t min_size) {
+  std::vector<int64_t> count(g, 0);
+  for (int64_t i = 0; i < g; ++i) count[s.comp[i]]++;
+  std::vector<int64_t> slot(g, -1);
+  std::vector<std::vector<int64_t>> kids;
+  for (int64_t i = 0; i < g; ++i) {
+    const int64_t c = s.comp[i];
+    if (count[c] < min_size || count[c] >= g) continue;
+    if (slot[c] < 0) {
+      slot[c] = int64_t(kids.size());
+      kids.emplace_back();
+    }
+    kids[slot[c]].push_back(i);
+  }
+  return kids;
+}
+
+Hierarchy* build_hierarchy(int64_t n, const float* pos, const float* vel, const int64_t* ids,
+                           const int64_t* fof_label, float L, int32_t f_num, int32_t f_den,
+                           int32_t min_size, int threads) {
+  auto* h = new Hierarchy();
+  h->n = n;
+  h->deepest.assign(n, -1);
+  // Level 0: FoF groups with at least min_size particles, by ascending label (= min id); members
+  // by ascending id.
+  std::vector<int64_t> order(n);
+  std::iota(order.begin(), order.end(), int64_t(0));
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return fof_label[a] != fof_label[b] ? fof_label[a] < fof_label[b] : ids[a] < ids[b];
+  });
+  for (int64_t s = 0; s < n;) {
+    int64_t e = s;
+    while (e < n && fof_label[order[e]] == fof_label[order[s]]) ++e;
+    if (e - s >= min_size) {
+      Node nd{-1, 0, ids[order[s]], e - s, int64_t(h->members.size())};
+      h->nodes.push_back(nd);
+      h->members.insert(h->members.end(), order.begin() + s, order.begin() + e);
+    }
+    s = e;
+  }
+  // Breadth-first: split every node of a level (independently, possibly in parallel), then
+  // append the children in (parent, min id) order. Levels therefore appear in order.
+  int64_t level_begin = 0;
+  int32_t level = 0;
+  while (level_begin < int64_t(h->nodes.size())) {
+    const int64_t level_end = int64_t(h->nodes.size());
+    const int64_t count = level_end - level_begin;
+    std::vector<std::vector<std::vector<int64_t>>> kids(count);
+    parallel_for(count, threads, [&](int64_t q) {
+      const Node nd = h->nodes[level_begin + q];
+      const int64_t* mem = h->members.data() + nd.off;
+      std::vector<float> u, v(3 * nd.size);
+      unwrap_node(pos, mem, nd.size, L, u);
+      for (int64_t a = 0; a < nd.size; ++a)
+        for (int d = 0; d < 3; ++d) v[3 * a + d] = vel[3 * mem[a] + d];
+      SplitResult sr;
+      split_node(u.data(), v.data(), nd.size, f_num, f_den, sr);
+      kids[q] = children_of(sr, nd.size, min_size);
+    });
+    for (int64_t q = 0; q < count; ++q) {
+      const int64_t parent = level_begin + q;
+      for (auto& kid : kids[q]) {
+        const Node pn = h->nodes[parent];
+        Node nd{parent, level + 1, ids[h->members[pn.off + kid[0]]], int64_t(kid.size()),
+                int64_t(h->members.size())};
+        for (int64_t a : kid) h->members.push_back(h->members[pn.off + a]);
+        h->nodes.push_back(nd);
+      }
+    }
+    level_begin = level_end;
+    ++level;
+  }
+  for (int64_t q = 0; q < int64_t(h->nodes.size()); ++q)
+    for (int64_t a = 0; a < h->nodes[q].size; ++a) h->deepest[h->members[h->nodes[q].off + a]] = q;
+  return h;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI (ctypes). Every array is host memory owned by the caller; positions/velocities are
+// float32 [n][3], ids int64 [n]. Functions return 0 on success, -1 on invalid arguments.
+extern "C" {
+
+// Brute-force 3D FoF over all pairs: labels[i] = smallest id of i's component.
+int or_fof3d_brute(int64_t n, const float* pos, const int64_t* ids, float L, float ll,
+                   int64_t* labels) {
+  if (n < 0 || (n > 0 && (!pos || !ids || !labels))) return -1;
+  const float hL = 0.5f * L, ll2 = ll * ll;
+  UnionFind uf(n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = i + 1; j < n; ++j)
+      if (fof_linked(pos, i, j, L, hL, ll2)) uf.unite(i, j);
+  labels_from_uf(n, ids, uf, labels);
+  return 0;
+}
+
+// 3D FoF with a cell grid: cells of side L/nc >= 1.01 ll, so any linked pair lies in the same or
+// adjacent (periodic) cells; each pair of candidate particles is tested with the same predicate
+// as the brute-force version. Cell coordinates are computed in float64.
+int or_fof3d_grid(int64_t n, const float* pos, const int64_t* ids, float L, float ll,
+                  int64_t* labels) {
+  if (n < 0 || (n > 0 && (!pos || !ids || !labels))) return -1;
+  if (!(ll > 0.f) || !(L > 0.f)) return -1;
+  const float hL = 0.5f * L, ll2 = ll * ll;
+  int64_t nc = int64_t(std::floor(double(L) / (1.01 * double(ll))));
+  nc = std::max<int64_t>(1, std::min<int64_t>(nc, 1 << 20));
+  auto cell_of = [&](int64_t i, int d) {
+    int64_t c = int64_t(std::floor(double(pos[3 * i + d]) * double(nc) / double(L)));
+    return std::min<int64_t>(std::max<int64_t>(c, 0), nc - 1);
+  };
+  auto key = [&](int64_t cx, int64_t cy, int64_t cz) { return (cz * nc + cy) * nc + cx; };
+  std::vector<std::pair<int64_t, int64_t>> kp(n);
+  for (int64_t i = 0; i < n; ++i) kp[i] = {key(cell_of(i, 0), cell_of(i, 1), cell_of(i, 2)), i};
+  std::sort(kp.begin(), kp.end());
+  std::unordered_map<int64_t, std::pair<int64_t, int64_t>> cells;
+  cells.reserve(size_t(n) * 2 + 1);
+  for (int64_t s = 0; s < n;) {
+    int64_t e = s;
+    while (e < n && kp[e].first == kp[s].first) ++e;
+    cells[kp[s].first] = {s, e};
+    s = e;
+  }
+  UnionFind uf(n);
+  for (const auto& cell : cells) {
+    const int64_t k = cell.first;
+    const int64_t cx = k % nc, cy = (k / nc) % nc, cz = k / (nc * nc);
+    for (int64_t oz = -1; oz <= 1; ++oz)
+      for (int64_t oy = -1; oy <= 1; ++oy)
+        for (int64_t ox = -1; ox <= 1; ++ox) {
+          const int64_t k2 = key((cx + ox + nc) % nc, (cy + oy + nc) % nc, (cz + oz + nc) % nc);
+          if (k2 < k) continue;  // each unordered cell pair once (duplicates are harmless)
+          auto it = cells.find(k2);
+          if (it == cells.end()) continue;
+          for (int64_t a = cell.second.first; a < cell.second.second; ++a)
+            for (int64_t b = it->second.first; b < it->second.second; ++b) {
+              const int64_t i = kp[a].second, j = kp[b].second;
+              if (i != j && fof_linked(pos, i, j, L, hL, ll2)) uf.unite(i, j);
+            }
+        }
+  }
+  labels_from_uf(n, ids, uf, labels);
+  return 0;
+}
+
+// CRO sum of a float64 array.
+double or_cro_sum(const double* a, int64_t m) {
+  return cro_sum(m, [&](int64_t i) { return a[i]; });
+}
+
+// One level of 6D FoF on a single node given as float32 u[g][3], v[g][3] (members in ascending
+// id order, u already relative to the reference member). Outputs: inv_sx2, inv_sv2, l2 (3
+// floats), nn2[g], comp[g] (smallest member position of each member's component).
+int or_split_node(int64_t g, const float* u, const float* v, int32_t f_num, int32_t f_den,
+                  float* scal_out, float* nn2_out, int64_t* comp_out) {
+  if (g < 2 || f_num <= 0 || f_den <= 0 || f_num > f_den) return -1;
+  SplitResult sr;
+  split_node(u, v, g, f_num, f_den, sr);
+  scal_out[0] = sr.inv_sx2;
+  scal_out[1] = sr.inv_sv2;
+  scal_out[2] = sr.l2;
+  std::memcpy(nn2_out, sr.nn2.data(), sizeof(float) * g);
+  std::memcpy(comp_out, sr.comp.data(), sizeof(int64_t) * g);
+  return 0;
+}
+
+// Build the hierarchy; returns an opaque handle (free with or_hierarchy_free).
+void* or_hierarchy(int64_t n, const float* pos, const float* vel, const int64_t* ids,
+                   const int64_t* fof_label, float L, int32_t f_num, int32_t f_den,
+                   int32_t min_size, int32_t threads, int64_t* n_nodes, int64_t* n_members) {
+  if (n < 0 || f_num <= 0 || f_den <= 0 || f_num > f_den || min_size < 2) return nullptr;
+  Hierarchy* h = build_hierarchy(n, pos, vel, ids, fof_label, L, f_num, f_den, min_size, threads);
+  *n_nodes = int64_t(h->nodes.size());
+  *n_members = int64_t(h->members.size());
+  return h;
+}
+
+// Copy the hierarchy out: node arrays [n_nodes], member_off [n_nodes + 1],
+// member_idx [n_members], deepest [n].
+int or_hierarchy_copy(void* handle, int64_t* parent, int32_t* level, int64_t* min_id,
+                      int64_t* size, int64_t* member_off, int64_t* member_idx, int64_t* deepest) {
+  auto* h = static_cast<Hierarchy*>(handle);
+  if (!h) return -1;
+  const int64_t nn = int64_t(h->nodes.size());
+  for (int64_t q = 0; q < nn; ++q) {
+    parent[q] = h->nodes[q].parent;
+    level[q] = h->nodes[q].level;
+    min_id[q] = h->nodes[q].min_id;
+    size[q] = h->nodes[q].size;
+    member_off[q] = h->nodes[q].off;
+  }
+  member_off[nn] = int64_t(h->members.size());
+  std::memcpy(member_idx, h->members.data(), sizeof(int64_t) * h->members.size());
+  std::memcpy(deepest, h->deepest.data(), sizeof(int64_t) * h->n);
+  return 0;
+}
+
+void or_hierarchy_free(void* handle) { delete static_cast<Hierarchy*>(handle); }
+
+// Unbinding over every node of the hierarchy (member CSR: member_off [n_nodes+1], member_idx).
+// Per node with reference member r (its first = smallest-id member) and u = wrap(x - x_r):
+//   phi_i  = -(G m) * CRO_j( j == i ? 0 : 1 / sqrt(((Dx*Dx + Dy*Dy) + Dz*Dz) + eps^2) ),
+//            D = (double)u_j - (double)u_i, eps^2 = (double)eps * (double)eps;
+//   v_bulk = CRO(v) / g;  KE_i = 0.5 * ((dvx*dvx + dvy*dvy) + dvz*dvz), dv = (double)v_i - v_bulk;
+//   bound_i = (KE_i + phi_i < 0); N_b = #bound; halo iff N_b >= min_size and
+//   bf_den * N_b >= bf_num * g; M_b = N_b * m.
+// Outputs per member (CSR order): phi [n_members] (may be NULL), bound [n_members];
+// per node: n_bound, is_halo, m_bound.
+int or_unbind(int64_t n_nodes, const int64_t* member_off, const int64_t* member_idx,
+              const float* pos, const float* vel, float L, float eps, double G, double m,
+              int32_t min_size, int32_t bf_num, int32_t bf_den, int32_t threads, double* phi,
+              uint8_t* bound, int64_t* n_bound, uint8_t* is_halo, double* m_bound) {
+  if (n_nodes < 0 || bf_den <= 0) return -1;
+  const double Gm = G * m;
+  const double eps2 = double(eps) * double(eps);
+  parallel_for(n_nodes, threads, [&](int64_t q) {
+    const int64_t off = member_off[q], g = member_off[q + 1] - member_off[q];
+    const int64_t* mem = member_idx + off;
+    std::vector<float> u;
+    unwrap_node(pos, mem, g, L, u);
+    double vb[3];
+    for (int d = 0; d < 3; ++d)
+      vb[d] = cro_sum(g, [&](int64_t a) { return double(vel[3 * mem[a] + d]); }) / double(g);
+    int64_t nb = 0;
+    for (int64_t i = 0; i < g; ++i) {
+      const double s = cro_sum(g, [&](int64_t j) {
+        if (j == i) return 0.0;
+        const double dx = double(u[3 * j]) - double(u[3 * i]);
+        const double dy = double(u[3 * j + 1]) - double(u[3 * i + 1]);
+        const double dz = double(u[3 * j + 2]) - double(u[3 * i + 2]);
+        const double r2 = (dx * dx + dy * dy) + dz * dz;
+        return 1.0 / std::sqrt(r2 + eps2);
+      });
+      const double p = -(Gm * s);
+      const double dvx = double(vel[3 * mem[i]]) - vb[0];
+      const double dvy = double(vel[3 * mem[i] + 1]) - vb[1];
+      const double dvz = double(vel[3 * mem[i] + 2]) - vb[2];
+      const double ke = 0.5 * ((dvx * dvx + dvy * dvy) + dvz * dvz);
+      const bool b = (ke + p) < 0.0;
+      if (phi) phi[off + i] = p;
+      bound[off + i] = b ? 1 : 0;
+      nb += b ? 1 : 0;
+    }
+    n_bound[q] = nb;
+    is_halo[q] = (nb >= min_size && int64_t(bf_den) * nb >= int64_t(bf_num) * g) ? 1 : 0;
+    m_bound[q] = double(nb) * m;
+  });
+  return 0;
+}
+
+// Halo properties per node over its bound members (CRO sums over all members in ascending id
+// order, unbound members contributing 0.0), 20 float64 per node:
+//   [0] n, [1] n_bound, [2] is_halo, [3] m_bound, [4..6] centre, [7..9] bulk velocity,
+//   [10] sigma_x, [11] sigma_v, [12] r_vir, [13..18] inertia xx yy zz xy xz yz, [19] unused 0.
+// centre = x_r + mean(u) wrapped once into [0, L); sigma^2 = sum_d (CRO(w_d^2)/N_b - mean_d^2)
+// (clamped at 0); r_vir = cbrt(3 M_b / (4 pi 200 rho_bar)), rho_bar = n_total m / L^3;
+// inertia I_ab = CRO((u_a - mean_a)(u_b - mean_b)) / N_b. All zero except [0..3] when N_b = 0.
+int or_props(int64_t n_nodes, const int64_t* member_off, const int64_t* member_idx,
+             const float* pos, const float* vel, const uint8_t* bound, const uint8_t* is_halo,
+             float L, double m, int64_t n_total, int32_t threads, double* props) {
+  if (n_nodes < 0 || n_total <= 0) return -1;
+  const double rho_bar = double(n_total) * m / (double(L) * double(L) * double(L));
+  const double pi = 3.14159265358979323846;
+  parallel_for(n_nodes, threads, [&](int64_t q) {
+    const int64_t off = member_off[q], g = member_off[q + 1] - member_off[q];
+    const int64_t* mem = member_idx + off;
+    const uint8_t* bd = bound + off;
+    double* P = props + 20 * q;
+    for (int k = 0; k < 20; ++k) P[k] = 0.0;
+    std::vector<float> u;
+    unwrap_node(pos, mem, g, L, u);
+    int64_t nb = 0;
+    for (int64_t a = 0; a < g; ++a) nb += bd[a] ? 1 : 0;
+    P[0] = double(g);
+    P[1] = double(nb);
+    P[2] = is_halo[q] ? 1.0 : 0.0;
+    P[3] = double(nb) * m;
+    if (nb == 0) return;
+    const double nbd = double(nb);
+    double mu[3], mv[3];
+    double varx = 0.0, varv = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      mu[d] = cro_sum(g, [&](int64_t a) { return bd[a] ? double(u[3 * a + d]) : 0.0; }) / nbd;
+      mv[d] = cro_sum(g, [&](int64_t a) { return bd[a] ? double(vel[3 * mem[a] + d]) : 0.0; }) / nbd;
+      const double qx = cro_sum(g, [&](int64_t a) {
+        return bd[a] ? double(u[3 * a + d]) * double(u[3 * a + d]) : 0.0; });
+      const double qv = cro_sum(g, [&](int64_t a) {
+        return bd[a] ? double(vel[3 * mem[a] + d]) * double(vel[3 * mem[a] + d]) : 0.0; });
+      const double tx = qx / nbd - mu[d] * mu[d];
+      const double tv = qv / nbd - mv[d] * mv[d];
+      varx = (d == 0) ? tx : varx + tx;
+      varv = (d == 0) ? tv : varv + tv;
+    }
+    for (int d = 0; d < 3; ++d) {
+      double c = double(pos[3 * mem[0] + d]) + mu[d];
+      if (c < 0.0) c = c + double(L);
+      else if (c >= double(L)) c = c - double(L);
+      P[4 + d] = c;
+      P[7 + d] = mv[d];
+    }
+    P[10] = std::sqrt(varx > 0.0 ? varx : 0.0);
+    P[11] = std::sqrt(varv > 0.0 ? varv : 0.0);
+    P[12] = std::cbrt(3.0 * P[3] / (4.0 * pi * 200.0 * rho_bar));
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k) {
+      P[13 + k] = cro_sum(g, [&](int64_t a) {
+        if (!bd[a]) return 0.0;
+        const double da = double(u[3 * a + ia[k]]) - mu[ia[k]];
+        const double db = double(u[3 * a + ib[k]]) - mu[ib[k]];
+        return da * db;
+      }) / nbd;
+    }
+  });
+  return 0;
+}
+
+}  // extern "C"
