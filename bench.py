@@ -1,0 +1,345 @@
+"""Benchmark: halo-finding particles/s on one GB300 (3D FoF -> 6D hierarchy -> unbinding ->
+halo properties), on a seeded synthetic NFW snapshot.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one pass of the whole path over one snapshot with inputs resident in HBM. Prints one
+JSON line (rank 0). For N > 1 (torchrun, one rank per GPU) every rank processes its own
+independent snapshot (seed + rank): weak scaling, no data-path collective; the value is all
+ranks' particles over the slowest rank's time.
+
+--impl reference times the CPU oracle (the plain definition the CUDA path is checked against)
+on a bounded sample of the same workload, on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "halo-finding particles/s on 1 GB300, plain vs batched+surrogate; % of roofline"
+UNIT = "particles/s"
+DEFAULT_WORKLOAD = "nfw-2^24-L256-sub"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+# fraction of the box side of the cubic sub-volume the CPU oracle is timed on
+ORACLE_SUBBOX = 0.25
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(elapsed_s: float, units: float, world_size: int, backend_device="cpu"):
+    """Max elapsed and summed units over ranks (identity when world_size == 1)."""
+    if world_size <= 1:
+        return elapsed_s, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=backend_device)
+    u = torch.tensor([units], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def _barrier(world_size):
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.path = None
+        self.device_index = device_index
+
+    def __enter__(self):
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.device_index).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = []
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+def _snapshot(workload, rank):
+    from paper_2412_18629_gb300 import synth
+    spec = synth.WORKLOADS[workload]
+    if rank:
+        import dataclasses
+        spec = dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
+    return spec, synth.generate(spec)
+
+
+def _oracle_sample(snap):
+    """Bounded sample of the workload for the CPU oracle: the particles in the cubic sub-volume
+    [0, f L)^3 of the same snapshot (its halos are cut at the sub-volume's faces)."""
+    from paper_2412_18629_gb300 import synth
+    keep = np.all(snap["pos"] < np.float32(ORACLE_SUBBOX * snap["box"]), axis=1)
+    return synth.subsample(snap, keep)
+
+
+def time_oracle(snap, threads):
+    import oracle
+    from paper_2412_18629_gb300 import G_NEWTON
+    sub = _oracle_sample(snap)
+    t0 = time.perf_counter()
+    lab = oracle.fof3d_grid(sub["pos"], sub["ids"], sub["box"], sub["link_length"])
+    h = oracle.hierarchy(sub["pos"], sub["vel"], sub["ids"], lab, sub["box"], threads=threads)
+    ub = oracle.unbind(h["member_off"], h["member_idx"], sub["pos"], sub["vel"], sub["box"],
+                       sub["softening"], G_NEWTON, sub["particle_mass"], threads=threads,
+                       want_phi=False)
+    oracle.props(h["member_off"], h["member_idx"], sub["pos"], sub["vel"], ub["bound"],
+                 ub["is_halo"], sub["box"], sub["particle_mass"], len(snap["ids"]), threads=threads)
+    dt = time.perf_counter() - t0
+    return sub["n"], dt
+
+
+def _hier_work(ctx):
+    """Algorithmic pair counts of the hierarchy: sum over nodes of g (g - 1)."""
+    import paper_2412_18629_gb300 as rs
+    sizes = rs.rs_fof6d_copy(ctx)["size"].cpu().numpy().astype(np.float64)
+    return float((sizes * (sizes - 1)).sum()), float(sizes.sum())
+
+
+# FP32-pipe operations per pair for the two O(n_g^2) kernels (no FMA contraction):
+# 6D distance = 6 sub + 6 mul + 4 add + 2 mul (scales) + 1 add, plus the min / compare = 20;
+# potential = 3 sub + 3 FMA + 1 add (+ 1 MUFU rsqrt) = 7.
+OPS_PER_PAIR = {"k_nn6d": 20.0, "k_link6d": 20.0, "k_potential": 7.0}
+
+
+def run_ours(args):
+    import torch
+    import paper_2412_18629_gb300 as rs
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    spec, snap = _snapshot(args.workload, rank)
+    ctx = rs.Context(box=snap["box"], link_len=snap["link_length"], softening=snap["softening"],
+                     particle_mass=snap["particle_mass"], device=local)
+    pos = torch.from_numpy(snap["pos"]).cuda()
+    vel = torch.from_numpy(snap["vel"]).cuda()
+    ids = torch.from_numpy(snap["ids"]).cuda()
+    n = len(snap["ids"])
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lab, _ = rs.rs_fof3d(ctx, pos, ids)
+        rs.rs_fof6d(ctx, pos, vel, ids, lab)
+        _, bound, nfb = rs.rs_unbind(ctx, pos, vel, want_potential=False)
+        props = rs.rs_halo_props(ctx)
+        return lab, bound, props, nfb
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pairs, members = _hier_work(ctx)
+    # ---- device-resident timed region
+    ctx.profile(True)
+    l0 = ctx.kernel_launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        _barrier(ws)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, _, _, nfb = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        _barrier(ws)
+    launches = ctx.kernel_launches - l0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    prof = ctx.profile_totals()
+    ctx.profile(False)
+    clocks = clk.summary()
+    t_max, units = aggregate(elapsed, float(n) * args.steps, ws, f"cuda:{local}")
+    value = units / t_max
+    # ---- end to end through the public API with host buffers
+    pin = {k: torch.from_numpy(snap[k]).pin_memory() for k in ("pos", "vel", "ids")}
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    e_pos, e_vel, e_ids = (torch.empty_like(pos), torch.empty_like(vel), torch.empty_like(ids))
+    out_lab = torch.empty(n, dtype=torch.int64).pin_memory()
+
+    def e2e_step():
+        e_pos.copy_(pin["pos"], non_blocking=True)
+        e_vel.copy_(pin["vel"], non_blocking=True)
+        e_ids.copy_(pin["ids"], non_blocking=True)
+        lab, _ = rs.rs_fof3d(ctx, e_pos, e_ids)
+        rs.rs_fof6d(ctx, e_pos, e_vel, e_ids, lab)
+        _, bound, _ = rs.rs_unbind(ctx, e_pos, e_vel, want_potential=False)
+        props = rs.rs_halo_props(ctx)
+        out_lab.copy_(lab, non_blocking=True)
+        b_h = bound.cpu()
+        p_h = props.cpu()
+        return b_h.numel() + p_h.numel() + out_lab.numel() * 8
+
+    e2e_step()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    e0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        d2h = e2e_step()
+    torch.cuda.synchronize()
+    e_el = time.perf_counter() - e0
+    e_max, e_units = aggregate(e_el, float(n) * args.steps, ws, f"cuda:{local}")
+    # ---- roofline of the dominant instrumented kernel
+    dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else None
+    roof = None
+    if dom:
+        name, (ms, cnt) = dom
+        peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2070e6
+        if name in OPS_PER_PAIR:
+            pr = pairs if name != "k_link6d" else pairs / 2.0
+            work = pr * OPS_PER_PAIR[name] * args.steps
+            achieved = work / (ms / 1e3)
+            roof = {"bound": "alu", "kernel": name, "achieved": achieved / 1e12,
+                    "peak": peak_ops / 1e12, "unit": "Tops/s", "frac": achieved / peak_ops,
+                    "traffic": None, "launches": cnt, "kernel_ms_per_step": ms / args.steps,
+                    "peak_note": "FP32-pipe lane operations at 2070 MHz (152 SMs x 128 lanes)"}
+        else:
+            roof = {"bound": "hbm", "kernel": name, "achieved": None, "peak": None,
+                    "unit": "GB/s", "frac": None, "traffic": None}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        ns, dt = time_oracle(snap, threads)
+        cpu = {"value": ns / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"particles in the sub-volume [0, {ORACLE_SUBBOX} L)^3 of the same "
+                         f"snapshot ({ns} particles, {dt:.1f} s): FoF, hierarchy, unbinding, props"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "box": snap["box"], "seed": spec.seed,
+                       "form": "plain", "nodes": int(ctx.n_nodes), "members": int(ctx.n_members),
+                       "pairs": pairs, "l2": "inputs and hierarchy larger than L2 (no flush)",
+                       "parallelism": f"independent snapshots x{ws}"},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e_units / e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clocks,
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "fallback_members": nfb,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    spec, snap = _snapshot(args.workload, 0)
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        time_oracle(snap, threads)
+    tot_n, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        ns, dt = time_oracle(snap, threads)
+        tot_n += ns
+        tot_t += dt
+    value = tot_n / tot_t
+    sample = (f"particles in the sub-volume [0, {ORACLE_SUBBOX} L)^3 of the same snapshot "
+              f"({tot_n // max(args.steps, 1)} per step)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "form": "oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * rs_gb300.h -- C ABI of the GB300 halo-finding core (librs_gb300.so).
+ *
+ * The library runs, on one GPU, the data-parallel core of the Rockstar halo finder that
+ * MPI-Rockstar parallelises (arXiv:2412.18629, Section "Parallelization": per-process 3D
+ * friends-of-friends, then subhalo finding inside every FoF halo from 6D phase-space
+ * information; Summary: halo properties such as the inertia tensor):
+ *
+ *   rs_fof3d      periodic 3D FoF over a snapshot -> per-particle group labels
+ *   rs_fof6d      recursive 6D phase-space FoF inside every FoF group -> node hierarchy
+ *   rs_unbind     potential + kinetic energy per (node, member) -> bound flags, halo decision
+ *   rs_halo_props per-node properties over bound members (centre, velocity, dispersions,
+ *                 r_vir, inertia tensor)
+ *
+ * Conventions for every call:
+ *   - Return value: RS_OK (0) or one of the RS_ERR_* codes below; rs_last_error(ctx) then
+ *     returns a message owned by the context (valid until the next call on it). No call throws.
+ *   - Array arguments are DEVICE pointers owned by the caller, unless a comment says "host".
+ *     Positions and velocities are float32 [n][3] (x, y, z contiguous per particle); ids are
+ *     int64 [n], non-negative and unique.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream). Calls that return host-visible counts synchronise that stream before returning.
+ *   - The context owns its scratch memory and the hierarchy built by rs_fof6d; those stay
+ *     valid until the next rs_fof6d on the same context or rs_ctx_destroy. A context is used
+ *     by one host thread at a time.
+ *   - Results are deterministic and identical to the CPU oracle's definitions: 3D labels,
+ *     6D memberships, bound flags and halo decisions bit for bit; potentials within 1e-5
+ *     relative of the float64 value.
+ */
+#ifndef RS_GB300_H
+#define RS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RS_OK 0
+#define RS_ERR_INVALID_ARG 1 /* a pointer, size or configuration value is out of range */
+#define RS_ERR_CUDA 2        /* a CUDA runtime call or kernel launch failed */
+#define RS_ERR_OOM 3         /* device scratch memory could not be allocated */
+#define RS_ERR_TIMEOUT 4     /* a bounded device-side wait ran out (status word set) */
+#define RS_ERR_CAPACITY 5    /* a fixed-size buffer is too small for this input */
+#define RS_ERR_STATE 6       /* the call needs an earlier call on this context first */
+
+/* Parameters shared by every call of a context.
+ * box_L, link_len and softening are the float32 values the float32 arithmetic uses; the
+ * caller rounds them once (link_len = float(b * L / n^(1/3)), b = 0.28). */
+typedef struct rs_config {
+  float box_L;                /* periodic box side (Mpc/h); positions must lie in [0, box_L) */
+  float link_len;             /* 3D linking length ll; pairs with d^2 <= ll*ll are linked */
+  float softening;            /* Plummer softening eps of the potential (Mpc/h) */
+  float reserved0;
+  double particle_mass;       /* m (Msun/h), equal for all particles */
+  double G;                   /* gravitational constant, 4.30091e-9 Mpc (km/s)^2 / Msun */
+  int32_t f_num, f_den;       /* linked fraction f = f_num / f_den of the 6D FoF (7, 10) */
+  int32_t min_halo_particles; /* minimum node size and minimum bound count (10) */
+  int32_t bound_num, bound_den; /* halo iff bound_den * N_bound >= bound_num * n (1, 2) */
+  int32_t reserved1[3];
+} rs_config;
+
+/* Per-node halo properties written by rs_halo_props (all over the node's BOUND members). */
+typedef struct rs_halo_props_t {
+  int64_t n;          /* members of the node */
+  int64_t n_bound;    /* bound members */
+  int64_t is_halo;    /* 1 if the node passes the halo decision */
+  double m_bound;     /* n_bound * particle_mass */
+  double pos[3];      /* centre: reference member + mean offset, wrapped into [0, box_L) */
+  double vel[3];      /* bulk velocity */
+  double sigma_x;     /* sqrt of the total (3D) position variance */
+  double sigma_v;     /* sqrt of the total (3D) velocity variance */
+  double r_vir;       /* (3 m_bound / (4 pi 200 rho_bar))^(1/3), rho_bar = n_total m / L^3 */
+  double inertia[6];  /* second moments about the centre / n_bound: xx yy zz xy xz yz */
+  double reserved;
+} rs_halo_props_t;
+
+typedef struct rs_ctx rs_ctx;
+
+/* Create a context on CUDA device `device` with a copy of *cfg. Validates cfg
+ * (box_L > 0, 0 < link_len < box_L / 5... see rs_fof3d, f_num in (0, f_den], min >= 2).
+ * out: host pointer receiving the context. No device memory is allocated yet. */
+int rs_ctx_create(rs_ctx** out, const rs_config* cfg, int device);
+
+/* Free the context and all device memory it owns. NULL is accepted. */
+int rs_ctx_destroy(rs_ctx* ctx);
+
+/* Message for the last failed call on ctx (empty string after success). */
+const char* rs_last_error(rs_ctx* ctx);
+
+/* Number of kernels this context has launched since it was created (host counter). */
+int64_t rs_kernel_launches(rs_ctx* ctx);
+
+/* 3D friends-of-friends (Section "Parallelization"). Particles i and j are linked iff
+ *   d = x_j - x_i (float32, per dimension), wrapped once: d > L/2 -> d - L, d < -L/2 -> d + L;
+ *   (dx*dx + dy*dy) + dz*dz <= link_len*link_len, all float32, no fused multiply-add.
+ * Groups are the connected components of the link graph.
+ * n:            particles (0 <= n < 2^32 - 1).
+ * pos:          float32 [n][3], device, in [0, box_L).
+ * ids:          int64 [n], device, unique and >= 0.
+ * label_out:    int64 [n], device: the smallest id of the particle's group (input order).
+ * n_groups_out: host; number of groups (singletons included). May be NULL.
+ * Synchronises `stream` when n_groups_out is not NULL.
+ * Errors: RS_ERR_INVALID_ARG (null pointer with n > 0; box_L / link_len beyond the 4096-cell
+ * grid), RS_ERR_OOM, RS_ERR_CUDA. */
+int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t* ids, int64_t* label_out,
+             int64_t* n_groups_out, void* stream);
+
+/* 6D phase-space FoF hierarchy inside every FoF group (Section "Parallelization"; metric,
+ * f = 0.7 and recursion from Rockstar). Level 0 = FoF groups (by fof_label) with at least
+ * min_halo_particles members. For a node with members in ascending id order and reference
+ * member r (smallest id):
+ *   u_i = wrapped x_i - x_r (float32, rs_fof3d's wrap); sigma_x^2, sigma_v^2 = total variances
+ *   from float64 sums in the canonical reduction order; inv = float(1/sigma^2), 0 if sigma^2<=0;
+ *   d6(i,j) = fl(|u_j-u_i|^2 * inv_sx2) + fl(|v_j-v_i|^2 * inv_sv2) (float32, no FMA);
+ *   l2 = the k-th smallest nearest-neighbour d6, k = ceil(f_num*g/f_den) - 1 (0-based);
+ *   i ~ j iff d6(i,j) <= l2; children = components with >= min_halo_particles and < g
+ *   members, each split again with its own sigmas.
+ * Node order: level, then parent index, then smallest id (breadth first).
+ * n, pos, ids:   as rs_fof3d; vel float32 [n][3] device.
+ * fof_label:     int64 [n] device, a 3D FoF labelling (label = smallest id of the group).
+ * n_nodes_out, n_members_out: host, may be NULL; total nodes and total (node, member) pairs.
+ * Synchronises `stream`. Errors: RS_ERR_INVALID_ARG, RS_ERR_OOM, RS_ERR_CUDA. */
+int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* vel, const int64_t* ids,
+             const int64_t* fof_label, int64_t* n_nodes_out, int64_t* n_members_out,
+             void* stream);
+
+/* Copy the hierarchy of the last rs_fof6d out (device pointers; each may be NULL to skip):
+ * node_parent int64 [n_nodes] (-1 for level 0), node_level int32 [n_nodes], node_min_id int64,
+ * node_size int64, member_offsets int64 [n_nodes + 1], member_idx int64 [n_members] (particle
+ * indices, ascending id within each node), particle_deepest_node int64 [n] (-1 if none).
+ * Errors: RS_ERR_STATE if no hierarchy exists, RS_ERR_CUDA. */
+int rs_fof6d_copy(rs_ctx* ctx, int64_t* node_parent, int32_t* node_level, int64_t* node_min_id,
+                  int64_t* node_size, int64_t* member_offsets, int64_t* member_idx,
+                  int64_t* particle_deepest_node, void* stream);
+
+/* Unbinding of every node of the last rs_fof6d hierarchy (pos, vel: the same arrays).
+ * phi_i = -G m sum_{j != i} 1 / sqrt(|u_j - u_i|^2 + eps^2) over the node's members;
+ * KE_i = 0.5 |v_i - v_bulk|^2 (float64, v_bulk = mean member velocity); bound iff
+ * KE_i + phi_i < 0 with phi the float64 canonical-order sum; halo iff
+ * N_bound >= min_halo_particles and bound_den * N_bound >= bound_num * n.
+ * The potential is computed in float32 with a certified error bound; members whose energy
+ * is within that bound of zero are recomputed exactly in float64, so flags are exact.
+ * potential_out: float32 [n_members] device (member CSR order) or NULL.
+ * bound_out:     uint8 [n_members] device (member CSR order), 1 = bound.
+ * n_fallback_out: host, may be NULL: members recomputed in float64.
+ * Synchronises `stream`. Errors: RS_ERR_STATE (no hierarchy), RS_ERR_INVALID_ARG,
+ * RS_ERR_CUDA. */
+int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float* potential_out,
+              uint8_t* bound_out, int64_t* n_fallback_out, void* stream);
+
+/* Halo properties of every node of the hierarchy over its bound members (last rs_unbind),
+ * float64 sums in the canonical reduction order over members in ascending id order with
+ * unbound members contributing 0.
+ * props_out: rs_halo_props_t [n_nodes] device. Errors: RS_ERR_STATE, RS_ERR_CUDA. */
+int rs_halo_props(rs_ctx* ctx, rs_halo_props_t* props_out, void* stream);
+
+/* Float64 sum of a[0..m) in the canonical reduction order every float64 sum of the path uses
+ * (chunks of 1024; lane l of a chunk adds terms l, l+32, ... in order; lanes combine by the
+ * halving tree; chunk totals by the level-by-level pairwise tree, odd element carried up).
+ * a: float64 [m] device; out: float64 [1] device. Exposed so the order can be checked alone.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
+int rs_cro_sum(rs_ctx* ctx, int64_t m, const double* a, double* out, void* stream);
+
+/* Per-kernel CUDA-event timing of the dominant kernels (k_fof_link, k_sort_*, k_nn6d,
+ * k_link6d, k_select_l2, k_potential, k_fallback). rs_profile(ctx, 1) clears the totals and
+ * starts recording events on each launch's stream; rs_profile(ctx, 0) stops. The paper reports
+ * whole-run wall times only; this is instrumentation, not part of the method.
+ * rs_profile_get: totals of entry `index` (0-based, in first-seen order): kernel name (host
+ * buffer of name_cap bytes), summed milliseconds and launch count (host). Waits for the
+ * recorded events. Errors: RS_ERR_CAPACITY when index is past the last entry. */
+int rs_profile(rs_ctx* ctx, int enable);
+int rs_profile_get(rs_ctx* ctx, int index, char* name, int name_cap, double* total_ms,
+                   int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_GB300_H */

@@ -1,0 +1,257 @@
+"""Python binding of librs_gb300.so, the GB300 halo-finding core (C ABI in include/rs_gb300.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA kernels. Tensors
+are PyTorch CUDA tensors (PyTorch supplies device memory and streams); functions carry the C
+ABI's names and fail loudly when the library is missing, since there is no fallback.
+
+    ctx = Context(box=256.0, link_len=0.28, softening=0.01, particle_mass=1e10)
+    labels, n_groups = rs_fof3d(ctx, pos, ids)
+    n_nodes, n_members = rs_fof6d(ctx, pos, vel, ids, labels)
+    phi, bound, n_fallback = rs_unbind(ctx, pos, vel)
+    props = rs_halo_props(ctx)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librs_gb300.so")
+G_NEWTON = 4.30091e-9
+
+RS_OK = 0
+_ERRORS = {1: "RS_ERR_INVALID_ARG", 2: "RS_ERR_CUDA", 3: "RS_ERR_OOM", 4: "RS_ERR_TIMEOUT",
+           5: "RS_ERR_CAPACITY", 6: "RS_ERR_STATE"}
+
+# rs_halo_props_t: n, n_bound, is_halo (int64) then 17 float64 = 20 eight-byte fields.
+PROPS_FIELDS = 20
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rs_config(ctypes.Structure):
+    _fields_ = [
+        ("box_L", ctypes.c_float), ("link_len", ctypes.c_float), ("softening", ctypes.c_float),
+        ("reserved0", ctypes.c_float), ("particle_mass", ctypes.c_double),
+        ("G", ctypes.c_double), ("f_num", ctypes.c_int32), ("f_den", ctypes.c_int32),
+        ("min_halo_particles", ctypes.c_int32), ("bound_num", ctypes.c_int32),
+        ("bound_den", ctypes.c_int32), ("reserved1", ctypes.c_int32 * 3),
+    ]
+
+
+def load_library():
+    """Load librs_gb300.so (built by __graft_entry__.build() / build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() first "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.rs_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(rs_config), ctypes.c_int]
+        lib.rs_ctx_destroy.argtypes = [P]
+        lib.rs_last_error.argtypes = [P]
+        lib.rs_last_error.restype = ctypes.c_char_p
+        lib.rs_kernel_launches.argtypes = [P]
+        lib.rs_kernel_launches.restype = i64
+        lib.rs_fof3d.argtypes = [P, i64, P, P, P, ctypes.POINTER(i64), P]
+        lib.rs_fof6d.argtypes = [P, i64, P, P, P, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]
+        lib.rs_fof6d_copy.argtypes = [P, P, P, P, P, P, P, P, P]
+        lib.rs_unbind.argtypes = [P, P, P, P, P, ctypes.POINTER(i64), P]
+        lib.rs_halo_props.argtypes = [P, P, P]
+        lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
+        lib.rs_profile.argtypes = [P, ctypes.c_int]
+        lib.rs_profile_get.argtypes = [P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_fof3d", "rs_fof6d", "rs_fof6d_copy",
+                     "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile", "rs_profile_get"):
+            getattr(lib, name).restype = i32
+        _lib = lib
+        return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_dev(t, dtype, shape_tail=None, name="tensor"):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name} must have shape [n, {shape_tail}]")
+
+
+class Context:
+    """An rs_ctx: configuration plus the library-owned scratch and hierarchy state."""
+
+    def __init__(self, box, link_len, softening, particle_mass, G=G_NEWTON, f=(7, 10),
+                 min_halo_particles=10, bound_frac=(1, 2), device=0):
+        self.lib = load_library()
+        cfg = rs_config()
+        cfg.box_L, cfg.link_len, cfg.softening = float(box), float(link_len), float(softening)
+        cfg.particle_mass, cfg.G = float(particle_mass), float(G)
+        cfg.f_num, cfg.f_den = int(f[0]), int(f[1])
+        cfg.min_halo_particles = int(min_halo_particles)
+        cfg.bound_num, cfg.bound_den = int(bound_frac[0]), int(bound_frac[1])
+        self.cfg = cfg
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        rc = self.lib.rs_ctx_create(ctypes.byref(h), ctypes.byref(cfg), self.device)
+        if rc != RS_OK:
+            raise RSError(rc, "rs_ctx_create failed")
+        self.handle = h
+
+    def check(self, rc):
+        if rc != RS_OK:
+            raise RSError(rc, self.lib.rs_last_error(self.handle).decode())
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.rs_kernel_launches(self.handle))
+
+    def profile(self, enable=True):
+        """Start (clearing totals) or stop CUDA-event timing of the dominant kernels."""
+        self.check(self.lib.rs_profile(self.handle, 1 if enable else 0))
+
+    def profile_totals(self):
+        """{kernel: (total_ms, launches)} recorded since profile(True)."""
+        out = {}
+        buf = ctypes.create_string_buffer(128)
+        ms, cnt = ctypes.c_double(0), ctypes.c_int64(0)
+        k = 0
+        while self.lib.rs_profile_get(self.handle, k, buf, 128, ctypes.byref(ms),
+                                      ctypes.byref(cnt)) == RS_OK:
+            out[buf.value.decode()] = (ms.value, cnt.value)
+            k += 1
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rs_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rs_fof3d(ctx, pos, ids, label_out=None, stream=None):
+    """3D FoF labels (smallest id per group, int64 [n]) and the number of groups."""
+    torch = _torch()
+    _check_dev(pos, torch.float32, (3,), "pos")
+    _check_dev(ids, torch.int64, None, "ids")
+    n = pos.shape[0]
+    if label_out is None:
+        label_out = torch.empty(n, dtype=torch.int64, device=pos.device)
+    ng = ctypes.c_int64(0)
+    ctx.check(ctx.lib.rs_fof3d(ctx.handle, n, _ptr(pos), _ptr(ids), _ptr(label_out),
+                               ctypes.byref(ng), _stream(stream)))
+    return label_out, ng.value
+
+
+def rs_fof6d(ctx, pos, vel, ids, fof_label, stream=None):
+    """Build the 6D hierarchy inside the context; returns (n_nodes, n_members)."""
+    torch = _torch()
+    _check_dev(pos, torch.float32, (3,), "pos")
+    _check_dev(vel, torch.float32, (3,), "vel")
+    _check_dev(ids, torch.int64, None, "ids")
+    _check_dev(fof_label, torch.int64, None, "fof_label")
+    nn, nm = ctypes.c_int64(0), ctypes.c_int64(0)
+    ctx.check(ctx.lib.rs_fof6d(ctx.handle, pos.shape[0], _ptr(pos), _ptr(vel), _ptr(ids),
+                               _ptr(fof_label), ctypes.byref(nn), ctypes.byref(nm),
+                               _stream(stream)))
+    ctx.n_nodes, ctx.n_members, ctx.n_particles = nn.value, nm.value, pos.shape[0]
+    return nn.value, nm.value
+
+
+def rs_fof6d_copy(ctx, stream=None):
+    """Hierarchy arrays as CUDA tensors (parent, level, min_id, size, member_off, member_idx,
+    deepest)."""
+    torch = _torch()
+    dev = torch.device("cuda", ctx.device)
+    nn, nm, n = ctx.n_nodes, ctx.n_members, ctx.n_particles
+    out = {
+        "parent": torch.empty(nn, dtype=torch.int64, device=dev),
+        "level": torch.empty(nn, dtype=torch.int32, device=dev),
+        "min_id": torch.empty(nn, dtype=torch.int64, device=dev),
+        "size": torch.empty(nn, dtype=torch.int64, device=dev),
+        "member_off": torch.empty(nn + 1, dtype=torch.int64, device=dev),
+        "member_idx": torch.empty(nm, dtype=torch.int64, device=dev),
+        "deepest": torch.empty(n, dtype=torch.int64, device=dev),
+    }
+    ctx.check(ctx.lib.rs_fof6d_copy(ctx.handle, *(_ptr(out[k]) for k in (
+        "parent", "level", "min_id", "size", "member_off", "member_idx", "deepest")),
+        _stream(stream)))
+    return out
+
+
+def rs_unbind(ctx, pos, vel, want_potential=True, bound_out=None, stream=None):
+    """Per (node, member): float32 potential (or None), uint8 bound flag; and the number of
+    members whose flag needed the exact float64 potential."""
+    torch = _torch()
+    dev = pos.device
+    phi = torch.empty(ctx.n_members, dtype=torch.float32, device=dev) if want_potential else None
+    if bound_out is None:
+        bound_out = torch.empty(ctx.n_members, dtype=torch.uint8, device=dev)
+    nfb = ctypes.c_int64(0)
+    ctx.check(ctx.lib.rs_unbind(ctx.handle, _ptr(pos), _ptr(vel), _ptr(phi), _ptr(bound_out),
+                                ctypes.byref(nfb), _stream(stream)))
+    return phi, bound_out, nfb.value
+
+
+def rs_halo_props(ctx, props_out=None, stream=None):
+    """rs_halo_props_t per node as a uint8 CUDA tensor [n_nodes, 160] (see props_to_float64)."""
+    torch = _torch()
+    if props_out is None:
+        props_out = torch.empty((ctx.n_nodes, 8 * PROPS_FIELDS), dtype=torch.uint8,
+                                device=torch.device("cuda", ctx.device))
+    ctx.check(ctx.lib.rs_halo_props(ctx.handle, _ptr(props_out), _stream(stream)))
+    return props_out
+
+
+def props_to_float64(raw):
+    """rs_halo_props_t rows -> float64 [n, 20]: n, n_bound, is_halo, m_bound, pos[3], vel[3],
+    sigma_x, sigma_v, r_vir, inertia[6], reserved."""
+    torch = _torch()
+    raw = raw.contiguous()
+    as_i = raw.view(torch.int64).reshape(-1, PROPS_FIELDS)
+    out = raw.view(torch.float64).reshape(-1, PROPS_FIELDS).clone()
+    out[:, :3] = as_i[:, :3].to(torch.float64)
+    return out
+
+
+def rs_cro_sum(ctx, a, stream=None):
+    """Canonical-order float64 sum of a CUDA float64 tensor (returns a 1-element tensor)."""
+    torch = _torch()
+    _check_dev(a, torch.float64, None, "a")
+    out = torch.empty(1, dtype=torch.float64, device=a.device)
+    ctx.check(ctx.lib.rs_cro_sum(ctx.handle, a.numel(), _ptr(a), _ptr(out), _stream(stream)))
+    return out

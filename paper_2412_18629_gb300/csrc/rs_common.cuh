@@ -1,0 +1,230 @@
+// Internal definitions shared by the library's translation units: the context, scratch
+// buffers, error handling, and small device helpers (exact float32/float64 arithmetic,
+// union-find, warp reductions in the canonical order).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/rs_gb300.h"
+
+namespace rs {
+
+// ------------------------------------------------------------------------------------------
+// Scratch buffers: grow-only device allocations owned by the context, one per slot.
+enum Slot : int {
+  // rs_fof3d
+  S_KEY_A, S_KEY_B, S_VAL_A, S_VAL_B, S_SORT_HIST, S_POS_SORTED, S_ROW_START, S_CELL_END,
+  S_PARENT, S_MINID, S_COUNTER,
+  // rs_fof6d (level work)
+  S_GKEY_A, S_GKEY_B, S_GVAL_A, S_GVAL_B, S_NN2, S_UF, S_ROOT_CNT, S_CHILD_IDX, S_FLAGS,
+  S_SCAN_TMP, S_CHUNK_OFF, S_CHUNK_SUM, S_NODE_TMP, S_SELECT,
+  // hierarchy state (persists until the next rs_fof6d)
+  S_H_MEM, S_H_MNODE, S_H_U, S_H_V, S_H_NODE_OFF, S_H_NODE_SIZE, S_H_NODE_PARENT,
+  S_H_NODE_LEVEL, S_H_NODE_MINID, S_H_NODE_REF, S_H_NODE_INV, S_H_DEEPEST, S_H_WORK,
+  // rs_unbind / rs_halo_props state
+  S_U_PHI, S_U_BOUND, S_U_NB, S_U_VBULK, S_U_AMBIG, S_U_FLAGS,
+  S_NUM_SLOTS
+};
+
+struct Buffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace rs
+
+struct rs_ctx {
+  rs_config cfg;
+  int device = 0;
+  char err[512] = {0};
+  rs::Buffer buf[rs::S_NUM_SLOTS];
+  int64_t launches = 0;
+  // host pinned mailbox for small device->host results
+  int64_t* host_box = nullptr;
+  // hierarchy state
+  bool have_hier = false;
+  int64_t n_particles = 0;
+  int64_t n_nodes = 0;
+  int64_t n_members = 0;
+  int32_t n_levels = 0;
+  bool have_unbind = false;
+  const float* h_pos = nullptr;  // arrays the hierarchy's U, V were gathered from
+  const float* h_vel = nullptr;
+  // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
+  bool profile = false;
+  struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_free;
+  struct ProfTot {
+    std::string name;
+    double ms;
+    int64_t launches;
+  };
+  std::vector<ProfTot> prof_tot;
+};
+
+namespace rs {
+
+int set_error(rs_ctx* ctx, int code, const char* fmt, ...);
+
+// Device buffer of at least `bytes` for `slot` (contents undefined on growth).
+void* scratch(rs_ctx* ctx, int slot, size_t bytes);
+
+template <class T>
+T* scratch_t(rs_ctx* ctx, int slot, size_t count) {
+  return static_cast<T*>(scratch(ctx, slot, count * sizeof(T)));
+}
+
+// Propagates an error code out of the calling entry point.
+#define RS_TRY(expr)            \
+  do {                          \
+    int _rc = (expr);           \
+    if (_rc != RS_OK) return _rc; \
+  } while (0)
+
+#define RS_CUDA(ctx, expr)                                                            \
+  do {                                                                                \
+    cudaError_t _e = (expr);                                                          \
+    if (_e != cudaSuccess)                                                            \
+      return rs::set_error((ctx), RS_ERR_CUDA, "%s: %s (%s:%d)", #expr,               \
+                           cudaGetErrorString(_e), __FILE__, __LINE__);               \
+  } while (0)
+
+// CUDA-event timing around one launch when profiling is on (records on the launch stream).
+struct ProfScope {
+  rs_ctx* ctx;
+  cudaStream_t st;
+  int idx = -1;
+  ProfScope(rs_ctx* c, const char* name, cudaStream_t s);
+  ~ProfScope();
+};
+
+// Check the launch that was just enqueued and count it.
+int after_launch(rs_ctx* ctx, const char* name);
+#define RS_LAUNCHED(ctx, name) RS_TRY(rs::after_launch((ctx), (name)))
+
+inline unsigned grid_for(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 0x7fffffff) g = 0x7fffffff;
+  return unsigned(g);
+}
+
+// ------------------------------------------------------------------------------------------
+// Primitive device algorithms (rs_primitives.cu).
+//
+// LSD radix sort of (key, value) pairs over bits [0, nbits) of the 64-bit key; stable.
+// Sorted output ends in (*keys_out, *vals_out), which point into the given A/B buffers.
+int radix_sort_u64(rs_ctx* ctx, int64_t n, int nbits, uint64_t* keys_a, uint32_t* vals_a,
+                   uint64_t* keys_b, uint32_t* vals_b, uint64_t** keys_out,
+                   uint32_t** vals_out, cudaStream_t st);
+
+// Exclusive prefix sum of int64 values in place; returns the total via *total_dev (device).
+int exclusive_scan_i64(rs_ctx* ctx, int64_t n, int64_t* data, int64_t* total_dev,
+                       cudaStream_t st);
+
+// Copy `bytes` device -> host mailbox and synchronise the stream.
+int read_back(rs_ctx* ctx, const void* dev, size_t bytes, cudaStream_t st);
+
+// Device arrays of the 6D hierarchy held by a context (valid after rs_fof6d). Members are
+// stored node after node, each node's members in ascending id order.
+struct Hier {
+  uint32_t* mem;       // particle index per (node, member)
+  uint32_t* mnode;     // node per member position
+  float4* U;           // member offset from the node's reference (smallest-id) member
+  float4* V;           // member velocity
+  int64_t* node_off;   // [nodes + 1] member offsets
+  int64_t* node_size;
+  int64_t* node_parent;
+  int32_t* node_level;
+  int64_t* node_minid;
+  float4* inv;         // (inv_sx2, inv_sv2, l2, 0) of the node's 6D split
+  float4* ref;         // reference member position
+  int64_t* deepest;    // [n] deepest node per particle, -1 if none
+};
+Hier hier_of(rs_ctx* ctx);
+
+}  // namespace rs
+
+// ------------------------------------------------------------------------------------------
+// Device helpers
+namespace rsd {
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// float32 periodic minimum-image difference b - a, never contracted or reassociated.
+__device__ __forceinline__ float wrap_diff(float a, float b, float L, float hL) {
+  float d = __fsub_rn(b, a);
+  if (d > hL) {
+    d = __fsub_rn(d, L);
+  } else if (d < -hL) {
+    d = __fadd_rn(d, L);
+  }
+  return d;
+}
+
+// (dx*dx + dy*dy) + dz*dz in float32 with every operation rounded separately.
+__device__ __forceinline__ float sq3(float dx, float dy, float dz) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Union-find over uint32 indices; roots are the smallest index of their set. Parent reads
+// bypass L1 (other SMs write them); stale values are still ancestors, so reads stay valid.
+__device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t x) {
+  uint32_t p = __ldcg(parent + x);
+  while (p != x) {
+    const uint32_t gp = __ldcg(parent + p);
+    if (gp != p) parent[x] = gp;  // path halving (benign race: gp is an ancestor of x)
+    x = p;
+    p = gp;
+  }
+  return x;
+}
+
+__device__ __forceinline__ uint32_t uf_find_ro(const uint32_t* parent, uint32_t x) {
+  uint32_t p = __ldcg(parent + x);
+  while (p != x) {
+    x = p;
+    p = __ldcg(parent + x);
+  }
+  return x;
+}
+
+// Hook the larger root under the smaller; retries when another thread moved a root first.
+__device__ __forceinline__ void uf_unite(uint32_t* parent, uint32_t a, uint32_t b) {
+  while (true) {
+    a = uf_find(parent, a);
+    b = uf_find(parent, b);
+    if (a == b) return;
+    if (a < b) {
+      const uint32_t t = a;
+      a = b;
+      b = t;
+    }
+    const uint32_t old = atomicCAS(parent + a, a, b);
+    if (old == a) return;
+  }
+}
+
+// Canonical-order combination of the 32 lane partial sums of a warp: halving tree
+// s[l] += s[l + off], off = 16 .. 1, realised as an xor butterfly (IEEE + commutes, so lane
+// 0 ends with exactly the halving-tree value).
+__device__ __forceinline__ double warp_cro_combine(double s) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off));
+  return s;
+}
+
+}  // namespace rsd

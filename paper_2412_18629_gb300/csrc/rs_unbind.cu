@@ -1,0 +1,389 @@
+// Unbinding and halo properties over every node of the 6D hierarchy.
+//
+// Potential: phi_i = -G m sum_{j != i} (|u_j - u_i|^2 + eps^2)^(-1/2) over the node's members.
+//   k_potential   float32 direct sum: block = (node, i-tile of 256), j-tiles of 256 float4 in
+//                 shared memory, FMA + rsqrt per pair, 32-term blocks added with Kahan
+//                 compensation. Certified relative error bound B (see kCertB).
+//   k_flags       float64 kinetic energy against the node's bulk velocity (canonical-order sum),
+//                 E = KE + phi~. |E| > 2 B |phi~| decides the flag; otherwise the member is queued
+//                 for the exact float64 potential.
+//   k_fallback    one warp per queued member: the float64 potential in the canonical reduction
+//                 order, bit-identical to the definition, then the exact flag.
+//   k_halo        bound count, halo decision, bound mass per node.
+// Properties (rs_halo_props): canonical-order sums over bound members (unbound contribute 0).
+#include <cmath>
+
+#include "rs_cro.cuh"
+
+namespace rs {
+int gather_members(rs_ctx* ctx, int64_t mb, int64_t me, int64_t nb, int64_t ne, const float* pos,
+                   const float* vel, cudaStream_t st);
+}  // namespace rs
+
+using namespace rs;
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kPotTile = 256;
+
+// Relative error bound of the float32 potential sum (all terms positive):
+//   per term: operands rounded (3 differences, 3 fused steps, eps^2) <= ~6u relative in r^2, so
+//   <= 3u after the square root, plus rsqrt.approx's 2^-22.9 (~2.2u): <= 8u allowing slack;
+//   32-term sequential blocks: <= 31u; Kahan-compensated sum of the blocks: <= 2u + O(N u^2).
+//   Total <= 41u + 1e-12 with u = 2^-24; the flag test uses twice this.
+constexpr double kU = 5.9604644775390625e-08;
+constexpr double kCertB = 41.0 * kU + 1e-12;
+
+__global__ void k_tiles(int64_t nn, const int64_t* __restrict__ node_size, int tile,
+                        int64_t* __restrict__ out) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < nn) out[k] = (node_size[k] + tile - 1) / tile;
+}
+
+__global__ void __launch_bounds__(kPotTile)
+k_potential(int64_t nn, const int64_t* __restrict__ tile_off, const int64_t* __restrict__ node_off,
+            const int64_t* __restrict__ node_size, const float4* __restrict__ U, float eps2,
+            float* __restrict__ S_out) {
+  __shared__ float4 su[kPotTile];
+  const int64_t b = blockIdx.x;
+  if (b >= tile_off[nn]) return;
+  const int64_t q = rsd::upper_bound_i64(tile_off, nn, b) - 1;
+  const int64_t t = b - tile_off[q];
+  const int64_t base = node_off[q], g = node_size[q];
+  const int64_t i = t * kPotTile + threadIdx.x;
+  const bool valid = i < g;
+  const float4 ui = valid ? U[base + i] : make_float4(0, 0, 0, 0);
+  float S = 0.f, C = 0.f;
+  for (int64_t j0 = 0; j0 < g; j0 += kPotTile) {
+    const int64_t j = j0 + threadIdx.x;
+    if (j < g) su[threadIdx.x] = U[base + j];
+    __syncthreads();
+    const int jn = int(rsd::min64(kPotTile, g - j0));
+    const int self = int(i - j0);  // in [0, jn) only on the diagonal tile
+    for (int jb = 0; jb < jn; jb += 32) {
+      const int je = min(jb + 32, jn);
+      float blk = 0.f;
+      for (int jj = jb; jj < je; ++jj) {
+        const float4 uj = su[jj];
+        const float dx = __fsub_rn(uj.x, ui.x);
+        const float dy = __fsub_rn(uj.y, ui.y);
+        const float dz = __fsub_rn(uj.z, ui.z);
+        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2)));
+        const float w = rsqrtf(r2);
+        blk = __fadd_rn(blk, jj == self ? 0.f : w);
+      }
+      const float y = __fsub_rn(blk, C);
+      const float tt = __fadd_rn(S, y);
+      C = __fsub_rn(__fsub_rn(tt, S), y);
+      S = tt;
+    }
+    __syncthreads();
+  }
+  if (valid) S_out[base + i] = S;
+}
+
+struct VelTerm {
+  const float4* V;
+  __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
+    const float4 v = V[p];
+    acc[0] = __dadd_rn(acc[0], double(v.x));
+    acc[1] = __dadd_rn(acc[1], double(v.y));
+    acc[2] = __dadd_rn(acc[2], double(v.z));
+  }
+};
+
+__device__ __forceinline__ double kinetic(float4 v, const double* vsum, double g) {
+  const double dvx = __dsub_rn(double(v.x), __ddiv_rn(vsum[0], g));
+  const double dvy = __dsub_rn(double(v.y), __ddiv_rn(vsum[1], g));
+  const double dvz = __dsub_rn(double(v.z), __ddiv_rn(vsum[2], g));
+  const double s = __dadd_rn(__dadd_rn(__dmul_rn(dvx, dvx), __dmul_rn(dvy, dvy)), __dmul_rn(dvz, dvz));
+  return __dmul_rn(0.5, s);
+}
+
+__global__ void k_flags(int64_t m, const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_size,
+                        const float4* __restrict__ V, const double* __restrict__ vsum,
+                        const float* __restrict__ S, double Gm, double certB,
+                        uint8_t* __restrict__ bound, float* __restrict__ phi_out,
+                        uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  const uint32_t q = mnode[p];
+  const double ke = kinetic(V[p], vsum + 3 * int64_t(q), double(node_size[q]));
+  const double ph = -__dmul_rn(Gm, double(S[p]));
+  const double e = __dadd_rn(ke, ph);
+  if (phi_out) phi_out[p] = __double2float_rn(ph);
+  if (fabs(e) > __dmul_rn(2.0 * certB, fabs(ph))) {
+    bound[p] = e < 0.0 ? 1 : 0;
+  } else {
+    bound[p] = 0;
+    const unsigned long long k = atomicAdd(n_ambig, 1ull);
+    ambig[k] = uint32_t(p);
+  }
+}
+
+// Exact float64 potential of queued members, canonical reduction order over j in member order
+// with the self term 0.0; one warp per member.
+__global__ void __launch_bounds__(kT)
+k_fallback(const unsigned long long* __restrict__ n_ambig, const uint32_t* __restrict__ ambig,
+           const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_off,
+           const int64_t* __restrict__ node_size, const float4* __restrict__ U,
+           const float4* __restrict__ V, const double* __restrict__ vsum, double eps2, double Gm,
+           uint8_t* __restrict__ bound, float* __restrict__ phi_out) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long total = *n_ambig;
+  for (unsigned long long w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < total;
+       w += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const uint32_t p = ambig[w];
+    const uint32_t q = mnode[p];
+    const int64_t base = node_off[q], g = node_size[q];
+    const int64_t i = int64_t(p) - base;
+    const float4 ui = U[p];
+    const double xi = ui.x, yi = ui.y, zi = ui.z;
+    rsd::CroTree tree;
+    for (int64_t c = 0; c * 1024 < g; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < 32; ++k) {
+        const int64_t j = c * 1024 + lane + 32 * k;
+        if (j < g) {
+          double term = 0.0;
+          if (j != i) {
+            const float4 uj = U[base + j];
+            const double dx = __dsub_rn(double(uj.x), xi);
+            const double dy = __dsub_rn(double(uj.y), yi);
+            const double dz = __dsub_rn(double(uj.z), zi);
+            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            term = __ddiv_rn(1.0, __dsqrt_rn(__dadd_rn(r2, eps2)));
+          }
+          acc = __dadd_rn(acc, term);
+        }
+      }
+      tree.push(rsd::warp_cro_combine(acc));
+    }
+    if (lane == 0) {
+      const double ph = -__dmul_rn(Gm, tree.result());
+      const double ke = kinetic(V[p], vsum + 3 * int64_t(q), double(g));
+      bound[p] = __dadd_rn(ke, ph) < 0.0 ? 1 : 0;
+      if (phi_out) phi_out[p] = __double2float_rn(ph);
+    }
+  }
+}
+
+__global__ void k_bound_count(int64_t m, const uint32_t* __restrict__ mnode, const uint8_t* __restrict__ bound,
+                              unsigned long long* __restrict__ nb) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p < m && bound[p]) atomicAdd(nb + mnode[p], 1ull);
+}
+
+__global__ void k_copy_u8(int64_t n, const uint8_t* __restrict__ a, uint8_t* __restrict__ b) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Properties
+struct PropTerm1 {  // bound-masked u, u^2, v, v^2
+  const float4* U;
+  const float4* V;
+  const uint8_t* bound;
+  __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
+    if (!bound[p]) {
+#pragma unroll
+      for (int s = 0; s < 12; ++s) acc[s] = __dadd_rn(acc[s], 0.0);
+      return;
+    }
+    const float4 u = U[p], v = V[p];
+    const double a[3] = {double(u.x), double(u.y), double(u.z)};
+    const double b[3] = {double(v.x), double(v.y), double(v.z)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      acc[d] = __dadd_rn(acc[d], a[d]);
+      acc[3 + d] = __dadd_rn(acc[3 + d], __dmul_rn(a[d], a[d]));
+      acc[6 + d] = __dadd_rn(acc[6 + d], b[d]);
+      acc[9 + d] = __dadd_rn(acc[9 + d], __dmul_rn(b[d], b[d]));
+    }
+  }
+};
+
+struct PropTerm2 {  // bound-masked second moments about the bound mean
+  const float4* U;
+  const uint8_t* bound;
+  const double* mean;  // [node][3]
+  __device__ __forceinline__ void add(int64_t q, int64_t p, int64_t, double* acc) const {
+    if (!bound[p]) {
+#pragma unroll
+      for (int s = 0; s < 6; ++s) acc[s] = __dadd_rn(acc[s], 0.0);
+      return;
+    }
+    const float4 u = U[p];
+    const double* mu = mean + 3 * q;
+    const double d[3] = {__dsub_rn(double(u.x), mu[0]), __dsub_rn(double(u.y), mu[1]),
+                         __dsub_rn(double(u.z), mu[2])};
+    acc[0] = __dadd_rn(acc[0], __dmul_rn(d[0], d[0]));
+    acc[1] = __dadd_rn(acc[1], __dmul_rn(d[1], d[1]));
+    acc[2] = __dadd_rn(acc[2], __dmul_rn(d[2], d[2]));
+    acc[3] = __dadd_rn(acc[3], __dmul_rn(d[0], d[1]));
+    acc[4] = __dadd_rn(acc[4], __dmul_rn(d[0], d[2]));
+    acc[5] = __dadd_rn(acc[5], __dmul_rn(d[1], d[2]));
+  }
+};
+
+__global__ void k_prop_means(int64_t nn, const unsigned long long* __restrict__ nb,
+                             const double* __restrict__ s1, double* __restrict__ mean) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= nn) return;
+  const double c = double(nb[q]);
+  for (int d = 0; d < 3; ++d) mean[3 * q + d] = nb[q] ? __ddiv_rn(s1[12 * q + d], c) : 0.0;
+}
+
+__global__ void k_prop_final(int64_t nn, const int64_t* __restrict__ node_size,
+                             const unsigned long long* __restrict__ nb, const uint8_t* __restrict__ is_halo,
+                             const double* __restrict__ s1, const double* __restrict__ s2,
+                             const double* __restrict__ mean, const float4* __restrict__ ref,
+                             float L, double m, double rho_bar, rs_halo_props_t* __restrict__ out) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= nn) return;
+  rs_halo_props_t P;
+  memset(&P, 0, sizeof(P));
+  P.n = node_size[q];
+  P.n_bound = int64_t(nb[q]);
+  P.is_halo = is_halo[q];
+  P.m_bound = __dmul_rn(double(nb[q]), m);
+  if (nb[q] > 0) {
+    const double c = double(nb[q]);
+    const double* S = s1 + 12 * q;
+    double varx = 0.0, varv = 0.0;
+    const float rp[3] = {ref[q].x, ref[q].y, ref[q].z};
+    for (int d = 0; d < 3; ++d) {
+      const double mu = mean[3 * q + d];
+      const double mv = __ddiv_rn(S[6 + d], c);
+      const double tx = __dsub_rn(__ddiv_rn(S[3 + d], c), __dmul_rn(mu, mu));
+      const double tv = __dsub_rn(__ddiv_rn(S[9 + d], c), __dmul_rn(mv, mv));
+      varx = (d == 0) ? tx : __dadd_rn(varx, tx);
+      varv = (d == 0) ? tv : __dadd_rn(varv, tv);
+      double cen = __dadd_rn(double(rp[d]), mu);
+      if (cen < 0.0) cen = __dadd_rn(cen, double(L));
+      else if (cen >= double(L)) cen = __dsub_rn(cen, double(L));
+      P.pos[d] = cen;
+      P.vel[d] = mv;
+    }
+    P.sigma_x = __dsqrt_rn(varx > 0.0 ? varx : 0.0);
+    P.sigma_v = __dsqrt_rn(varv > 0.0 ? varv : 0.0);
+    const double pi = 3.14159265358979323846;
+    P.r_vir = cbrt(__ddiv_rn(__dmul_rn(3.0, P.m_bound),
+                             __dmul_rn(__dmul_rn(__dmul_rn(4.0, pi), 200.0), rho_bar)));
+    for (int k = 0; k < 6; ++k) P.inertia[k] = __ddiv_rn(s2[6 * q + k], c);
+  }
+  out[q] = P;
+}
+
+__global__ void k_halo_decide(int64_t nn, const int64_t* __restrict__ node_size,
+                              const unsigned long long* __restrict__ nb, int min_size, int bnum, int bden,
+                              uint8_t* __restrict__ is_halo) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= nn) return;
+  const int64_t c = int64_t(nb[q]);
+  is_halo[q] = (c >= min_size && int64_t(bden) * c >= int64_t(bnum) * node_size[q]) ? 1 : 0;
+}
+
+}  // namespace
+
+extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float* potential_out,
+                         uint8_t* bound_out, int64_t* n_fallback_out, void* stream) {
+  if (!ctx) return RS_ERR_INVALID_ARG;
+  ctx->err[0] = 0;
+  ctx->have_unbind = false;
+  if (!ctx->have_hier) return set_error(ctx, RS_ERR_STATE, "rs_fof6d has not run on this context");
+  const int64_t m = ctx->n_members, nn = ctx->n_nodes;
+  if (m > 0 && !bound_out) return set_error(ctx, RS_ERR_INVALID_ARG, "bound_out is NULL");
+  if (m > 0 && (!pos || !vel)) return set_error(ctx, RS_ERR_INVALID_ARG, "null pos/vel");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  RS_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (pos != ctx->h_pos || vel != ctx->h_vel) {  // other arrays than rs_fof6d's: re-gather
+    RS_TRY(gather_members(ctx, 0, m, 0, nn, pos, vel, st));
+    ctx->h_pos = pos;
+    ctx->h_vel = vel;
+  }
+  Hier h = hier_of(ctx);
+  uint8_t* bound = scratch_t<uint8_t>(ctx, S_U_BOUND, size_t(std::max<int64_t>(m, 1)));
+  float* S = scratch_t<float>(ctx, S_U_PHI, size_t(std::max<int64_t>(m, 1)));
+  unsigned long long* nb = scratch_t<unsigned long long>(ctx, S_U_NB, size_t(std::max<int64_t>(nn, 1)));
+  double* vsum = scratch_t<double>(ctx, S_U_VBULK, size_t(std::max<int64_t>(nn, 1)) * 3);
+  uint32_t* ambig = scratch_t<uint32_t>(ctx, S_U_AMBIG, size_t(std::max<int64_t>(m, 1)));
+  uint8_t* halo = scratch_t<uint8_t>(ctx, S_U_FLAGS, size_t(std::max<int64_t>(nn, 1)));
+  int64_t* tile_off = scratch_t<int64_t>(ctx, S_SELECT, size_t(nn) + 1);
+  unsigned long long* n_ambig = scratch_t<unsigned long long>(ctx, S_COUNTER, 8);
+  if (!bound || !S || !nb || !vsum || !ambig || !halo || !tile_off || !n_ambig) return RS_ERR_OOM;
+  int64_t nfb = 0;
+  if (m > 0) {
+    const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
+    const float eps = ctx->cfg.softening;
+    RS_TRY((cro_segmented<3, VelTerm>(ctx, nn, h.node_off, h.node_size, m, VelTerm{h.V}, vsum, st)));
+    k_tiles<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, kPotTile, tile_off);
+    RS_LAUNCHED(ctx, "k_tiles");
+    RS_TRY(exclusive_scan_i64(ctx, nn, tile_off, tile_off + nn, st));
+    const int64_t tiles_ub = nn + m / kPotTile + 1;
+    {
+      ProfScope prof_(ctx, "k_potential", st);
+      k_potential<<<grid_for(tiles_ub, 1), kPotTile, 0, st>>>(nn, tile_off, h.node_off, h.node_size, h.U,
+                                                             eps * eps, S);
+    }
+    RS_LAUNCHED(ctx, "k_potential");
+    RS_CUDA(ctx, cudaMemsetAsync(n_ambig, 0, 8, st));
+    k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vsum, S, Gm, kCertB, bound,
+                                           potential_out, ambig, n_ambig);
+    RS_LAUNCHED(ctx, "k_flags");
+    {
+      ProfScope prof_(ctx, "k_fallback", st);
+      k_fallback<<<152 * 8, kT, 0, st>>>(n_ambig, ambig, h.mnode, h.node_off, h.node_size, h.U, h.V,
+                                         vsum, double(eps) * double(eps), Gm, bound, potential_out);
+    }
+    RS_LAUNCHED(ctx, "k_fallback");
+    RS_CUDA(ctx, cudaMemsetAsync(nb, 0, 8 * nn, st));
+    k_bound_count<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, bound, nb);
+    RS_LAUNCHED(ctx, "k_bound_count");
+    k_halo_decide<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, nb, ctx->cfg.min_halo_particles,
+                                                  ctx->cfg.bound_num, ctx->cfg.bound_den, halo);
+    RS_LAUNCHED(ctx, "k_halo_decide");
+    k_copy_u8<<<grid_for(m, kT), kT, 0, st>>>(m, bound, bound_out);
+    RS_LAUNCHED(ctx, "k_copy_u8");
+    RS_TRY(read_back(ctx, n_ambig, 8, st));
+    nfb = ctx->host_box[0];
+  }
+  if (n_fallback_out) *n_fallback_out = nfb;
+  ctx->have_unbind = true;
+  return RS_OK;
+}
+
+extern "C" int rs_halo_props(rs_ctx* ctx, rs_halo_props_t* props_out, void* stream) {
+  if (!ctx) return RS_ERR_INVALID_ARG;
+  ctx->err[0] = 0;
+  if (!ctx->have_hier || !ctx->have_unbind)
+    return set_error(ctx, RS_ERR_STATE, "rs_halo_props needs rs_fof6d and rs_unbind first");
+  const int64_t m = ctx->n_members, nn = ctx->n_nodes;
+  if (nn == 0) return RS_OK;
+  if (!props_out) return set_error(ctx, RS_ERR_INVALID_ARG, "props_out is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  RS_CUDA(ctx, cudaSetDevice(ctx->device));
+  Hier h = hier_of(ctx);
+  uint8_t* bound = static_cast<uint8_t*>(ctx->buf[S_U_BOUND].ptr);
+  unsigned long long* nb = static_cast<unsigned long long*>(ctx->buf[S_U_NB].ptr);
+  uint8_t* halo = static_cast<uint8_t*>(ctx->buf[S_U_FLAGS].ptr);
+  double* s1 = scratch_t<double>(ctx, S_NODE_TMP, size_t(nn) * 12);
+  double* s2 = scratch_t<double>(ctx, S_GVAL_B, size_t(nn) * 6);
+  double* mean = scratch_t<double>(ctx, S_GKEY_B, size_t(nn) * 3);
+  if (!s1 || !s2 || !mean) return RS_ERR_OOM;
+  RS_TRY((cro_segmented<12, PropTerm1>(ctx, nn, h.node_off, h.node_size, m, PropTerm1{h.U, h.V, bound},
+                                       s1, st)));
+  k_prop_means<<<grid_for(nn, kT), kT, 0, st>>>(nn, nb, s1, mean);
+  RS_LAUNCHED(ctx, "k_prop_means");
+  RS_TRY((cro_segmented<6, PropTerm2>(ctx, nn, h.node_off, h.node_size, m, PropTerm2{h.U, bound, mean},
+                                      s2, st)));
+  const double L = ctx->cfg.box_L;
+  const double rho_bar = double(ctx->n_particles) * ctx->cfg.particle_mass / (L * L * L);
+  k_prop_final<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, nb, halo, s1, s2, mean, h.ref,
+                                               ctx->cfg.box_L, ctx->cfg.particle_mass, rho_bar,
+                                               props_out);
+  RS_LAUNCHED(ctx, "k_prop_final");
+  return RS_OK;
+}

@@ -1,0 +1,51 @@
+"""rs_fof6d (CUDA) vs the oracle's 6D phase-space FoF hierarchy: node table, member lists and
+deepest-node map bit for bit (Section "Parallelization": subhalo finding per FoF halo from 6D
+phase-space information)."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import assert_hier_equal, gpu_pipeline, small_snapshot
+from paper_2412_18629_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,box,seed,n_max", [(1 << 13, 20.0, 21, 1500), (1 << 15, 32.0, 22, 4000),
+                                              (1 << 16, 40.0, 23, 12000)])
+def test_hierarchy_small(n, box, seed, n_max):
+    s = small_snapshot(n, box, seed, n_max=n_max)
+    g = gpu_pipeline(s, stages=("fof3d", "fof6d"))
+    lab = oracle.fof3d(s["pos"], s["ids"], s["box"], s["link_length"])
+    assert np.array_equal(g["labels"], lab)
+    o = oracle.hierarchy(s["pos"], s["vel"], s["ids"], lab, s["box"])
+    assert_hier_equal(g["hier"], o)
+    assert o["level"].max() >= 1
+
+
+def test_hierarchy_2e18_workload():
+    s = synth.generate(synth.WORKLOADS["nfw-2^18-L64"])
+    g = gpu_pipeline(s, stages=("fof3d", "fof6d"))
+    lab = oracle.fof3d(s["pos"], s["ids"], s["box"], s["link_length"])
+    assert np.array_equal(g["labels"], lab)
+    assert_hier_equal(g["hier"], oracle.hierarchy(s["pos"], s["vel"], s["ids"], lab, s["box"]))
+
+
+def test_no_groups_and_tiny_groups():
+    rng = np.random.default_rng(3)
+    n = 2000
+    snap = {"pos": rng.uniform(0, 100, (n, 3)).astype(np.float32),
+            "vel": rng.normal(0, 10, (n, 3)).astype(np.float32),
+            "ids": rng.permutation(n).astype(np.int64), "box": 100.0, "link_length": 0.05,
+            "softening": 0.01, "particle_mass": 1e10}
+    g = gpu_pipeline(snap, stages=("fof3d", "fof6d"))
+    assert g["n_nodes"] == 0 and g["n_members"] == 0 and np.all(g["hier"]["deepest"] == -1)
+
+
+def test_velocity_scaling_invariance_on_gpu():
+    s = small_snapshot(1 << 14, 25.0, 24)
+    a = gpu_pipeline(s, stages=("fof3d", "fof6d"))
+    s2 = dict(s)
+    s2["vel"] = s["vel"] * np.float32(2.0)
+    b = gpu_pipeline(s2, stages=("fof3d", "fof6d"))
+    assert_hier_equal(a["hier"], b["hier"])

@@ -1,0 +1,72 @@
+"""rs_unbind / rs_halo_props (CUDA) vs the oracle: bound flags, bound counts and halo decisions
+bit for bit; float32 potential within 1e-5 relative of the float64 definition; properties
+(float64 canonical-order sums) bit for bit except r_vir (cube root, within 4 ulp)."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import gpu_ctx, gpu_pipeline, oracle_pipeline, small_snapshot, to_dev
+from paper_2412_18629_gb300 import G_NEWTON, synth
+
+pytestmark = pytest.mark.gpu
+
+POT_RTOL = 1e-5
+
+
+def _compare(g, o):
+    ub = o["unbind"]
+    assert np.array_equal(g["bound"], ub["bound"])
+    rel = np.abs(g["phi"].astype(np.float64) - ub["phi"]) / np.abs(ub["phi"])
+    assert rel.max() <= POT_RTOL, rel.max()
+    P, Q = g["props"], o["props"]
+    assert np.array_equal(P[:, 1], ub["n_bound"].astype(np.float64))
+    assert np.array_equal(P[:, 2], ub["is_halo"].astype(np.float64))
+    assert np.array_equal(P[:, 3], ub["m_bound"])
+    exact = [c for c in range(20) if c != 12]
+    assert np.array_equal(P[:, exact], Q[:, exact]), np.argwhere(P[:, exact] != Q[:, exact])[:5]
+    np.testing.assert_allclose(P[:, 12], Q[:, 12], rtol=4 * 2.0 ** -52, atol=0)
+
+
+@pytest.mark.parametrize("n,box,seed,n_max", [(1 << 13, 20.0, 31, 1500), (1 << 15, 32.0, 32, 5000)])
+def test_unbind_props_small(n, box, seed, n_max):
+    s = small_snapshot(n, box, seed, n_max=n_max)
+    g = gpu_pipeline(s)
+    o = oracle_pipeline(s)
+    _compare(g, o)
+
+
+def test_unbind_props_2e18_workload():
+    s = synth.generate(synth.WORKLOADS["nfw-2^18-L64"])
+    g = gpu_pipeline(s)
+    o = oracle_pipeline(s, labels=g["labels"])
+    assert np.array_equal(g["labels"], oracle.fof3d(s["pos"], s["ids"], s["box"], s["link_length"]))
+    _compare(g, o)
+
+
+def test_energy_shifted_members_take_the_exact_path():
+    """Velocities of some members are set so that KE = -phi (1 +- 1e-7) in their node's frame:
+    the float32 potential cannot decide them, so the exact float64 path must, and flags must
+    still match the definition."""
+    s = small_snapshot(1 << 13, 20.0, 33, n_max=1500)
+    o = oracle_pipeline(s, stages=("fof3d", "fof6d", "unbind"))
+    h, ub = o["hier"], o["unbind"]
+    q = int(np.argmax(h["size"]))                       # a level-0 node (FoF group)
+    lo, hi = h["member_off"][q], h["member_off"][q + 1]
+    mem = h["member_idx"][lo:hi]
+    rng = np.random.default_rng(0)
+    pick = rng.choice(len(mem), size=min(64, len(mem) // 8), replace=False)
+    phi = ub["phi"][lo:hi][pick]
+    sgn = np.where(rng.random(len(pick)) < 0.5, 1.0 - 1e-7, 1.0 + 1e-7)
+    speed = np.sqrt(-2.0 * phi * sgn)
+    d = rng.normal(size=(len(pick), 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    vel = s["vel"].copy()
+    for _ in range(8):                                   # settle the node's bulk velocity
+        vb = vel[mem].astype(np.float64).mean(0)
+        vel[mem[pick]] = (vb + d * speed[:, None]).astype(np.float32)
+    s2 = dict(s)
+    s2["vel"] = vel
+    g = gpu_pipeline(s2)
+    o2 = oracle_pipeline(s2, labels=g["labels"])
+    assert g["n_fallback"] >= len(pick) // 2
+    _compare(g, o2)
