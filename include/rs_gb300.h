@@ -134,6 +134,11 @@ int rs_fof6d_copy(rs_ctx* ctx, int64_t* node_parent, int32_t* node_level, int64_
                   int64_t* node_size, int64_t* member_offsets, int64_t* member_idx,
                   int64_t* particle_deepest_node, void* stream);
 
+/* Per-node parameters of the 6D split of the last rs_fof6d: float32 [n_nodes][4] device =
+ * (inv_sx2, inv_sv2, l2, 0): the inverse total position and velocity variances of the node and
+ * its adaptive squared link length. Errors: RS_ERR_STATE, RS_ERR_CUDA. */
+int rs_fof6d_node_params(rs_ctx* ctx, float* params_out, void* stream);
+
 /* Unbinding of every node of the last rs_fof6d hierarchy (pos, vel: the same arrays).
  * phi_i = -G m sum_{j != i} 1 / sqrt(|u_j - u_i|^2 + eps^2) over the node's members;
  * KE_i = 0.5 |v_i - v_bulk|^2 (float64, v_bulk = mean member velocity); bound iff
@@ -161,6 +166,13 @@ int rs_halo_props(rs_ctx* ctx, rs_halo_props_t* props_out, void* stream);
  * a: float64 [m] device; out: float64 [1] device. Exposed so the order can be checked alone.
  * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
 int rs_cro_sum(rs_ctx* ctx, int64_t m, const double* a, double* out, void* stream);
+
+/* Stable LSD radix sort of (key, value) pairs by key bits [0, nbits), in place: the sort that
+ * orders particles by cell key for the 3D FoF cell list and members by (group, id) for the 6D
+ * hierarchy. keys: uint64 [n] device; vals: uint32 [n] device (moved with their keys; equal
+ * keys keep their input order). Uses the context's scratch. Errors: RS_ERR_INVALID_ARG
+ * (n >= 2^32 - 1, nbits > 64), RS_ERR_OOM, RS_ERR_CUDA. */
+int rs_sort_pairs(rs_ctx* ctx, int64_t n, int nbits, uint64_t* keys, uint32_t* vals, void* stream);
 
 /* Per-kernel CUDA-event timing of the dominant kernels (k_fof_link, k_sort_*, k_nn6d,
  * k_link6d, k_select_l2, k_potential, k_fallback). rs_profile(ctx, 1) clears the totals and

@@ -67,14 +67,17 @@ def load_library():
         lib.rs_fof3d.argtypes = [P, i64, P, P, P, ctypes.POINTER(i64), P]
         lib.rs_fof6d.argtypes = [P, i64, P, P, P, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]
         lib.rs_fof6d_copy.argtypes = [P, P, P, P, P, P, P, P, P]
+        lib.rs_fof6d_node_params.argtypes = [P, P, P]
         lib.rs_unbind.argtypes = [P, P, P, P, P, ctypes.POINTER(i64), P]
         lib.rs_halo_props.argtypes = [P, P, P]
         lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
+        lib.rs_sort_pairs.argtypes = [P, i64, ctypes.c_int, P, P, P]
         lib.rs_profile.argtypes = [P, ctypes.c_int]
         lib.rs_profile_get.argtypes = [P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_fof3d", "rs_fof6d", "rs_fof6d_copy",
-                     "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile", "rs_profile_get"):
+                     "rs_fof6d_node_params", "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile",
+                     "rs_profile_get", "rs_sort_pairs"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -213,6 +216,14 @@ def rs_fof6d_copy(ctx, stream=None):
     return out
 
 
+def rs_fof6d_node_params(ctx, stream=None):
+    """float32 [n_nodes, 4] CUDA tensor: (inv_sx2, inv_sv2, l2, 0) of each node's 6D split."""
+    torch = _torch()
+    out = torch.empty((ctx.n_nodes, 4), dtype=torch.float32, device=torch.device("cuda", ctx.device))
+    ctx.check(ctx.lib.rs_fof6d_node_params(ctx.handle, _ptr(out), _stream(stream)))
+    return out
+
+
 def rs_unbind(ctx, pos, vel, want_potential=True, bound_out=None, stream=None):
     """Per (node, member): float32 potential (or None), uint8 bound flag; and the number of
     members whose flag needed the exact float64 potential."""
@@ -246,6 +257,16 @@ def props_to_float64(raw):
     out = raw.view(torch.float64).reshape(-1, PROPS_FIELDS).clone()
     out[:, :3] = as_i[:, :3].to(torch.float64)
     return out
+
+
+def rs_sort_pairs(ctx, keys, vals, nbits=64, stream=None):
+    """Stable in-place sort of (uint64 key as int64 tensor, uint32 value as int32 tensor)."""
+    torch = _torch()
+    _check_dev(keys, torch.int64, None, "keys")
+    _check_dev(vals, torch.int32, None, "vals")
+    ctx.check(ctx.lib.rs_sort_pairs(ctx.handle, keys.numel(), int(nbits), _ptr(keys), _ptr(vals),
+                                    _stream(stream)))
+    return keys, vals
 
 
 def rs_cro_sum(ctx, a, stream=None):

@@ -118,3 +118,25 @@ extern "C" int rs_cro_sum(rs_ctx* ctx, int64_t m, const double* a, double* out, 
   RS_LAUNCHED(ctx, "k_seg_init");
   return cro_segmented<1, ArrayTerm>(ctx, 1, seg, seg + 1, m, ArrayTerm{a}, out, st);
 }
+
+extern "C" int rs_sort_pairs(rs_ctx* ctx, int64_t n, int nbits, uint64_t* keys, uint32_t* vals,
+                             void* stream) {
+  if (!ctx) return RS_ERR_INVALID_ARG;
+  ctx->err[0] = 0;
+  if (n < 0 || nbits < 0 || nbits > 64 || (n > 0 && (!keys || !vals)))
+    return set_error(ctx, RS_ERR_INVALID_ARG, "bad arguments");
+  if (n <= 1 || nbits == 0) return RS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  RS_CUDA(ctx, cudaSetDevice(ctx->device));
+  uint64_t* kb = scratch_t<uint64_t>(ctx, S_KEY_B, size_t(n));
+  uint32_t* vb = scratch_t<uint32_t>(ctx, S_VAL_B, size_t(n));
+  if (!kb || !vb) return RS_ERR_OOM;
+  uint64_t* ko;
+  uint32_t* vo;
+  RS_TRY(radix_sort_u64(ctx, n, nbits, keys, vals, kb, vb, &ko, &vo, st));
+  if (ko != keys) {
+    RS_CUDA(ctx, cudaMemcpyAsync(keys, ko, 8 * size_t(n), cudaMemcpyDeviceToDevice, st));
+    RS_CUDA(ctx, cudaMemcpyAsync(vals, vo, 4 * size_t(n), cudaMemcpyDeviceToDevice, st));
+  }
+  return RS_OK;
+}

@@ -95,13 +95,22 @@ __global__ void k_level0_nodes(int64_t nruns, const int64_t* __restrict__ run_st
   node_minid[q] = ids[vals[run_start[r]]];
 }
 
-__global__ void k_level0_members(int64_t n, const int64_t* __restrict__ run_idx,
+// run_heads holds the exclusive scan of the head flags: a run start sees its own run index,
+// any later element of run r sees r + 1.
+__device__ __forceinline__ int64_t run_of(const uint64_t* keys, int b, const int64_t* run_heads,
+                                          int64_t i) {
+  const bool head = (i == 0 || (keys[i] >> b) != (keys[i - 1] >> b));
+  return run_heads[i] - (head ? 0 : 1);
+}
+
+__global__ void k_level0_members(int64_t n, const uint64_t* __restrict__ keys, int b,
+                                 const int64_t* __restrict__ run_heads,
                                  const int64_t* __restrict__ run_start, const int64_t* __restrict__ keep,
                                  const int64_t* __restrict__ mem_off, const uint32_t* __restrict__ vals,
                                  uint32_t* __restrict__ mem) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int64_t r = run_idx[i];
+  const int64_t r = run_of(keys, b, run_heads, i);
   if (!keep[r]) return;
   mem[mem_off[r] + (i - run_start[r])] = vals[i];
 }
@@ -578,7 +587,8 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
                                                        mem_off, vals, ids, h.node_off, h.node_size,
                                                        h.node_parent, h.node_level, h.node_minid);
       RS_LAUNCHED(ctx, "k_level0_nodes");
-      k_level0_members<<<grid_for(n, kT), kT, 0, st>>>(n, head, run_start, keep, mem_off, vals, h.mem);
+      k_level0_members<<<grid_for(n, kT), kT, 0, st>>>(n, keys, b, head, run_start, keep, mem_off,
+                                                       vals, h.mem);
       RS_LAUNCHED(ctx, "k_level0_members");
     }
     k_fill_i64<<<1, 1, 0, st>>>(1, h.node_off + nodes, members);
@@ -726,5 +736,17 @@ extern "C" int rs_fof6d_copy(rs_ctx* ctx, int64_t* node_parent, int32_t* node_le
     k_u32_to_i64<<<grid_for(nm, kT), kT, 0, st>>>(nm, h.mem, member_idx);
     RS_LAUNCHED(ctx, "k_u32_to_i64");
   }
+  return RS_OK;
+}
+
+extern "C" int rs_fof6d_node_params(rs_ctx* ctx, float* params_out, void* stream) {
+  if (!ctx) return RS_ERR_INVALID_ARG;
+  ctx->err[0] = 0;
+  if (!ctx->have_hier) return set_error(ctx, RS_ERR_STATE, "rs_fof6d has not run on this context");
+  if (!params_out && ctx->n_nodes) return set_error(ctx, RS_ERR_INVALID_ARG, "params_out is NULL");
+  RS_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (ctx->n_nodes)
+    RS_CUDA(ctx, cudaMemcpyAsync(params_out, hier_of(ctx).inv, 16 * ctx->n_nodes,
+                                 cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
   return RS_OK;
 }

@@ -92,8 +92,8 @@ constexpr int kTile = kSortThreads * kKeysPerThread;  // 2048
 constexpr int kMaxSortBlocks = 1216;                   // 8 x 152 SMs
 
 __global__ void __launch_bounds__(kSortThreads)
-k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int64_t tiles_per_block,
-            uint32_t* __restrict__ hist) {
+k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t dmask,
+            int64_t tiles_per_block, uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[kSortWarps][kRadix];
   const int warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < kSortWarps * kRadix; t += blockDim.x) (&h[0][0])[t] = 0;
@@ -101,7 +101,7 @@ k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int64_t til
   const int64_t begin = int64_t(blockIdx.x) * tiles_per_block * kTile;
   const int64_t end = min(n, begin + tiles_per_block * kTile);
   for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x)
-    atomicAdd(&h[warp][(keys[i] >> shift) & (kRadix - 1)], 1u);
+    atomicAdd(&h[warp][(keys[i] >> shift) & dmask], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
     uint32_t s = 0;
@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(1024) k_scan_u32_single(uint32_t* data, int64_
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_scatter(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n,
-               int shift, int64_t tiles_per_block, const uint32_t* __restrict__ offsets) {
+               int shift, uint32_t dmask, int64_t tiles_per_block,
+               const uint32_t* __restrict__ offsets) {
   __shared__ uint64_t skey[kTile];
   __shared__ uint32_t sval[kTile];
   __shared__ uint32_t wcount[kSortWarps][kRadix];
@@ -178,7 +179,7 @@ k_sort_scatter(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict_
       const bool valid = e < cnt;
       key[k] = valid ? keys_in[tbase + e] : 0ull;
       val[k] = valid ? vals_in[tbase + e] : 0u;
-      dig[k] = valid ? uint32_t((key[k] >> shift) & (kRadix - 1)) : uint32_t(kRadix);
+      dig[k] = valid ? uint32_t((key[k] >> shift) & dmask) : uint32_t(kRadix);
     }
 #pragma unroll
     for (int k = 0; k < kKeysPerThread; ++k) {
@@ -238,7 +239,7 @@ k_sort_scatter(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict_
       const int pos = k * kSortThreads + threadIdx.x;
       if (pos < cnt) {
         const uint64_t kk = skey[pos];
-        const uint32_t d = uint32_t((kk >> shift) & (kRadix - 1));
+        const uint32_t d = uint32_t((kk >> shift) & dmask);
         const uint32_t dest = run[d] + (uint32_t(pos) - tile_start[d]);
         keys_out[dest] = kk;
         vals_out[dest] = sval[pos];
@@ -270,17 +271,19 @@ int radix_sort_u64(rs_ctx* ctx, int64_t n, int nbits, uint64_t* keys_a, uint32_t
   uint64_t* kout = keys_b;
   uint32_t* vout = vals_b;
   for (int shift = 0; shift < nbits; shift += kRadixBits) {
+    const int dbits = std::min(kRadixBits, nbits - shift);
+    const uint32_t dmask = (1u << dbits) - 1u;
     {
       ProfScope prof_(ctx, "k_sort_hist", st);
-      k_sort_hist<<<unsigned(blocks), kSortThreads, 0, st>>>(kin, n, shift, tpb, hist);
+      k_sort_hist<<<unsigned(blocks), kSortThreads, 0, st>>>(kin, n, shift, dmask, tpb, hist);
     }
     RS_LAUNCHED(ctx, "k_sort_hist");
     k_scan_u32_single<<<1, 1024, 0, st>>>(hist, int64_t(kRadix) * blocks);
     RS_LAUNCHED(ctx, "k_scan_u32_single");
     {
       ProfScope prof_(ctx, "k_sort_scatter", st);
-      k_sort_scatter<<<unsigned(blocks), kSortThreads, 0, st>>>(kin, vin, kout, vout, n, shift, tpb,
-                                                               hist);
+      k_sort_scatter<<<unsigned(blocks), kSortThreads, 0, st>>>(kin, vin, kout, vout, n, shift, dmask,
+                                                               tpb, hist);
     }
     RS_LAUNCHED(ctx, "k_sort_scatter");
     std::swap(kin, kout);
