@@ -167,6 +167,19 @@ int rs_halo_props(rs_ctx* ctx, rs_halo_props_t* props_out, void* stream);
  * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
 int rs_cro_sum(rs_ctx* ctx, int64_t m, const double* a, double* out, void* stream);
 
+/* rs_cro_sum without any device allocation, for callers that cannot allocate: code running
+ * while a stream is being captured into a CUDA graph, allocator or memory-pool callbacks, or
+ * hosts that forbid the library from using the device heap. The paper has no counterpart; this
+ * is a library convenience. Same result as rs_cro_sum, bit for bit, with no context.
+ * Scratch: a file-scope device array of 65536 float64 chunk totals (512 KiB, held on every GPU
+ * that loads the library until the process exits), so m is limited to 2^26 terms.
+ * The first call on a device (with that device current) looks up the array's device address;
+ * make that first call before any stream capture. Calls share the array and keep the last
+ * call's contents: calls whose kernels overlap on the GPU race and must be serialised.
+ * a: float64 [m] device; out: float64 [1] device; stream: cudaStream_t as void*.
+ * Errors: RS_ERR_INVALID_ARG (m < 0, null pointer), RS_ERR_CAPACITY (m > 2^26), RS_ERR_CUDA. */
+int rs_cro_sum_noalloc(int64_t m, const double* a, double* out, void* stream);
+
 /* Stable LSD radix sort of (key, value) pairs by key bits [0, nbits), in place: the sort that
  * orders particles by cell key for the 3D FoF cell list and members by (group, id) for the 6D
  * hierarchy. keys: uint64 [n] device; vals: uint32 [n] device (moved with their keys; equal

@@ -72,12 +72,13 @@ def load_library():
         lib.rs_halo_props.argtypes = [P, P, P]
         lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
         lib.rs_sort_pairs.argtypes = [P, i64, ctypes.c_int, P, P, P]
+        lib.rs_cro_sum_noalloc.argtypes = [i64, P, P, P]
         lib.rs_profile.argtypes = [P, ctypes.c_int]
         lib.rs_profile_get.argtypes = [P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_fof3d", "rs_fof6d", "rs_fof6d_copy",
                      "rs_fof6d_node_params", "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile",
-                     "rs_profile_get", "rs_sort_pairs"):
+                     "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -275,4 +276,17 @@ def rs_cro_sum(ctx, a, stream=None):
     _check_dev(a, torch.float64, None, "a")
     out = torch.empty(1, dtype=torch.float64, device=a.device)
     ctx.check(ctx.lib.rs_cro_sum(ctx.handle, a.numel(), _ptr(a), _ptr(out), _stream(stream)))
+    return out
+
+
+def rs_cro_sum_noalloc(a, out=None, stream=None):
+    """rs_cro_sum without a context or any device allocation by the library (for callers that
+    cannot allocate); limited to 2^26 terms. Returns the 1-element output tensor."""
+    torch = _torch()
+    _check_dev(a, torch.float64, None, "a")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=a.device)
+    rc = load_library().rs_cro_sum_noalloc(a.numel(), _ptr(a), _ptr(out), _stream(stream))
+    if rc != RS_OK:
+        raise RSError(rc, "rs_cro_sum_noalloc failed")
     return out
