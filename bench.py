@@ -34,7 +34,7 @@ DEFAULT_WORKLOAD = "nfw-2^24-L256-sub"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # fraction of the box side of the cubic sub-volume the CPU oracle is timed on
-ORACLE_SUBBOX = 0.25
+ORACLE_SUBBOX = 0.5
 
 
 def _dist():

@@ -63,6 +63,7 @@ class SnapshotSpec:
 # The five workloads: sizes, boxes and halo ranges of the configurations this build is measured on.
 WORKLOADS = {
     "nfw-2^18-L64": SnapshotSpec(n=1 << 18, box=64.0, seed=0, n_max=3.0e4, sub_levels=0),
+    "nfw-2^21-L128-sub": SnapshotSpec(n=1 << 21, box=128.0, seed=5, n_max=3.0e4, sub_levels=1),
     "nfw-2^24-L256-sub": SnapshotSpec(n=1 << 24, box=256.0, seed=1, n_max=3.0e4, sub_levels=1),
     "nfw-2^25-L320-sub": SnapshotSpec(n=1 << 25, box=320.0, seed=2, n_max=5.0e5, sub_levels=1),
     "nfw-2^27-L512-sub3": SnapshotSpec(n=1 << 27, box=512.0, seed=3, n_max=2.0e6, sub_levels=3),
