@@ -172,6 +172,64 @@ def _hier_work(ctx):
 OPS_PER_PAIR = {"k_nn6d": 20.0, "k_link6d": 20.0, "k_potential": 7.0}
 
 
+def _measure(ctx, pos, vel, ids, n, args, ws, local):
+    """Warm up, then time exactly args.steps steps of the whole path on device-resident inputs."""
+    import torch
+    import paper_2412_18629_gb300 as rs
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lab, _ = rs.rs_fof3d(ctx, pos, ids)
+        rs.rs_fof6d(ctx, pos, vel, ids, lab)
+        _, bound, nfb = rs.rs_unbind(ctx, pos, vel, want_potential=False)
+        props = rs.rs_halo_props(ctx)
+        return nfb
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pairs, _ = _hier_work(ctx)
+    ctx.profile(True)
+    l0 = ctx.kernel_launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        _barrier(ws)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            nfb = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        _barrier(ws)
+    launches = ctx.kernel_launches - l0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    prof = ctx.profile_totals()
+    ctx.profile(False)
+    t_max, units = aggregate(elapsed, float(n) * args.steps, ws, f"cuda:{local}")
+    return {"value": units / t_max, "ms_per_step": t_max / args.steps * 1e3, "launches": launches,
+            "prof": prof, "pairs": pairs, "clocks": clk.summary(), "fallback": nfb}
+
+
+def _roofline(prof, pairs, steps):
+    """Roofline entry of the dominant instrumented kernel (largest summed CUDA-event time)."""
+    if not prof:
+        return None
+    name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2070e6
+    base = name.replace("_pruned", "").replace("_blocked", "")
+    if base in OPS_PER_PAIR and not name.endswith("_pruned"):
+        pr = pairs if base != "k_link6d" else pairs / 2.0
+        work = pr * OPS_PER_PAIR[base] * steps
+        achieved = work / (ms / 1e3)
+        return {"bound": "alu", "kernel": name, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None, "launches": cnt,
+                "kernel_ms_per_step": ms / steps,
+                "peak_note": "FP32-pipe lane operations at 2070 MHz (152 SMs x 128 lanes)"}
+    return {"bound": "alu", "kernel": name, "achieved": None, "peak": peak_ops / 1e12,
+            "unit": "Tops/s", "frac": None, "traffic": None, "launches": cnt,
+            "kernel_ms_per_step": ms / steps}
+
+
 def run_ours(args):
     import torch
     import paper_2412_18629_gb300 as rs
@@ -181,46 +239,20 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     spec, snap = _snapshot(args.workload, rank)
-    ctx = rs.Context(box=snap["box"], link_len=snap["link_length"], softening=snap["softening"],
-                     particle_mass=snap["particle_mass"], device=local)
     pos = torch.from_numpy(snap["pos"]).cuda()
     vel = torch.from_numpy(snap["vel"]).cuda()
     ids = torch.from_numpy(snap["ids"]).cuda()
     n = len(snap["ids"])
-    stream = torch.cuda.current_stream()
-
-    def step():
-        lab, _ = rs.rs_fof3d(ctx, pos, ids)
-        rs.rs_fof6d(ctx, pos, vel, ids, lab)
-        _, bound, nfb = rs.rs_unbind(ctx, pos, vel, want_potential=False)
-        props = rs.rs_halo_props(ctx)
-        return lab, bound, props, nfb
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    pairs, members = _hier_work(ctx)
-    # ---- device-resident timed region
-    ctx.profile(True)
-    l0 = ctx.kernel_launches
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        _barrier(ws)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            _, _, _, nfb = step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        _barrier(ws)
-    launches = ctx.kernel_launches - l0
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    prof = ctx.profile_totals()
-    ctx.profile(False)
-    clocks = clk.summary()
-    t_max, units = aggregate(elapsed, float(n) * args.steps, ws, f"cuda:{local}")
-    value = units / t_max
-    # ---- end to end through the public API with host buffers
+    forms = ("plain", "batched") if args.form == "both" else (args.form,)
+    res, ctxs = {}, {}
+    for form in forms:
+        ctxs[form] = rs.Context(box=snap["box"], link_len=snap["link_length"],
+                                softening=snap["softening"], particle_mass=snap["particle_mass"],
+                                device=local, mode=form)
+        res[form] = _measure(ctxs[form], pos, vel, ids, n, args, ws, local)
+    head = "batched" if "batched" in res else forms[0]
+    ctx, r = ctxs[head], res[head]
+    # ---- end to end through the public API with host buffers (headline form)
     pin = {k: torch.from_numpy(snap[k]).pin_memory() for k in ("pos", "vel", "ids")}
     h2d = sum(t.numel() * t.element_size() for t in pin.values())
     e_pos, e_vel, e_ids = (torch.empty_like(pos), torch.empty_like(vel), torch.empty_like(ids))
@@ -249,23 +281,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     e_el = time.perf_counter() - e0
     e_max, e_units = aggregate(e_el, float(n) * args.steps, ws, f"cuda:{local}")
-    # ---- roofline of the dominant instrumented kernel
-    dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else None
-    roof = None
-    if dom:
-        name, (ms, cnt) = dom
-        peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2070e6
-        if name in OPS_PER_PAIR:
-            pr = pairs if name != "k_link6d" else pairs / 2.0
-            work = pr * OPS_PER_PAIR[name] * args.steps
-            achieved = work / (ms / 1e3)
-            roof = {"bound": "alu", "kernel": name, "achieved": achieved / 1e12,
-                    "peak": peak_ops / 1e12, "unit": "Tops/s", "frac": achieved / peak_ops,
-                    "traffic": None, "launches": cnt, "kernel_ms_per_step": ms / args.steps,
-                    "peak_note": "FP32-pipe lane operations at 2070 MHz (152 SMs x 128 lanes)"}
-        else:
-            roof = {"bound": "hbm", "kernel": name, "achieved": None, "peak": None,
-                    "unit": "GB/s", "frac": None, "traffic": None}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -275,23 +290,28 @@ def run_ours(args):
                          f"snapshot ({ns} particles, {dt:.1f} s): FoF, hierarchy, unbinding, props"}
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "box": snap["box"], "seed": spec.seed,
-                       "form": "plain", "nodes": int(ctx.n_nodes), "members": int(ctx.n_members),
-                       "pairs": pairs, "l2": "inputs and hierarchy larger than L2 (no flush)",
+                       "form": head, "nodes": int(ctx.n_nodes), "members": int(ctx.n_members),
+                       "pairs": r["pairs"], "l2": "inputs and hierarchy larger than L2 (no flush)",
                        "parallelism": f"independent snapshots x{ws}"},
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": _roofline(r["prof"], r["pairs"], args.steps), "cpu_baseline": cpu,
             "e2e": {"value": e_units / e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clocks,
-            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-            "fallback_members": nfb,
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "forms": {f: {"value": v["value"], "ms_per_step": v["ms_per_step"],
+                          "gpu_launches": v["launches"], "fallback_members": v["fallback"],
+                          "kernels_ms_per_step": {k: t[0] / args.steps for k, t in v["prof"].items()},
+                          "roofline": _roofline(v["prof"], v["pairs"], args.steps),
+                          "clocks": v["clocks"]}
+                      for f, v in res.items()},
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
+    for c in ctxs.values():
+        c.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -332,6 +352,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", choices=("plain", "batched", "both"), default="both")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -57,7 +57,10 @@ typedef struct rs_config {
   int32_t f_num, f_den;       /* linked fraction f = f_num / f_den of the 6D FoF (7, 10) */
   int32_t min_halo_particles; /* minimum node size and minimum bound count (10) */
   int32_t bound_num, bound_den; /* halo iff bound_den * N_bound >= bound_num * n (1, 2) */
-  int32_t reserved1[3];
+  int32_t batched;            /* 0 = plain form (brute-force pair kernels); 1 = batched form
+                                 (exactly pruned 6D searches, blocked potential); identical
+                                 outputs */
+  int32_t reserved1[2];
 } rs_config;
 
 /* Per-node halo properties written by rs_halo_props (all over the node's BOUND members). */

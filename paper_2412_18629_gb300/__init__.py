@@ -43,7 +43,8 @@ class rs_config(ctypes.Structure):
         ("reserved0", ctypes.c_float), ("particle_mass", ctypes.c_double),
         ("G", ctypes.c_double), ("f_num", ctypes.c_int32), ("f_den", ctypes.c_int32),
         ("min_halo_particles", ctypes.c_int32), ("bound_num", ctypes.c_int32),
-        ("bound_den", ctypes.c_int32), ("reserved1", ctypes.c_int32 * 3),
+        ("bound_den", ctypes.c_int32), ("batched", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32 * 2),
     ]
 
 
@@ -115,7 +116,7 @@ class Context:
     """An rs_ctx: configuration plus the library-owned scratch and hierarchy state."""
 
     def __init__(self, box, link_len, softening, particle_mass, G=G_NEWTON, f=(7, 10),
-                 min_halo_particles=10, bound_frac=(1, 2), device=0):
+                 min_halo_particles=10, bound_frac=(1, 2), device=0, mode="plain"):
         self.lib = load_library()
         cfg = rs_config()
         cfg.box_L, cfg.link_len, cfg.softening = float(box), float(link_len), float(softening)
@@ -123,6 +124,10 @@ class Context:
         cfg.f_num, cfg.f_den = int(f[0]), int(f[1])
         cfg.min_halo_particles = int(min_halo_particles)
         cfg.bound_num, cfg.bound_den = int(bound_frac[0]), int(bound_frac[1])
+        if mode not in ("plain", "batched"):
+            raise ValueError("mode must be 'plain' or 'batched'")
+        cfg.batched = 1 if mode == "batched" else 0
+        self.mode = mode
         self.cfg = cfg
         self.device = int(device)
         h = ctypes.c_void_p()

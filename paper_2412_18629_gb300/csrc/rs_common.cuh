@@ -31,7 +31,9 @@ enum Slot : int {
   S_H_MEM, S_H_MNODE, S_H_U, S_H_V, S_H_NODE_OFF, S_H_NODE_SIZE, S_H_NODE_PARENT,
   S_H_NODE_LEVEL, S_H_NODE_MINID, S_H_NODE_REF, S_H_NODE_INV, S_H_DEEPEST, S_H_WORK,
   // rs_unbind / rs_halo_props state
-  S_U_PHI, S_U_BOUND, S_U_NB, S_U_VBULK, S_U_AMBIG, S_U_FLAGS,
+  S_U_PHI, S_U_BOUND, S_U_NB, S_U_VBULK, S_U_AMBIG, S_U_FLAGS, S_U_TILEBIG,
+  // batched form: pruned 6D searches
+  S_P_MEANU, S_P_MEANV, S_P_US, S_P_VS, S_P_SP, S_P_BOFF, S_P_BUCKET, S_P_BOX,
   S_NUM_SLOTS
 };
 

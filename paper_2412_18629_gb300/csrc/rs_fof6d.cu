@@ -462,6 +462,14 @@ Hier hier_of(rs_ctx* ctx) {
   return h;
 }
 
+// Batched form: exactly pruned nearest-neighbour and link searches (rs_prune6d.cu).
+int prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m,
+                    const double* sums, cudaStream_t st);
+int prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, float* nn2,
+               cudaStream_t st);
+int prune6d_link(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, const float* nn2,
+                 uint32_t* uf, cudaStream_t st);
+
 // Gather U, V (and node reference positions) for member positions [mb, me) and nodes [nb, ne).
 int gather_members(rs_ctx* ctx, int64_t mb, int64_t me, int64_t nb, int64_t ne, const float* pos,
                    const float* vel, cudaStream_t st);
@@ -619,16 +627,23 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     int64_t* cidx = scratch_t<int64_t>(ctx, S_CHILD_IDX, size_t(m) + 1);
     int64_t* mpos = scratch_t<int64_t>(ctx, S_GKEY_A, size_t(m) + 1);
     if (!tile_off || !nn2 || !uf || !cnt || !cflag || !cidx || !mpos) return RS_ERR_OOM;
-    k_tile_counts<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, kTile6, tile_off);
-    RS_LAUNCHED(ctx, "k_tile_counts");
-    RS_TRY(exclusive_scan_i64(ctx, nn, tile_off, tile_off + nn, st));
+    const bool batched = ctx->cfg.batched != 0;
     const int64_t tiles_ub = nn + m / kTile6 + 1;
-    {
-      ProfScope prof_(ctx, "k_nn6d", st);
-      k_nn6d<<<grid_for(tiles_ub, 1), kTile6, 0, st>>>(nb, nn, tile_off, h.node_off, h.node_size, h.inv,
-                                                      h.U, h.V, nn2, mb);
+    if (batched) {
+      RS_TRY(prune6d_prepare(ctx, nb, nn, mb, m, sums, st));
+      RS_TRY(prune6d_nn(ctx, nb, nn, mb, m, nn2, st));
+      h = hier_of(ctx);
+    } else {
+      k_tile_counts<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, kTile6, tile_off);
+      RS_LAUNCHED(ctx, "k_tile_counts");
+      RS_TRY(exclusive_scan_i64(ctx, nn, tile_off, tile_off + nn, st));
+      {
+        ProfScope prof_(ctx, "k_nn6d", st);
+        k_nn6d<<<grid_for(tiles_ub, 1), kTile6, 0, st>>>(nb, nn, tile_off, h.node_off, h.node_size, h.inv,
+                                                        h.U, h.V, nn2, mb);
+      }
+      RS_LAUNCHED(ctx, "k_nn6d");
     }
-    RS_LAUNCHED(ctx, "k_nn6d");
     {
       ProfScope prof_(ctx, "k_select_l2", st);
       k_select_l2<<<unsigned(nn), kT, 0, st>>>(nb, h.node_off, h.node_size, nn2, mb, f_num, f_den, h.inv);
@@ -636,12 +651,16 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     RS_LAUNCHED(ctx, "k_select_l2");
     k_iota_u32<<<grid_for(m, kT), kT, 0, st>>>(m, uf);
     RS_LAUNCHED(ctx, "k_iota_u32");
-    {
-      ProfScope prof_(ctx, "k_link6d", st);
-      k_link6d<<<grid_for(tiles_ub, 1), kTile6, 0, st>>>(nb, nn, tile_off, h.node_off, h.node_size, h.inv,
-                                                        h.U, h.V, nn2, uf, mb);
+    if (batched) {
+      RS_TRY(prune6d_link(ctx, nb, nn, mb, m, nn2, uf, st));
+    } else {
+      {
+        ProfScope prof_(ctx, "k_link6d", st);
+        k_link6d<<<grid_for(tiles_ub, 1), kTile6, 0, st>>>(nb, nn, tile_off, h.node_off, h.node_size,
+                                                          h.inv, h.U, h.V, nn2, uf, mb);
+      }
+      RS_LAUNCHED(ctx, "k_link6d");
     }
-    RS_LAUNCHED(ctx, "k_link6d");
     RS_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * m, st));
     k_comp_count<<<grid_for(m, kT), kT, 0, st>>>(m, uf, cnt);
     RS_LAUNCHED(ctx, "k_comp_count");

@@ -83,6 +83,118 @@ k_potential(int64_t nn, const int64_t* __restrict__ tile_off, const int64_t* __r
   if (valid) S_out[base + i] = S;
 }
 
+// Register-blocked variant for nodes larger than kBlockedMin: each of the 128 threads of a
+// block owns 4 members (i = 512 t + tid + 128 k), so one 16-B shared load serves 4 pairs. The
+// per-member summation is unchanged (32-term sequential blocks, Kahan across blocks), so the
+// certified bound kCertB holds as is. The self pair is tested only on the diagonal j-tiles.
+constexpr int kBlkThreads = 128;
+constexpr int kBlkR = 4;
+constexpr int kBlkTile = kBlkThreads * kBlkR;  // 512 members per block
+constexpr int64_t kBlockedMin = 384;
+
+__global__ void k_tiles_split(int64_t nn, const int64_t* __restrict__ node_size,
+                              int64_t* __restrict__ small, int64_t* __restrict__ big) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= nn) return;
+  const int64_t g = node_size[k];
+  small[k] = g > kBlockedMin ? 0 : (g + kPotTile - 1) / kPotTile;
+  big[k] = g > kBlockedMin ? (g + kBlkTile - 1) / kBlkTile : 0;
+}
+
+__global__ void __launch_bounds__(kBlkThreads)
+k_potential_blocked(int64_t nn, const int64_t* __restrict__ tile_off,
+                    const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
+                    const float4* __restrict__ U, float eps2, float* __restrict__ S_out) {
+  __shared__ float4 su[kBlkThreads];
+  const int64_t b = blockIdx.x;
+  if (b >= tile_off[nn]) return;
+  const int64_t q = rsd::upper_bound_i64(tile_off, nn, b) - 1;
+  const int64_t t = b - tile_off[q];
+  const int64_t base = node_off[q], g = node_size[q];
+  float4 ui[kBlkR];
+  float S[kBlkR], C[kBlkR];
+#pragma unroll
+  for (int k = 0; k < kBlkR; ++k) {
+    const int64_t i = t * kBlkTile + threadIdx.x + kBlkThreads * k;
+    ui[k] = i < g ? U[base + i] : make_float4(0, 0, 0, 0);
+    S[k] = 0.f;
+    C[k] = 0.f;
+  }
+  for (int64_t j0 = 0; j0 < g; j0 += kBlkThreads) {
+    const int64_t j = j0 + threadIdx.x;
+    if (j < g) su[threadIdx.x] = U[base + j];
+    __syncthreads();
+    const int jn = int(rsd::min64(kBlkThreads, g - j0));
+    const int64_t jt = j0 / kBlkThreads - t * kBlkR;  // diagonal tile for member slot jt
+    if (jt >= 0 && jt < kBlkR) {
+      for (int jb = 0; jb < jn; jb += 32) {
+        const int je = min(jb + 32, jn);
+        float blk[kBlkR] = {0.f, 0.f, 0.f, 0.f};
+        for (int jj = jb; jj < je; ++jj) {
+          const float4 uj = su[jj];
+#pragma unroll
+          for (int k = 0; k < kBlkR; ++k) {
+            const float dx = __fsub_rn(uj.x, ui[k].x);
+            const float dy = __fsub_rn(uj.y, ui[k].y);
+            const float dz = __fsub_rn(uj.z, ui[k].z);
+            const float w = rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2))));
+            blk[k] = __fadd_rn(blk[k], (k == jt && jj == int(threadIdx.x)) ? 0.f : w);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kBlkR; ++k) {
+          const float y = __fsub_rn(blk[k], C[k]);
+          const float tt = __fadd_rn(S[k], y);
+          C[k] = __fsub_rn(__fsub_rn(tt, S[k]), y);
+          S[k] = tt;
+        }
+      }
+    } else {
+      for (int jb = 0; jb < jn; jb += 32) {
+        const int je = min(jb + 32, jn);
+        float blk[kBlkR] = {0.f, 0.f, 0.f, 0.f};
+        if (je - jb == 32) {
+#pragma unroll 8
+          for (int jj = jb; jj < jb + 32; ++jj) {
+            const float4 uj = su[jj];
+#pragma unroll
+            for (int k = 0; k < kBlkR; ++k) {
+              const float dx = __fsub_rn(uj.x, ui[k].x);
+              const float dy = __fsub_rn(uj.y, ui[k].y);
+              const float dz = __fsub_rn(uj.z, ui[k].z);
+              blk[k] = __fadd_rn(blk[k], rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2)))));
+            }
+          }
+        } else {
+          for (int jj = jb; jj < je; ++jj) {
+            const float4 uj = su[jj];
+#pragma unroll
+            for (int k = 0; k < kBlkR; ++k) {
+              const float dx = __fsub_rn(uj.x, ui[k].x);
+              const float dy = __fsub_rn(uj.y, ui[k].y);
+              const float dz = __fsub_rn(uj.z, ui[k].z);
+              blk[k] = __fadd_rn(blk[k], rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2)))));
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kBlkR; ++k) {
+          const float y = __fsub_rn(blk[k], C[k]);
+          const float tt = __fadd_rn(S[k], y);
+          C[k] = __fsub_rn(__fsub_rn(tt, S[k]), y);
+          S[k] = tt;
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < kBlkR; ++k) {
+    const int64_t i = t * kBlkTile + threadIdx.x + kBlkThreads * k;
+    if (i < g) S_out[base + i] = S[k];
+  }
+}
+
 struct VelTerm {
   const float4* V;
   __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
@@ -319,16 +431,26 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
     const float eps = ctx->cfg.softening;
     RS_TRY((cro_segmented<3, VelTerm>(ctx, nn, h.node_off, h.node_size, m, VelTerm{h.V}, vsum, st)));
-    k_tiles<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, kPotTile, tile_off);
-    RS_LAUNCHED(ctx, "k_tiles");
+    int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
+    if (!tile_big) return RS_ERR_OOM;
+    k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, tile_off, tile_big);
+    RS_LAUNCHED(ctx, "k_tiles_split");
     RS_TRY(exclusive_scan_i64(ctx, nn, tile_off, tile_off + nn, st));
+    RS_TRY(exclusive_scan_i64(ctx, nn, tile_big, tile_big + nn, st));
     const int64_t tiles_ub = nn + m / kPotTile + 1;
+    const int64_t big_ub = m / (kBlockedMin + 1) + m / kBlkTile + 1;
     {
       ProfScope prof_(ctx, "k_potential", st);
       k_potential<<<grid_for(tiles_ub, 1), kPotTile, 0, st>>>(nn, tile_off, h.node_off, h.node_size, h.U,
                                                              eps * eps, S);
     }
     RS_LAUNCHED(ctx, "k_potential");
+    {
+      ProfScope prof_(ctx, "k_potential_blocked", st);
+      k_potential_blocked<<<grid_for(big_ub, 1), kBlkThreads, 0, st>>>(nn, tile_big, h.node_off, h.node_size,
+                                                                      h.U, eps * eps, S);
+    }
+    RS_LAUNCHED(ctx, "k_potential_blocked");
     RS_CUDA(ctx, cudaMemsetAsync(n_ambig, 0, 8, st));
     k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vsum, S, Gm, kCertB, bound,
                                            potential_out, ambig, n_ambig);

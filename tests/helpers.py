@@ -18,11 +18,11 @@ def to_dev(snap):
             torch.from_numpy(snap["ids"]).cuda())
 
 
-def gpu_pipeline(snap, ctx=None, stages=("fof3d", "fof6d", "unbind", "props")):
+def gpu_pipeline(snap, ctx=None, stages=("fof3d", "fof6d", "unbind", "props"), mode="plain"):
     """Run the requested stages on cuda:0; return host numpy results."""
     import torch
     import paper_2412_18629_gb300 as rs
-    ctx = ctx or gpu_ctx(snap)
+    ctx = ctx or gpu_ctx(snap, mode=mode)
     pos, vel, ids = to_dev(snap)
     out = {}
     lab, ng = rs.rs_fof3d(ctx, pos, ids)

@@ -27,17 +27,19 @@ def _compare(g, o):
     np.testing.assert_allclose(P[:, 12], Q[:, 12], rtol=4 * 2.0 ** -52, atol=0)
 
 
+@pytest.mark.parametrize("mode", ("plain", "batched"))
 @pytest.mark.parametrize("n,box,seed,n_max", [(1 << 13, 20.0, 31, 1500), (1 << 15, 32.0, 32, 5000)])
-def test_unbind_props_small(n, box, seed, n_max):
+def test_unbind_props_small(n, box, seed, n_max, mode):
     s = small_snapshot(n, box, seed, n_max=n_max)
-    g = gpu_pipeline(s)
+    g = gpu_pipeline(s, mode=mode)
     o = oracle_pipeline(s)
     _compare(g, o)
 
 
-def test_unbind_props_2e18_workload():
+@pytest.mark.parametrize("mode", ("plain", "batched"))
+def test_unbind_props_2e18_workload(mode):
     s = synth.generate(synth.WORKLOADS["nfw-2^18-L64"])
-    g = gpu_pipeline(s)
+    g = gpu_pipeline(s, mode=mode)
     o = oracle_pipeline(s, labels=g["labels"])
     assert np.array_equal(g["labels"], oracle.fof3d(s["pos"], s["ids"], s["box"], s["link_length"]))
     _compare(g, o)
@@ -66,7 +68,7 @@ def test_energy_shifted_members_take_the_exact_path():
         vel[mem[pick]] = (vb + d * speed[:, None]).astype(np.float32)
     s2 = dict(s)
     s2["vel"] = vel
-    g = gpu_pipeline(s2)
+    g = gpu_pipeline(s2, mode="batched")
     o2 = oracle_pipeline(s2, labels=g["labels"])
     assert g["n_fallback"] >= len(pick) // 2
     _compare(g, o2)
