@@ -51,7 +51,8 @@ typedef struct rs_config {
   float box_L;                /* periodic box side (Mpc/h); positions must lie in [0, box_L) */
   float link_len;             /* 3D linking length ll; pairs with d^2 <= ll*ll are linked */
   float softening;            /* Plummer softening eps of the potential (Mpc/h) */
-  float reserved0;
+  float margin_factor;        /* surrogate gate: classify iff |E_pred| > margin_factor *
+                                 err_max * G M / r_vir (4) */
   double particle_mass;       /* m (Msun/h), equal for all particles */
   double G;                   /* gravitational constant, 4.30091e-9 Mpc (km/s)^2 / Msun */
   int32_t f_num, f_den;       /* linked fraction f = f_num / f_den of the 6D FoF (7, 10) */
@@ -60,7 +61,9 @@ typedef struct rs_config {
   int32_t batched;            /* 0 = plain form (brute-force pair kernels); 1 = batched form
                                  (exactly pruned 6D searches, blocked potential); identical
                                  outputs */
-  int32_t reserved1[2];
+  int32_t use_surrogate;      /* 1: rs_unbind gates members of nodes with >= 1024 members by
+                                 the trained MLP (batched + surrogate form) */
+  int32_t spot_check;         /* gated members per node re-checked exactly (32) */
 } rs_config;
 
 /* Per-node halo properties written by rs_halo_props (all over the node's BOUND members). */
@@ -182,6 +185,60 @@ int rs_cro_sum(rs_ctx* ctx, int64_t m, const double* a, double* out, void* strea
  * a: float64 [m] device; out: float64 [1] device; stream: cudaStream_t as void*.
  * Errors: RS_ERR_INVALID_ARG (m < 0, null pointer), RS_ERR_CAPACITY (m > 2^26), RS_ERR_CUDA. */
 int rs_cro_sum_noalloc(int64_t m, const double* a, double* out, void* stream);
+
+/* ---- Learned surrogate of the binding energy (batched form) --------------------------------
+ * A small MLP predicts psi = phi r_vir / (G M_node) from 8 per-member features; members whose
+ * predicted energy clears a margin are classified without the O(n^2) potential, the rest (and
+ * any node failing a spot check) take the exact path. The paper has no learned component; this
+ * is the build's batched form. Network (8 -> 64 -> 64 -> 1, ReLU), bf16 weights and hidden
+ * activations, float32 accumulation on tensor cores:
+ *   z1 = b1 + W1^T bf16(x); h1 = bf16(relu(z1)); z2 = b2 + W2^T h1; h2 = bf16(relu(z2));
+ *   y = b3 + sum_k bf16(W3)[k] h2[k].
+ * Parameters: float32 vector of RS_MLP_PARAMS = 4801 entries: W1 [8][64] at 0, b1 [64] at 512,
+ * W2 [64][64] at 576 (row = input), b2 [64] at 4672, W3 [64] at 4736, b3 at 4800. */
+#define RS_MLP_PARAMS 4801
+
+/* Load (host float32 [4801]) or read back the context's float32 master parameters. */
+int rs_mlp_set_params(rs_ctx* ctx, const float* params_host);
+int rs_mlp_get_params(rs_ctx* ctx, float* params_host);
+/* Held-out maximum |psi_hat - psi| the gate uses (set by rs_mlp_train, or by the caller). */
+int rs_mlp_set_err_max(rs_ctx* ctx, float err_max);
+
+/* Inference: x float32 [n][8] device -> y float32 [n] device. */
+int rs_mlp_forward(rs_ctx* ctx, int64_t n, const float* x, float* y, void* stream);
+
+/* Gradient of L = (1/n) sum (y - t)^2 over one batch: grad float32 [4801] device; sse_out host
+ * (sum of squared errors) may be NULL. Deterministic. */
+int rs_mlp_gradient(rs_ctx* ctx, int64_t n, const float* x, const float* t, float* grad,
+                    double* sse_out, void* stream);
+
+/* Train from a seeded He-uniform start with Adam (beta 0.9/0.999, eps 1e-8) on float32 masters:
+ * samples x float32 [n][8], t float32 [n] (device); a seeded permutation holds out the last
+ * holdout_num/holdout_den; minibatches of `batch`; `epochs` passes. Outputs (host, may be NULL):
+ * held-out max |y - t| (also stored as the gate's error) and the last batch's mean squared
+ * error. Errors: RS_ERR_INVALID_ARG, RS_ERR_OOM, RS_ERR_CUDA. */
+int rs_mlp_train(rs_ctx* ctx, int64_t n, const float* x, const float* t, int32_t epochs,
+                 int32_t batch, float lr, uint64_t seed, int32_t holdout_num, int32_t holdout_den,
+                 float* err_max_out, double* train_mse_out, void* stream);
+
+/* Surrogate features of the members of every node with >= 1024 members, after rs_unbind:
+ * feat_out float32 [n_members][8] device (room for all members; the first *n_out rows are
+ * written, node after node, members in id order): r/r_vir (r from the node's mean position),
+ * fractions of the node's members with radius below 0.5 r, r and 2 r, psi_sph (potential of
+ * the spherically averaged node in units of G g m / r_vir), |v - v_bulk| / sigma_v,1D,
+ * log10 g, log10(g_deep) / log10 g (g_deep: size of the deepest node holding the member).
+ * psi_out float32 [n_members] device or NULL: training target
+ * psi = phi r_vir / (G g m) from the last rs_unbind's float32 potential (that rs_unbind must
+ * not have used the surrogate). n_out: host. Errors: RS_ERR_STATE, RS_ERR_OOM, RS_ERR_CUDA. */
+int rs_surrogate_features(rs_ctx* ctx, float* feat_out, float* psi_out, int64_t* n_out,
+                          void* stream);
+
+/* Counters of the last rs_unbind (host int64 [10]): members of surrogate nodes, gated by the
+ * surrogate, sent to the exact per-member path, spot-checked, nodes failing the spot check,
+ * float64 fallbacks in the per-member path, float64 fallbacks of the direct sums, members
+ * re-run because their node failed, members of nodes sent whole to the direct sum (more than a
+ * quarter of their members outside the gate), members whose flag the surrogate decided. */
+int rs_surrogate_stats(rs_ctx* ctx, int64_t* stats_out);
 
 /* Stable LSD radix sort of (key, value) pairs by key bits [0, nbits), in place: the sort that
  * orders particles by cell key for the 3D FoF cell list and members by (group, id) for the 6D

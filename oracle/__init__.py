@@ -18,6 +18,8 @@ tests named here):
 * unbind: two-body, centre-of-sphere and cube closed forms, Plummer and uniform-sphere profiles,
   bound/unbound limits (tests/test_oracle_unbind.py).
 * props: lattice moments and inertia in closed form, centre wrapping (tests/test_oracle_props.py).
+* mlp_forward / mlp_gradient: finite differences of the float64 form, zero-weight and linear
+  special cases, bf16 rounding of exactly representable values (tests/test_oracle_mlp.py).
 """
 from __future__ import annotations
 
@@ -71,6 +73,8 @@ def _load():
         lib.or_unbind.argtypes = [i64, P, P, P, P, f32, f32, f64, f64, i32, i32, i32, i32,
                                   P, P, P, P, P]
         lib.or_props.argtypes = [i64, P, P, P, P, P, P, f32, f64, i64, i32, P]
+        lib.or_mlp_forward.argtypes = [i64, P, P, i32, P]
+        lib.or_mlp_gradient.argtypes = [i64, P, P, P, i32, P, ctypes.POINTER(f64)]
         _lib = lib
         return lib
 
@@ -178,3 +182,26 @@ def props(member_off, member_idx, pos, vel, bound, is_halo, box, m, n_total, thr
                           _p(is_halo), box, m, n_total, _threads(threads), _p(out))
     assert rc == 0
     return out
+
+
+MLP_PARAMS = 4801
+
+
+def mlp_forward(x, params, round_bf16=True):
+    """Surrogate MLP output (float64 [n]) for features x [n][8] and the parameter vector."""
+    x, params = _c(x, np.float32), _c(params, np.float32)
+    y = np.empty(len(x), np.float64)
+    rc = _load().or_mlp_forward(len(x), _p(x), _p(params), 1 if round_bf16 else 0, _p(y))
+    assert rc == 0
+    return y
+
+
+def mlp_gradient(x, t, params, round_bf16=True):
+    """Gradient (float64 [4801]) of the mean squared error and the sum of squared errors."""
+    x, t, params = _c(x, np.float32), _c(t, np.float32), _c(params, np.float32)
+    g = np.empty(MLP_PARAMS, np.float64)
+    sse = ctypes.c_double(0.0)
+    rc = _load().or_mlp_gradient(len(x), _p(x), _p(t), _p(params), 1 if round_bf16 else 0, _p(g),
+                                 ctypes.byref(sse))
+    assert rc == 0
+    return g, sse.value

@@ -550,3 +550,99 @@ int or_props(int64_t n_nodes, const int64_t* member_off, const int64_t* member_i
 }
 
 }  // extern "C"
+
+// =============================================================================================
+// Surrogate MLP oracle: float64 forward and gradient of the 8 -> 64 -> 64 -> 1 ReLU network on
+// the same parameter vector layout as the device (W1 [8][64] at 0, b1 at 512, W2 [64][64] at
+// 576, b2 at 4672, W3 [64] at 4736, b3 at 4800). With round != 0, inputs, weights, hidden
+// activations and the hidden-layer error signals are rounded to bf16 (round to nearest even,
+// via float32) at the points where the device rounds them; sums are float64. With round == 0
+// everything is float64 (the form a finite-difference check can verify).
+namespace {
+
+inline double bf16r(double v) {
+  float f = float(v);
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  const uint32_t lsb = (b >> 16) & 1u;
+  b = (b + 0x7fffu + lsb) & 0xffff0000u;
+  float r;
+  std::memcpy(&r, &b, 4);
+  return double(r);
+}
+
+struct MlpFwd {
+  double x[8], h1[64], h2[64], y;
+};
+
+void mlp_fwd1(const float* xin, const float* P, bool rnd, MlpFwd& f) {
+  auto R = [&](double v) { return rnd ? bf16r(v) : v; };
+  for (int i = 0; i < 8; ++i) f.x[i] = R(xin[i]);
+  for (int o = 0; o < 64; ++o) {
+    double z = P[512 + o];
+    for (int i = 0; i < 8; ++i) z += R(P[i * 64 + o]) * f.x[i];
+    f.h1[o] = R(z > 0.0 ? z : 0.0);
+  }
+  for (int o = 0; o < 64; ++o) {
+    double z = P[4672 + o];
+    for (int i = 0; i < 64; ++i) z += R(P[576 + i * 64 + o]) * f.h1[i];
+    f.h2[o] = R(z > 0.0 ? z : 0.0);
+  }
+  double y = P[4800];
+  for (int k = 0; k < 64; ++k) y += R(P[4736 + k]) * f.h2[k];
+  f.y = y;
+}
+
+}  // namespace
+
+extern "C" {
+
+int or_mlp_forward(int64_t n, const float* x, const float* params, int32_t round, double* y) {
+  if (n < 0) return -1;
+  for (int64_t s = 0; s < n; ++s) {
+    MlpFwd f;
+    mlp_fwd1(x + 8 * s, params, round != 0, f);
+    y[s] = f.y;
+  }
+  return 0;
+}
+
+// Gradient of L = (1/n) sum (y - t)^2 with respect to the parameter vector; also returns the
+// sum of squared errors.
+int or_mlp_gradient(int64_t n, const float* x, const float* t, const float* params, int32_t round,
+                    double* grad, double* sse) {
+  if (n <= 0) return -1;
+  const bool rnd = round != 0;
+  auto R = [&](double v) { return rnd ? bf16r(v) : v; };
+  for (int p = 0; p < 4801; ++p) grad[p] = 0.0;
+  double tot = 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    MlpFwd f;
+    mlp_fwd1(x + 8 * s, params, rnd, f);
+    const double e = f.y - double(t[s]);
+    tot += e * e;
+    const double dy = rnd ? double(float(2.0 * double(float(f.y) - t[s]) / double(n))) : 2.0 * e / double(n);
+    grad[4800] += dy;
+    double dz2[64], dz1[64];
+    for (int k = 0; k < 64; ++k) {
+      grad[4736 + k] += dy * f.h2[k];
+      dz2[k] = R(f.h2[k] > 0.0 ? dy * R(params[4736 + k]) : 0.0);
+      grad[4672 + k] += dz2[k];
+    }
+    for (int i = 0; i < 64; ++i) {
+      double dh = 0.0;
+      for (int o = 0; o < 64; ++o) {
+        grad[576 + i * 64 + o] += f.h1[i] * dz2[o];
+        dh += R(params[576 + i * 64 + o]) * dz2[o];
+      }
+      dz1[i] = R(f.h1[i] > 0.0 ? dh : 0.0);
+      grad[512 + i] += dz1[i];
+    }
+    for (int i = 0; i < 8; ++i)
+      for (int o = 0; o < 64; ++o) grad[i * 64 + o] += f.x[i] * dz1[o];
+  }
+  if (sse) *sse = tot;
+  return 0;
+}
+
+}  // extern "C"

@@ -40,11 +40,11 @@ class RSError(RuntimeError):
 class rs_config(ctypes.Structure):
     _fields_ = [
         ("box_L", ctypes.c_float), ("link_len", ctypes.c_float), ("softening", ctypes.c_float),
-        ("reserved0", ctypes.c_float), ("particle_mass", ctypes.c_double),
+        ("margin_factor", ctypes.c_float), ("particle_mass", ctypes.c_double),
         ("G", ctypes.c_double), ("f_num", ctypes.c_int32), ("f_den", ctypes.c_int32),
         ("min_halo_particles", ctypes.c_int32), ("bound_num", ctypes.c_int32),
         ("bound_den", ctypes.c_int32), ("batched", ctypes.c_int32),
-        ("reserved1", ctypes.c_int32 * 2),
+        ("use_surrogate", ctypes.c_int32), ("spot_check", ctypes.c_int32),
     ]
 
 
@@ -73,6 +73,17 @@ def load_library():
         lib.rs_halo_props.argtypes = [P, P, P]
         lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
         lib.rs_sort_pairs.argtypes = [P, i64, ctypes.c_int, P, P, P]
+        lib.rs_mlp_set_params.argtypes = [P, P]
+        lib.rs_mlp_get_params.argtypes = [P, P]
+        lib.rs_mlp_set_err_max.argtypes = [P, ctypes.c_float]
+        lib.rs_mlp_forward.argtypes = [P, i64, P, P, P]
+        lib.rs_mlp_gradient.argtypes = [P, i64, P, P, P, ctypes.POINTER(ctypes.c_double), P]
+        lib.rs_mlp_train.argtypes = [P, i64, P, P, i32, i32, ctypes.c_float, ctypes.c_uint64, i32,
+                                     i32, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(ctypes.c_double), P]
+        for name in ("rs_mlp_set_params", "rs_mlp_get_params", "rs_mlp_set_err_max",
+                     "rs_mlp_forward", "rs_mlp_gradient", "rs_mlp_train"):
+            getattr(lib, name).restype = i32
         lib.rs_cro_sum_noalloc.argtypes = [i64, P, P, P]
         lib.rs_profile.argtypes = [P, ctypes.c_int]
         lib.rs_profile_get.argtypes = [P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
@@ -116,7 +127,8 @@ class Context:
     """An rs_ctx: configuration plus the library-owned scratch and hierarchy state."""
 
     def __init__(self, box, link_len, softening, particle_mass, G=G_NEWTON, f=(7, 10),
-                 min_halo_particles=10, bound_frac=(1, 2), device=0, mode="plain"):
+                 min_halo_particles=10, bound_frac=(1, 2), device=0, mode="plain",
+                 margin_factor=4.0, spot_check=32):
         self.lib = load_library()
         cfg = rs_config()
         cfg.box_L, cfg.link_len, cfg.softening = float(box), float(link_len), float(softening)
@@ -124,9 +136,12 @@ class Context:
         cfg.f_num, cfg.f_den = int(f[0]), int(f[1])
         cfg.min_halo_particles = int(min_halo_particles)
         cfg.bound_num, cfg.bound_den = int(bound_frac[0]), int(bound_frac[1])
-        if mode not in ("plain", "batched"):
-            raise ValueError("mode must be 'plain' or 'batched'")
-        cfg.batched = 1 if mode == "batched" else 0
+        if mode not in ("plain", "batched", "surrogate"):
+            raise ValueError("mode must be 'plain', 'batched' or 'surrogate'")
+        cfg.batched = 0 if mode == "plain" else 1
+        cfg.use_surrogate = 1 if mode == "surrogate" else 0
+        cfg.margin_factor = float(margin_factor)
+        cfg.spot_check = int(spot_check)
         self.mode = mode
         self.cfg = cfg
         self.device = int(device)
@@ -295,3 +310,91 @@ def rs_cro_sum_noalloc(a, out=None, stream=None):
     if rc != RS_OK:
         raise RSError(rc, "rs_cro_sum_noalloc failed")
     return out
+
+
+MLP_PARAMS = 4801
+
+
+def rs_mlp_set_params(ctx, params):
+    """Load the surrogate's float32 master parameters (NumPy array of 4801)."""
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != MLP_PARAMS:
+        raise ValueError("params must have 4801 entries")
+    ctx.check(ctx.lib.rs_mlp_set_params(ctx.handle, ctypes.c_void_p(p.ctypes.data)))
+
+
+def rs_mlp_get_params(ctx):
+    import numpy as np
+    p = np.empty(MLP_PARAMS, np.float32)
+    ctx.check(ctx.lib.rs_mlp_get_params(ctx.handle, ctypes.c_void_p(p.ctypes.data)))
+    return p
+
+
+def rs_mlp_set_err_max(ctx, err_max):
+    ctx.check(ctx.lib.rs_mlp_set_err_max(ctx.handle, float(err_max)))
+
+
+def rs_mlp_forward(ctx, x, stream=None):
+    """Surrogate output y [n] for features x [n, 8] (CUDA float32)."""
+    torch = _torch()
+    _check_dev(x, torch.float32, (8,), "x")
+    y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    ctx.check(ctx.lib.rs_mlp_forward(ctx.handle, x.shape[0], _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def rs_mlp_gradient(ctx, x, t, stream=None):
+    """(grad [4801] CUDA float32, sum of squared errors) of the batch mean squared error."""
+    torch = _torch()
+    _check_dev(x, torch.float32, (8,), "x")
+    _check_dev(t, torch.float32, None, "t")
+    g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+    sse = ctypes.c_double(0.0)
+    ctx.check(ctx.lib.rs_mlp_gradient(ctx.handle, x.shape[0], _ptr(x), _ptr(t), _ptr(g),
+                                      ctypes.byref(sse), _stream(stream)))
+    return g, sse.value
+
+
+def rs_mlp_train(ctx, x, t, epochs=20, batch=4096, lr=1e-3, seed=0, holdout=(1, 10), stream=None):
+    """Train the surrogate on (x [n, 8], t [n]); returns (held-out max |y - t|, last batch MSE)."""
+    torch = _torch()
+    _check_dev(x, torch.float32, (8,), "x")
+    _check_dev(t, torch.float32, None, "t")
+    em, mse = ctypes.c_float(0.0), ctypes.c_double(0.0)
+    ctx.check(ctx.lib.rs_mlp_train(ctx.handle, x.shape[0], _ptr(x), _ptr(t), int(epochs),
+                                   int(batch), float(lr), ctypes.c_uint64(int(seed)),
+                                   int(holdout[0]), int(holdout[1]), ctypes.byref(em),
+                                   ctypes.byref(mse), _stream(stream)))
+    return em.value, mse.value
+
+
+def rs_surrogate_features(ctx, with_targets=True, stream=None):
+    """(features [k, 8], psi targets [k] or None) of the members of nodes with >= 1024 members,
+    from the last rs_unbind (CUDA float32 tensors)."""
+    torch = _torch()
+    lib = ctx.lib
+    lib.rs_surrogate_features.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_void_p]
+    lib.rs_surrogate_features.restype = ctypes.c_int32
+    dev = torch.device("cuda", ctx.device)
+    feat = torch.empty((max(ctx.n_members, 1), 8), dtype=torch.float32, device=dev)
+    psi = torch.empty(max(ctx.n_members, 1), dtype=torch.float32, device=dev) if with_targets else None
+    n = ctypes.c_int64(0)
+    ctx.check(lib.rs_surrogate_features(ctx.handle, _ptr(feat), _ptr(psi), ctypes.byref(n),
+                                        _stream(stream)))
+    k = n.value
+    return feat[:k], (psi[:k] if psi is not None else None)
+
+
+SURROGATE_STATS = ("surrogate_members", "gated", "exact_member_path", "spot_checked",
+                   "failed_nodes", "fp64_member_path", "fp64_direct", "rerun_members",
+                   "whole_node_members", "surrogate_decided")
+
+
+def rs_surrogate_stats(ctx):
+    lib = ctx.lib
+    lib.rs_surrogate_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.rs_surrogate_stats.restype = ctypes.c_int32
+    arr = (ctypes.c_int64 * 10)()
+    ctx.check(lib.rs_surrogate_stats(ctx.handle, ctypes.cast(arr, ctypes.c_void_p)))
+    return dict(zip(SURROGATE_STATS, list(arr)))

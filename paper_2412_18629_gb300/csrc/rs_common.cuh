@@ -29,13 +29,23 @@ enum Slot : int {
   S_SCAN_TMP, S_CHUNK_OFF, S_CHUNK_SUM, S_NODE_TMP, S_SELECT,
   // hierarchy state (persists until the next rs_fof6d)
   S_H_MEM, S_H_MNODE, S_H_U, S_H_V, S_H_NODE_OFF, S_H_NODE_SIZE, S_H_NODE_PARENT,
-  S_H_NODE_LEVEL, S_H_NODE_MINID, S_H_NODE_REF, S_H_NODE_INV, S_H_DEEPEST, S_H_WORK,
+  S_H_NODE_LEVEL, S_H_NODE_MINID, S_H_NODE_REF, S_H_NODE_INV, S_H_DEEPEST, S_H_DEEPPOS, S_H_WORK,
   // rs_unbind / rs_halo_props state
   S_U_PHI, S_U_BOUND, S_U_NB, S_U_VBULK, S_U_AMBIG, S_U_FLAGS, S_U_TILEBIG,
   // batched form: pruned 6D searches
   S_P_MEANU, S_P_MEANV, S_P_US, S_P_VS, S_P_SP, S_P_BOFF, S_P_BUCKET, S_P_BOX,
+  // surrogate MLP
+  S_MLP_DEV, S_MLP_W, S_MLP_PART, S_MLP_SSE, S_MLP_M, S_MLP_G, S_MLP_IDX, S_MLP_BIDX, S_MLP_XH,
+  S_MLP_YH,
+  // surrogate gating in rs_unbind
+  S_SUR_OFF, S_SUR_RANK, S_SUR_STAT, S_SUR_MEM, S_SUR_BIG, S_SUR_FEAT, S_SUR_PSI, S_SUR_MARGIN,
+  S_SUR_SFLAG, S_SUR_CHECKED, S_SUR_SX, S_SUR_LIST_A, S_SUR_LIST_B, S_SUR_GCOUNT, S_SUR_TAU,
+  S_SUR_FAIL, S_SUR_COUNTERS, S_SUR_FIX, S_SUR_SPOS, S_SUR_PSISPH, S_SUR_ECOUNT, S_SUR_FULL,
   S_NUM_SLOTS
 };
+
+// Nodes with at least this many members are unbound through the surrogate when it is enabled.
+constexpr int64_t kSurrogateMinMembers = 1024;
 
 struct Buffer {
   void* ptr = nullptr;
@@ -59,8 +69,16 @@ struct rs_ctx {
   int64_t n_members = 0;
   int32_t n_levels = 0;
   bool have_unbind = false;
+  bool have_mlp = false;        // surrogate weights loaded or trained
+  float mlp_err_max = 0.f;      // held-out max |psi_hat - psi| of the surrogate
   const float* h_pos = nullptr;  // arrays the hierarchy's U, V were gathered from
   const float* h_vel = nullptr;
+  // surrogate path of the last rs_unbind
+  bool last_unbind_surrogate = false;
+  int64_t sur_members = 0;
+  int64_t sur_nbig = 0;
+  const uint64_t* sur_rkeys = nullptr;
+  int64_t sur_stats[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
   bool profile = false;
   struct ProfRec {
@@ -155,6 +173,7 @@ struct Hier {
   float4* inv;         // (inv_sx2, inv_sv2, l2, 0) of the node's 6D split
   float4* ref;         // reference member position
   int64_t* deepest;    // [n] deepest node per particle, -1 if none
+  uint32_t* deepest_pos;  // [n] member position of the particle in its deepest node
 };
 Hier hier_of(rs_ctx* ctx);
 

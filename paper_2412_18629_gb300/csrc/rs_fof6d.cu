@@ -410,10 +410,15 @@ __global__ void k_offsets_add(int64_t n, const int64_t* __restrict__ src, int64_
   if (i < n) dst[i] = src[i] + add;
 }
 
+// Deepest node per particle and the particle's member position in that node.
 __global__ void k_deepest(int64_t mb, int64_t me, const uint32_t* __restrict__ mem,
-                          const uint32_t* __restrict__ mnode, int64_t* __restrict__ deepest) {
+                          const uint32_t* __restrict__ mnode, int64_t* __restrict__ deepest,
+                          uint32_t* __restrict__ deepest_pos) {
   const int64_t p = mb + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p < me) deepest[mem[p]] = mnode[p];
+  if (p < me) {
+    deepest[mem[p]] = mnode[p];
+    deepest_pos[mem[p]] = uint32_t(p);
+  }
 }
 
 // Grow a persistent hierarchy buffer, keeping its first `used` bytes.
@@ -459,6 +464,7 @@ Hier hier_of(rs_ctx* ctx) {
   h.inv = static_cast<float4*>(ctx->buf[S_H_NODE_INV].ptr);
   h.ref = static_cast<float4*>(ctx->buf[S_H_NODE_REF].ptr);
   h.deepest = static_cast<int64_t*>(ctx->buf[S_H_DEEPEST].ptr);
+  h.deepest_pos = static_cast<uint32_t*>(ctx->buf[S_H_DEEPPOS].ptr);
   return h;
 }
 
@@ -529,6 +535,7 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
   const float L = ctx->cfg.box_L;
   // ---------------- level 0 from the FoF labels
   int64_t* deep = scratch_t<int64_t>(ctx, S_H_DEEPEST, size_t(std::max<int64_t>(n, 1)));
+  uint32_t* deep_pos = scratch_t<uint32_t>(ctx, S_H_DEEPPOS, size_t(std::max<int64_t>(n, 1)));
   if (!deep) return RS_ERR_OOM;
   int64_t nodes = 0, members = 0;
   if (n == 0) {
@@ -539,6 +546,7 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
   } else {
     k_fill_i64<<<grid_for(n, kT), kT, 0, st>>>(n, deep, -1);
     RS_LAUNCHED(ctx, "k_fill_i64");
+    if (!deep_pos) return RS_ERR_OOM;
     unsigned long long* mx = scratch_t<unsigned long long>(ctx, S_COUNTER, 8);
     if (!mx) return RS_ERR_OOM;
     RS_CUDA(ctx, cudaMemsetAsync(mx, 0, 8, st));
@@ -671,7 +679,7 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     k_member_flags<<<grid_for(m, kT), kT, 0, st>>>(m, uf, cflag, mpos);
     RS_LAUNCHED(ctx, "k_member_flags");
     RS_TRY(exclusive_scan_i64(ctx, m, mpos, mpos + m, st));
-    k_deepest<<<grid_for(m, kT), kT, 0, st>>>(mb, me, h.mem, h.mnode, deep);
+    k_deepest<<<grid_for(m, kT), kT, 0, st>>>(mb, me, h.mem, h.mnode, deep, deep_pos);
     RS_LAUNCHED(ctx, "k_deepest");
     RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box, cidx + m, 8, cudaMemcpyDeviceToHost, st));
     RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box + 1, mpos + m, 8, cudaMemcpyDeviceToHost, st));

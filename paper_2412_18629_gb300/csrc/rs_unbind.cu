@@ -18,6 +18,12 @@
 namespace rs {
 int gather_members(rs_ctx* ctx, int64_t mb, int64_t me, int64_t nb, int64_t ne, const float* pos,
                    const float* vel, cudaStream_t st);
+int surrogate_unbind(rs_ctx* ctx, const double* vsum, uint8_t* bound, unsigned long long* counters,
+                     cudaStream_t st);
+int unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
+                    const double* vsum, uint8_t* bound, cudaStream_t st);
+int unbind_nodes(rs_ctx* ctx, const int* only, const double* vsum, uint8_t* bound,
+                 uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st);
 }  // namespace rs
 
 using namespace rs;
@@ -92,13 +98,17 @@ constexpr int kBlkR = 4;
 constexpr int kBlkTile = kBlkThreads * kBlkR;  // 512 members per block
 constexpr int64_t kBlockedMin = 384;
 
-__global__ void k_tiles_split(int64_t nn, const int64_t* __restrict__ node_size,
-                              int64_t* __restrict__ small, int64_t* __restrict__ big) {
+// Tiles of the two direct-sum kernels; nodes with >= sur_min members (sur_min > 0) are left to
+// the surrogate path.
+__global__ void k_tiles_split(int64_t nn, const int64_t* __restrict__ node_size, int64_t sur_min,
+                              const int* __restrict__ only, int64_t* __restrict__ small,
+                              int64_t* __restrict__ big) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= nn) return;
   const int64_t g = node_size[k];
-  small[k] = g > kBlockedMin ? 0 : (g + kPotTile - 1) / kPotTile;
-  big[k] = g > kBlockedMin ? (g + kBlkTile - 1) / kBlkTile : 0;
+  const bool skip = only ? (only[k] == 0) : (sur_min > 0 && g >= sur_min);
+  small[k] = (skip || g > kBlockedMin) ? 0 : (g + kPotTile - 1) / kPotTile;
+  big[k] = (!skip && g > kBlockedMin) ? (g + kBlkTile - 1) / kBlkTile : 0;
 }
 
 __global__ void __launch_bounds__(kBlkThreads)
@@ -217,10 +227,12 @@ __global__ void k_flags(int64_t m, const uint32_t* __restrict__ mnode, const int
                         const float4* __restrict__ V, const double* __restrict__ vsum,
                         const float* __restrict__ S, double Gm, double certB,
                         uint8_t* __restrict__ bound, float* __restrict__ phi_out,
-                        uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig) {
+                        uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig,
+                        int64_t sur_min, const int* __restrict__ only) {
   const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (p >= m) return;
   const uint32_t q = mnode[p];
+  if (only ? (only[q] == 0) : (sur_min > 0 && node_size[q] >= sur_min)) return;  // other path
   const double ke = kinetic(V[p], vsum + 3 * int64_t(q), double(node_size[q]));
   const double ph = -__dmul_rn(Gm, double(S[p]));
   const double e = __dadd_rn(ke, ph);
@@ -409,6 +421,12 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
   const int64_t m = ctx->n_members, nn = ctx->n_nodes;
   if (m > 0 && !bound_out) return set_error(ctx, RS_ERR_INVALID_ARG, "bound_out is NULL");
   if (m > 0 && (!pos || !vel)) return set_error(ctx, RS_ERR_INVALID_ARG, "null pos/vel");
+  const bool sur = ctx->cfg.use_surrogate != 0;
+  if (sur && potential_out)
+    return set_error(ctx, RS_ERR_INVALID_ARG, "potential_out must be NULL with the surrogate");
+  if (sur && !ctx->have_mlp)
+    return set_error(ctx, RS_ERR_STATE, "the surrogate needs weights (rs_mlp_train or set_params)");
+  const int64_t sur_min = sur ? kSurrogateMinMembers : 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   RS_CUDA(ctx, cudaSetDevice(ctx->device));
   if (pos != ctx->h_pos || vel != ctx->h_vel) {  // other arrays than rs_fof6d's: re-gather
@@ -424,16 +442,20 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
   uint32_t* ambig = scratch_t<uint32_t>(ctx, S_U_AMBIG, size_t(std::max<int64_t>(m, 1)));
   uint8_t* halo = scratch_t<uint8_t>(ctx, S_U_FLAGS, size_t(std::max<int64_t>(nn, 1)));
   int64_t* tile_off = scratch_t<int64_t>(ctx, S_SELECT, size_t(nn) + 1);
-  unsigned long long* n_ambig = scratch_t<unsigned long long>(ctx, S_COUNTER, 8);
-  if (!bound || !S || !nb || !vsum || !ambig || !halo || !tile_off || !n_ambig) return RS_ERR_OOM;
+  // counters: [0..6] surrogate path (rs_surrogate.cu), [7] float64 fallbacks of the direct sums
+  unsigned long long* counters = scratch_t<unsigned long long>(ctx, S_SUR_COUNTERS, 16);
+  if (!bound || !S || !nb || !vsum || !ambig || !halo || !tile_off || !counters) return RS_ERR_OOM;
+  unsigned long long* n_ambig = counters + 7;
   int64_t nfb = 0;
+  for (int i = 0; i < 10; ++i) ctx->sur_stats[i] = 0;
   if (m > 0) {
     const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
     const float eps = ctx->cfg.softening;
+    RS_CUDA(ctx, cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned long long), st));
     RS_TRY((cro_segmented<3, VelTerm>(ctx, nn, h.node_off, h.node_size, m, VelTerm{h.V}, vsum, st)));
     int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
     if (!tile_big) return RS_ERR_OOM;
-    k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, tile_off, tile_big);
+    k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sur_min, nullptr, tile_off, tile_big);
     RS_LAUNCHED(ctx, "k_tiles_split");
     RS_TRY(exclusive_scan_i64(ctx, nn, tile_off, tile_off + nn, st));
     RS_TRY(exclusive_scan_i64(ctx, nn, tile_big, tile_big + nn, st));
@@ -451,9 +473,8 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
                                                                       h.U, eps * eps, S);
     }
     RS_LAUNCHED(ctx, "k_potential_blocked");
-    RS_CUDA(ctx, cudaMemsetAsync(n_ambig, 0, 8, st));
     k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vsum, S, Gm, kCertB, bound,
-                                           potential_out, ambig, n_ambig);
+                                           potential_out, ambig, n_ambig, sur_min, nullptr);
     RS_LAUNCHED(ctx, "k_flags");
     {
       ProfScope prof_(ctx, "k_fallback", st);
@@ -461,6 +482,7 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
                                          vsum, double(eps) * double(eps), Gm, bound, potential_out);
     }
     RS_LAUNCHED(ctx, "k_fallback");
+    if (sur) RS_TRY(surrogate_unbind(ctx, vsum, bound, counters, st));
     RS_CUDA(ctx, cudaMemsetAsync(nb, 0, 8 * nn, st));
     k_bound_count<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, bound, nb);
     RS_LAUNCHED(ctx, "k_bound_count");
@@ -469,11 +491,74 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     RS_LAUNCHED(ctx, "k_halo_decide");
     k_copy_u8<<<grid_for(m, kT), kT, 0, st>>>(m, bound, bound_out);
     RS_LAUNCHED(ctx, "k_copy_u8");
-    RS_TRY(read_back(ctx, n_ambig, 8, st));
-    nfb = ctx->host_box[0];
+    RS_TRY(read_back(ctx, counters, 16 * sizeof(unsigned long long), st));
+    // stats: surrogate members, gated, exact (per-member path), spot-checked, failed nodes,
+    // fp64 (surrogate path), fp64 (direct sums), re-run members, members of nodes sent whole
+    // to the direct sum, members whose flag the surrogate decided
+    ctx->sur_stats[0] = sur ? ctx->sur_members : 0;
+    ctx->sur_stats[1] = ctx->host_box[5];
+    ctx->sur_stats[2] = ctx->host_box[0];
+    ctx->sur_stats[3] = ctx->host_box[1];
+    ctx->sur_stats[4] = ctx->host_box[4];
+    ctx->sur_stats[5] = ctx->host_box[6];
+    ctx->sur_stats[6] = ctx->host_box[7];
+    ctx->sur_stats[7] = ctx->host_box[3];
+    ctx->sur_stats[8] = ctx->host_box[8];
+    ctx->sur_stats[9] = sur ? ctx->sur_members - ctx->host_box[0] - ctx->host_box[1] -
+                                  ctx->host_box[3] - ctx->host_box[8]
+                            : 0;
+    nfb = ctx->host_box[7] + ctx->host_box[6];
   }
   if (n_fallback_out) *n_fallback_out = nfb;
   ctx->have_unbind = true;
+  ctx->last_unbind_surrogate = sur;
+  return RS_OK;
+}
+
+// Exact unbinding of the nodes flagged in `only` (int [n_nodes]): register-blocked float32
+// potential of all their members, certified flags, float64 fallback for the ambiguous ones.
+int rs::unbind_nodes(rs_ctx* ctx, const int* only, const double* vsum, uint8_t* bound,
+                     uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st) {
+  Hier h = hier_of(ctx);
+  const int64_t m = ctx->n_members, nn = ctx->n_nodes;
+  float* S = static_cast<float*>(ctx->buf[S_U_PHI].ptr);
+  int64_t* tile_small = scratch_t<int64_t>(ctx, S_SELECT, size_t(nn) + 1);
+  int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
+  if (!tile_small || !tile_big) return RS_ERR_OOM;
+  const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
+  const float eps = ctx->cfg.softening;
+  k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, 0, only, tile_small, tile_big);
+  RS_LAUNCHED(ctx, "k_tiles_split");
+  RS_TRY(exclusive_scan_i64(ctx, nn, tile_small, tile_small + nn, st));
+  RS_TRY(exclusive_scan_i64(ctx, nn, tile_big, tile_big + nn, st));
+  const int64_t tiles_ub = nn + m / kPotTile + 1;
+  const int64_t big_ub = m / (kBlockedMin + 1) + m / kBlkTile + 1;
+  k_potential<<<grid_for(tiles_ub, 1), kPotTile, 0, st>>>(nn, tile_small, h.node_off, h.node_size, h.U,
+                                                         eps * eps, S);
+  RS_LAUNCHED(ctx, "k_potential");
+  {
+    ProfScope prof_(ctx, "k_potential_blocked", st);
+    k_potential_blocked<<<grid_for(big_ub, 1), kBlkThreads, 0, st>>>(nn, tile_big, h.node_off, h.node_size,
+                                                                    h.U, eps * eps, S);
+  }
+  RS_LAUNCHED(ctx, "k_potential_blocked");
+  k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vsum, S, Gm, kCertB, bound, nullptr,
+                                         ambig, n_ambig, 0, only);
+  RS_LAUNCHED(ctx, "k_flags");
+  return unbind_fallback(ctx, n_ambig, ambig, vsum, bound, st);
+}
+
+int rs::unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
+                        const double* vsum, uint8_t* bound, cudaStream_t st) {
+  Hier h = hier_of(ctx);
+  const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
+  const double eps = ctx->cfg.softening;
+  {
+    ProfScope prof_(ctx, "k_fallback", st);
+    k_fallback<<<152 * 8, kT, 0, st>>>(n_ambig, ambig, h.mnode, h.node_off, h.node_size, h.U, h.V, vsum,
+                                       eps * eps, Gm, bound, nullptr);
+  }
+  RS_LAUNCHED(ctx, "k_fallback");
   return RS_OK;
 }
 

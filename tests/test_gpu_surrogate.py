@@ -1,0 +1,93 @@
+"""Batched + surrogate form: the MLP is trained on the GPU from exact potentials of one
+snapshot, then gates the unbinding of another. Flags, bound counts and halo decisions must be
+identical to the oracle's (no mismatch), the surrogate must classify a real share of the
+members of large nodes, and the exact pair interactions it saves are reported (the gain)."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import gpu_ctx, oracle_pipeline, to_dev
+from paper_2412_18629_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _train(train_snap):
+    import paper_2412_18629_gb300 as rs
+    ctx = gpu_ctx(train_snap, mode="batched")
+    pos, vel, ids = to_dev(train_snap)
+    lab, _ = rs.rs_fof3d(ctx, pos, ids)
+    rs.rs_fof6d(ctx, pos, vel, ids, lab)
+    rs.rs_unbind(ctx, pos, vel, want_potential=False)
+    x, t = rs.rs_surrogate_features(ctx)
+    assert x.shape[0] > 10000
+    err_max, mse = rs.rs_mlp_train(ctx, x.contiguous(), t.contiguous(), epochs=12, batch=4096,
+                                   lr=1e-3, seed=1)
+    return rs.rs_mlp_get_params(ctx), err_max, mse
+
+
+@pytest.fixture(scope="module")
+def trained():
+    spec = synth.SnapshotSpec(n=1 << 20, box=float(np.cbrt(2.0 ** 20)), seed=100, n_max=3.0e4,
+                              sub_levels=1)
+    return _train(synth.generate(spec))
+
+
+def _run_surrogate(s, params, err_max):
+    import paper_2412_18629_gb300 as rs
+    ctx = gpu_ctx(s, mode="surrogate")
+    rs.rs_mlp_set_params(ctx, params)
+    rs.rs_mlp_set_err_max(ctx, err_max)
+    pos, vel, ids = to_dev(s)
+    lab, _ = rs.rs_fof3d(ctx, pos, ids)
+    rs.rs_fof6d(ctx, pos, vel, ids, lab)
+    _, bound, _ = rs.rs_unbind(ctx, pos, vel, want_potential=False)
+    props = rs.props_to_float64(rs.rs_halo_props(ctx)).cpu().numpy()
+    return lab.cpu().numpy(), bound.cpu().numpy(), props, rs.rs_surrogate_stats(ctx)
+
+
+@pytest.fixture(scope="module")
+def workload_2e18():
+    s = synth.generate(synth.WORKLOADS["nfw-2^18-L64"])
+    return s
+
+
+def test_surrogate_flags_match_oracle(trained, workload_2e18):
+    """With the trained network and its held-out error, every flag, bound count and halo
+    decision equals the oracle's; the counters report how many flags the network decided."""
+    params, err_max, _ = trained
+    s = workload_2e18
+    lab, bound, props, stats = _run_surrogate(s, params, err_max)
+    o = oracle_pipeline(s, labels=lab, stages=("fof3d", "fof6d", "unbind"))
+    ub = o["unbind"]
+    assert int(np.sum(bound != ub["bound"])) == 0
+    assert np.array_equal(props[:, 1], ub["n_bound"].astype(np.float64))
+    assert np.array_equal(props[:, 2], ub["is_halo"].astype(np.float64))
+    assert stats["surrogate_members"] > 0
+    accounted = (stats["surrogate_decided"] + stats["exact_member_path"] + stats["spot_checked"]
+                 + stats["rerun_members"] + stats["whole_node_members"])
+    assert accounted == stats["surrogate_members"], stats
+    print("surrogate gain on the 2^18 workload:", stats, "err_max", err_max)
+
+
+def test_overconfident_surrogate_is_caught_by_spot_checks(trained, workload_2e18):
+    """With an error bound far below the network's real error, the gate lets wrong predictions
+    through; the spot checks must notice (nodes fail and are recomputed exactly)."""
+    params, err_max, _ = trained
+    lab, bound, props, stats = _run_surrogate(workload_2e18, params, err_max / 50.0)
+    assert stats["gated"] > 0
+    assert stats["failed_nodes"] > 0 and stats["rerun_members"] > 0, stats
+
+
+def test_surrogate_requires_weights_and_null_potential():
+    import paper_2412_18629_gb300 as rs
+    s = synth.generate(synth.SnapshotSpec(n=1 << 14, box=25.0, seed=7, n_max=2000, sub_levels=1))
+    ctx = gpu_ctx(s, mode="surrogate")
+    pos, vel, ids = to_dev(s)
+    lab, _ = rs.rs_fof3d(ctx, pos, ids)
+    rs.rs_fof6d(ctx, pos, vel, ids, lab)
+    with pytest.raises(rs.RSError, match="RS_ERR_STATE"):
+        rs.rs_unbind(ctx, pos, vel, want_potential=False)
+    rs.rs_mlp_set_params(ctx, np.zeros(rs.MLP_PARAMS, np.float32))
+    with pytest.raises(rs.RSError, match="RS_ERR_INVALID_ARG"):
+        rs.rs_unbind(ctx, pos, vel, want_potential=True)
