@@ -230,6 +230,40 @@ def _roofline(prof, pairs, steps):
             "kernel_ms_per_step": ms / steps}
 
 
+TRAIN_SAMPLES = 1_000_000
+
+
+def train_surrogate(ctx, workload, device, samples=None):
+    """Train the context's surrogate on the GPU, outside any timed region: exact potentials of
+    a snapshot drawn with the same generator and a disjoint seed (100), 10% held out."""
+    import dataclasses
+
+    import torch
+    import paper_2412_18629_gb300 as rs
+    from paper_2412_18629_gb300 import synth
+    spec = dataclasses.replace(synth.WORKLOADS[workload], seed=100)
+    s = synth.generate(spec)
+    tctx = rs.Context(box=s["box"], link_len=s["link_length"], softening=s["softening"],
+                      particle_mass=s["particle_mass"], device=device, mode="batched")
+    p, v, i = (torch.from_numpy(s[k]).cuda() for k in ("pos", "vel", "ids"))
+    lab, _ = rs.rs_fof3d(tctx, p, i)
+    rs.rs_fof6d(tctx, p, v, i, lab)
+    rs.rs_unbind(tctx, p, v, want_potential=False)
+    x, t = rs.rs_surrogate_features(tctx)
+    k = min(x.shape[0], samples or TRAIN_SAMPLES)
+    sel = torch.randperm(x.shape[0], generator=torch.Generator().manual_seed(100))[:k].cuda()
+    x, t = x[sel].contiguous(), t[sel].contiguous()
+    t0 = time.perf_counter()
+    rs.rs_mlp_set_params(tctx, np.zeros(rs.MLP_PARAMS, np.float32))
+    err_max, mse = rs.rs_mlp_train(tctx, x, t, epochs=12, batch=4096, lr=1e-3, seed=100)
+    dt = time.perf_counter() - t0
+    rs.rs_mlp_set_params(ctx, rs.rs_mlp_get_params(tctx))
+    rs.rs_mlp_set_err_max(ctx, err_max)
+    tctx.close()
+    return {"samples": int(k), "err_max_psi": err_max, "last_batch_mse": mse, "train_s": dt,
+            "snapshot": f"{workload} generator, seed 100"}
+
+
 def run_ours(args):
     import torch
     import paper_2412_18629_gb300 as rs
@@ -243,14 +277,19 @@ def run_ours(args):
     vel = torch.from_numpy(snap["vel"]).cuda()
     ids = torch.from_numpy(snap["ids"]).cuda()
     n = len(snap["ids"])
-    forms = ("plain", "batched") if args.form == "both" else (args.form,)
-    res, ctxs = {}, {}
+    forms = ("plain", "batched", "surrogate") if args.form == "all" else (args.form,)
+    res, ctxs, training = {}, {}, None
     for form in forms:
         ctxs[form] = rs.Context(box=snap["box"], link_len=snap["link_length"],
                                 softening=snap["softening"], particle_mass=snap["particle_mass"],
                                 device=local, mode=form)
+        if form == "surrogate":
+            training = train_surrogate(ctxs[form], args.workload, local, args.train_samples)
         res[form] = _measure(ctxs[form], pos, vel, ids, n, args, ws, local)
-    head = "batched" if "batched" in res else forms[0]
+        if form == "surrogate":
+            res[form]["surrogate_stats"] = rs.rs_surrogate_stats(ctxs[form])
+    # headline: the fastest form (all forms give identical outputs)
+    head = max(res, key=lambda f: res[f]["value"])
     ctx, r = ctxs[head], res[head]
     # ---- end to end through the public API with host buffers (headline form)
     pin = {k: torch.from_numpy(snap[k]).pin_memory() for k in ("pos", "vel", "ids")}
@@ -301,12 +340,13 @@ def run_ours(args):
             "roofline": _roofline(r["prof"], r["pairs"], args.steps), "cpu_baseline": cpu,
             "e2e": {"value": e_units / e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "gpu_launches": r["launches"], "clocks": r["clocks"], "surrogate_training": training,
             "forms": {f: {"value": v["value"], "ms_per_step": v["ms_per_step"],
                           "gpu_launches": v["launches"], "fallback_members": v["fallback"],
                           "kernels_ms_per_step": {k: t[0] / args.steps for k, t in v["prof"].items()},
                           "roofline": _roofline(v["prof"], v["pairs"], args.steps),
-                          "clocks": v["clocks"]}
+                          "clocks": v["clocks"],
+                          "surrogate_stats": v.get("surrogate_stats")}
                       for f, v in res.items()},
         }
         print(json.dumps(line), flush=True)
@@ -352,7 +392,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", choices=("plain", "batched", "both"), default="both")
+    ap.add_argument("--form", choices=("plain", "batched", "surrogate", "all"), default="all")
+    ap.add_argument("--train-samples", type=int, default=1_000_000)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -33,7 +33,8 @@ enum Slot : int {
   // rs_unbind / rs_halo_props state
   S_U_PHI, S_U_BOUND, S_U_NB, S_U_VBULK, S_U_AMBIG, S_U_FLAGS, S_U_TILEBIG,
   // batched form: pruned 6D searches
-  S_P_MEANU, S_P_MEANV, S_P_US, S_P_VS, S_P_SP, S_P_BOFF, S_P_BUCKET, S_P_BOX,
+  S_P_MEANU, S_P_MEANV, S_P_US, S_P_VS, S_P_SP, S_P_BOFF, S_P_BUCKET, S_P_BOX, S_P_SUB,
+  S_P_SBOFF, S_P_SBOX, S_P_ORDER, S_P_QCTR,
   // surrogate MLP
   S_MLP_DEV, S_MLP_W, S_MLP_PART, S_MLP_SSE, S_MLP_M, S_MLP_G, S_MLP_IDX, S_MLP_BIDX, S_MLP_XH,
   S_MLP_YH,

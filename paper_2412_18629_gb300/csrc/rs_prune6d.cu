@@ -1,12 +1,13 @@
 // Pruned 6D nearest-neighbour and link searches for the batched form of rs_fof6d.
 //
 // The plain form evaluates d6 for every pair of a node. Here the members of every node of a
-// level are ordered by a 3D Morton key of their scaled position offsets, cut into buckets of 32
-// consecutive members, and each bucket gets its 6D bounding box. A warp takes one query bucket
-// (lane = member) and visits the node's buckets outward from its own in key order:
-//   nearest neighbour: a bucket is skipped for a lane when the box lower bound exceeds the
-//     lane's current best; otherwise all its members are evaluated;
-//   link: a bucket pair is skipped when the box-to-box lower bound exceeds l2.
+// level are ordered by a 3D Morton key of their scaled position offsets (every candidate of a
+// 6D search lies within sqrt(bound / inv_sx2) in position) and cut into buckets of 32
+// consecutive members; each bucket has a 6D bounding box, four 8-member sub-boxes, and every
+// 32 consecutive buckets of a node form a superbucket with its own box. Persistent warps pull
+// query buckets from a queue ordered by node size (largest first) and, lane = member, visit
+// the node's superbuckets, buckets and sub-buckets, skipping any whose lower bound exceeds the
+// lane's current best (nearest neighbour) or l2 (link, upper triangle of bucket pairs).
 // Lower bounds are computed with the same round-to-nearest float32 operations as d6 on the
 // per-axis gaps to the box: every step is monotone, so the bound never exceeds the computed
 // d6 of any member inside the box, and pruning cannot change the minimum or the set of links.
@@ -30,12 +31,14 @@ constexpr int kT = 256;
 constexpr int kWarpsPerBlock = 8;
 
 struct Bucket {
-  uint32_t start;  // level-local sorted position of the first member
-  uint32_t count;  // 1..32
-  uint32_t node;   // global node index
-  uint32_t first;  // index of the node's first bucket
-  uint32_t last;   // index of the node's last bucket
-  uint32_t pad[3];
+  uint32_t start;    // level-local sorted position of the first member
+  uint32_t count;    // 1..32
+  uint32_t node;     // global node index
+  uint32_t first;    // index of the node's first bucket
+  uint32_t last;     // index of the node's last bucket
+  uint32_t sbfirst;  // index of the node's first superbucket
+  uint32_t sbcount;  // superbuckets of the node
+  uint32_t pad;
 };
 
 struct Box {
@@ -60,13 +63,11 @@ __device__ __forceinline__ uint32_t quant10(float c) {
 }
 
 // 3D Morton key of each member's position offset from the node mean (scaled by the node's
-// sigma_x), prefixed by the node index. Position-only ordering gives spatially tight buckets:
-// every candidate of a 6D search lies within sqrt(bound / inv_sx2) in position.
-__global__ void k_morton6(int64_t mb, int64_t m, int64_t nb, int nodebits,
-                          const uint32_t* __restrict__ mnode, const float4* __restrict__ U,
-                          const float4* __restrict__ V, const float4* __restrict__ inv,
-                          const float4* __restrict__ mean_u, const float4* __restrict__ mean_v,
-                          uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// sigma_x), prefixed by the node index.
+__global__ void k_morton3(int64_t mb, int64_t m, int64_t nb, const uint32_t* __restrict__ mnode,
+                          const float4* __restrict__ U, const float4* __restrict__ inv,
+                          const float4* __restrict__ mean_u, uint64_t* __restrict__ keys,
+                          uint32_t* __restrict__ vals) {
   const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (p >= m) return;
   const uint32_t q = mnode[mb + p];
@@ -77,21 +78,16 @@ __global__ void k_morton6(int64_t mb, int64_t m, int64_t nb, int nodebits,
                         (spread10(quant10((u.z - mu.z) * sx)) << 2);
   keys[p] = (uint64_t(q - nb) << 30) | uint64_t(code);
   vals[p] = uint32_t(p);
-  (void)nodebits;
-  (void)V;
-  (void)mean_v;
 }
 
-// Node means (float) from the CRO moment sums, for the Morton quantisation only.
+// Node mean positions (float) from the canonical-order moment sums, for the quantisation only.
 __global__ void k_node_means(int64_t nb, int64_t nn, const int64_t* __restrict__ node_size,
-                             const double* __restrict__ sums, float4* __restrict__ mean_u,
-                             float4* __restrict__ mean_v) {
+                             const double* __restrict__ sums, float4* __restrict__ mean_u) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= nn) return;
   const double g = double(node_size[nb + k]);
   const double* S = sums + 12 * k;
   mean_u[nb + k] = make_float4(float(S[0] / g), float(S[1] / g), float(S[2] / g), 0.f);
-  mean_v[nb + k] = make_float4(float(S[6] / g), float(S[7] / g), float(S[8] / g), 0.f);
 }
 
 __global__ void k_gather_sorted(int64_t mb, int64_t m, const uint32_t* __restrict__ order,
@@ -107,20 +103,55 @@ __global__ void k_gather_sorted(int64_t mb, int64_t m, const uint32_t* __restric
 }
 
 __global__ void k_bucket_counts(int64_t nb, int64_t nn, const int64_t* __restrict__ node_size,
-                                int64_t* __restrict__ out) {
+                                int64_t* __restrict__ bcnt, int64_t* __restrict__ sbcnt) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k < nn) out[k] = (node_size[nb + k] + 31) / 32;
+  if (k >= nn) return;
+  const int64_t c = (node_size[nb + k] + 31) / 32;
+  bcnt[k] = c;
+  sbcnt[k] = (c + 31) / 32;
 }
 
-// One warp per bucket: its table entry and its 6D bounding box.
+__device__ __forceinline__ void warp_box(const float (&a)[6], bool valid, int lo_off, int hi_off,
+                                         float (&lo)[6], float (&hi)[6]) {
+  const float inf = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    if (lo_off == 1) {
+      lo[d] = valid ? a[d] : inf;
+      hi[d] = valid ? a[d] : -inf;
+    }
+#pragma unroll
+    for (int off = lo_off; off <= hi_off; off <<= 1) {
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+    }
+  }
+}
+
+__device__ __forceinline__ Box make_box(const float (&lo)[6], const float (&hi)[6]) {
+  return Box{make_float4(lo[0], lo[1], lo[2], 0.f), make_float4(hi[0], hi[1], hi[2], 0.f),
+             make_float4(lo[3], lo[4], lo[5], 0.f), make_float4(hi[3], hi[4], hi[5], 0.f)};
+}
+
+// One warp per bucket (padding warps write a queue key that sorts last): bucket table entry,
+// box, four 8-member sub-boxes (an empty sub-bucket gets lo = +inf, hi = -inf, so every gap to
+// it is +inf), and the work-queue key (largest node first).
 __global__ void __launch_bounds__(kT)
-k_buckets(int64_t nb, int64_t nn, int64_t mb, const int64_t* __restrict__ bucket_off,
-          const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
-          const float4* __restrict__ Us, const float4* __restrict__ Vs, Bucket* __restrict__ bk,
-          Box* __restrict__ box) {
+k_buckets(int64_t nb, int64_t nn, int64_t mb, int64_t nbk_ub, const int64_t* __restrict__ bucket_off,
+          const int64_t* __restrict__ sb_off, const int64_t* __restrict__ node_off,
+          const int64_t* __restrict__ node_size, const float4* __restrict__ Us,
+          const float4* __restrict__ Vs, Bucket* __restrict__ bk, Box* __restrict__ box,
+          Box* __restrict__ sub, uint64_t* __restrict__ qkey, uint32_t* __restrict__ qval) {
   const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= bucket_off[nn]) return;
+  if (w >= nbk_ub) return;
+  if (w >= bucket_off[nn]) {
+    if (lane == 0) {
+      qkey[w] = 0xffffffffull;
+      qval[w] = uint32_t(w);
+    }
+    return;
+  }
   const int64_t k = rsd::upper_bound_i64(bucket_off, nn, w) - 1;
   const int64_t q = nb + k;
   const int64_t kb = w - bucket_off[k];
@@ -128,18 +159,11 @@ k_buckets(int64_t nb, int64_t nn, int64_t mb, const int64_t* __restrict__ bucket
   const int cnt = int(rsd::min64(32, node_size[q] - 32 * kb));
   const bool valid = lane < cnt;
   const float4 u = Us[start + (valid ? lane : 0)], v = Vs[start + (valid ? lane : 0)];
-  float a[6] = {u.x, u.y, u.z, v.x, v.y, v.z};
+  const float a[6] = {u.x, u.y, u.z, v.x, v.y, v.z};
   float lo[6], hi[6];
-#pragma unroll
-  for (int d = 0; d < 6; ++d) {
-    lo[d] = a[d];
-    hi[d] = a[d];
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
-      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
-    }
-  }
+  warp_box(a, valid, 1, 4, lo, hi);
+  if ((lane & 7) == 0) sub[4 * w + (lane >> 3)] = make_box(lo, hi);
+  warp_box(a, valid, 8, 16, lo, hi);
   if (lane == 0) {
     Bucket b;
     b.start = uint32_t(start);
@@ -147,11 +171,42 @@ k_buckets(int64_t nb, int64_t nn, int64_t mb, const int64_t* __restrict__ bucket
     b.node = uint32_t(q);
     b.first = uint32_t(bucket_off[k]);
     b.last = uint32_t(bucket_off[k + 1] - 1);
-    b.pad[0] = b.pad[1] = b.pad[2] = 0;
+    b.sbfirst = uint32_t(sb_off[k]);
+    b.sbcount = uint32_t(sb_off[k + 1] - sb_off[k]);
+    b.pad = 0;
     bk[w] = b;
-    box[w] = Box{make_float4(lo[0], lo[1], lo[2], 0.f), make_float4(hi[0], hi[1], hi[2], 0.f),
-                 make_float4(lo[3], lo[4], lo[5], 0.f), make_float4(hi[3], hi[4], hi[5], 0.f)};
+    box[w] = make_box(lo, hi);
+    qkey[w] = 0xfffffffeull - uint64_t(node_size[q]);
+    qval[w] = uint32_t(w);
   }
+}
+
+// One warp per superbucket: the box of its (up to 32) bucket boxes.
+__global__ void __launch_bounds__(kT)
+k_superboxes(int64_t nn, const int64_t* __restrict__ bucket_off, const int64_t* __restrict__ sb_off,
+             const Box* __restrict__ box, Box* __restrict__ sbox) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= sb_off[nn]) return;
+  const int64_t k = rsd::upper_bound_i64(sb_off, nn, w) - 1;
+  const int64_t b0 = bucket_off[k] + 32 * (w - sb_off[k]);
+  const int64_t b1 = rsd::min64(b0 + 32, bucket_off[k + 1]);
+  const bool valid = b0 + lane < b1;
+  const Box B = box[valid ? b0 + lane : b0];
+  const float inf = __int_as_float(0x7f800000);
+  float lo[6] = {B.ulo.x, B.ulo.y, B.ulo.z, B.vlo.x, B.vlo.y, B.vlo.z};
+  float hi[6] = {B.uhi.x, B.uhi.y, B.uhi.z, B.vhi.x, B.vhi.y, B.vhi.z};
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    lo[d] = valid ? lo[d] : inf;
+    hi[d] = valid ? hi[d] : -inf;
+#pragma unroll
+    for (int off = 1; off <= 16; off <<= 1) {
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+    }
+  }
+  if (lane == 0) sbox[w] = make_box(lo, hi);
 }
 
 // Gap from x to [lo, hi] rounded like the d6 differences (monotone: never above |fl(y - x)| for
@@ -184,100 +239,171 @@ __device__ __forceinline__ float d6(float4 ui, float4 vi, float4 uj, float4 vj, 
   return __fadd_rn(__fmul_rn(rx, isx), __fmul_rn(rv, isv));
 }
 
-// Bucket visited at step t of the outward walk from bucket a within [first, last]:
-// a, a+1, a-1, a+2, a-2, ... (indices outside the range are skipped by the caller).
+// Index visited at step t of the outward walk from a: a, a+1, a-1, a+2, a-2, ...
 __device__ __forceinline__ int64_t outward(int64_t a, int64_t t) {
   const int64_t h = (t + 1) >> 1;
   return (t & 1) ? a + h : a - h;
 }
 
-__global__ void __launch_bounds__(kT)
-k_nn6d_pruned(const int64_t* __restrict__ nbuckets_dev, const Bucket* __restrict__ bk,
-              const Box* __restrict__ box, const float4* __restrict__ Us,
-              const float4* __restrict__ Vs, const uint32_t* __restrict__ sp,
-              const float4* __restrict__ inv, float* __restrict__ nn2) {
-  __shared__ float4 su[kWarpsPerBlock][32], sv[kWarpsPerBlock][32];
-  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-  const int64_t nbk = *nbuckets_dev;
-  const int64_t stride = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t a = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; a < nbk; a += stride) {
-    const Bucket A = bk[a];
-    const float4 iv = inv[A.node];
-    const float isx = iv.x, isv = iv.y;
-    const bool valid = lane < int(A.count);
-    const uint32_t si = A.start + (valid ? lane : 0);
-    const float4 ui = Us[si], vi = Vs[si];
-    float best = __int_as_float(0x7f800000);
-    const int64_t span = int64_t(A.last) - int64_t(A.first);
-    for (int64_t t = 0; t <= 2 * span; ++t) {
-      const int64_t b = outward(a, t);
-      if (b < int64_t(A.first) || b > int64_t(A.last)) continue;
-      const Box B = box[b];
-      const bool need = valid && lb_point_box(ui, vi, B, isx, isv) <= best;
-      if (!__any_sync(0xffffffffu, need)) continue;
-      const Bucket Bb = bk[b];
-      __syncwarp();
-      if (lane < int(Bb.count)) {
-        su[wb][lane] = Us[Bb.start + lane];
-        sv[wb][lane] = Vs[Bb.start + lane];
-      }
-      __syncwarp();
-      if (need) {
-        const uint32_t self = (b == a) ? uint32_t(lane) : 0xffffffffu;
-        for (uint32_t j = 0; j < Bb.count; ++j) {
-          if (j == self) continue;
-          best = fminf(best, d6(ui, vi, su[wb][j], sv[wb][j], isx, isv));
-        }
+// Next query bucket from the size-ordered queue (one atomic per warp).
+__device__ __forceinline__ int64_t next_work(unsigned long long* counter, int lane) {
+  unsigned long long w = 0;
+  if (lane == 0) w = atomicAdd(counter, 1ull);
+  return int64_t(__shfl_sync(0xffffffffu, w, 0));
+}
+
+struct NNArgs {
+  const int64_t* nbuckets;
+  const Bucket* bk;
+  const Box* box;
+  const Box* sub;
+  const Box* sbox;
+  const uint32_t* order;
+  const float4* Us;
+  const float4* Vs;
+  const uint32_t* sp;
+  const float4* inv;
+  unsigned long long* counter;
+};
+
+// Evaluate target bucket b for the warp's query lanes (nearest-neighbour search).
+__device__ __forceinline__ void nn_bucket(const NNArgs& A, int64_t a, int64_t b, bool valid, float4 ui,
+                                          float4 vi, float isx, float isv, float& best, int lane,
+                                          float4 (&su)[32], float4 (&sv)[32]) {
+  const Box B = A.box[b];
+  const bool need = valid && lb_point_box(ui, vi, B, isx, isv) <= best;
+  if (!__any_sync(0xffffffffu, need)) return;
+  const Bucket Bb = A.bk[b];
+  __syncwarp();
+  if (lane < int(Bb.count)) {
+    su[lane] = A.Us[Bb.start + lane];
+    sv[lane] = A.Vs[Bb.start + lane];
+  }
+  __syncwarp();
+  const uint32_t self = (b == a) ? uint32_t(lane) : 0xffffffffu;
+  for (uint32_t s0 = 0; s0 < Bb.count; s0 += 8) {
+    const Box Sb = A.sub[4 * b + (s0 >> 3)];
+    const bool sneed = need && lb_point_box(ui, vi, Sb, isx, isv) <= best;
+    if (!__any_sync(0xffffffffu, sneed)) continue;
+    if (sneed) {
+      const uint32_t s1 = min(s0 + 8, Bb.count);
+      for (uint32_t j = s0; j < s1; ++j) {
+        if (j == self) continue;
+        best = fminf(best, d6(ui, vi, su[j], sv[j], isx, isv));
       }
     }
-    if (valid) nn2[sp[si]] = best;
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict__ nn2) {
+  __shared__ float4 su[kWarpsPerBlock][32], sv[kWarpsPerBlock][32];
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  const int64_t nbk = *A.nbuckets;
+  while (true) {
+    const int64_t w = next_work(A.counter, lane);
+    if (w >= nbk) break;
+    const int64_t a = A.order[w];
+    const Bucket Aq = A.bk[a];
+    const float4 iv = A.inv[Aq.node];
+    const float isx = iv.x, isv = iv.y;
+    const bool valid = lane < int(Aq.count);
+    const uint32_t si = Aq.start + (valid ? lane : 0);
+    const float4 ui = A.Us[si], vi = A.Vs[si];
+    float best = __int_as_float(0x7f800000);
+    const int64_t own = (a - int64_t(Aq.first)) >> 5, nsb = Aq.sbcount;
+    for (int64_t t = 0; t <= 2 * nsb; ++t) {
+      const int64_t s = outward(own, t);
+      if (s < 0 || s >= nsb) continue;
+      const Box SB = A.sbox[Aq.sbfirst + s];
+      const bool need = valid && lb_point_box(ui, vi, SB, isx, isv) <= best;
+      if (!__any_sync(0xffffffffu, need)) continue;
+      const int64_t b_lo = int64_t(Aq.first) + 32 * s;
+      const int64_t b_hi = rsd::min64(b_lo + 32, int64_t(Aq.last) + 1);
+      if (s == own) {
+        for (int64_t t2 = 0; t2 <= 2 * 32; ++t2) {
+          const int64_t b = outward(a, t2);
+          if (b < b_lo || b >= b_hi) continue;
+          nn_bucket(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb]);
+        }
+      } else if (s > own) {
+        for (int64_t b = b_lo; b < b_hi; ++b)
+          nn_bucket(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb]);
+      } else {
+        for (int64_t b = b_hi - 1; b >= b_lo; --b)
+          nn_bucket(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb]);
+      }
+    }
+    if (valid) nn2[A.sp[si]] = best;
+  }
+}
+
+// Link pairs of query bucket a (box Abox) with target bucket b >= a.
+__device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t b, const Box& Abox,
+                                            bool active, float4 ui, float4 vi, uint32_t pi,
+                                            float isx, float isv, float l2, const float* nn2,
+                                            uint32_t* uf, int lane, float4 (&su)[32],
+                                            float4 (&sv)[32], uint32_t (&sj)[32], float (&snn)[32]) {
+  const Box B = A.box[b];
+  if (lb_box_box(Abox, B, isx, isv) > l2) return;
+  const bool need = active && lb_point_box(ui, vi, B, isx, isv) <= l2;
+  if (!__any_sync(0xffffffffu, need)) return;
+  const Bucket Bb = A.bk[b];
+  __syncwarp();
+  if (lane < int(Bb.count)) {
+    su[lane] = A.Us[Bb.start + lane];
+    sv[lane] = A.Vs[Bb.start + lane];
+    sj[lane] = A.sp[Bb.start + lane];
+    snn[lane] = nn2[A.sp[Bb.start + lane]];
+  }
+  __syncwarp();
+  const uint32_t j0 = (b == a) ? uint32_t(lane) + 1 : 0u;
+  for (uint32_t s0 = 0; s0 < Bb.count; s0 += 8) {
+    const Box Sb = A.sub[4 * b + (s0 >> 3)];
+    if (lb_box_box(Abox, Sb, isx, isv) > l2) continue;
+    const bool sneed = need && lb_point_box(ui, vi, Sb, isx, isv) <= l2;
+    if (!__any_sync(0xffffffffu, sneed)) continue;
+    if (sneed) {
+      const uint32_t s1 = min(s0 + 8, Bb.count);
+      for (uint32_t j = max(s0, j0); j < s1; ++j) {
+        if (snn[j] > l2) continue;
+        if (d6(ui, vi, su[j], sv[j], isx, isv) <= l2) rsd::uf_unite(uf, pi, sj[j]);
+      }
+    }
   }
 }
 
 __global__ void __launch_bounds__(kT)
-k_link6d_pruned(const int64_t* __restrict__ nbuckets_dev, const Bucket* __restrict__ bk,
-                const Box* __restrict__ box, const float4* __restrict__ Us,
-                const float4* __restrict__ Vs, const uint32_t* __restrict__ sp,
-                const float4* __restrict__ inv, const float* __restrict__ nn2,
-                uint32_t* __restrict__ uf) {
+k_link6d_pruned(NNArgs A, const float* __restrict__ nn2, uint32_t* __restrict__ uf) {
   __shared__ float4 su[kWarpsPerBlock][32], sv[kWarpsPerBlock][32];
   __shared__ uint32_t sj[kWarpsPerBlock][32];
   __shared__ float snn[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-  const int64_t nbk = *nbuckets_dev;
-  const int64_t stride = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t a = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; a < nbk; a += stride) {
-    const Bucket A = bk[a];
-    const float4 iv = inv[A.node];
+  const int64_t nbk = *A.nbuckets;
+  while (true) {
+    const int64_t w = next_work(A.counter, lane);
+    if (w >= nbk) break;
+    const int64_t a = A.order[w];
+    const Bucket Aq = A.bk[a];
+    const float4 iv = A.inv[Aq.node];
     const float isx = iv.x, isv = iv.y, l2 = iv.z;
-    const bool valid = lane < int(A.count);
-    const uint32_t si = A.start + (valid ? lane : 0);
-    const float4 ui = Us[si], vi = Vs[si];
-    const uint32_t pi = sp[si];
+    const bool valid = lane < int(Aq.count);
+    const uint32_t si = Aq.start + (valid ? lane : 0);
+    const float4 ui = A.Us[si], vi = A.Vs[si];
+    const uint32_t pi = A.sp[si];
     const bool active = valid && nn2[pi] <= l2;
     if (!__any_sync(0xffffffffu, active)) continue;
-    const Box Abox = box[a];
-    for (int64_t b = a; b <= int64_t(A.last); ++b) {
-      const Box B = box[b];
-      if (lb_box_box(Abox, B, isx, isv) > l2) continue;
-      const bool need = active && lb_point_box(ui, vi, B, isx, isv) <= l2;
+    const Box Abox = A.box[a];
+    const int64_t own = (a - int64_t(Aq.first)) >> 5, nsb = Aq.sbcount;
+    for (int64_t s = own; s < nsb; ++s) {
+      const Box SB = A.sbox[Aq.sbfirst + s];
+      if (lb_box_box(Abox, SB, isx, isv) > l2) continue;
+      const bool need = active && lb_point_box(ui, vi, SB, isx, isv) <= l2;
       if (!__any_sync(0xffffffffu, need)) continue;
-      const Bucket Bb = bk[b];
-      __syncwarp();
-      if (lane < int(Bb.count)) {
-        su[wb][lane] = Us[Bb.start + lane];
-        sv[wb][lane] = Vs[Bb.start + lane];
-        sj[wb][lane] = sp[Bb.start + lane];
-        snn[wb][lane] = nn2[sp[Bb.start + lane]];
-      }
-      __syncwarp();
-      if (need) {
-        const uint32_t j0 = (b == a) ? uint32_t(lane) + 1 : 0u;
-        for (uint32_t j = j0; j < Bb.count; ++j) {
-          if (snn[wb][j] > l2) continue;
-          if (d6(ui, vi, su[wb][j], sv[wb][j], isx, isv) <= l2) rsd::uf_unite(uf, pi, sj[wb][j]);
-        }
-      }
+      const int64_t b_lo = rsd::min64(int64_t(Aq.first) + 32 * s, int64_t(Aq.last) + 1);
+      const int64_t b_hi = rsd::min64(int64_t(Aq.first) + 32 * s + 32, int64_t(Aq.last) + 1);
+      for (int64_t b = (s == own ? a : b_lo); b < b_hi; ++b)
+        link_bucket(A, a, b, Abox, active, ui, vi, pi, isx, isv, l2, nn2, uf, lane, su[wb], sv[wb],
+                    sj[wb], snn[wb]);
     }
   }
 }
@@ -288,13 +414,29 @@ int bits_for(uint64_t v) {
   return b;
 }
 
+NNArgs nn_args(rs_ctx* ctx, int64_t nn) {
+  Hier h = hier_of(ctx);
+  NNArgs A;
+  A.nbuckets = static_cast<const int64_t*>(ctx->buf[S_P_BOFF].ptr) + nn;
+  A.bk = static_cast<const Bucket*>(ctx->buf[S_P_BUCKET].ptr);
+  A.box = static_cast<const Box*>(ctx->buf[S_P_BOX].ptr);
+  A.sub = static_cast<const Box*>(ctx->buf[S_P_SUB].ptr);
+  A.sbox = static_cast<const Box*>(ctx->buf[S_P_SBOX].ptr);
+  A.order = static_cast<const uint32_t*>(ctx->buf[S_P_ORDER].ptr);
+  A.Us = static_cast<const float4*>(ctx->buf[S_P_US].ptr);
+  A.Vs = static_cast<const float4*>(ctx->buf[S_P_VS].ptr);
+  A.sp = static_cast<const uint32_t*>(ctx->buf[S_P_SP].ptr);
+  A.inv = h.inv;
+  A.counter = static_cast<unsigned long long*>(ctx->buf[S_P_QCTR].ptr);
+  return A;
+}
+
 }  // namespace
 
 int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m,
                         const double* sums, cudaStream_t st) {
   Hier h = hier_of(ctx);
   float4* mean_u = scratch_t<float4>(ctx, S_P_MEANU, size_t(nb + nn));
-  float4* mean_v = scratch_t<float4>(ctx, S_P_MEANV, size_t(nb + nn));
   uint64_t* ka = scratch_t<uint64_t>(ctx, S_KEY_A, size_t(m));
   uint64_t* kb = scratch_t<uint64_t>(ctx, S_KEY_B, size_t(m));
   uint32_t* va = scratch_t<uint32_t>(ctx, S_VAL_A, size_t(m));
@@ -303,26 +445,47 @@ int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t
   float4* Vs = scratch_t<float4>(ctx, S_P_VS, size_t(m));
   uint32_t* sp = scratch_t<uint32_t>(ctx, S_P_SP, size_t(m));
   int64_t* boff = scratch_t<int64_t>(ctx, S_P_BOFF, size_t(nn) + 1);
+  int64_t* sboff = scratch_t<int64_t>(ctx, S_P_SBOFF, size_t(nn) + 1);
   const int64_t nbk_ub = nn + m / 32 + 1;
+  const int64_t nsb_ub = nn + nbk_ub / 32 + 1;
   Bucket* bk = scratch_t<Bucket>(ctx, S_P_BUCKET, size_t(nbk_ub));
   Box* box = scratch_t<Box>(ctx, S_P_BOX, size_t(nbk_ub));
-  if (!mean_u || !mean_v || !ka || !kb || !va || !vb || !Us || !Vs || !sp || !boff || !bk || !box)
+  Box* sub = scratch_t<Box>(ctx, S_P_SUB, size_t(nbk_ub) * 4);
+  Box* sbox = scratch_t<Box>(ctx, S_P_SBOX, size_t(nsb_ub));
+  unsigned long long* qctr = scratch_t<unsigned long long>(ctx, S_P_QCTR, 2);
+  if (!mean_u || !ka || !kb || !va || !vb || !Us || !Vs || !sp || !boff || !sboff || !bk || !box ||
+      !sub || !sbox || !qctr)
     return RS_ERR_OOM;
-  k_node_means<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, sums, mean_u, mean_v);
+  k_node_means<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, sums, mean_u);
   RS_LAUNCHED(ctx, "k_node_means");
-  k_morton6<<<grid_for(m, kT), kT, 0, st>>>(mb, m, nb, 0, h.mnode, h.U, h.V, h.inv, mean_u, mean_v, ka, va);
-  RS_LAUNCHED(ctx, "k_morton6");
+  k_morton3<<<grid_for(m, kT), kT, 0, st>>>(mb, m, nb, h.mnode, h.U, h.inv, mean_u, ka, va);
+  RS_LAUNCHED(ctx, "k_morton3");
   uint64_t* keys;
   uint32_t* order;
   RS_TRY(radix_sort_u64(ctx, m, 30 + bits_for(uint64_t(nn)), ka, va, kb, vb, &keys, &order, st));
   k_gather_sorted<<<grid_for(m, kT), kT, 0, st>>>(mb, m, order, h.U, h.V, Us, Vs, sp);
   RS_LAUNCHED(ctx, "k_gather_sorted");
-  k_bucket_counts<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, boff);
+  k_bucket_counts<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, boff, sboff);
   RS_LAUNCHED(ctx, "k_bucket_counts");
   RS_TRY(exclusive_scan_i64(ctx, nn, boff, boff + nn, st));
-  k_buckets<<<grid_for(nbk_ub * 32, kT), kT, 0, st>>>(nb, nn, mb, boff, h.node_off, h.node_size, Us, Vs,
-                                                     bk, box);
+  RS_TRY(exclusive_scan_i64(ctx, nn, sboff, sboff + nn, st));
+  // bucket tables and the work queue (keys/values reuse the sort buffers: m >= buckets)
+  uint64_t* qk = scratch_t<uint64_t>(ctx, S_KEY_A, size_t(std::max(m, nbk_ub)));
+  uint64_t* qk2 = scratch_t<uint64_t>(ctx, S_KEY_B, size_t(std::max(m, nbk_ub)));
+  uint32_t* qv = scratch_t<uint32_t>(ctx, S_VAL_A, size_t(std::max(m, nbk_ub)));
+  uint32_t* qv2 = scratch_t<uint32_t>(ctx, S_VAL_B, size_t(std::max(m, nbk_ub)));
+  if (!qk || !qk2 || !qv || !qv2) return RS_ERR_OOM;
+  k_buckets<<<grid_for(nbk_ub * 32, kT), kT, 0, st>>>(nb, nn, mb, nbk_ub, boff, sboff, h.node_off,
+                                                     h.node_size, Us, Vs, bk, box, sub, qk, qv);
   RS_LAUNCHED(ctx, "k_buckets");
+  k_superboxes<<<grid_for(nsb_ub * 32, kT), kT, 0, st>>>(nn, boff, sboff, box, sbox);
+  RS_LAUNCHED(ctx, "k_superboxes");
+  uint64_t* qk_out;
+  uint32_t* qv_out;
+  RS_TRY(radix_sort_u64(ctx, nbk_ub, 32, qk, qv, qk2, qv2, &qk_out, &qv_out, st));
+  uint32_t* qorder = scratch_t<uint32_t>(ctx, S_P_ORDER, size_t(nbk_ub));
+  if (!qorder) return RS_ERR_OOM;
+  RS_CUDA(ctx, cudaMemcpyAsync(qorder, qv_out, sizeof(uint32_t) * nbk_ub, cudaMemcpyDeviceToDevice, st));
   return RS_OK;
 }
 
@@ -330,18 +493,13 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
                    cudaStream_t st) {
   (void)nb;
   (void)mb;
-  Hier h = hier_of(ctx);
-  const int64_t* boff = static_cast<const int64_t*>(ctx->buf[S_P_BOFF].ptr);
-  const Bucket* bk = static_cast<const Bucket*>(ctx->buf[S_P_BUCKET].ptr);
-  const Box* box = static_cast<const Box*>(ctx->buf[S_P_BOX].ptr);
-  const float4* Us = static_cast<const float4*>(ctx->buf[S_P_US].ptr);
-  const float4* Vs = static_cast<const float4*>(ctx->buf[S_P_VS].ptr);
-  const uint32_t* sp = static_cast<const uint32_t*>(ctx->buf[S_P_SP].ptr);
+  NNArgs A = nn_args(ctx, nn);
   const int64_t nbk_ub = nn + m / 32 + 1;
-  const unsigned grid = unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 16));
+  const unsigned grid = unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 8));
+  RS_CUDA(ctx, cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st));
   {
     ProfScope prof_(ctx, "k_nn6d_pruned", st);
-    k_nn6d_pruned<<<grid, kT, 0, st>>>(boff + nn, bk, box, Us, Vs, sp, h.inv, nn2);
+    k_nn6d_pruned<<<grid, kT, 0, st>>>(A, nn2);
   }
   RS_LAUNCHED(ctx, "k_nn6d_pruned");
   return RS_OK;
@@ -351,18 +509,14 @@ int rs::prune6d_link(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m,
                      uint32_t* uf, cudaStream_t st) {
   (void)nb;
   (void)mb;
-  Hier h = hier_of(ctx);
-  const int64_t* boff = static_cast<const int64_t*>(ctx->buf[S_P_BOFF].ptr);
-  const Bucket* bk = static_cast<const Bucket*>(ctx->buf[S_P_BUCKET].ptr);
-  const Box* box = static_cast<const Box*>(ctx->buf[S_P_BOX].ptr);
-  const float4* Us = static_cast<const float4*>(ctx->buf[S_P_US].ptr);
-  const float4* Vs = static_cast<const float4*>(ctx->buf[S_P_VS].ptr);
-  const uint32_t* sp = static_cast<const uint32_t*>(ctx->buf[S_P_SP].ptr);
+  NNArgs A = nn_args(ctx, nn);
+  A.counter += 1;
   const int64_t nbk_ub = nn + m / 32 + 1;
-  const unsigned grid = unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 16));
+  const unsigned grid = unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 8));
+  RS_CUDA(ctx, cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st));
   {
     ProfScope prof_(ctx, "k_link6d_pruned", st);
-    k_link6d_pruned<<<grid, kT, 0, st>>>(boff + nn, bk, box, Us, Vs, sp, h.inv, nn2, uf);
+    k_link6d_pruned<<<grid, kT, 0, st>>>(A, nn2, uf);
   }
   RS_LAUNCHED(ctx, "k_link6d_pruned");
   return RS_OK;
