@@ -77,8 +77,8 @@ int read_back(rs_ctx* ctx, const void* dev, size_t bytes, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Radix sort. One pass per 8-bit digit: per-block digit histograms (k_sort_hist), one exclusive
-// scan over the digit-major histogram table (k_sort_scan), then a stable scatter
+// Radix sort. One pass per 8-bit digit: per-block digit histograms (k_sort_hist), a scan of
+// each digit's row of the digit-major histogram table (k_sort_scan_rows), then a stable scatter
 // (k_sort_scatter) in which each block ranks its tiles with warp match masks, reorders a tile
 // in shared memory and writes each digit's run contiguously.
 namespace {
@@ -110,47 +110,49 @@ k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t dm
   }
 }
 
-// Exclusive scan of m uint32 values by one block of 1024 threads, looping over segments.
-__global__ void __launch_bounds__(1024) k_scan_u32_single(uint32_t* data, int64_t m) {
-  __shared__ uint32_t part[1024];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  constexpr int kPer = 8;
-  for (int64_t base = 0; base < m; base += 1024 * kPer) {
-    uint32_t v[kPer];
-    uint32_t s = 0;
-    const int64_t my = base + int64_t(threadIdx.x) * kPer;
+// Scan of the digit-major histogram table, one block per digit: each row (the digit's count in
+// every sort block, in block order) becomes its exclusive prefix, and the row total goes to
+// totals[d]. The scatter adds the exclusive prefix of the totals over the digits.
+constexpr int kScanRowThreads = 256;
+
+__global__ void __launch_bounds__(kScanRowThreads)
+k_sort_scan_rows(uint32_t* __restrict__ hist, int64_t nblocks, uint32_t* __restrict__ totals) {
+  __shared__ uint32_t wsum[kScanRowThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* row = hist + int64_t(blockIdx.x) * nblocks;
+  const int64_t per = (nblocks + kScanRowThreads - 1) / kScanRowThreads;
+  const int64_t b0 = rsd::min64(nblocks, int64_t(threadIdx.x) * per);
+  const int64_t b1 = rsd::min64(nblocks, b0 + per);
+  uint32_t s = 0;
+  for (int64_t b = b0; b < b1; ++b) s += row[b];
+  uint32_t incl = s;
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      v[k] = (my + k < m) ? data[my + k] : 0u;
-      s += v[k];
-    }
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-      uint32_t t = (threadIdx.x >= off) ? part[threadIdx.x - off] : 0u;
-      __syncthreads();
-      part[threadIdx.x] += t;
-      __syncthreads();
-    }
-    uint32_t run = carry + part[threadIdx.x] - s;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      if (my + k < m) data[my + k] = run;
-      run += v[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += part[1023];
-    __syncthreads();
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += t;
   }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kScanRowThreads / 32; ++w) {
+    if (w < warp) before += wsum[w];
+    all += wsum[w];
+  }
+  uint32_t run = before + incl - s;
+  for (int64_t b = b0; b < b1; ++b) {
+    const uint32_t c = row[b];
+    row[b] = run;
+    run += c;
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = all;
 }
 
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_scatter(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n,
                int shift, uint32_t dmask, int64_t tiles_per_block,
-               const uint32_t* __restrict__ offsets) {
+               const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ totals) {
   __shared__ uint64_t skey[kTile];
   __shared__ uint32_t sval[kTile];
   __shared__ uint32_t wcount[kSortWarps][kRadix];
@@ -159,8 +161,29 @@ k_sort_scatter(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict_
   __shared__ uint32_t tot[kRadix];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
-    run[d] = offsets[int64_t(d) * gridDim.x + blockIdx.x];
+  if (threadIdx.x < 32) {  // run[d] = (digits < d over all blocks) + (digit d in blocks before)
+    uint32_t v[kRadix / 32];
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kRadix / 32; ++q) {
+      v[q] = totals[lane * (kRadix / 32) + q];
+      s += v[q];
+    }
+    uint32_t incl = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += t;
+    }
+    uint32_t ex = incl - s;
+#pragma unroll
+    for (int q = 0; q < kRadix / 32; ++q) {
+      const int d = lane * (kRadix / 32) + q;
+      run[d] = ex + offsets[int64_t(d) * gridDim.x + blockIdx.x];
+      ex += v[q];
+    }
+  }
+  __syncthreads();
   const int64_t tile0 = int64_t(blockIdx.x) * tiles_per_block;
   const int64_t ntiles_total = (n + kTile - 1) / kTile;
   const int64_t tile1 = min(ntiles_total, tile0 + tiles_per_block);
@@ -264,8 +287,9 @@ int radix_sort_u64(rs_ctx* ctx, int64_t n, int nbits, uint64_t* keys_a, uint32_t
   int64_t blocks = rsd::min64(ntiles, kMaxSortBlocks);
   const int64_t tpb = (ntiles + blocks - 1) / blocks;
   blocks = (ntiles + tpb - 1) / tpb;
-  uint32_t* hist = scratch_t<uint32_t>(ctx, S_SORT_HIST, size_t(kRadix) * blocks);
+  uint32_t* hist = scratch_t<uint32_t>(ctx, S_SORT_HIST, size_t(kRadix) * (blocks + 1));
   if (!hist) return RS_ERR_OOM;
+  uint32_t* totals = hist + size_t(kRadix) * blocks;
   uint64_t* kin = keys_a;
   uint32_t* vin = vals_a;
   uint64_t* kout = keys_b;
@@ -278,12 +302,12 @@ int radix_sort_u64(rs_ctx* ctx, int64_t n, int nbits, uint64_t* keys_a, uint32_t
       k_sort_hist<<<unsigned(blocks), kSortThreads, 0, st>>>(kin, n, shift, dmask, tpb, hist);
     }
     RS_LAUNCHED(ctx, "k_sort_hist");
-    k_scan_u32_single<<<1, 1024, 0, st>>>(hist, int64_t(kRadix) * blocks);
-    RS_LAUNCHED(ctx, "k_scan_u32_single");
+    k_sort_scan_rows<<<kRadix, kScanRowThreads, 0, st>>>(hist, blocks, totals);
+    RS_LAUNCHED(ctx, "k_sort_scan_rows");
     {
       ProfScope prof_(ctx, "k_sort_scatter", st);
       k_sort_scatter<<<unsigned(blocks), kSortThreads, 0, st>>>(kin, vin, kout, vout, n, shift, dmask,
-                                                               tpb, hist);
+                                                               tpb, hist, totals);
     }
     RS_LAUNCHED(ctx, "k_sort_scatter");
     std::swap(kin, kout);

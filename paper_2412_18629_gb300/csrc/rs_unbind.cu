@@ -90,110 +90,131 @@ k_potential(int64_t nn, const int64_t* __restrict__ tile_off, const int64_t* __r
 }
 
 // Register-blocked variant for nodes larger than kBlockedMin: each of the 128 threads of a
-// block owns 4 members (i = 512 t + tid + 128 k), so one 16-B shared load serves 4 pairs. The
-// per-member summation is unchanged (32-term sequential blocks, Kahan across blocks), so the
-// certified bound kCertB holds as is. The self pair is tested only on the diagonal j-tiles.
+// block owns 4 members (i = 512 t + tid + 128 k), processed as two packed pairs with the
+// float32x2 add / fma instructions (each half rounded exactly like the scalar operation, so
+// the results are bit-identical to the scalar form). Staged members are stored duplicated,
+// (x, x, y, y) and (z, z), so a shared load yields the packed operands directly; differences
+// are formed as u_j + (-u_i), which equals fl(u_j - u_i). The per-member summation is
+// unchanged (32-term sequential blocks, Kahan across blocks), so the certified bound kCertB
+// holds as is. The self pair is tested only on the diagonal j-tiles. Blocks are ordered by
+// the node's size class, largest first, so the longest blocks start first.
 constexpr int kBlkThreads = 128;
 constexpr int kBlkR = 4;
 constexpr int kBlkTile = kBlkThreads * kBlkR;  // 512 members per block
 constexpr int64_t kBlockedMin = 384;
 
 // Tiles of the two direct-sum kernels; nodes with >= sur_min members (sur_min > 0) are left to
-// the surrogate path.
+// the surrogate path. Also the sort key of the blocked tiles' order (size class, descending).
 __global__ void k_tiles_split(int64_t nn, const int64_t* __restrict__ node_size, int64_t sur_min,
                               const int* __restrict__ only, int64_t* __restrict__ small,
-                              int64_t* __restrict__ big) {
+                              int64_t* __restrict__ big, uint64_t* __restrict__ okey,
+                              uint32_t* __restrict__ oval) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= nn) return;
   const int64_t g = node_size[k];
   const bool skip = only ? (only[k] == 0) : (sur_min > 0 && g >= sur_min);
+  const bool blocked = !skip && g > kBlockedMin;
   small[k] = (skip || g > kBlockedMin) ? 0 : (g + kPotTile - 1) / kPotTile;
-  big[k] = (!skip && g > kBlockedMin) ? (g + kBlkTile - 1) / kBlkTile : 0;
+  big[k] = blocked ? (g + kBlkTile - 1) / kBlkTile : 0;
+  okey[k] = blocked ? uint64_t(63 - __clzll(g)) ^ 63u : 255u;
+  oval[k] = uint32_t(k);
+}
+
+__global__ void k_perm_tiles(int64_t nn, const uint32_t* __restrict__ perm,
+                             const int64_t* __restrict__ big, int64_t* __restrict__ out) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r < nn) out[r] = big[perm[r]];
+}
+
+__device__ __forceinline__ void pot_pair(float4 a, float2 zz, float2 nx, float2 ny, float2 nz,
+                                         float2 e2, float2& w) {
+  const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx);
+  const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny);
+  const float2 dz = __fadd2_rn(zz, nz);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+  w = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
 }
 
 __global__ void __launch_bounds__(kBlkThreads)
-k_potential_blocked(int64_t nn, const int64_t* __restrict__ tile_off,
+k_potential_blocked(int64_t nn, const int64_t* __restrict__ tile_off, const uint32_t* __restrict__ perm,
                     const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
                     const float4* __restrict__ U, float eps2, float* __restrict__ S_out) {
-  __shared__ float4 su[kBlkThreads];
+  __shared__ float4 sxy[kBlkThreads];
+  __shared__ float2 sz[kBlkThreads];
   const int64_t b = blockIdx.x;
   if (b >= tile_off[nn]) return;
-  const int64_t q = rsd::upper_bound_i64(tile_off, nn, b) - 1;
-  const int64_t t = b - tile_off[q];
+  const int64_t r = rsd::upper_bound_i64(tile_off, nn, b) - 1;
+  const int64_t q = perm[r];
+  const int64_t t = b - tile_off[r];
   const int64_t base = node_off[q], g = node_size[q];
-  float4 ui[kBlkR];
+  float2 nx[kBlkR / 2], ny[kBlkR / 2], nz[kBlkR / 2];
   float S[kBlkR], C[kBlkR];
 #pragma unroll
+  for (int p = 0; p < kBlkR / 2; ++p) {
+    const int64_t i0 = t * kBlkTile + threadIdx.x + kBlkThreads * (2 * p);
+    const int64_t i1 = i0 + kBlkThreads;
+    const float4 u0 = i0 < g ? U[base + i0] : make_float4(0, 0, 0, 0);
+    const float4 u1 = i1 < g ? U[base + i1] : make_float4(0, 0, 0, 0);
+    nx[p] = make_float2(-u0.x, -u1.x);
+    ny[p] = make_float2(-u0.y, -u1.y);
+    nz[p] = make_float2(-u0.z, -u1.z);
+  }
+#pragma unroll
   for (int k = 0; k < kBlkR; ++k) {
-    const int64_t i = t * kBlkTile + threadIdx.x + kBlkThreads * k;
-    ui[k] = i < g ? U[base + i] : make_float4(0, 0, 0, 0);
     S[k] = 0.f;
     C[k] = 0.f;
   }
+  const float2 e2 = make_float2(eps2, eps2);
   for (int64_t j0 = 0; j0 < g; j0 += kBlkThreads) {
     const int64_t j = j0 + threadIdx.x;
-    if (j < g) su[threadIdx.x] = U[base + j];
+    if (j < g) {
+      const float4 u = U[base + j];
+      sxy[threadIdx.x] = make_float4(u.x, u.x, u.y, u.y);
+      sz[threadIdx.x] = make_float2(u.z, u.z);
+    }
     __syncthreads();
     const int jn = int(rsd::min64(kBlkThreads, g - j0));
     const int64_t jt = j0 / kBlkThreads - t * kBlkR;  // diagonal tile for member slot jt
-    if (jt >= 0 && jt < kBlkR) {
-      for (int jb = 0; jb < jn; jb += 32) {
-        const int je = min(jb + 32, jn);
-        float blk[kBlkR] = {0.f, 0.f, 0.f, 0.f};
-        for (int jj = jb; jj < je; ++jj) {
-          const float4 uj = su[jj];
+    const bool diag = jt >= 0 && jt < kBlkR;
+    for (int jb = 0; jb < jn; jb += 32) {
+      const int je = min(jb + 32, jn);
+      float2 blk[kBlkR / 2];
 #pragma unroll
-          for (int k = 0; k < kBlkR; ++k) {
-            const float dx = __fsub_rn(uj.x, ui[k].x);
-            const float dy = __fsub_rn(uj.y, ui[k].y);
-            const float dz = __fsub_rn(uj.z, ui[k].z);
-            const float w = rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2))));
-            blk[k] = __fadd_rn(blk[k], (k == jt && jj == int(threadIdx.x)) ? 0.f : w);
+      for (int p = 0; p < kBlkR / 2; ++p) blk[p] = make_float2(0.f, 0.f);
+      if (!diag && je - jb == 32) {
+#pragma unroll 8
+        for (int jj = jb; jj < jb + 32; ++jj) {
+          const float4 a = sxy[jj];
+          const float2 zz = sz[jj];
+#pragma unroll
+          for (int p = 0; p < kBlkR / 2; ++p) {
+            float2 w;
+            pot_pair(a, zz, nx[p], ny[p], nz[p], e2, w);
+            blk[p] = __fadd2_rn(blk[p], w);
           }
         }
+      } else {
+        for (int jj = jb; jj < je; ++jj) {
+          const float4 a = sxy[jj];
+          const float2 zz = sz[jj];
+          const bool self = diag && jj == int(threadIdx.x);
 #pragma unroll
-        for (int k = 0; k < kBlkR; ++k) {
-          const float y = __fsub_rn(blk[k], C[k]);
-          const float tt = __fadd_rn(S[k], y);
-          C[k] = __fsub_rn(__fsub_rn(tt, S[k]), y);
-          S[k] = tt;
+          for (int p = 0; p < kBlkR / 2; ++p) {
+            float2 w;
+            pot_pair(a, zz, nx[p], ny[p], nz[p], e2, w);
+            if (self && jt == 2 * p) w.x = 0.f;
+            if (self && jt == 2 * p + 1) w.y = 0.f;
+            blk[p] = __fadd2_rn(blk[p], w);
+          }
         }
       }
-    } else {
-      for (int jb = 0; jb < jn; jb += 32) {
-        const int je = min(jb + 32, jn);
-        float blk[kBlkR] = {0.f, 0.f, 0.f, 0.f};
-        if (je - jb == 32) {
-#pragma unroll 8
-          for (int jj = jb; jj < jb + 32; ++jj) {
-            const float4 uj = su[jj];
 #pragma unroll
-            for (int k = 0; k < kBlkR; ++k) {
-              const float dx = __fsub_rn(uj.x, ui[k].x);
-              const float dy = __fsub_rn(uj.y, ui[k].y);
-              const float dz = __fsub_rn(uj.z, ui[k].z);
-              blk[k] = __fadd_rn(blk[k], rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2)))));
-            }
-          }
-        } else {
-          for (int jj = jb; jj < je; ++jj) {
-            const float4 uj = su[jj];
-#pragma unroll
-            for (int k = 0; k < kBlkR; ++k) {
-              const float dx = __fsub_rn(uj.x, ui[k].x);
-              const float dy = __fsub_rn(uj.y, ui[k].y);
-              const float dz = __fsub_rn(uj.z, ui[k].z);
-              blk[k] = __fadd_rn(blk[k], rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2)))));
-            }
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < kBlkR; ++k) {
-          const float y = __fsub_rn(blk[k], C[k]);
-          const float tt = __fadd_rn(S[k], y);
-          C[k] = __fsub_rn(__fsub_rn(tt, S[k]), y);
-          S[k] = tt;
-        }
+      for (int k = 0; k < kBlkR; ++k) {
+        const float bk = (k & 1) ? blk[k >> 1].y : blk[k >> 1].x;
+        const float y = __fsub_rn(bk, C[k]);
+        const float tt = __fadd_rn(S[k], y);
+        C[k] = __fsub_rn(__fsub_rn(tt, S[k]), y);
+        S[k] = tt;
       }
     }
     __syncthreads();
@@ -410,6 +431,49 @@ __global__ void k_halo_decide(int64_t nn, const int64_t* __restrict__ node_size,
   is_halo[q] = (c >= min_size && int64_t(bden) * c >= int64_t(bnum) * node_size[q]) ? 1 : 0;
 }
 
+// Float32 direct sums S_i = sum_{j != i} (|u_j - u_i|^2 + eps^2)^(-1/2) of every member of the
+// selected nodes (only[k] != 0 if `only` is given, else nodes below sur_min when sur_min > 0,
+// else all): nodes up to kBlockedMin members by k_potential, larger ones by the blocked kernel
+// with its tiles ordered by node size class, largest first.
+int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, float* S, cudaStream_t st) {
+  Hier h = hier_of(ctx);
+  const int64_t m = ctx->n_members, nn = ctx->n_nodes;
+  const float eps = ctx->cfg.softening;
+  int64_t* tile_small = scratch_t<int64_t>(ctx, S_SELECT, size_t(nn) + 1);
+  int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
+  int64_t* tile_perm = scratch_t<int64_t>(ctx, S_U_TILEPERM, size_t(nn) + 1);
+  uint64_t* ka = scratch_t<uint64_t>(ctx, S_U_OKEY_A, size_t(nn));
+  uint64_t* kb = scratch_t<uint64_t>(ctx, S_U_OKEY_B, size_t(nn));
+  uint32_t* va = scratch_t<uint32_t>(ctx, S_U_OVAL_A, size_t(nn));
+  uint32_t* vb = scratch_t<uint32_t>(ctx, S_U_OVAL_B, size_t(nn));
+  if (!tile_small || !tile_big || !tile_perm || !ka || !kb || !va || !vb) return RS_ERR_OOM;
+  k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sur_min, only, tile_small, tile_big,
+                                                 ka, va);
+  RS_LAUNCHED(ctx, "k_tiles_split");
+  uint64_t* ko;
+  uint32_t* perm;
+  RS_TRY(radix_sort_u64(ctx, nn, 8, ka, va, kb, vb, &ko, &perm, st));
+  k_perm_tiles<<<grid_for(nn, kT), kT, 0, st>>>(nn, perm, tile_big, tile_perm);
+  RS_LAUNCHED(ctx, "k_perm_tiles");
+  RS_TRY(exclusive_scan_i64(ctx, nn, tile_small, tile_small + nn, st));
+  RS_TRY(exclusive_scan_i64(ctx, nn, tile_perm, tile_perm + nn, st));
+  const int64_t tiles_ub = nn + m / kPotTile + 1;
+  const int64_t big_ub = m / (kBlockedMin + 1) + m / kBlkTile + 1;
+  {
+    ProfScope prof_(ctx, "k_potential", st);
+    k_potential<<<grid_for(tiles_ub, 1), kPotTile, 0, st>>>(nn, tile_small, h.node_off, h.node_size, h.U,
+                                                           eps * eps, S);
+  }
+  RS_LAUNCHED(ctx, "k_potential");
+  {
+    ProfScope prof_(ctx, "k_potential_blocked", st);
+    k_potential_blocked<<<grid_for(big_ub, 1), kBlkThreads, 0, st>>>(nn, tile_perm, perm, h.node_off,
+                                                                    h.node_size, h.U, eps * eps, S);
+  }
+  RS_LAUNCHED(ctx, "k_potential_blocked");
+  return RS_OK;
+}
+
 }  // namespace
 
 extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float* potential_out,
@@ -441,10 +505,9 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
   double* vsum = scratch_t<double>(ctx, S_U_VBULK, size_t(std::max<int64_t>(nn, 1)) * 3);
   uint32_t* ambig = scratch_t<uint32_t>(ctx, S_U_AMBIG, size_t(std::max<int64_t>(m, 1)));
   uint8_t* halo = scratch_t<uint8_t>(ctx, S_U_FLAGS, size_t(std::max<int64_t>(nn, 1)));
-  int64_t* tile_off = scratch_t<int64_t>(ctx, S_SELECT, size_t(nn) + 1);
   // counters: [0..6] surrogate path (rs_surrogate.cu), [7] float64 fallbacks of the direct sums
   unsigned long long* counters = scratch_t<unsigned long long>(ctx, S_SUR_COUNTERS, 16);
-  if (!bound || !S || !nb || !vsum || !ambig || !halo || !tile_off || !counters) return RS_ERR_OOM;
+  if (!bound || !S || !nb || !vsum || !ambig || !halo || !counters) return RS_ERR_OOM;
   unsigned long long* n_ambig = counters + 7;
   int64_t nfb = 0;
   for (int i = 0; i < 10; ++i) ctx->sur_stats[i] = 0;
@@ -453,26 +516,7 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     const float eps = ctx->cfg.softening;
     RS_CUDA(ctx, cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned long long), st));
     RS_TRY((cro_segmented<3, VelTerm>(ctx, nn, h.node_off, h.node_size, m, VelTerm{h.V}, vsum, st)));
-    int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
-    if (!tile_big) return RS_ERR_OOM;
-    k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sur_min, nullptr, tile_off, tile_big);
-    RS_LAUNCHED(ctx, "k_tiles_split");
-    RS_TRY(exclusive_scan_i64(ctx, nn, tile_off, tile_off + nn, st));
-    RS_TRY(exclusive_scan_i64(ctx, nn, tile_big, tile_big + nn, st));
-    const int64_t tiles_ub = nn + m / kPotTile + 1;
-    const int64_t big_ub = m / (kBlockedMin + 1) + m / kBlkTile + 1;
-    {
-      ProfScope prof_(ctx, "k_potential", st);
-      k_potential<<<grid_for(tiles_ub, 1), kPotTile, 0, st>>>(nn, tile_off, h.node_off, h.node_size, h.U,
-                                                             eps * eps, S);
-    }
-    RS_LAUNCHED(ctx, "k_potential");
-    {
-      ProfScope prof_(ctx, "k_potential_blocked", st);
-      k_potential_blocked<<<grid_for(big_ub, 1), kBlkThreads, 0, st>>>(nn, tile_big, h.node_off, h.node_size,
-                                                                      h.U, eps * eps, S);
-    }
-    RS_LAUNCHED(ctx, "k_potential_blocked");
+    RS_TRY(direct_potential(ctx, sur_min, nullptr, S, st));
     k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vsum, S, Gm, kCertB, bound,
                                            potential_out, ambig, n_ambig, sur_min, nullptr);
     RS_LAUNCHED(ctx, "k_flags");
@@ -522,26 +566,8 @@ int rs::unbind_nodes(rs_ctx* ctx, const int* only, const double* vsum, uint8_t* 
   Hier h = hier_of(ctx);
   const int64_t m = ctx->n_members, nn = ctx->n_nodes;
   float* S = static_cast<float*>(ctx->buf[S_U_PHI].ptr);
-  int64_t* tile_small = scratch_t<int64_t>(ctx, S_SELECT, size_t(nn) + 1);
-  int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
-  if (!tile_small || !tile_big) return RS_ERR_OOM;
   const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
-  const float eps = ctx->cfg.softening;
-  k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, 0, only, tile_small, tile_big);
-  RS_LAUNCHED(ctx, "k_tiles_split");
-  RS_TRY(exclusive_scan_i64(ctx, nn, tile_small, tile_small + nn, st));
-  RS_TRY(exclusive_scan_i64(ctx, nn, tile_big, tile_big + nn, st));
-  const int64_t tiles_ub = nn + m / kPotTile + 1;
-  const int64_t big_ub = m / (kBlockedMin + 1) + m / kBlkTile + 1;
-  k_potential<<<grid_for(tiles_ub, 1), kPotTile, 0, st>>>(nn, tile_small, h.node_off, h.node_size, h.U,
-                                                         eps * eps, S);
-  RS_LAUNCHED(ctx, "k_potential");
-  {
-    ProfScope prof_(ctx, "k_potential_blocked", st);
-    k_potential_blocked<<<grid_for(big_ub, 1), kBlkThreads, 0, st>>>(nn, tile_big, h.node_off, h.node_size,
-                                                                    h.U, eps * eps, S);
-  }
-  RS_LAUNCHED(ctx, "k_potential_blocked");
+  RS_TRY(direct_potential(ctx, 0, only, S, st));
   k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vsum, S, Gm, kCertB, bound, nullptr,
                                          ambig, n_ambig, 0, only);
   RS_LAUNCHED(ctx, "k_flags");
