@@ -82,17 +82,6 @@ k_gather_pos(int64_t n, const uint32_t* __restrict__ idx, const float* __restric
   posS[i] = make_float4(pos[3 * s], pos[3 * s + 1], pos[3 * s + 2], 0.f);
 }
 
-// row_start[r] = first sorted position whose row (key >> xb) is >= r, for r in [0, nrows].
-__global__ void __launch_bounds__(kThreads)
-k_row_start(int64_t n, const uint64_t* __restrict__ keys, int xb, int64_t nrows,
-            uint32_t* __restrict__ row_start) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i > n) return;
-  const int64_t r = (i < n) ? int64_t(keys[i] >> xb) : nrows;
-  const int64_t rp = (i == 0) ? -1 : int64_t(keys[i - 1] >> xb);
-  for (int64_t q = rp + 1; q <= r; ++q) row_start[q] = uint32_t(i);
-}
-
 __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* __restrict__ a, uint32_t lo,
                                                     uint32_t hi, uint64_t v) {
   while (lo < hi) {
@@ -100,6 +89,16 @@ __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* __restrict__
     if (a[mid] < v) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+// row_start[r] = first sorted position whose row (key >> xb) is >= r, for r in [0, nrows]: one
+// thread per row, binary search over the sorted keys (neighbouring rows share search paths).
+__global__ void __launch_bounds__(kThreads)
+k_row_start(int64_t n, const uint64_t* __restrict__ keys, int xb, int64_t nrows,
+            uint32_t* __restrict__ row_start) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r > nrows) return;
+  row_start[r] = lower_bound_u64(keys, 0u, uint32_t(n), uint64_t(r) << xb);
 }
 
 __device__ __forceinline__ uint32_t upper_bound_u64(const uint64_t* __restrict__ a, uint32_t lo,
@@ -272,7 +271,7 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
   RS_TRY(radix_sort_u64(ctx, n, 3 * g.xb, ka, va, kb, vb, &keys, &idx, st));
   k_gather_pos<<<grid, kThreads, 0, st>>>(n, idx, pos, posS);
   RS_LAUNCHED(ctx, "k_gather_pos");
-  k_row_start<<<grid_for(n + 1, kThreads), kThreads, 0, st>>>(n, keys, g.xb, g.nrows, row_start);
+  k_row_start<<<grid_for(g.nrows + 1, kThreads), kThreads, 0, st>>>(n, keys, g.xb, g.nrows, row_start);
   RS_LAUNCHED(ctx, "k_row_start");
   {
     ProfScope prof_(ctx, "k_cell_bounds", st);

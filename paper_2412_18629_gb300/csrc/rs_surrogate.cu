@@ -23,7 +23,7 @@
 
 namespace rs {
 int mlp_forward(rs_ctx* ctx, int64_t n, const float* x, float* y, cudaStream_t st);
-int surrogate_unbind(rs_ctx* ctx, const double* vsum, uint8_t* bound, unsigned long long* counters,
+int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned long long* counters,
                      cudaStream_t st);
 }  // namespace rs
 
@@ -174,7 +174,7 @@ __global__ void k_sur_features(int64_t ns, const uint32_t* __restrict__ sur_mem,
                                const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_off,
                                const int64_t* __restrict__ node_size, const float4* __restrict__ U,
                                const float4* __restrict__ V, const NodeStat* __restrict__ st,
-                               const double* __restrict__ vsum, const uint64_t* __restrict__ rkeys,
+                               const double* __restrict__ vbulk, const uint64_t* __restrict__ rkeys,
                                const float* __restrict__ psi_sph, const uint32_t* __restrict__ mem,
                                const int64_t* __restrict__ deepest,
                                const uint32_t* __restrict__ deepest_pos, float* __restrict__ feat) {
@@ -189,9 +189,8 @@ __global__ void k_sur_features(int64_t ns, const uint32_t* __restrict__ sur_mem,
   const float f1 = float(count_below(rkeys, lo, hi, r)) * inv_g;
   const float f2 = float(count_below(rkeys, lo, hi, 2.0f * r)) * inv_g;
   const float4 v = V[p];
-  const double gd = double(g);
-  const float dvx = v.x - float(vsum[3 * q] / gd), dvy = v.y - float(vsum[3 * q + 1] / gd),
-              dvz = v.z - float(vsum[3 * q + 2] / gd);
+  const float dvx = v.x - float(vbulk[3 * q]), dvy = v.y - float(vbulk[3 * q + 1]),
+              dvz = v.z - float(vbulk[3 * q + 2]);
   const uint32_t part = mem[p];
   const int64_t d = deepest[part];
   const float sub = psi_sph[deepest_pos[part]] * (float(node_size[d]) / float(g)) *
@@ -217,10 +216,10 @@ __global__ void k_sur_targets(int64_t ns, const uint32_t* __restrict__ sur_mem,
   psi[k] = float(-double(S[p]) * double(st[q].r_vir) / double(node_size[q]));
 }
 
-__device__ __forceinline__ double kinetic(float4 v, const double* vsum, double g) {
-  const double dvx = __dsub_rn(double(v.x), __ddiv_rn(vsum[0], g));
-  const double dvy = __dsub_rn(double(v.y), __ddiv_rn(vsum[1], g));
-  const double dvz = __dsub_rn(double(v.z), __ddiv_rn(vsum[2], g));
+__device__ __forceinline__ double kinetic(float4 v, const double* vb) {
+  const double dvx = __dsub_rn(double(v.x), vb[0]);
+  const double dvy = __dsub_rn(double(v.y), vb[1]);
+  const double dvz = __dsub_rn(double(v.z), vb[2]);
   const double s = __dadd_rn(__dadd_rn(__dmul_rn(dvx, dvx), __dmul_rn(dvy, dvy)), __dmul_rn(dvz, dvz));
   return __dmul_rn(0.5, s);
 }
@@ -230,7 +229,7 @@ __device__ __forceinline__ double kinetic(float4 v, const double* vsum, double g
 // sums, [8] members of nodes sent whole to the direct sum
 __global__ void k_sur_gate(int64_t ns, const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
                            const int64_t* __restrict__ node_size, const float4* __restrict__ V,
-                           const double* __restrict__ vsum, const NodeStat* __restrict__ st,
+                           const double* __restrict__ vbulk, const NodeStat* __restrict__ st,
                            const float* __restrict__ psi_hat, float thr_psi, uint8_t* __restrict__ bound,
                            uint8_t* __restrict__ sflag, float* __restrict__ margin,
                            unsigned int* __restrict__ gcount, unsigned int* __restrict__ ecount,
@@ -239,7 +238,7 @@ __global__ void k_sur_gate(int64_t ns, const uint32_t* __restrict__ sur_mem, con
   if (k >= ns) return;
   const uint32_t p = sur_mem[k], q = mnode[p];
   const double gmr = st[q].gm_over_rvir;
-  const double e = kinetic(V[p], vsum + 3 * int64_t(q), double(node_size[q])) + double(psi_hat[k]) * gmr;
+  const double e = kinetic(V[p], vbulk + 3 * int64_t(q)) + double(psi_hat[k]) * gmr;
   const double thr = double(thr_psi) * gmr;
   if (fabs(e) > thr) {
     const uint8_t f = e < 0.0 ? 1 : 0;
@@ -342,7 +341,7 @@ __global__ void __launch_bounds__(kT)
 k_pot_member(const unsigned long long* __restrict__ count, const uint32_t* __restrict__ list,
              const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
              const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
-             const float4* __restrict__ U, const float4* __restrict__ V, const double* __restrict__ vsum,
+             const float4* __restrict__ U, const float4* __restrict__ V, const double* __restrict__ vbulk,
              float eps2, double Gm, float* __restrict__ Sx, uint8_t* __restrict__ bound,
              uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig) {
   const int lane = threadIdx.x & 31;
@@ -378,7 +377,7 @@ k_pot_member(const unsigned long long* __restrict__ count, const uint32_t* __res
     if (lane == 0) {
       Sx[k] = S;
       const double ph = -__dmul_rn(Gm, double(S));
-      const double e = __dadd_rn(kinetic(V[p], vsum + 3 * int64_t(q), double(g)), ph);
+      const double e = __dadd_rn(kinetic(V[p], vbulk + 3 * int64_t(q)), ph);
       if (fabs(e) > __dmul_rn(2.0 * kCertB2, fabs(ph))) {
         bound[p] = e < 0.0 ? 1 : 0;
       } else {
@@ -441,13 +440,13 @@ int bits_for(uint64_t v) {
 
 namespace rs {
 int unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
-                    const double* vsum, uint8_t* bound, cudaStream_t st);
-int unbind_nodes(rs_ctx* ctx, const int* only, const double* vsum, uint8_t* bound,
+                    const double* vbulk, uint8_t* bound, cudaStream_t st);
+int unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t* bound,
                  uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st);
 
 // Shared set-up: big-node member list, node statistics, radial sort, features.
 // Returns the number of surrogate members through *ns_out (host).
-static int sur_prepare(rs_ctx* ctx, const double* vsum, int64_t* ns_out, cudaStream_t st) {
+static int sur_prepare(rs_ctx* ctx, const double* vbulk, int64_t* ns_out, cudaStream_t st) {
   Hier h = hier_of(ctx);
   const int64_t nn = ctx->n_nodes, m = ctx->n_members;
   int64_t* sur_off = scratch_t<int64_t>(ctx, S_SUR_OFF, size_t(nn) + 1);
@@ -506,19 +505,19 @@ static int sur_prepare(rs_ctx* ctx, const double* vsum, int64_t* ns_out, cudaStr
   {
     ProfScope prof_(ctx, "k_sur_features", st);
     k_sur_features<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_off, h.node_size, h.U,
-                                                   h.V, stt, vsum, rkeys, psi_sph, h.mem, h.deepest,
+                                                   h.V, stt, vbulk, rkeys, psi_sph, h.mem, h.deepest,
                                                    h.deepest_pos, feat);
   }
   RS_LAUNCHED(ctx, "k_sur_features");
   return RS_OK;
 }
 
-int surrogate_unbind(rs_ctx* ctx, const double* vsum, uint8_t* bound, unsigned long long* counters,
+int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned long long* counters,
                      cudaStream_t st) {
   Hier h = hier_of(ctx);
   const int64_t nn = ctx->n_nodes;
   int64_t ns = 0;
-  RS_TRY(sur_prepare(ctx, vsum, &ns, st));
+  RS_TRY(sur_prepare(ctx, vbulk, &ns, st));
   ctx->sur_members = ns;
   if (ns == 0) return RS_OK;
   const NodeStat* stt = static_cast<const NodeStat*>(ctx->buf[S_SUR_STAT].ptr);
@@ -548,7 +547,7 @@ int surrogate_unbind(rs_ctx* ctx, const double* vsum, uint8_t* bound, unsigned l
   RS_CUDA(ctx, cudaMemsetAsync(fail, 0, 4 * nn, st));
   RS_CUDA(ctx, cudaMemsetAsync(full, 0, 4 * nn, st));
   const float thr_psi = ctx->cfg.margin_factor * ctx->mlp_err_max;
-  k_sur_gate<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_size, h.V, vsum, stt, psi_hat,
+  k_sur_gate<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_size, h.V, vbulk, stt, psi_hat,
                                              thr_psi, bound, sflag, margin, gcount, ecount, counters);
   RS_LAUNCHED(ctx, "k_sur_gate");
   if (ctx->sur_nbig > 0) {
@@ -559,7 +558,7 @@ int surrogate_unbind(rs_ctx* ctx, const double* vsum, uint8_t* bound, unsigned l
   k_sur_exact_list<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, sflag, full, exact_list, counters);
   RS_LAUNCHED(ctx, "k_sur_exact_list");
   // nodes mostly outside the gate: whole-node blocked direct sum
-  RS_TRY(unbind_nodes(ctx, full, vsum, bound, ambig, counters + 2, st));
+  RS_TRY(unbind_nodes(ctx, full, vbulk, bound, ambig, counters + 2, st));
   k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 7);
   RS_LAUNCHED(ctx, "k_acc_counter");
   if (ctx->sur_nbig > 0) {
@@ -579,10 +578,10 @@ int surrogate_unbind(rs_ctx* ctx, const double* vsum, uint8_t* bound, unsigned l
     {
       ProfScope prof_(ctx, "k_pot_member", st);
       k_pot_member<<<grid, kT, 0, st>>>(counters + pass, list, sur_mem, h.mnode, h.node_off, h.node_size,
-                                        h.U, h.V, vsum, eps * eps, Gm, Sx, bound, ambig, counters + 2);
+                                        h.U, h.V, vbulk, eps * eps, Gm, Sx, bound, ambig, counters + 2);
     }
     RS_LAUNCHED(ctx, "k_pot_member");
-    RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vsum, bound, st));
+    RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vbulk, bound, st));
     k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
     RS_LAUNCHED(ctx, "k_acc_counter");
   }
@@ -595,10 +594,10 @@ int surrogate_unbind(rs_ctx* ctx, const double* vsum, uint8_t* bound, unsigned l
   {
     ProfScope prof_(ctx, "k_pot_member", st);
     k_pot_member<<<grid, kT, 0, st>>>(counters + 3, exact_list, sur_mem, h.mnode, h.node_off, h.node_size,
-                                      h.U, h.V, vsum, eps * eps, Gm, Sx, bound, ambig, counters + 2);
+                                      h.U, h.V, vbulk, eps * eps, Gm, Sx, bound, ambig, counters + 2);
   }
   RS_LAUNCHED(ctx, "k_pot_member");
-  RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vsum, bound, st));
+  RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vbulk, bound, st));
   k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
   RS_LAUNCHED(ctx, "k_acc_counter");
   k_count_fail<<<grid_for(nn, kT), kT, 0, st>>>(nn, fail, counters);
@@ -618,9 +617,9 @@ extern "C" int rs_surrogate_features(rs_ctx* ctx, float* feat_out, float* psi_ou
     return set_error(ctx, RS_ERR_STATE, "targets need an rs_unbind without the surrogate");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   RS_CUDA(ctx, cudaSetDevice(ctx->device));
-  const double* vsum = static_cast<const double*>(ctx->buf[S_U_VBULK].ptr);
+  const double* vbulk = static_cast<const double*>(ctx->buf[S_U_VBULK].ptr);
   int64_t ns = 0;
-  RS_TRY(sur_prepare(ctx, vsum, &ns, st));
+  RS_TRY(sur_prepare(ctx, vbulk, &ns, st));
   *n_out = ns;
   if (ns == 0) return RS_OK;
   if (feat_out)

@@ -18,11 +18,11 @@
 namespace rs {
 int gather_members(rs_ctx* ctx, int64_t mb, int64_t me, int64_t nb, int64_t ne, const float* pos,
                    const float* vel, cudaStream_t st);
-int surrogate_unbind(rs_ctx* ctx, const double* vsum, uint8_t* bound, unsigned long long* counters,
+int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned long long* counters,
                      cudaStream_t st);
 int unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
-                    const double* vsum, uint8_t* bound, cudaStream_t st);
-int unbind_nodes(rs_ctx* ctx, const int* only, const double* vsum, uint8_t* bound,
+                    const double* vbulk, uint8_t* bound, cudaStream_t st);
+int unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t* bound,
                  uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st);
 }  // namespace rs
 
@@ -236,16 +236,24 @@ struct VelTerm {
   }
 };
 
-__device__ __forceinline__ double kinetic(float4 v, const double* vsum, double g) {
-  const double dvx = __dsub_rn(double(v.x), __ddiv_rn(vsum[0], g));
-  const double dvy = __dsub_rn(double(v.y), __ddiv_rn(vsum[1], g));
-  const double dvz = __dsub_rn(double(v.z), __ddiv_rn(vsum[2], g));
+// Bulk velocity of every node, vbulk = (canonical-order sum of v) / g, in place (one float64
+// division per node and axis instead of one per member).
+__global__ void k_vbulk(int64_t nn, const int64_t* __restrict__ node_size, double* __restrict__ v) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= 3 * nn) return;
+  v[k] = __ddiv_rn(v[k], double(node_size[k / 3]));
+}
+
+__device__ __forceinline__ double kinetic(float4 v, const double* vb) {
+  const double dvx = __dsub_rn(double(v.x), vb[0]);
+  const double dvy = __dsub_rn(double(v.y), vb[1]);
+  const double dvz = __dsub_rn(double(v.z), vb[2]);
   const double s = __dadd_rn(__dadd_rn(__dmul_rn(dvx, dvx), __dmul_rn(dvy, dvy)), __dmul_rn(dvz, dvz));
   return __dmul_rn(0.5, s);
 }
 
 __global__ void k_flags(int64_t m, const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_size,
-                        const float4* __restrict__ V, const double* __restrict__ vsum,
+                        const float4* __restrict__ V, const double* __restrict__ vbulk,
                         const float* __restrict__ S, double Gm, double certB,
                         uint8_t* __restrict__ bound, float* __restrict__ phi_out,
                         uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig,
@@ -254,7 +262,7 @@ __global__ void k_flags(int64_t m, const uint32_t* __restrict__ mnode, const int
   if (p >= m) return;
   const uint32_t q = mnode[p];
   if (only ? (only[q] == 0) : (sur_min > 0 && node_size[q] >= sur_min)) return;  // other path
-  const double ke = kinetic(V[p], vsum + 3 * int64_t(q), double(node_size[q]));
+  const double ke = kinetic(V[p], vbulk + 3 * int64_t(q));
   const double ph = -__dmul_rn(Gm, double(S[p]));
   const double e = __dadd_rn(ke, ph);
   if (phi_out) phi_out[p] = __double2float_rn(ph);
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(kT)
 k_fallback(const unsigned long long* __restrict__ n_ambig, const uint32_t* __restrict__ ambig,
            const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_off,
            const int64_t* __restrict__ node_size, const float4* __restrict__ U,
-           const float4* __restrict__ V, const double* __restrict__ vsum, double eps2, double Gm,
+           const float4* __restrict__ V, const double* __restrict__ vbulk, double eps2, double Gm,
            uint8_t* __restrict__ bound, float* __restrict__ phi_out) {
   const int lane = threadIdx.x & 31;
   const unsigned long long total = *n_ambig;
@@ -307,7 +315,7 @@ k_fallback(const unsigned long long* __restrict__ n_ambig, const uint32_t* __res
     }
     if (lane == 0) {
       const double ph = -__dmul_rn(Gm, tree.result());
-      const double ke = kinetic(V[p], vsum + 3 * int64_t(q), double(g));
+      const double ke = kinetic(V[p], vbulk + 3 * int64_t(q));
       bound[p] = __dadd_rn(ke, ph) < 0.0 ? 1 : 0;
       if (phi_out) phi_out[p] = __double2float_rn(ph);
     }
@@ -502,12 +510,12 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
   uint8_t* bound = scratch_t<uint8_t>(ctx, S_U_BOUND, size_t(std::max<int64_t>(m, 1)));
   float* S = scratch_t<float>(ctx, S_U_PHI, size_t(std::max<int64_t>(m, 1)));
   unsigned long long* nb = scratch_t<unsigned long long>(ctx, S_U_NB, size_t(std::max<int64_t>(nn, 1)));
-  double* vsum = scratch_t<double>(ctx, S_U_VBULK, size_t(std::max<int64_t>(nn, 1)) * 3);
+  double* vbulk = scratch_t<double>(ctx, S_U_VBULK, size_t(std::max<int64_t>(nn, 1)) * 3);
   uint32_t* ambig = scratch_t<uint32_t>(ctx, S_U_AMBIG, size_t(std::max<int64_t>(m, 1)));
   uint8_t* halo = scratch_t<uint8_t>(ctx, S_U_FLAGS, size_t(std::max<int64_t>(nn, 1)));
   // counters: [0..6] surrogate path (rs_surrogate.cu), [7] float64 fallbacks of the direct sums
   unsigned long long* counters = scratch_t<unsigned long long>(ctx, S_SUR_COUNTERS, 16);
-  if (!bound || !S || !nb || !vsum || !ambig || !halo || !counters) return RS_ERR_OOM;
+  if (!bound || !S || !nb || !vbulk || !ambig || !halo || !counters) return RS_ERR_OOM;
   unsigned long long* n_ambig = counters + 7;
   int64_t nfb = 0;
   for (int i = 0; i < 10; ++i) ctx->sur_stats[i] = 0;
@@ -515,18 +523,20 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
     const float eps = ctx->cfg.softening;
     RS_CUDA(ctx, cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned long long), st));
-    RS_TRY((cro_segmented<3, VelTerm>(ctx, nn, h.node_off, h.node_size, m, VelTerm{h.V}, vsum, st)));
+    RS_TRY((cro_segmented<3, VelTerm>(ctx, nn, h.node_off, h.node_size, m, VelTerm{h.V}, vbulk, st)));
+    k_vbulk<<<grid_for(3 * nn, kT), kT, 0, st>>>(nn, h.node_size, vbulk);  // sums -> bulk velocities
+    RS_LAUNCHED(ctx, "k_vbulk");
     RS_TRY(direct_potential(ctx, sur_min, nullptr, S, st));
-    k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vsum, S, Gm, kCertB, bound,
+    k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vbulk, S, Gm, kCertB, bound,
                                            potential_out, ambig, n_ambig, sur_min, nullptr);
     RS_LAUNCHED(ctx, "k_flags");
     {
       ProfScope prof_(ctx, "k_fallback", st);
       k_fallback<<<152 * 8, kT, 0, st>>>(n_ambig, ambig, h.mnode, h.node_off, h.node_size, h.U, h.V,
-                                         vsum, double(eps) * double(eps), Gm, bound, potential_out);
+                                         vbulk, double(eps) * double(eps), Gm, bound, potential_out);
     }
     RS_LAUNCHED(ctx, "k_fallback");
-    if (sur) RS_TRY(surrogate_unbind(ctx, vsum, bound, counters, st));
+    if (sur) RS_TRY(surrogate_unbind(ctx, vbulk, bound, counters, st));
     RS_CUDA(ctx, cudaMemsetAsync(nb, 0, 8 * nn, st));
     k_bound_count<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, bound, nb);
     RS_LAUNCHED(ctx, "k_bound_count");
@@ -561,27 +571,27 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
 
 // Exact unbinding of the nodes flagged in `only` (int [n_nodes]): register-blocked float32
 // potential of all their members, certified flags, float64 fallback for the ambiguous ones.
-int rs::unbind_nodes(rs_ctx* ctx, const int* only, const double* vsum, uint8_t* bound,
+int rs::unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t* bound,
                      uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st) {
   Hier h = hier_of(ctx);
   const int64_t m = ctx->n_members, nn = ctx->n_nodes;
   float* S = static_cast<float*>(ctx->buf[S_U_PHI].ptr);
   const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
   RS_TRY(direct_potential(ctx, 0, only, S, st));
-  k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vsum, S, Gm, kCertB, bound, nullptr,
+  k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vbulk, S, Gm, kCertB, bound, nullptr,
                                          ambig, n_ambig, 0, only);
   RS_LAUNCHED(ctx, "k_flags");
-  return unbind_fallback(ctx, n_ambig, ambig, vsum, bound, st);
+  return unbind_fallback(ctx, n_ambig, ambig, vbulk, bound, st);
 }
 
 int rs::unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
-                        const double* vsum, uint8_t* bound, cudaStream_t st) {
+                        const double* vbulk, uint8_t* bound, cudaStream_t st) {
   Hier h = hier_of(ctx);
   const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
   const double eps = ctx->cfg.softening;
   {
     ProfScope prof_(ctx, "k_fallback", st);
-    k_fallback<<<152 * 8, kT, 0, st>>>(n_ambig, ambig, h.mnode, h.node_off, h.node_size, h.U, h.V, vsum,
+    k_fallback<<<152 * 8, kT, 0, st>>>(n_ambig, ambig, h.mnode, h.node_off, h.node_size, h.U, h.V, vbulk,
                                        eps * eps, Gm, bound, nullptr);
   }
   RS_LAUNCHED(ctx, "k_fallback");
