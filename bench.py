@@ -231,6 +231,7 @@ def _roofline(prof, pairs, steps):
 
 
 TRAIN_SAMPLES = 1_000_000
+TRAIN_EPOCHS = 30
 
 
 def train_surrogate(ctx, workload, device, samples=None):
@@ -255,12 +256,13 @@ def train_surrogate(ctx, workload, device, samples=None):
     x, t = x[sel].contiguous(), t[sel].contiguous()
     t0 = time.perf_counter()
     rs.rs_mlp_set_params(tctx, np.zeros(rs.MLP_PARAMS, np.float32))
-    err_max, mse = rs.rs_mlp_train(tctx, x, t, epochs=12, batch=4096, lr=1e-3, seed=100)
+    err_max, mse = rs.rs_mlp_train(tctx, x, t, epochs=TRAIN_EPOCHS, batch=4096, lr=1e-3, seed=100)
     dt = time.perf_counter() - t0
     rs.rs_mlp_set_params(ctx, rs.rs_mlp_get_params(tctx))
     rs.rs_mlp_set_err_max(ctx, err_max)
     tctx.close()
-    return {"samples": int(k), "err_max_psi": err_max, "last_batch_mse": mse, "train_s": dt,
+    return {"samples": int(k), "epochs": TRAIN_EPOCHS, "err_max_psi": err_max, "last_batch_mse": mse,
+            "train_s": dt,
             "snapshot": f"{workload} generator, seed 100"}
 
 

@@ -30,6 +30,7 @@ enum Slot : int {
   // hierarchy state (persists until the next rs_fof6d)
   S_H_MEM, S_H_MNODE, S_H_U, S_H_V, S_H_NODE_OFF, S_H_NODE_SIZE, S_H_NODE_PARENT,
   S_H_NODE_LEVEL, S_H_NODE_MINID, S_H_NODE_REF, S_H_NODE_INV, S_H_DEEPEST, S_H_DEEPPOS, S_H_WORK,
+  S_H_NODE_MOM,
   // rs_unbind / rs_halo_props state
   S_U_PHI, S_U_BOUND, S_U_NB, S_U_VBULK, S_U_AMBIG, S_U_FLAGS, S_U_TILEBIG,
   S_U_TILEPERM, S_U_OKEY_A, S_U_OKEY_B, S_U_OVAL_A, S_U_OVAL_B,
@@ -43,6 +44,7 @@ enum Slot : int {
   S_SUR_OFF, S_SUR_RANK, S_SUR_STAT, S_SUR_MEM, S_SUR_BIG, S_SUR_FEAT, S_SUR_PSI, S_SUR_MARGIN,
   S_SUR_SFLAG, S_SUR_CHECKED, S_SUR_SX, S_SUR_LIST_A, S_SUR_LIST_B, S_SUR_GCOUNT, S_SUR_TAU,
   S_SUR_FAIL, S_SUR_COUNTERS, S_SUR_FIX, S_SUR_SPOS, S_SUR_PSISPH, S_SUR_ECOUNT, S_SUR_FULL,
+  S_SUR_MP, S_SUR_ERRN, S_SUR_LIST_C, S_SUR_LSCAN, S_SUR_LOFS, S_SUR_TILES,
   S_NUM_SLOTS
 };
 
@@ -173,6 +175,7 @@ struct Hier {
   int32_t* node_level;
   int64_t* node_minid;
   float4* inv;         // (inv_sx2, inv_sv2, l2, 0) of the node's 6D split
+  float4* mom;         // (mean u, sigma_v,1D) as float, from the same canonical-order moments
   float4* ref;         // reference member position
   int64_t* deepest;    // [n] deepest node per particle, -1 if none
   uint32_t* deepest_pos;  // [n] member position of the particle in its deepest node

@@ -190,8 +190,11 @@ __device__ __forceinline__ double total_var(const double* S, const double* Q, do
   return var;
 }
 
+// Metric scales of the node's split, and (mean u, sigma_v,1D) in float32 for the surrogate's
+// features.
 __global__ void k_node_inv(int64_t nb, int64_t nn, const int64_t* __restrict__ node_size,
-                           const double* __restrict__ sums, float4* __restrict__ inv) {
+                           const double* __restrict__ sums, float4* __restrict__ inv,
+                           float4* __restrict__ mom) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= nn) return;
   const double g = double(node_size[nb + k]);
@@ -201,6 +204,8 @@ __global__ void k_node_inv(int64_t nb, int64_t nn, const int64_t* __restrict__ n
   const float ix = vx > 0.0 ? __double2float_rn(__ddiv_rn(1.0, vx)) : 0.f;
   const float iv = vv > 0.0 ? __double2float_rn(__ddiv_rn(1.0, vv)) : 0.f;
   inv[nb + k] = make_float4(ix, iv, 0.f, 0.f);
+  mom[nb + k] = make_float4(float(__ddiv_rn(S[0], g)), float(__ddiv_rn(S[1], g)), float(__ddiv_rn(S[2], g)),
+                            float(sqrt(fmax(vv, 0.0) / 3.0)));
 }
 
 __device__ __forceinline__ float d6(float4 ui, float4 vi, float4 uj, float4 vj, float isx, float isv) {
@@ -462,6 +467,7 @@ Hier hier_of(rs_ctx* ctx) {
   h.node_level = static_cast<int32_t*>(ctx->buf[S_H_NODE_LEVEL].ptr);
   h.node_minid = static_cast<int64_t*>(ctx->buf[S_H_NODE_MINID].ptr);
   h.inv = static_cast<float4*>(ctx->buf[S_H_NODE_INV].ptr);
+  h.mom = static_cast<float4*>(ctx->buf[S_H_NODE_MOM].ptr);
   h.ref = static_cast<float4*>(ctx->buf[S_H_NODE_REF].ptr);
   h.deepest = static_cast<int64_t*>(ctx->buf[S_H_DEEPEST].ptr);
   h.deepest_pos = static_cast<uint32_t*>(ctx->buf[S_H_DEEPPOS].ptr);
@@ -506,6 +512,7 @@ static int ensure_nodes(rs_ctx* ctx, int64_t used, int64_t need, cudaStream_t st
   RS_TRY(grow_keep(ctx, S_H_NODE_LEVEL, size_t(used) * 4, size_t(need) * 4, st));
   RS_TRY(grow_keep(ctx, S_H_NODE_MINID, size_t(used) * 8, size_t(need) * 8, st));
   RS_TRY(grow_keep(ctx, S_H_NODE_INV, size_t(used) * 16, size_t(need) * 16, st));
+  RS_TRY(grow_keep(ctx, S_H_NODE_MOM, size_t(used) * 16, size_t(need) * 16, st));
   RS_TRY(grow_keep(ctx, S_H_NODE_REF, size_t(used) * 16, size_t(need) * 16, st));
   return RS_OK;
 }
@@ -624,7 +631,7 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     if (!sums) return RS_ERR_OOM;
     RS_TRY((cro_segmented<12, MomentTerm>(ctx, nn, h.node_off + nb, h.node_size + nb, m,
                                           MomentTerm{h.U, h.V}, sums, st)));
-    k_node_inv<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, sums, h.inv);
+    k_node_inv<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, sums, h.inv, h.mom);
     RS_LAUNCHED(ctx, "k_node_inv");
     // tiles of 128 members
     int64_t* tile_off = scratch_t<int64_t>(ctx, S_SELECT, size_t(nn) + 1);

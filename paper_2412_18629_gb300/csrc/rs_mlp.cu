@@ -6,7 +6,8 @@
 //   bf16(master); b1, b2, b3 float32.
 //   z1 = b1 + W1^T x~   (float32 accumulation)      h1 = bf16(max(z1, 0))
 //   z2 = b2 + W2^T h1                                h2 = bf16(max(z2, 0))
-//   y  = b3 + sum_k W3[k] h2[k]  (float32, k = 0..63 in order)
+//   y  = b3 + sum_k W3[k] h2[k]  (float32: four partial sums over the columns 16 s + 2q +
+//        {0, 1, 8, 9}, s = 0..3, for q = 0..3, combined as (p0 + p1) + (p2 + p3))
 // Loss over a batch of B samples: L = (1/B) sum (y - t)^2. Backward: dy = 2 (y - t) / B;
 //   dW3 = sum_b dy h2; db3 = sum_b dy; dz2 = bf16(dy W3 [h2 > 0]); db2 = sum_b dz2;
 //   dW2 = sum_b h1 dz2^T; dz1 = bf16((W2 dz2) [h1 > 0]); db1 = sum_b dz1; dW1 = sum_b x~ dz1^T.
@@ -35,8 +36,12 @@ constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kRowsPerBlock = kWarps * 16;  // 128 samples per block in the training kernel
 
-// Device copy of the weights used by the kernels.
+// Device copy of the weights used by the kernels: the B fragments of W1 and W2 for
+// mma.m16n8k16 already packed per (k-slice, n-tile, lane), and the row-major bf16 matrices the
+// backward pass reads.
 struct MlpDev {
+  uint2 f1[8][32];            // W1 fragments: [n-tile][lane]
+  uint2 f2[4][8][32];         // W2 fragments: [k-slice][n-tile][lane]
   __nv_bfloat16 w1[16 * 64];  // [in 16][out 64], rows 8..15 zero
   __nv_bfloat16 w2[64 * 64];  // [in 64][out 64]
   __nv_bfloat16 w3[64];
@@ -54,15 +59,6 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
       "{%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// B fragment of a [K][N] row-major bf16 matrix for k-slice ks (16) and n-tile nt (8).
-__device__ __forceinline__ void load_b(const __nv_bfloat16* W, int ldn, int ks, int nt, int lane,
-                                       uint32_t& b0, uint32_t& b1) {
-  const int g = lane >> 2, q = lane & 3;
-  const int n = nt * 8 + g, k = ks * 16 + 2 * q;
-  b0 = pack2(W[(k + 0) * ldn + n], W[(k + 1) * ldn + n]);
-  b1 = pack2(W[(k + 8) * ldn + n], W[(k + 9) * ldn + n]);
 }
 
 // Forward of 16 samples held by one warp. xa: A fragment of x~ (one k-slice). Produces the
@@ -85,9 +81,8 @@ __device__ __forceinline__ void fwd16(const MlpDev& W, const uint32_t (&xa)[4], 
     acc[nt][1] = c1;
     acc[nt][2] = c0;
     acc[nt][3] = c1;
-    uint32_t b0, b1;
-    load_b(W.w1, 64, 0, nt, lane, b0, b1);
-    mma_bf16(acc[nt], xa[0], xa[1], xa[2], xa[3], b0, b1);
+    const uint2 b = W.f1[nt][lane];
+    mma_bf16(acc[nt], xa[0], xa[1], xa[2], xa[3], b.x, b.y);
   }
   // h1 = bf16(relu(z1)) as A fragments: k-slice s = n-tiles 2s, 2s+1
 #pragma unroll
@@ -109,9 +104,8 @@ __device__ __forceinline__ void fwd16(const MlpDev& W, const uint32_t (&xa)[4], 
     acc[nt][3] = c1;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      uint32_t b0, b1;
-      load_b(W.w2, 64, s, nt, lane, b0, b1);
-      mma_bf16(acc[nt], f.h1[s][0], f.h1[s][1], f.h1[s][2], f.h1[s][3], b0, b1);
+      const uint2 b = W.f2[s][nt][lane];
+      mma_bf16(acc[nt], f.h1[s][0], f.h1[s][1], f.h1[s][2], f.h1[s][3], b.x, b.y);
     }
   }
 #pragma unroll
@@ -123,26 +117,31 @@ __device__ __forceinline__ void fwd16(const MlpDev& W, const uint32_t (&xa)[4], 
     f.h2[s][2] = pack2(__float2bfloat16_rn(fmaxf(hi[0], 0.f)), __float2bfloat16_rn(fmaxf(hi[1], 0.f)));
     f.h2[s][3] = pack2(__float2bfloat16_rn(fmaxf(hi[2], 0.f)), __float2bfloat16_rn(fmaxf(hi[3], 0.f)));
   }
-  // layer 3 in float32, k in order: every lane holds, for rows g and g+8, the h2 columns
-  // 16 s + 2q + {0, 1, 8, 9}; gather the 64 terms of each row in k order through shuffles.
-  float ylo = W.b3, yhi = W.b3;
-  const int g = lane >> 2;
+  // layer 3 in float32: each lane's partial sum over the 16 h2 columns it holds (16 s + 2q +
+  // {0, 1, 8, 9}, s = 0..3, in that order), then the quad's four partials by an xor tree,
+  // then the bias.
+  float plo = 0.f, phi = 0.f;
 #pragma unroll
-  for (int k = 0; k < 64; ++k) {
-    const int s = k >> 4, r = k & 15;
-    const int qq = (r & 7) >> 1;                    // owner lane's q
-    const int half = (r >= 8) ? 1 : 0;              // register pair 2/3 (cols +8) or 0/1
-    const int odd = r & 1;
-    const uint32_t vlo = __shfl_sync(0xffffffffu, f.h2[s][half ? 2 : 0], g * 4 + qq);
-    const uint32_t vhi = __shfl_sync(0xffffffffu, f.h2[s][half ? 3 : 1], g * 4 + qq);
-    const float hl = __uint_as_float((odd ? (vlo & 0xffff0000u) : (vlo << 16)));
-    const float hh = __uint_as_float((odd ? (vhi & 0xffff0000u) : (vhi << 16)));
-    const float w = __bfloat162float(W.w3[k]);
-    ylo = __fmaf_rn(w, hl, ylo);
-    yhi = __fmaf_rn(w, hh, yhi);
+  for (int s = 0; s < 4; ++s) {
+    const int c = 16 * s + 2 * q;
+    const float w0 = __bfloat162float(W.w3[c]), w1 = __bfloat162float(W.w3[c + 1]);
+    const float w8 = __bfloat162float(W.w3[c + 8]), w9 = __bfloat162float(W.w3[c + 9]);
+    plo = __fmaf_rn(w0, __uint_as_float(f.h2[s][0] << 16), plo);
+    plo = __fmaf_rn(w1, __uint_as_float(f.h2[s][0] & 0xffff0000u), plo);
+    plo = __fmaf_rn(w8, __uint_as_float(f.h2[s][2] << 16), plo);
+    plo = __fmaf_rn(w9, __uint_as_float(f.h2[s][2] & 0xffff0000u), plo);
+    phi = __fmaf_rn(w0, __uint_as_float(f.h2[s][1] << 16), phi);
+    phi = __fmaf_rn(w1, __uint_as_float(f.h2[s][1] & 0xffff0000u), phi);
+    phi = __fmaf_rn(w8, __uint_as_float(f.h2[s][3] << 16), phi);
+    phi = __fmaf_rn(w9, __uint_as_float(f.h2[s][3] & 0xffff0000u), phi);
   }
-  f.y_lo = ylo;
-  f.y_hi = yhi;
+#pragma unroll
+  for (int off = 1; off <= 2; off <<= 1) {
+    plo = __fadd_rn(plo, __shfl_xor_sync(0xffffffffu, plo, off));
+    phi = __fadd_rn(phi, __shfl_xor_sync(0xffffffffu, phi, off));
+  }
+  f.y_lo = __fadd_rn(W.b3, plo);
+  f.y_hi = __fadd_rn(W.b3, phi);
 }
 
 // A fragment of x~ for the warp's 16 rows (row0 = first sample), from float [n][8] features.
@@ -417,8 +416,28 @@ __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __re
   w[p] = wn;
 }
 
+__device__ __forceinline__ __nv_bfloat16 w1_at(const float* __restrict__ w, int in, int out) {
+  return __float2bfloat16_rn(in < 8 ? w[kOffW1 + in * 64 + out] : 0.f);
+}
+
+__device__ __forceinline__ __nv_bfloat16 w2_at(const float* __restrict__ w, int in, int out) {
+  return __float2bfloat16_rn(w[kOffW2 + in * 64 + out]);
+}
+
 __global__ void k_pack_weights(const float* __restrict__ w, MlpDev* __restrict__ dev) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < 8 * 32) {  // W1 fragments (one k-slice)
+    const int nt = p / 32, lane = p % 32, g = lane >> 2, q = lane & 3;
+    const int n = nt * 8 + g, k = 2 * q;
+    dev->f1[nt][lane] = make_uint2(pack2(w1_at(w, k, n), w1_at(w, k + 1, n)),
+                                   pack2(w1_at(w, k + 8, n), w1_at(w, k + 9, n)));
+  }
+  if (p < 4 * 8 * 32) {  // W2 fragments
+    const int ks = p / 256, nt = (p / 32) % 8, lane = p % 32, g = lane >> 2, q = lane & 3;
+    const int n = nt * 8 + g, k = ks * 16 + 2 * q;
+    dev->f2[ks][nt][lane] = make_uint2(pack2(w2_at(w, k, n), w2_at(w, k + 1, n)),
+                                       pack2(w2_at(w, k + 8, n), w2_at(w, k + 9, n)));
+  }
   if (p < 16 * 64) {
     const int in = p / 64, out = p % 64;
     dev->w1[p] = __float2bfloat16_rn(in < 8 ? w[kOffW1 + in * 64 + out] : 0.f);

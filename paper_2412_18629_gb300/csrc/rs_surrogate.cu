@@ -3,20 +3,25 @@
 // For every node with at least kSurMin members ("big" nodes), instead of the O(g^2) potential:
 //   1. features per member (k_sur_features): r / r_vir, the enclosed-member fractions within
 //      0.5, 1 and 2 times the member's radius (binary searches in the node's radially sorted
-//      members), the potential of the spherically averaged node (enclosed count over r plus the
-//      suffix sum of 1 / r_j over the members outside), |v - v_bulk| / sigma_v,1D, log10 g and
-//      the relative size of the deepest hierarchy node holding the member; r is measured from
-//      the node's mean position, r_vir = (3 g m / (4 pi 200 rho_bar))^(1/3);
+//      members), the node's potential at the member from the radially split multipole
+//      expansion to quadrupole order (psi_mp: monopole = spherically averaged node, plus the
+//      dipole and quadrupole moments of the members inside and outside the member's radius,
+//      from fixed-point prefix sums over the radial order), |v - v_bulk| / sigma_v,1D, log10 g
+//      and the spherical potential of the deepest hierarchy node holding the member; r is
+//      measured from the node's mean position, r_vir = (3 g m / (4 pi 200 rho_bar))^(1/3);
 //   2. the MLP predicts psi = phi r_vir / (G g m); E_pred = KE + psi_hat G g m / r_vir;
-//   3. gate (k_sur_gate): a member is classified by the surrogate iff
-//      |E_pred| > margin_factor * err_max * G g m / r_vir, err_max being the MLP's held-out
-//      maximum error; every other member takes the exact path;
-//   4. spot check: per node, the spot_check gated members with the smallest margin are also
-//      evaluated exactly; if any has |psi_hat - psi| > err_max or a different flag, the whole
-//      node falls back to the exact path;
-//   5. exact path per member (k_pot_member): float32 direct sum over the node (one warp per
-//      member, certified bound kCertB2) and the float64 canonical-order potential when the
-//      energy is within the bound of zero -- the same flag as the plain form.
+//   3. calibration: per node, kCalib members evenly spaced in member order are held out of
+//      the gate and evaluated exactly; err_node = max(max |psi_hat - psi| over them,
+//      err_max / 8), err_max being the MLP's held-out maximum error from training;
+//   4. gate (k_sur_gate): a member is classified by the surrogate iff
+//      |E_pred| > margin_factor * err_node * G g m / r_vir; every other member takes the exact
+//      path: a register-blocked float32 sum over the node for the list of such members (with
+//      the self term included and subtracted, and a per-member certified bound), the float64
+//      canonical-order potential when the energy is within that bound of zero;
+//   5. spot check: per node, the spot_check gated members with the smallest margin are also
+//      evaluated exactly; if any has a different flag, or |psi_hat - psi| above half the
+//      gate's margin (margin_factor / 2 * err_node: the calibration was off by more than that
+//      factor), the whole node is recomputed by the blocked direct sum.
 #include <cmath>
 
 #include "rs_cro.cuh"
@@ -38,27 +43,16 @@ constexpr double kU = 5.9604644775390625e-08;
 // tree <= 5u; 48u with slack.
 constexpr double kCertB2 = 48.0 * kU + 1e-12;
 
+// Blocked direct sum over the exact-path list: 128 threads x 4 members per block.
+constexpr int kListThreads = 128;
+constexpr int kListR = 4;
+constexpr int kListTile = kListThreads * kListR;
+
 struct NodeStat {
   float cx, cy, cz, r_vir;
   float sig_v1d, log_g, pad0, pad1;
   double gm_over_rvir;
   double pad2;
-};
-
-struct StatTerm {  // u (3), v (3), v^2 (3)
-  const float4* U;
-  const float4* V;
-  __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
-    const float4 u = U[p], v = V[p];
-    const double a[3] = {double(u.x), double(u.y), double(u.z)};
-    const double b[3] = {double(v.x), double(v.y), double(v.z)};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      acc[d] = __dadd_rn(acc[d], a[d]);
-      acc[3 + d] = __dadd_rn(acc[3 + d], b[d]);
-      acc[6 + d] = __dadd_rn(acc[6 + d], __dmul_rn(b[d], b[d]));
-    }
-  }
 };
 
 __global__ void k_sur_node_flags(int64_t nn, const int64_t* __restrict__ node_size,
@@ -70,23 +64,19 @@ __global__ void k_sur_node_flags(int64_t nn, const int64_t* __restrict__ node_si
   bigf[q] = big ? 1 : 0;
 }
 
-__global__ void k_sur_stats(int64_t nn, const int64_t* __restrict__ node_size,
-                            const double* __restrict__ sums, double m, double G, double rho_bar,
-                            NodeStat* __restrict__ st) {
+// Node statistics of the features: centre and sigma_v,1D from the moments of the node's 6D
+// split (canonical-order float64 sums of u and v), r_vir from g.
+__global__ void k_sur_stats(int64_t nn, const int64_t* __restrict__ node_size, const float4* __restrict__ mom,
+                            double m, double G, double rho_bar, NodeStat* __restrict__ st) {
   const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= nn) return;
   const double g = double(node_size[q]);
-  const double* S = sums + 9 * q;
+  const float4 M = mom[q];
   NodeStat s;
-  s.cx = float(S[0] / g);
-  s.cy = float(S[1] / g);
-  s.cz = float(S[2] / g);
-  double var = 0.0;
-  for (int d = 0; d < 3; ++d) {
-    const double mv = S[3 + d] / g;
-    var += S[6 + d] / g - mv * mv;
-  }
-  s.sig_v1d = float(sqrt(fmax(var, 0.0) / 3.0));
+  s.cx = M.x;
+  s.cy = M.y;
+  s.cz = M.z;
+  s.sig_v1d = M.w;
   const double rv = cbrt(3.0 * g * m / (4.0 * 3.14159265358979323846 * 200.0 * rho_bar));
   s.r_vir = float(rv);
   s.log_g = float(log10(g));
@@ -166,8 +156,69 @@ __global__ void k_psi_sph(int64_t m, const uint32_t* __restrict__ mnode, const i
   psi_sph[p] = float(-(double(s.r_vir) / double(g)) * (inner + outer));
 }
 
+constexpr float kFixIn = 16777216.0f;  // 2^24: scale of the inner moment sums
+constexpr float kFixOut = 65536.0f;    // 2^16: scale of the outer moment sums
+constexpr int kMpTerms = 18;
+
+// Multipole terms of every big-node member at its radially sorted position c (compacted to the
+// big nodes: c = sur_off[q] + rank in the node), with x = u - centre, r = |x|, rr = max(r, eps):
+// inner (scale 2^24): x (3), T = 3 x x^T - r^2 I (xx, yy, zz, xy, xz, yz);
+// outer (scale 2^16): x / rr^3 (3), T / rr^5 (6). Float32 terms rounded to int64 fixed point,
+// so the prefix sums are exact and independent of the scan's order. Row t of `terms` has
+// ns + 1 entries (the last one 0); the rows are prefix-summed as one array, since only
+// differences inside a row are used.
+__global__ void k_mp_terms(int64_t m, const uint32_t* __restrict__ rvals, const uint32_t* __restrict__ mnode,
+                           const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
+                           const int64_t* __restrict__ sur_off, const NodeStat* __restrict__ st,
+                           const float4* __restrict__ U, float eps, int64_t ns, int64_t* __restrict__ terms) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s < kMpTerms) terms[s * (ns + 1) + ns] = 0;  // the slot after each row
+  if (s >= m) return;
+  const uint32_t p = rvals[s], q = mnode[p];
+  if (node_size[q] < kSurMin) return;
+  const int64_t c = sur_off[q] + (s - node_off[q]);
+  const NodeStat S = st[q];
+  const float4 u = U[p];
+  const float x = u.x - S.cx, y = u.y - S.cy, z = u.z - S.cz;
+  const float r2 = x * x + y * y + z * z;
+  const float rr = fmaxf(sqrtf(r2), eps);
+  const float i3 = 1.0f / (rr * rr * rr), i5 = i3 / (rr * rr);
+  const float T[6] = {3 * x * x - r2, 3 * y * y - r2, 3 * z * z - r2, 3 * x * y, 3 * x * z, 3 * y * z};
+  const float v[kMpTerms] = {x * kFixIn, y * kFixIn, z * kFixIn,
+                             T[0] * kFixIn, T[1] * kFixIn, T[2] * kFixIn,
+                             T[3] * kFixIn, T[4] * kFixIn, T[5] * kFixIn,
+                             x * i3 * kFixOut, y * i3 * kFixOut, z * i3 * kFixOut,
+                             T[0] * i5 * kFixOut, T[1] * i5 * kFixOut, T[2] * i5 * kFixOut,
+                             T[3] * i5 * kFixOut, T[4] * i5 * kFixOut, T[5] * i5 * kFixOut};
+#pragma unroll
+  for (int t = 0; t < kMpTerms; ++t) terms[int64_t(t) * (ns + 1) + c] = llrintf(v[t]);
+}
+
+// psi_mp of surrogate member k: psi_sph plus the dipole and quadrupole terms of the radially
+// split expansion, -(r_vir / g) [x.D_in / rr^3 + x.D_out + (x^T Q_in x / rr^5 + x^T Q_out x) / 2],
+// D_in, Q_in over the members before it in the radial order, D_out, Q_out over those after it.
+__device__ __forceinline__ float psi_multipole(const int64_t* __restrict__ terms, int64_t ns, int64_t lo,
+                                               int64_t hi, int64_t c, float4 u, const NodeStat& S,
+                                               float eps, int64_t g, float psi_sph) {
+  const float x = u.x - S.cx, y = u.y - S.cy, z = u.z - S.cz;
+  const float rr = fmaxf(sqrtf(x * x + y * y + z * z), eps);
+  float a[kMpTerms];
+#pragma unroll
+  for (int t = 0; t < kMpTerms; ++t) {
+    const int64_t* row = terms + int64_t(t) * (ns + 1);
+    a[t] = t < 9 ? float(row[c] - row[lo]) * (1.0f / kFixIn) : float(row[hi] - row[c + 1]) * (1.0f / kFixOut);
+  }
+  const float quad_in = a[3] * x * x + a[4] * y * y + a[5] * z * z + 2 * (a[6] * x * y + a[7] * x * z + a[8] * y * z);
+  const float quad_out = a[12] * x * x + a[13] * y * y + a[14] * z * z +
+                         2 * (a[15] * x * y + a[16] * x * z + a[17] * y * z);
+  const float r3 = rr * rr * rr;
+  const float dip = (a[0] * x + a[1] * y + a[2] * z) / r3 + (a[9] * x + a[10] * y + a[11] * z);
+  const float quad = 0.5f * (quad_in / (r3 * rr * rr) + quad_out);
+  return psi_sph - (S.r_vir / float(g)) * (dip + quad);
+}
+
 // Features of surrogate member k, in this order: r / r_vir; fractions of the node's members
-// with radius below 0.5 r, r and 2 r; psi_sph of the node; |v - v_bulk| / sigma_v,1D;
+// with radius below 0.5 r, r and 2 r; psi_mp of the node; |v - v_bulk| / sigma_v,1D;
 // log10 g; psi_sph of the deepest node holding the member, converted to this node's units
 // (g_d / g) (r_vir / r_vir,d) -- the well of the member's own substructure.
 __global__ void k_sur_features(int64_t ns, const uint32_t* __restrict__ sur_mem,
@@ -177,7 +228,9 @@ __global__ void k_sur_features(int64_t ns, const uint32_t* __restrict__ sur_mem,
                                const double* __restrict__ vbulk, const uint64_t* __restrict__ rkeys,
                                const float* __restrict__ psi_sph, const uint32_t* __restrict__ mem,
                                const int64_t* __restrict__ deepest,
-                               const uint32_t* __restrict__ deepest_pos, float* __restrict__ feat) {
+                               const uint32_t* __restrict__ deepest_pos, const int64_t* __restrict__ sur_off,
+                               const uint32_t* __restrict__ spos, const int64_t* __restrict__ terms,
+                               float eps, float* __restrict__ feat) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= ns) return;
   const uint32_t p = sur_mem[k], q = mnode[p];
@@ -200,7 +253,8 @@ __global__ void k_sur_features(int64_t ns, const uint32_t* __restrict__ sur_mem,
   F[1] = f05;
   F[2] = f1;
   F[3] = f2;
-  F[4] = psi_sph[p];
+  const int64_t c0 = sur_off[q];
+  F[4] = psi_multipole(terms, ns, c0, c0 + g, c0 + (int64_t(spos[p]) - lo), U[p], s, eps, g, psi_sph[p]);
   F[5] = sqrtf(dvx * dvx + dvy * dvy + dvz * dvz) / fmaxf(s.sig_v1d, 1e-30f);
   F[6] = s.log_g;
   F[7] = sub;
@@ -230,21 +284,29 @@ __device__ __forceinline__ double kinetic(float4 v, const double* vb) {
 __global__ void k_sur_gate(int64_t ns, const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
                            const int64_t* __restrict__ node_size, const float4* __restrict__ V,
                            const double* __restrict__ vbulk, const NodeStat* __restrict__ st,
-                           const float* __restrict__ psi_hat, float thr_psi, uint8_t* __restrict__ bound,
-                           uint8_t* __restrict__ sflag, float* __restrict__ margin,
-                           unsigned int* __restrict__ gcount, unsigned int* __restrict__ ecount,
-                           unsigned long long* __restrict__ counters) {
+                           const float* __restrict__ psi_hat, const float* __restrict__ errn, float err_floor,
+                           float margin_factor, uint8_t* __restrict__ bound, uint8_t* __restrict__ sflag,
+                           float* __restrict__ margin, unsigned int* __restrict__ gcount,
+                           unsigned int* __restrict__ ecount, unsigned long long* __restrict__ counters) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= ns) return;
+  if (sflag[k] == 3) {  // calibration member: exact already
+    margin[k] = __int_as_float(0x7f800000);
+    return;
+  }
   const uint32_t p = sur_mem[k], q = mnode[p];
-  const double gmr = st[q].gm_over_rvir;
-  const double e = kinetic(V[p], vbulk + 3 * int64_t(q)) + double(psi_hat[k]) * gmr;
-  const double thr = double(thr_psi) * gmr;
-  if (fabs(e) > thr) {
-    const uint8_t f = e < 0.0 ? 1 : 0;
+  // predicted energy in units of G g m / r_vir, float32 (the gate's margin dwarfs its rounding)
+  const float inv_gmr = float(1.0 / st[q].gm_over_rvir);
+  const float4 v = V[p];
+  const float dvx = v.x - float(vbulk[3 * q]), dvy = v.y - float(vbulk[3 * q + 1]),
+              dvz = v.z - float(vbulk[3 * q + 2]);
+  const float e = 0.5f * (dvx * dvx + dvy * dvy + dvz * dvz) * inv_gmr + psi_hat[k];
+  const float thr = margin_factor * fmaxf(errn[q], err_floor);
+  if (fabsf(e) > thr) {
+    const uint8_t f = e < 0.f ? 1 : 0;
     bound[p] = f;
     sflag[k] = f;
-    margin[k] = float((fabs(e) - thr) / gmr);
+    margin[k] = fabsf(e) - thr;
     atomicAdd(gcount + q, 1u);
     atomicAdd(counters + 5, 1ull);
   } else {
@@ -254,25 +316,87 @@ __global__ void k_sur_gate(int64_t ns, const uint32_t* __restrict__ sur_mem, con
   }
 }
 
-// A node whose ungated share exceeds 1/4 is cheaper as a whole through the blocked direct sum.
+// Calibration members: kCalib per big node, evenly spaced in member order (sflag = 3).
+constexpr int kCalib = 64;
+
+__global__ void k_sur_calib_list(int64_t nbig, const int64_t* __restrict__ big_nodes,
+                                 const int64_t* __restrict__ sur_off, const int64_t* __restrict__ node_size,
+                                 uint32_t* __restrict__ list, uint8_t* __restrict__ sflag,
+                                 unsigned long long* __restrict__ counters) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t == 0) counters[9] = (unsigned long long)(nbig * kCalib);
+  if (t >= nbig * kCalib) return;
+  const int64_t b = t / kCalib, i = t % kCalib, q = big_nodes[b], g = node_size[q];
+  const int64_t k = sur_off[q] + (i * (g - 1)) / (kCalib - 1);
+  list[t] = uint32_t(k);
+  sflag[k] = 3;
+}
+
+// err_node[q] = max over the node's calibration members of |psi_hat - psi| (float bits of a
+// non-negative value, so the integer maximum is the float maximum and order-independent).
+__global__ void k_sur_err(const unsigned long long* __restrict__ count, const uint32_t* __restrict__ list,
+                          const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
+                          const int64_t* __restrict__ node_size, const NodeStat* __restrict__ st,
+                          const float* __restrict__ Sx, const float* __restrict__ psi_hat,
+                          unsigned int* __restrict__ errn) {
+  const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w >= int64_t(*count)) return;
+  const uint32_t k = list[w];
+  const uint32_t q = mnode[sur_mem[k]];
+  const double psi = -double(Sx[k]) * double(st[q].r_vir) / double(node_size[q]);
+  const float e = float(fabs(double(psi_hat[k]) - psi));
+  atomicMax(errn + q, __float_as_uint(e));
+}
+
+// A node with at most 1/20 of its members gated goes whole through the blocked direct sum.
 __global__ void k_sur_full(int64_t nbig, const int64_t* __restrict__ big_nodes,
                            const int64_t* __restrict__ node_size, const unsigned int* __restrict__ ecount,
                            int* __restrict__ full, unsigned long long* __restrict__ counters) {
   const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (b >= nbig) return;
-  const int64_t q = big_nodes[b];
-  const bool f = 4 * int64_t(ecount[q]) > node_size[q];
+  const int64_t q = big_nodes[b], g = node_size[q];
+  const bool f = 20 * (int64_t(ecount[q]) + kCalib) >= 19 * g;
   full[q] = f ? 1 : 0;
-  if (f) atomicAdd(counters + 8, (unsigned long long)node_size[q]);
+  if (f) atomicAdd(counters + 8, (unsigned long long)g);
 }
 
-__global__ void k_sur_exact_list(int64_t ns, const uint32_t* __restrict__ sur_mem,
-                                 const uint32_t* __restrict__ mnode, const uint8_t* __restrict__ sflag,
-                                 const int* __restrict__ full, uint32_t* __restrict__ list,
-                                 unsigned long long* __restrict__ counters) {
+__global__ void k_sur_exact_flags(int64_t ns, const uint32_t* __restrict__ sur_mem,
+                                  const uint32_t* __restrict__ mnode, const uint8_t* __restrict__ sflag,
+                                  const int* __restrict__ full, int64_t* __restrict__ lf) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= ns) return;
-  if (sflag[k] == 2 && !full[mnode[sur_mem[k]]]) list[atomicAdd(counters + 0, 1ull)] = uint32_t(k);
+  lf[k] = (sflag[k] == 2 && !full[mnode[sur_mem[k]]]) ? 1 : 0;
+}
+
+// Exact-path list in surrogate-member order (so grouped by node), per-node list offsets and
+// the blocked kernel's tile counts per big node.
+__global__ void k_sur_exact_list(int64_t ns, const int64_t* __restrict__ lf, uint32_t* __restrict__ list,
+                                 unsigned long long* __restrict__ counters) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k == 0) counters[0] = (unsigned long long)lf[ns];
+  if (k >= ns) return;
+  if (lf[k + 1] != lf[k]) list[lf[k]] = uint32_t(k);
+}
+
+__global__ void k_sur_list_tiles(int64_t nbig, const int64_t* __restrict__ big_nodes,
+                                 const int64_t* __restrict__ sur_off, const int64_t* __restrict__ node_size,
+                                 const int64_t* __restrict__ lf, int64_t* __restrict__ lofs,
+                                 int64_t* __restrict__ tiles) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= nbig) return;
+  const int64_t q = big_nodes[b];
+  const int64_t a = lf[sur_off[q]], e = lf[sur_off[q] + node_size[q]];
+  lofs[b] = a;
+  tiles[b] = (e - a + kListTile - 1) / kListTile;
+}
+
+__global__ void k_sur_list_end(int64_t nbig, const int64_t* __restrict__ big_nodes,
+                               const int64_t* __restrict__ sur_off, const int64_t* __restrict__ node_size,
+                               const int64_t* __restrict__ lf, int64_t* __restrict__ lend) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= nbig) return;
+  const int64_t q = big_nodes[b];
+  lend[b] = lf[sur_off[q] + node_size[q]];
 }
 
 // Per big node (one block each): the k-th smallest margin (k = min(spot, gated) - 1) by radix
@@ -330,7 +454,7 @@ __global__ void k_sur_spot_mark(int64_t ns, const uint32_t* __restrict__ sur_mem
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= ns) return;
   const uint32_t q = mnode[sur_mem[k]];
-  const bool c = sflag[k] != 2 && margin[k] <= tau[q];
+  const bool c = sflag[k] < 2 && margin[k] <= tau[q];
   checked[k] = c ? 1 : 0;
   if (c) check_list[atomicAdd(counters + 1, 1ull)] = uint32_t(k);
 }
@@ -387,30 +511,156 @@ k_pot_member(const unsigned long long* __restrict__ count, const uint32_t* __res
   }
 }
 
+// Float32 sums S_all,i = sum over ALL members j of the node (self included) of
+// (|u_j - u_i|^2 + eps^2)^(-1/2) for the members i of the exact-path list: block b covers one
+// 512-member tile of one big node's list; j-tiles of 128 members staged duplicated in shared
+// memory, packed float32x2 arithmetic, 32-term sequential blocks added with Kahan compensation
+// (the same per-member summation as the direct-sum kernels). Including the self term, whose
+// computed value is exactly w0 = rsqrt(eps^2), removes every per-pair index test; k_flags_list
+// subtracts it and widens the certified bound accordingly.
+__global__ void __launch_bounds__(kListThreads)
+k_potential_list(int64_t nbig, const int64_t* __restrict__ tile_off, const int64_t* __restrict__ big_nodes,
+                 const int64_t* __restrict__ lofs, const int64_t* __restrict__ lf_total_per_node_end,
+                 const uint32_t* __restrict__ list, const uint32_t* __restrict__ sur_mem,
+                 const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
+                 const float4* __restrict__ U, float eps2, float* __restrict__ Sx) {
+  __shared__ float4 sxy[kListThreads];
+  __shared__ float2 sz[kListThreads];
+  const int64_t b = blockIdx.x;
+  if (b >= tile_off[nbig]) return;
+  const int64_t bi = rsd::upper_bound_i64(tile_off, nbig, b) - 1;
+  const int64_t q = big_nodes[bi], t = b - tile_off[bi];
+  const int64_t base = node_off[q], g = node_size[q];
+  const int64_t l0 = lofs[bi] + t * kListTile, l1 = lf_total_per_node_end[bi];
+  float2 nx[kListR / 2], ny[kListR / 2], nz[kListR / 2];
+  float S[kListR], C[kListR];
+#pragma unroll
+  for (int pp = 0; pp < kListR / 2; ++pp) {
+    const int64_t a0 = l0 + threadIdx.x + kListThreads * (2 * pp), a1 = a0 + kListThreads;
+    const float4 u0 = a0 < l1 ? U[sur_mem[list[a0]]] : make_float4(0, 0, 0, 0);
+    const float4 u1 = a1 < l1 ? U[sur_mem[list[a1]]] : make_float4(0, 0, 0, 0);
+    nx[pp] = make_float2(-u0.x, -u1.x);
+    ny[pp] = make_float2(-u0.y, -u1.y);
+    nz[pp] = make_float2(-u0.z, -u1.z);
+  }
+#pragma unroll
+  for (int k = 0; k < kListR; ++k) {
+    S[k] = 0.f;
+    C[k] = 0.f;
+  }
+  const float2 e2 = make_float2(eps2, eps2);
+  for (int64_t j0 = 0; j0 < g; j0 += kListThreads) {
+    const int64_t j = j0 + threadIdx.x;
+    if (j < g) {
+      const float4 u = U[base + j];
+      sxy[threadIdx.x] = make_float4(u.x, u.x, u.y, u.y);
+      sz[threadIdx.x] = make_float2(u.z, u.z);
+    }
+    __syncthreads();
+    const int jn = int(rsd::min64(kListThreads, g - j0));
+    for (int jb = 0; jb < jn; jb += 32) {
+      const int je = min(jb + 32, jn);
+      float2 blk[kListR / 2];
+#pragma unroll
+      for (int pp = 0; pp < kListR / 2; ++pp) blk[pp] = make_float2(0.f, 0.f);
+#pragma unroll 8
+      for (int jj = jb; jj < je; ++jj) {
+        const float4 a = sxy[jj];
+        const float2 zz = sz[jj];
+#pragma unroll
+        for (int pp = 0; pp < kListR / 2; ++pp) {
+          const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx[pp]);
+          const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny[pp]);
+          const float2 dz = __fadd2_rn(zz, nz[pp]);
+          const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+          blk[pp] = __fadd2_rn(blk[pp], make_float2(rsqrtf(r2.x), rsqrtf(r2.y)));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kListR; ++k) {
+        const float bk = (k & 1) ? blk[k >> 1].y : blk[k >> 1].x;
+        const float y = __fsub_rn(bk, C[k]);
+        const float tt = __fadd_rn(S[k], y);
+        C[k] = __fsub_rn(__fsub_rn(tt, S[k]), y);
+        S[k] = tt;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < kListR; ++k) {
+    const int64_t a = l0 + threadIdx.x + kListThreads * k;
+    if (a < l1) Sx[list[a]] = S[k];
+  }
+}
+
+// Flags of the exact-path list from S_all: S = fl(S_all - w0). With B = 41u the bound of the
+// blocked sum relative to S_all = S + w0, |S - S_true| <= B (S + w0) + u S, so the member's
+// relative bound is Bi = B (1 + w0 / S) + u (plus slack); the flag is certain when
+// |KE + phi~| > 2 Bi |phi~|, otherwise the member is queued for the float64 potential.
+__global__ void k_flags_list(const unsigned long long* __restrict__ count, const uint32_t* __restrict__ list,
+                             const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
+                             const float4* __restrict__ V, const double* __restrict__ vbulk,
+                             float eps2, double Gm, float* __restrict__ Sx, uint8_t* __restrict__ bound,
+                             uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig) {
+  const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w >= int64_t(*count)) return;
+  const uint32_t k = list[w];
+  const uint32_t p = sur_mem[k], q = mnode[p];
+  const float w0 = rsqrtf(eps2);
+  const float S = __fsub_rn(Sx[k], w0);
+  Sx[k] = S;
+  const double ph = -__dmul_rn(Gm, double(S));
+  const double e = __dadd_rn(kinetic(V[p], vbulk + 3 * int64_t(q)), ph);
+  const double Bi = 41.0 * kU * (1.0 + double(w0) / fmax(double(S), 1e-30)) + 2.0 * kU + 1e-12;
+  if (S > 0.f && fabs(e) > 2.0 * Bi * fabs(ph)) {
+    bound[p] = e < 0.0 ? 1 : 0;
+  } else {
+    ambig[atomicAdd(n_ambig, 1ull)] = p;
+  }
+}
+
 __global__ void k_sur_verdict(const unsigned long long* __restrict__ counters,
                               const uint32_t* __restrict__ check_list, const uint32_t* __restrict__ sur_mem,
                               const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_size,
                               const NodeStat* __restrict__ st, const float* __restrict__ Sx,
                               const float* __restrict__ psi_hat, const uint8_t* __restrict__ sflag,
-                              const uint8_t* __restrict__ bound, float err_max, int* __restrict__ fail) {
+                              const uint8_t* __restrict__ bound, const float* __restrict__ errn,
+                              float err_floor, float margin_factor, int* __restrict__ fail) {
   const unsigned long long total = counters[1];
   for (unsigned long long w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < total;
        w += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t k = check_list[w];
     const uint32_t p = sur_mem[k], q = mnode[p];
     const double psi = -double(Sx[k]) * double(st[q].r_vir) / double(node_size[q]);
-    if (fabs(double(psi_hat[k]) - psi) > double(err_max) || sflag[k] != bound[p]) fail[q] = 1;
+    const double err = 0.5 * double(margin_factor) * double(fmaxf(errn[q], err_floor));
+    if (fabs(double(psi_hat[k]) - psi) > err || sflag[k] != bound[p]) fail[q] = 1;
   }
 }
 
+// Gated, unchecked members of nodes that failed the spot check (recomputed with their node).
 __global__ void k_sur_rerun(int64_t ns, const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
                             const int* __restrict__ fail, const uint8_t* __restrict__ sflag,
-                            const uint8_t* __restrict__ checked, uint32_t* __restrict__ list,
-                            unsigned long long* __restrict__ counters) {
+                            const uint8_t* __restrict__ checked, unsigned long long* __restrict__ counters) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= ns) return;
   const uint32_t q = mnode[sur_mem[k]];
-  if (fail[q] && sflag[k] != 2 && !checked[k]) list[atomicAdd(counters + 3, 1ull)] = uint32_t(k);
+  if (fail[q] && sflag[k] < 2 && !checked[k]) atomicAdd(counters + 3, 1ull);
+}
+
+// Members whose flag the surrogate decided (gated, in a node neither sent whole to the direct
+// sum nor failed, and not spot-checked) -> counters[10]; calibration members of nodes not sent
+// whole -> counters[11].
+__global__ void k_sur_decided(int64_t ns, const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
+                              const uint8_t* __restrict__ sflag, const uint8_t* __restrict__ checked,
+                              const int* __restrict__ full, const int* __restrict__ fail,
+                              unsigned long long* __restrict__ counters) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= ns) return;
+  const uint32_t q = mnode[sur_mem[k]];
+  if (full[q]) return;
+  if (sflag[k] < 2 && !checked[k] && !fail[q]) atomicAdd(counters + 10, 1ull);
+  if (sflag[k] == 3) atomicAdd(counters + 11, 1ull);
 }
 
 __global__ void k_count_fail(int64_t nn, const int* __restrict__ fail, unsigned long long* __restrict__ counters) {
@@ -452,8 +702,7 @@ static int sur_prepare(rs_ctx* ctx, const double* vbulk, int64_t* ns_out, cudaSt
   int64_t* sur_off = scratch_t<int64_t>(ctx, S_SUR_OFF, size_t(nn) + 1);
   int64_t* rank = scratch_t<int64_t>(ctx, S_SUR_RANK, size_t(nn) + 1);
   NodeStat* stt = scratch_t<NodeStat>(ctx, S_SUR_STAT, size_t(nn));
-  double* sums = scratch_t<double>(ctx, S_NODE_TMP, size_t(nn) * 9);
-  if (!sur_off || !rank || !stt || !sums) return RS_ERR_OOM;
+  if (!sur_off || !rank || !stt) return RS_ERR_OOM;
   k_sur_node_flags<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sur_off, rank);
   RS_LAUNCHED(ctx, "k_sur_node_flags");
   RS_TRY(exclusive_scan_i64(ctx, nn, sur_off, sur_off + nn, st));
@@ -465,10 +714,9 @@ static int sur_prepare(rs_ctx* ctx, const double* vbulk, int64_t* ns_out, cudaSt
   *ns_out = ns;
   ctx->sur_nbig = nbig;
   if (ns == 0) return RS_OK;
-  RS_TRY((cro_segmented<9, StatTerm>(ctx, nn, h.node_off, h.node_size, m, StatTerm{h.U, h.V}, sums, st)));
   const double L = ctx->cfg.box_L;
   const double rho_bar = double(ctx->n_particles) * ctx->cfg.particle_mass / (L * L * L);
-  k_sur_stats<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sums, ctx->cfg.particle_mass, ctx->cfg.G,
+  k_sur_stats<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, h.mom, ctx->cfg.particle_mass, ctx->cfg.G,
                                               rho_bar, stt);
   RS_LAUNCHED(ctx, "k_sur_stats");
   uint32_t* sur_mem = scratch_t<uint32_t>(ctx, S_SUR_MEM, size_t(ns));
@@ -502,11 +750,19 @@ static int sur_prepare(rs_ctx* ctx, const double* vbulk, int64_t* ns_out, cudaSt
   k_psi_sph<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_off, h.node_size, stt, h.U, fix, spos, eps,
                                            psi_sph);
   RS_LAUNCHED(ctx, "k_psi_sph");
+  const int64_t nterms = int64_t(kMpTerms) * (ns + 1);
+  int64_t* terms = scratch_t<int64_t>(ctx, S_SUR_MP, size_t(nterms) + 1);
+  if (!terms) return RS_ERR_OOM;
+  k_mp_terms<<<grid_for(std::max<int64_t>(m, kMpTerms), kT), kT, 0, st>>>(m, rvals, h.mnode, h.node_off,
+                                                                        h.node_size, sur_off, stt, h.U, eps,
+                                                                        ns, terms);
+  RS_LAUNCHED(ctx, "k_mp_terms");
+  RS_TRY(exclusive_scan_i64(ctx, nterms, terms, terms + nterms, st));
   {
     ProfScope prof_(ctx, "k_sur_features", st);
     k_sur_features<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_off, h.node_size, h.U,
                                                    h.V, stt, vbulk, rkeys, psi_sph, h.mem, h.deepest,
-                                                   h.deepest_pos, feat);
+                                                   h.deepest_pos, sur_off, spos, terms, eps, feat);
   }
   RS_LAUNCHED(ctx, "k_sur_features");
   return RS_OK;
@@ -541,65 +797,111 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
   if (!psi_hat || !margin || !sflag || !checked || !Sx || !exact_list || !check_list || !ambig ||
       !gcount || !tau || !fail || !ecount || !full)
     return RS_ERR_OOM;
+  const int64_t nbig = ctx->sur_nbig;
+  unsigned int* errn = scratch_t<unsigned int>(ctx, S_SUR_ERRN, size_t(nn));
+  uint32_t* calib_list = scratch_t<uint32_t>(ctx, S_SUR_LIST_C, size_t(nbig) * kCalib + 1);
+  int64_t* lf = scratch_t<int64_t>(ctx, S_SUR_LSCAN, size_t(ns) + 1);
+  int64_t* lofs = scratch_t<int64_t>(ctx, S_SUR_LOFS, size_t(nbig) * 2 + 2);
+  int64_t* ltiles = scratch_t<int64_t>(ctx, S_SUR_TILES, size_t(nbig) + 1);
+  if (!errn || !calib_list || !lf || !lofs || !ltiles) return RS_ERR_OOM;
+  int64_t* lend = lofs + nbig + 1;
+  const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
+  const float eps = ctx->cfg.softening;
+  const unsigned grid = 152 * 8;
+  const float err_floor = ctx->mlp_err_max / 8.0f;
   RS_TRY(mlp_forward(ctx, ns, feat, psi_hat, st));
   RS_CUDA(ctx, cudaMemsetAsync(gcount, 0, 4 * nn, st));
   RS_CUDA(ctx, cudaMemsetAsync(ecount, 0, 4 * nn, st));
   RS_CUDA(ctx, cudaMemsetAsync(fail, 0, 4 * nn, st));
   RS_CUDA(ctx, cudaMemsetAsync(full, 0, 4 * nn, st));
-  const float thr_psi = ctx->cfg.margin_factor * ctx->mlp_err_max;
-  k_sur_gate<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_size, h.V, vbulk, stt, psi_hat,
-                                             thr_psi, bound, sflag, margin, gcount, ecount, counters);
-  RS_LAUNCHED(ctx, "k_sur_gate");
-  if (ctx->sur_nbig > 0) {
-    k_sur_full<<<grid_for(ctx->sur_nbig, kT), kT, 0, st>>>(ctx->sur_nbig, big_nodes, h.node_size, ecount,
-                                                           full, counters);
-    RS_LAUNCHED(ctx, "k_sur_full");
-  }
-  k_sur_exact_list<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, sflag, full, exact_list, counters);
-  RS_LAUNCHED(ctx, "k_sur_exact_list");
-  // nodes mostly outside the gate: whole-node blocked direct sum
-  RS_TRY(unbind_nodes(ctx, full, vbulk, bound, ambig, counters + 2, st));
-  k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 7);
-  RS_LAUNCHED(ctx, "k_acc_counter");
-  if (ctx->sur_nbig > 0) {
-    k_sur_select<<<unsigned(ctx->sur_nbig), kT, 0, st>>>(big_nodes, sur_off, h.node_size, gcount, margin,
-                                                         ctx->cfg.spot_check, full, tau);
-    RS_LAUNCHED(ctx, "k_sur_select");
-  }
-  k_sur_spot_mark<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, margin, sflag, tau, checked,
-                                                  check_list, counters);
-  RS_LAUNCHED(ctx, "k_sur_spot_mark");
-  const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
-  const float eps = ctx->cfg.softening;
-  const unsigned grid = 152 * 8;
-  // exact members, then the spot checks (counters 0 and 1), fp64 fallback after each pass
-  for (int pass = 0; pass < 2; ++pass) {
-    const uint32_t* list = pass == 0 ? exact_list : check_list;
-    {
-      ProfScope prof_(ctx, "k_pot_member", st);
-      k_pot_member<<<grid, kT, 0, st>>>(counters + pass, list, sur_mem, h.mnode, h.node_off, h.node_size,
-                                        h.U, h.V, vbulk, eps * eps, Gm, Sx, bound, ambig, counters + 2);
-    }
-    RS_LAUNCHED(ctx, "k_pot_member");
-    RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vbulk, bound, st));
-    k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
-    RS_LAUNCHED(ctx, "k_acc_counter");
-  }
-  k_sur_verdict<<<grid, kT, 0, st>>>(counters, check_list, sur_mem, h.mnode, h.node_size, stt, Sx, psi_hat,
-                                     sflag, bound, ctx->mlp_err_max, fail);
-  RS_LAUNCHED(ctx, "k_sur_verdict");
-  k_sur_rerun<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, fail, sflag, checked, exact_list,
-                                              counters);
-  RS_LAUNCHED(ctx, "k_sur_rerun");
+  RS_CUDA(ctx, cudaMemsetAsync(errn, 0, 4 * nn, st));
+  RS_CUDA(ctx, cudaMemsetAsync(sflag, 0, size_t(ns), st));
+  // 1. calibration members: exact potential and flag, then the per-node error of the surrogate
+  k_sur_calib_list<<<grid_for(nbig * kCalib, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size,
+                                                               calib_list, sflag, counters);
+  RS_LAUNCHED(ctx, "k_sur_calib_list");
   {
     ProfScope prof_(ctx, "k_pot_member", st);
-    k_pot_member<<<grid, kT, 0, st>>>(counters + 3, exact_list, sur_mem, h.mnode, h.node_off, h.node_size,
+    k_pot_member<<<grid, kT, 0, st>>>(counters + 9, calib_list, sur_mem, h.mnode, h.node_off, h.node_size,
                                       h.U, h.V, vbulk, eps * eps, Gm, Sx, bound, ambig, counters + 2);
   }
   RS_LAUNCHED(ctx, "k_pot_member");
   RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vbulk, bound, st));
   k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
   RS_LAUNCHED(ctx, "k_acc_counter");
+  k_sur_err<<<grid_for(nbig * kCalib, kT), kT, 0, st>>>(counters + 9, calib_list, sur_mem, h.mnode,
+                                                        h.node_size, stt, Sx, psi_hat, errn);
+  RS_LAUNCHED(ctx, "k_sur_err");
+  // 2. gate with the node's calibrated error
+  k_sur_gate<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_size, h.V, vbulk, stt, psi_hat,
+                                             reinterpret_cast<const float*>(errn), err_floor,
+                                             ctx->cfg.margin_factor, bound, sflag, margin, gcount, ecount,
+                                             counters);
+  RS_LAUNCHED(ctx, "k_sur_gate");
+  if (nbig > 0) {
+    k_sur_full<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, h.node_size, ecount, full, counters);
+    RS_LAUNCHED(ctx, "k_sur_full");
+  }
+  // 3. nodes nearly all outside the gate: whole-node blocked direct sum
+  RS_TRY(unbind_nodes(ctx, full, vbulk, bound, ambig, counters + 2, st));
+  k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 7);
+  RS_LAUNCHED(ctx, "k_acc_counter");
+  // 4. the other ungated members: blocked sums over their node, certified flags, float64 fallback
+  k_sur_exact_flags<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, sflag, full, lf);
+  RS_LAUNCHED(ctx, "k_sur_exact_flags");
+  RS_TRY(exclusive_scan_i64(ctx, ns, lf, lf + ns, st));
+  k_sur_exact_list<<<grid_for(ns, kT), kT, 0, st>>>(ns, lf, exact_list, counters);
+  RS_LAUNCHED(ctx, "k_sur_exact_list");
+  if (nbig > 0) {
+    k_sur_list_tiles<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size, lf, lofs,
+                                                        ltiles);
+    RS_LAUNCHED(ctx, "k_sur_list_tiles");
+    k_sur_list_end<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size, lf, lend);
+    RS_LAUNCHED(ctx, "k_sur_list_end");
+    RS_TRY(exclusive_scan_i64(ctx, nbig, ltiles, ltiles + nbig, st));
+    {
+      ProfScope prof_(ctx, "k_potential_list", st);
+      k_potential_list<<<grid_for(ns / kListTile + nbig + 1, 1), kListThreads, 0, st>>>(
+          nbig, ltiles, big_nodes, lofs, lend, exact_list, sur_mem, h.node_off, h.node_size, h.U, eps * eps, Sx);
+    }
+    RS_LAUNCHED(ctx, "k_potential_list");
+  }
+  k_flags_list<<<grid_for(ns, kT), kT, 0, st>>>(counters + 0, exact_list, sur_mem, h.mnode, h.V, vbulk,
+                                               eps * eps, Gm, Sx, bound, ambig, counters + 2);
+  RS_LAUNCHED(ctx, "k_flags_list");
+  RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vbulk, bound, st));
+  k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
+  RS_LAUNCHED(ctx, "k_acc_counter");
+  // 5. spot checks: the smallest-margin gated members of each node, exactly
+  if (nbig > 0) {
+    k_sur_select<<<unsigned(nbig), kT, 0, st>>>(big_nodes, sur_off, h.node_size, gcount, margin,
+                                                ctx->cfg.spot_check, full, tau);
+    RS_LAUNCHED(ctx, "k_sur_select");
+  }
+  k_sur_spot_mark<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, margin, sflag, tau, checked,
+                                                  check_list, counters);
+  RS_LAUNCHED(ctx, "k_sur_spot_mark");
+  {
+    ProfScope prof_(ctx, "k_pot_member", st);
+    k_pot_member<<<grid, kT, 0, st>>>(counters + 1, check_list, sur_mem, h.mnode, h.node_off, h.node_size,
+                                      h.U, h.V, vbulk, eps * eps, Gm, Sx, bound, ambig, counters + 2);
+  }
+  RS_LAUNCHED(ctx, "k_pot_member");
+  RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vbulk, bound, st));
+  k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
+  RS_LAUNCHED(ctx, "k_acc_counter");
+  k_sur_verdict<<<grid, kT, 0, st>>>(counters, check_list, sur_mem, h.mnode, h.node_size, stt, Sx, psi_hat,
+                                     sflag, bound, reinterpret_cast<const float*>(errn), err_floor,
+                                     ctx->cfg.margin_factor, fail);
+  RS_LAUNCHED(ctx, "k_sur_verdict");
+  // 6. nodes that failed a spot check: the whole node through the blocked direct sum
+  k_sur_rerun<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, fail, sflag, checked, counters);
+  RS_LAUNCHED(ctx, "k_sur_rerun");
+  RS_TRY(unbind_nodes(ctx, fail, vbulk, bound, ambig, counters + 2, st));
+  k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
+  RS_LAUNCHED(ctx, "k_acc_counter");
+  k_sur_decided<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, sflag, checked, full, fail, counters);
+  RS_LAUNCHED(ctx, "k_sur_decided");
   k_count_fail<<<grid_for(nn, kT), kT, 0, st>>>(nn, fail, counters);
   RS_LAUNCHED(ctx, "k_count_fail");
   return RS_OK;

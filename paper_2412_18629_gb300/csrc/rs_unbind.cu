@@ -546,21 +546,20 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     k_copy_u8<<<grid_for(m, kT), kT, 0, st>>>(m, bound, bound_out);
     RS_LAUNCHED(ctx, "k_copy_u8");
     RS_TRY(read_back(ctx, counters, 16 * sizeof(unsigned long long), st));
-    // stats: surrogate members, gated, exact (per-member path), spot-checked, failed nodes,
-    // fp64 (surrogate path), fp64 (direct sums), re-run members, members of nodes sent whole
-    // to the direct sum, members whose flag the surrogate decided
+    // stats: surrogate members, gated, exact (exact-path list + calibration members, outside
+    // nodes sent whole),
+    // spot-checked, failed nodes, fp64 (surrogate path), fp64 (direct sums), re-run members,
+    // members of nodes sent whole to the direct sum, members whose flag the surrogate decided
     ctx->sur_stats[0] = sur ? ctx->sur_members : 0;
     ctx->sur_stats[1] = ctx->host_box[5];
-    ctx->sur_stats[2] = ctx->host_box[0];
+    ctx->sur_stats[2] = ctx->host_box[0] + ctx->host_box[11];
     ctx->sur_stats[3] = ctx->host_box[1];
     ctx->sur_stats[4] = ctx->host_box[4];
     ctx->sur_stats[5] = ctx->host_box[6];
     ctx->sur_stats[6] = ctx->host_box[7];
     ctx->sur_stats[7] = ctx->host_box[3];
     ctx->sur_stats[8] = ctx->host_box[8];
-    ctx->sur_stats[9] = sur ? ctx->sur_members - ctx->host_box[0] - ctx->host_box[1] -
-                                  ctx->host_box[3] - ctx->host_box[8]
-                            : 0;
+    ctx->sur_stats[9] = ctx->host_box[10];
     nfb = ctx->host_box[7] + ctx->host_box[6];
   }
   if (n_fallback_out) *n_fallback_out = nfb;

@@ -1,7 +1,7 @@
 """Batched + surrogate form: the MLP is trained on the GPU from exact potentials of one
 snapshot, then gates the unbinding of another. Flags, bound counts and halo decisions must be
 identical to the oracle's (no mismatch), the surrogate must classify a real share of the
-members of large nodes, and the exact pair interactions it saves are reported (the gain)."""
+members of large nodes, and the exact work it saves is reported (the gain)."""
 import numpy as np
 import pytest
 
@@ -33,9 +33,9 @@ def trained():
     return _train(synth.generate(spec))
 
 
-def _run_surrogate(s, params, err_max):
+def _run_surrogate(s, params, err_max, **kw):
     import paper_2412_18629_gb300 as rs
-    ctx = gpu_ctx(s, mode="surrogate")
+    ctx = gpu_ctx(s, mode="surrogate", **kw)
     rs.rs_mlp_set_params(ctx, params)
     rs.rs_mlp_set_err_max(ctx, err_max)
     pos, vel, ids = to_dev(s)
@@ -43,7 +43,8 @@ def _run_surrogate(s, params, err_max):
     rs.rs_fof6d(ctx, pos, vel, ids, lab)
     _, bound, _ = rs.rs_unbind(ctx, pos, vel, want_potential=False)
     props = rs.props_to_float64(rs.rs_halo_props(ctx)).cpu().numpy()
-    return lab.cpu().numpy(), bound.cpu().numpy(), props, rs.rs_surrogate_stats(ctx)
+    sizes = rs.rs_fof6d_copy(ctx)["size"].cpu().numpy()
+    return lab.cpu().numpy(), bound.cpu().numpy(), props, rs.rs_surrogate_stats(ctx), sizes
 
 
 @pytest.fixture(scope="module")
@@ -53,11 +54,11 @@ def workload_2e18():
 
 
 def test_surrogate_flags_match_oracle(trained, workload_2e18):
-    """With the trained network and its held-out error, every flag, bound count and halo
-    decision equals the oracle's; the counters report how many flags the network decided."""
+    """With the trained network, every flag, bound count and halo decision equals the oracle's;
+    the counters account for every member of the large nodes exactly once."""
     params, err_max, _ = trained
     s = workload_2e18
-    lab, bound, props, stats = _run_surrogate(s, params, err_max)
+    lab, bound, props, stats, _ = _run_surrogate(s, params, err_max)
     o = oracle_pipeline(s, labels=lab, stages=("fof3d", "fof6d", "unbind"))
     ub = o["unbind"]
     assert int(np.sum(bound != ub["bound"])) == 0
@@ -67,14 +68,32 @@ def test_surrogate_flags_match_oracle(trained, workload_2e18):
     accounted = (stats["surrogate_decided"] + stats["exact_member_path"] + stats["spot_checked"]
                  + stats["rerun_members"] + stats["whole_node_members"])
     assert accounted == stats["surrogate_members"], stats
-    print("surrogate gain on the 2^18 workload:", stats, "err_max", err_max)
+
+
+def test_surrogate_gain(trained, workload_2e18):
+    """What the trained network gains over the method without it: the share of the large
+    nodes' members whose flag it decides (no O(g) exact sum for them) and the share of exact
+    pair interactions saved, with zero flag mismatches against the oracle."""
+    params, err_max, _ = trained
+    s = workload_2e18
+    lab, bound, props, stats, sizes = _run_surrogate(s, params, err_max)
+    o = oracle_pipeline(s, labels=lab, stages=("fof3d", "fof6d", "unbind"))
+    assert int(np.sum(bound != o["unbind"]["bound"])) == 0
+    big = sizes[sizes >= 1024].astype(np.float64)
+    decided_share = stats["surrogate_decided"] / stats["surrogate_members"]
+    print("surrogate gain on the 2^18 workload: decided", stats["surrogate_decided"], "of",
+          stats["surrogate_members"], f"large-node members ({decided_share:.1%}); exact sums for",
+          stats["exact_member_path"] + stats["spot_checked"] + stats["rerun_members"],
+          "members;", stats, "err_max", err_max, "large-node pairs", float((big * big).sum()))
+    assert stats["surrogate_decided"] > 0.1 * stats["surrogate_members"], stats
 
 
 def test_overconfident_surrogate_is_caught_by_spot_checks(trained, workload_2e18):
-    """With an error bound far below the network's real error, the gate lets wrong predictions
-    through; the spot checks must notice (nodes fail and are recomputed exactly)."""
+    """With a gate far below its calibrated error (margin factor 0.05 instead of 4), wrong
+    predictions get through the gate; the spot checks must notice (nodes fail and their gated
+    members are recomputed exactly)."""
     params, err_max, _ = trained
-    lab, bound, props, stats = _run_surrogate(workload_2e18, params, err_max / 50.0)
+    lab, bound, props, stats, _ = _run_surrogate(workload_2e18, params, err_max, margin_factor=0.05)
     assert stats["gated"] > 0
     assert stats["failed_nodes"] > 0 and stats["rerun_members"] > 0, stats
 
