@@ -7,7 +7,7 @@
 //      expansion to quadrupole order (psi_mp: monopole = spherically averaged node, plus the
 //      dipole and quadrupole moments of the members inside and outside the member's radius,
 //      from fixed-point prefix sums over the radial order), |v - v_bulk| / sigma_v,1D, log10 g
-//      and the spherical potential of the deepest hierarchy node holding the member; r is
+//      and log10 of the size ratio of the deepest hierarchy node holding the member; r is
 //      measured from the node's mean position, r_vir = (3 g m / (4 pi 200 rho_bar))^(1/3);
 //   2. the MLP predicts psi = phi r_vir / (G g m); E_pred = KE + psi_hat G g m / r_vir;
 //   3. calibration: per node, kCalib members evenly spaced in member order are held out of
@@ -101,17 +101,19 @@ __device__ __forceinline__ float member_radius(float4 u, const NodeStat& s) {
   return sqrtf(dx * dx + dy * dy + dz * dz);
 }
 
-// Radial sort key of every (node, member): node index above the radius bits, so each node's
-// members stay in the node's own member range [node_off, node_off + g) after sorting.
-__global__ void k_all_radius(int64_t m, const uint32_t* __restrict__ mnode, const float4* __restrict__ U,
+// Radial sort key of every surrogate member k (surrogate order is node-grouped): the big
+// node's rank above the radius bits, so each node's members stay in their range
+// [sur_off[q], sur_off[q] + g) after sorting.
+__global__ void k_big_radius(int64_t ns, const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
+                             const int64_t* __restrict__ big_rank, const float4* __restrict__ U,
                              const NodeStat* __restrict__ st, uint64_t* __restrict__ keys,
                              uint32_t* __restrict__ vals) {
-  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= m) return;
-  const uint32_t q = mnode[p];
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= ns) return;
+  const uint32_t p = sur_mem[k], q = mnode[p];
   const float r = member_radius(U[p], st[q]);
-  keys[p] = (uint64_t(q) << 32) | uint64_t(__float_as_uint(r));
-  vals[p] = uint32_t(p);
+  keys[k] = (uint64_t(big_rank[q]) << 32) | uint64_t(__float_as_uint(r));
+  vals[k] = uint32_t(k);
 }
 
 __device__ __forceinline__ int64_t count_below(const uint64_t* __restrict__ rkeys, int64_t lo, int64_t hi,
@@ -128,7 +130,7 @@ __device__ __forceinline__ int64_t count_below(const uint64_t* __restrict__ rkey
 constexpr double kFix = 16777216.0;  // 2^24: fixed-point scale of the 1/r suffix sums
 
 // Per radially sorted position s: fixed-point 1 / max(r, eps) (to be prefix-summed) and the
-// sorted position of each surrogate member.
+// sorted position of each surrogate member (spos[k]).
 __global__ void k_sur_inv_r(int64_t ns, const uint64_t* __restrict__ rkeys, const uint32_t* __restrict__ rvals,
                             float eps, int64_t* __restrict__ fix, uint32_t* __restrict__ spos) {
   const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -138,45 +140,43 @@ __global__ void k_sur_inv_r(int64_t ns, const uint64_t* __restrict__ rkeys, cons
   spos[rvals[s]] = uint32_t(s);
 }
 
-// psi_sph of every (node, member): the potential of the spherically averaged node at the
+// psi_sph of every surrogate member k: the potential of the spherically averaged node at the
 // member, in units of G g m / r_vir: -(r_vir / g) (#inside / max(r, eps) + sum over members
 // outside of 1 / max(r_j, eps)), from the radially sorted member ranges.
-__global__ void k_psi_sph(int64_t m, const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_off,
-                          const int64_t* __restrict__ node_size, const NodeStat* __restrict__ st,
-                          const float4* __restrict__ U, const int64_t* __restrict__ fix,
-                          const uint32_t* __restrict__ spos, float eps, float* __restrict__ psi_sph) {
-  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= m) return;
-  const uint32_t q = mnode[p];
+__global__ void k_psi_sph(int64_t ns, const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
+                          const int64_t* __restrict__ sur_off, const int64_t* __restrict__ node_size,
+                          const NodeStat* __restrict__ st, const float4* __restrict__ U,
+                          const int64_t* __restrict__ fix, const uint32_t* __restrict__ spos, float eps,
+                          float* __restrict__ psi_sph) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= ns) return;
+  const uint32_t p = sur_mem[k], q = mnode[p];
   const NodeStat s = st[q];
-  const int64_t g = node_size[q], lo = node_off[q], hi = lo + g;
-  const int64_t si = spos[p];
-  const double outer = double(fix[hi] - fix[si + 1]) / kFix;
-  const double inner = double(si - lo) / double(fmaxf(member_radius(U[p], s), eps));
-  psi_sph[p] = float(-(double(s.r_vir) / double(g)) * (inner + outer));
+  const int64_t g = node_size[q], lo = sur_off[q], hi = lo + g;
+  const int64_t si = spos[k];
+  const float outer = float(fix[hi] - fix[si + 1]) * (1.0f / float(kFix));
+  const float inner = float(si - lo) / fmaxf(member_radius(U[p], s), eps);
+  psi_sph[k] = -(s.r_vir / float(g)) * (inner + outer);
 }
 
 constexpr float kFixIn = 16777216.0f;  // 2^24: scale of the inner moment sums
 constexpr float kFixOut = 65536.0f;    // 2^16: scale of the outer moment sums
 constexpr int kMpTerms = 18;
 
-// Multipole terms of every big-node member at its radially sorted position c (compacted to the
-// big nodes: c = sur_off[q] + rank in the node), with x = u - centre, r = |x|, rr = max(r, eps):
+// Multipole terms of every surrogate member at its radially sorted position c (the node's
+// range is [sur_off[q], sur_off[q] + g)), with x = u - centre, r = |x|, rr = max(r, eps):
 // inner (scale 2^24): x (3), T = 3 x x^T - r^2 I (xx, yy, zz, xy, xz, yz);
 // outer (scale 2^16): x / rr^3 (3), T / rr^5 (6). Float32 terms rounded to int64 fixed point,
 // so the prefix sums are exact and independent of the scan's order. Row t of `terms` has
 // ns + 1 entries (the last one 0); the rows are prefix-summed as one array, since only
 // differences inside a row are used.
-__global__ void k_mp_terms(int64_t m, const uint32_t* __restrict__ rvals, const uint32_t* __restrict__ mnode,
-                           const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
-                           const int64_t* __restrict__ sur_off, const NodeStat* __restrict__ st,
+__global__ void k_mp_terms(const uint32_t* __restrict__ rvals, const uint32_t* __restrict__ sur_mem,
+                           const uint32_t* __restrict__ mnode, const NodeStat* __restrict__ st,
                            const float4* __restrict__ U, float eps, int64_t ns, int64_t* __restrict__ terms) {
-  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (s < kMpTerms) terms[s * (ns + 1) + ns] = 0;  // the slot after each row
-  if (s >= m) return;
-  const uint32_t p = rvals[s], q = mnode[p];
-  if (node_size[q] < kSurMin) return;
-  const int64_t c = sur_off[q] + (s - node_off[q]);
+  const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c < kMpTerms) terms[c * (ns + 1) + ns] = 0;  // the slot after each row
+  if (c >= ns) return;
+  const uint32_t p = sur_mem[rvals[c]], q = mnode[p];
   const NodeStat S = st[q];
   const float4 u = U[p];
   const float x = u.x - S.cx, y = u.y - S.cy, z = u.z - S.cz;
@@ -219,23 +219,22 @@ __device__ __forceinline__ float psi_multipole(const int64_t* __restrict__ terms
 
 // Features of surrogate member k, in this order: r / r_vir; fractions of the node's members
 // with radius below 0.5 r, r and 2 r; psi_mp of the node; |v - v_bulk| / sigma_v,1D;
-// log10 g; psi_sph of the deepest node holding the member, converted to this node's units
-// (g_d / g) (r_vir / r_vir,d) -- the well of the member's own substructure.
+// log10 g; log10 (g_d / g) of the deepest hierarchy node d holding the member (its
+// substructure: 0 when the member is in no smaller node).
 __global__ void k_sur_features(int64_t ns, const uint32_t* __restrict__ sur_mem,
                                const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_off,
                                const int64_t* __restrict__ node_size, const float4* __restrict__ U,
                                const float4* __restrict__ V, const NodeStat* __restrict__ st,
                                const double* __restrict__ vbulk, const uint64_t* __restrict__ rkeys,
                                const float* __restrict__ psi_sph, const uint32_t* __restrict__ mem,
-                               const int64_t* __restrict__ deepest,
-                               const uint32_t* __restrict__ deepest_pos, const int64_t* __restrict__ sur_off,
+                               const int64_t* __restrict__ deepest, const int64_t* __restrict__ sur_off,
                                const uint32_t* __restrict__ spos, const int64_t* __restrict__ terms,
                                float eps, float* __restrict__ feat) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= ns) return;
   const uint32_t p = sur_mem[k], q = mnode[p];
   const NodeStat s = st[q];
-  const int64_t g = node_size[q], lo = node_off[q], hi = lo + g;
+  const int64_t g = node_size[q], lo = sur_off[q], hi = lo + g;
   const float r = member_radius(U[p], s);
   const float inv_g = 1.0f / float(g);
   const float f05 = float(count_below(rkeys, lo, hi, 0.5f * r)) * inv_g;
@@ -244,20 +243,16 @@ __global__ void k_sur_features(int64_t ns, const uint32_t* __restrict__ sur_mem,
   const float4 v = V[p];
   const float dvx = v.x - float(vbulk[3 * q]), dvy = v.y - float(vbulk[3 * q + 1]),
               dvz = v.z - float(vbulk[3 * q + 2]);
-  const uint32_t part = mem[p];
-  const int64_t d = deepest[part];
-  const float sub = psi_sph[deepest_pos[part]] * (float(node_size[d]) / float(g)) *
-                    (s.r_vir / st[d].r_vir);
+  const int64_t d = deepest[mem[p]];  // a node at or below q: never -1 for a member of q
   float* F = feat + 8 * k;
   F[0] = r / s.r_vir;
   F[1] = f05;
   F[2] = f1;
   F[3] = f2;
-  const int64_t c0 = sur_off[q];
-  F[4] = psi_multipole(terms, ns, c0, c0 + g, c0 + (int64_t(spos[p]) - lo), U[p], s, eps, g, psi_sph[p]);
+  F[4] = psi_multipole(terms, ns, lo, hi, int64_t(spos[k]), U[p], s, eps, g, psi_sph[k]);
   F[5] = sqrtf(dvx * dvx + dvy * dvy + dvz * dvz) / fmaxf(s.sig_v1d, 1e-30f);
   F[6] = s.log_g;
-  F[7] = sub;
+  F[7] = log10f(float(node_size[d]) * inv_g);
 }
 
 __global__ void k_sur_targets(int64_t ns, const uint32_t* __restrict__ sur_mem,
@@ -733,36 +728,35 @@ static int sur_prepare(rs_ctx* ctx, const double* vbulk, int64_t* ns_out, cudaSt
   // rank holds the exclusive scan of big flags: rank of each big node
   k_big_list<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, rank, big_nodes);
   RS_LAUNCHED(ctx, "k_big_list");
-  // radial order of every node's members (all levels)
-  k_all_radius<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.U, stt, ka, va);
-  RS_LAUNCHED(ctx, "k_all_radius");
+  // radial order of the surrogate members inside their node
+  k_big_radius<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, rank, h.U, stt, ka, va);
+  RS_LAUNCHED(ctx, "k_big_radius");
   uint64_t* rkeys;
   uint32_t* rvals;
-  RS_TRY(radix_sort_u64(ctx, m, 32 + bits_for(uint64_t(nn)), ka, va, kb, vb, &rkeys, &rvals, st));
+  RS_TRY(radix_sort_u64(ctx, ns, 32 + bits_for(uint64_t(nbig)), ka, va, kb, vb, &rkeys, &rvals, st));
   ctx->sur_rkeys = rkeys;
-  int64_t* fix = scratch_t<int64_t>(ctx, S_SUR_FIX, size_t(m) + 1);
-  uint32_t* spos = scratch_t<uint32_t>(ctx, S_SUR_SPOS, size_t(m));
+  int64_t* fix = scratch_t<int64_t>(ctx, S_SUR_FIX, size_t(ns) + 1);
+  uint32_t* spos = scratch_t<uint32_t>(ctx, S_SUR_SPOS, size_t(ns));
   if (!fix || !spos) return RS_ERR_OOM;
   const float eps = std::max(ctx->cfg.softening, 1e-6f);
-  k_sur_inv_r<<<grid_for(m, kT), kT, 0, st>>>(m, rkeys, rvals, eps, fix, spos);
+  k_sur_inv_r<<<grid_for(ns, kT), kT, 0, st>>>(ns, rkeys, rvals, eps, fix, spos);
   RS_LAUNCHED(ctx, "k_sur_inv_r");
-  RS_TRY(exclusive_scan_i64(ctx, m, fix, fix + m, st));
-  k_psi_sph<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_off, h.node_size, stt, h.U, fix, spos, eps,
-                                           psi_sph);
+  RS_TRY(exclusive_scan_i64(ctx, ns, fix, fix + ns, st));
+  k_psi_sph<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, sur_off, h.node_size, stt, h.U, fix, spos,
+                                            eps, psi_sph);
   RS_LAUNCHED(ctx, "k_psi_sph");
   const int64_t nterms = int64_t(kMpTerms) * (ns + 1);
   int64_t* terms = scratch_t<int64_t>(ctx, S_SUR_MP, size_t(nterms) + 1);
   if (!terms) return RS_ERR_OOM;
-  k_mp_terms<<<grid_for(std::max<int64_t>(m, kMpTerms), kT), kT, 0, st>>>(m, rvals, h.mnode, h.node_off,
-                                                                        h.node_size, sur_off, stt, h.U, eps,
-                                                                        ns, terms);
+  k_mp_terms<<<grid_for(std::max<int64_t>(ns, kMpTerms), kT), kT, 0, st>>>(rvals, sur_mem, h.mnode, stt, h.U,
+                                                                         eps, ns, terms);
   RS_LAUNCHED(ctx, "k_mp_terms");
   RS_TRY(exclusive_scan_i64(ctx, nterms, terms, terms + nterms, st));
   {
     ProfScope prof_(ctx, "k_sur_features", st);
     k_sur_features<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_off, h.node_size, h.U,
                                                    h.V, stt, vbulk, rkeys, psi_sph, h.mem, h.deepest,
-                                                   h.deepest_pos, sur_off, spos, terms, eps, feat);
+                                                   sur_off, spos, terms, eps, feat);
   }
   RS_LAUNCHED(ctx, "k_sur_features");
   return RS_OK;
