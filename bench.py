@@ -126,12 +126,17 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
-def _snapshot(workload, rank):
+def synth_seed_for_rank(workload, rank):
+    """Seed of the independent snapshot rank `rank` processes (weak scaling, no exchange)."""
     from paper_2412_18629_gb300 import synth
-    spec = synth.WORKLOADS[workload]
-    if rank:
-        import dataclasses
-        spec = dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
+    return synth.WORKLOADS[workload].seed + 1000 * rank
+
+
+def _snapshot(workload, rank):
+    import dataclasses
+
+    from paper_2412_18629_gb300 import synth
+    spec = dataclasses.replace(synth.WORKLOADS[workload], seed=synth_seed_for_rank(workload, rank))
     return spec, synth.generate(spec)
 
 

@@ -52,7 +52,8 @@ typedef struct rs_config {
   float link_len;             /* 3D linking length ll; pairs with d^2 <= ll*ll are linked */
   float softening;            /* Plummer softening eps of the potential (Mpc/h) */
   float margin_factor;        /* surrogate gate: classify iff |E_pred| > margin_factor *
-                                 err_max * G M / r_vir (4) */
+                                 err_node * G M / r_vir (4); err_node is the node's
+                                 calibrated surrogate error (see rs_surrogate_stats) */
   double particle_mass;       /* m (Msun/h), equal for all particles */
   double G;                   /* gravitational constant, 4.30091e-9 Mpc (km/s)^2 / Msun */
   int32_t f_num, f_den;       /* linked fraction f = f_num / f_den of the 6D FoF (7, 10) */
@@ -190,10 +191,15 @@ int rs_cro_sum_noalloc(int64_t m, const double* a, double* out, void* stream);
  * A small MLP predicts psi = phi r_vir / (G M_node) from 8 per-member features; members whose
  * predicted energy clears a margin are classified without the O(n^2) potential, the rest (and
  * any node failing a spot check) take the exact path. The paper has no learned component; this
- * is the build's batched form. Network (8 -> 64 -> 64 -> 1, ReLU), bf16 weights and hidden
- * activations, float32 accumulation on tensor cores:
+ * is the build's batched + surrogate form. Per node with >= 1024 members, rs_unbind: evaluates
+ * 64 evenly spaced members exactly (held out of the gate) and takes err_node = max(max
+ * |psi_hat - psi| over them, err_max / 8); gates |E_pred| > margin_factor * err_node * G M /
+ * r_vir; re-checks exactly the spot_check gated members of smallest margin and recomputes the
+ * whole node exactly if one flag differs or one error exceeds margin_factor / 2 * err_node.
+ * Network (8 -> 64 -> 64 -> 1, ReLU), bf16 weights and hidden activations, float32
+ * accumulation on tensor cores:
  *   z1 = b1 + W1^T bf16(x); h1 = bf16(relu(z1)); z2 = b2 + W2^T h1; h2 = bf16(relu(z2));
- *   y = b3 + sum_k bf16(W3)[k] h2[k].
+ *   y = b3 + sum_k bf16(W3)[k] h2[k] (float32; four partial sums combined pairwise).
  * Parameters: float32 vector of RS_MLP_PARAMS = 4801 entries: W1 [8][64] at 0, b1 [64] at 512,
  * W2 [64][64] at 576 (row = input), b2 [64] at 4672, W3 [64] at 4736, b3 at 4800. */
 #define RS_MLP_PARAMS 4801
@@ -201,7 +207,8 @@ int rs_cro_sum_noalloc(int64_t m, const double* a, double* out, void* stream);
 /* Load (host float32 [4801]) or read back the context's float32 master parameters. */
 int rs_mlp_set_params(rs_ctx* ctx, const float* params_host);
 int rs_mlp_get_params(rs_ctx* ctx, float* params_host);
-/* Held-out maximum |psi_hat - psi| the gate uses (set by rs_mlp_train, or by the caller). */
+/* Held-out maximum |psi_hat - psi| from training (set by rs_mlp_train, or by the caller); the
+ * gate uses err_max / 8 as the floor of every node's calibrated error. */
 int rs_mlp_set_err_max(rs_ctx* ctx, float err_max);
 
 /* Inference: x float32 [n][8] device -> y float32 [n] device. */
@@ -224,9 +231,10 @@ int rs_mlp_train(rs_ctx* ctx, int64_t n, const float* x, const float* t, int32_t
 /* Surrogate features of the members of every node with >= 1024 members, after rs_unbind:
  * feat_out float32 [n_members][8] device (room for all members; the first *n_out rows are
  * written, node after node, members in id order): r/r_vir (r from the node's mean position),
- * fractions of the node's members with radius below 0.5 r, r and 2 r, psi_sph (potential of
- * the spherically averaged node in units of G g m / r_vir), |v - v_bulk| / sigma_v,1D,
- * log10 g, log10(g_deep) / log10 g (g_deep: size of the deepest node holding the member).
+ * fractions of the node's members with radius below 0.5 r, r and 2 r, psi_mp (the node's
+ * potential at the member from the radially split multipole expansion to quadrupole order,
+ * in units of G g m / r_vir), |v - v_bulk| / sigma_v,1D, log10 g, log10(g_deep / g) (g_deep:
+ * size of the deepest hierarchy node holding the member).
  * psi_out float32 [n_members] device or NULL: training target
  * psi = phi r_vir / (G g m) from the last rs_unbind's float32 potential (that rs_unbind must
  * not have used the surrogate). n_out: host. Errors: RS_ERR_STATE, RS_ERR_OOM, RS_ERR_CUDA. */
@@ -234,10 +242,12 @@ int rs_surrogate_features(rs_ctx* ctx, float* feat_out, float* psi_out, int64_t*
                           void* stream);
 
 /* Counters of the last rs_unbind (host int64 [10]): members of surrogate nodes, gated by the
- * surrogate, sent to the exact per-member path, spot-checked, nodes failing the spot check,
- * float64 fallbacks in the per-member path, float64 fallbacks of the direct sums, members
- * re-run because their node failed, members of nodes sent whole to the direct sum (more than a
- * quarter of their members outside the gate), members whose flag the surrogate decided. */
+ * surrogate, evaluated exactly (calibration members and the members outside the gate, in
+ * nodes not sent whole), spot-checked, nodes failing the spot check, float64 fallbacks in the
+ * surrogate path, float64 fallbacks of the direct sums, gated members recomputed because their
+ * node failed, members of nodes sent whole to the direct sum (at most 1/20 of their members
+ * gated), members whose flag the surrogate decided. Members = decided + exact + spot-checked +
+ * recomputed + whole-node. */
 int rs_surrogate_stats(rs_ctx* ctx, int64_t* stats_out);
 
 /* Stable LSD radix sort of (key, value) pairs by key bits [0, nbits), in place: the sort that
