@@ -165,10 +165,12 @@ def time_oracle(snap, threads):
 
 
 def _hier_work(ctx):
-    """Algorithmic pair counts of the hierarchy: sum over nodes of g (g - 1)."""
+    """Algorithmic pair counts of the hierarchy: sum over nodes of g (g - 1); also the part of
+    the nodes above 384 members (the blocked potential kernel's share)."""
     import paper_2412_18629_gb300 as rs
     sizes = rs.rs_fof6d_copy(ctx)["size"].cpu().numpy().astype(np.float64)
-    return float((sizes * (sizes - 1)).sum()), float(sizes.sum())
+    big = sizes[sizes > 384]
+    return float((sizes * (sizes - 1)).sum()), float((big * (big - 1)).sum())
 
 
 # FP32-pipe operations per pair for the two O(n_g^2) kernels (no FMA contraction):
@@ -193,7 +195,7 @@ def _measure(ctx, pos, vel, ids, n, args, ws, local):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    pairs, _ = _hier_work(ctx)
+    pairs, pairs_big = _hier_work(ctx)
     ctx.profile(True)
     l0 = ctx.kernel_launches
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -210,29 +212,89 @@ def _measure(ctx, pos, vel, ids, n, args, ws, local):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     prof = ctx.profile_totals()
     ctx.profile(False)
+    work = None
+    if ctx.mode != "plain":  # one untimed step through the counting variants of the 6D kernels
+        ctx.count_work(True)
+        step()
+        work = ctx.count_work(False)
     t_max, units = aggregate(elapsed, float(n) * args.steps, ws, f"cuda:{local}")
     return {"value": units / t_max, "ms_per_step": t_max / args.steps * 1e3, "launches": launches,
-            "prof": prof, "pairs": pairs, "clocks": clk.summary(), "fallback": nfb}
+            "prof": prof, "pairs": pairs, "pairs_big": pairs_big, "clocks": clk.summary(),
+            "fallback": nfb, "work": work, "n": n}
 
 
-def _roofline(prof, pairs, steps):
-    """Roofline entry of the dominant instrumented kernel (largest summed CUDA-event time)."""
+def _roofline(prof, pairs, steps, work=None):
+    """Roofline entry of the dominant instrumented kernel (largest summed CUDA-event time).
+    Brute-force pair kernels: algorithmic operations = pairs x operations per pair. Pruned 6D
+    kernels: the d6 evaluations and box lower bounds they perform (tallied in one untimed step
+    by the counting variants), 20 FP32 operations each."""
     if not prof:
         return None
     name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2070e6
     base = name.replace("_pruned", "").replace("_blocked", "")
-    if base in OPS_PER_PAIR and not name.endswith("_pruned"):
+    entry = {"bound": "alu", "kernel": name, "achieved": None, "peak": peak_ops / 1e12,
+             "unit": "Tops/s", "frac": None, "traffic": None, "launches": cnt,
+             "kernel_ms_per_step": ms / steps,
+             "peak_note": "FP32-pipe lane operations at 2070 MHz (152 SMs x 128 lanes)"}
+    work_ops = None
+    if name.endswith("_pruned") and work:
+        key = "nn" if base == "k_nn6d" else "link"
+        work_ops = (work[f"{key}_d6"] + work[f"{key}_box"]) * OPS_PER_PAIR["k_nn6d"] * steps
+        entry["work"] = {"d6_per_step": work[f"{key}_d6"], "box_tests_per_step": work[f"{key}_box"],
+                         "ops_each": OPS_PER_PAIR["k_nn6d"]}
+    elif base in OPS_PER_PAIR and not name.endswith("_pruned"):
         pr = pairs if base != "k_link6d" else pairs / 2.0
-        work = pr * OPS_PER_PAIR[base] * steps
-        achieved = work / (ms / 1e3)
-        return {"bound": "alu", "kernel": name, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None, "launches": cnt,
-                "kernel_ms_per_step": ms / steps,
-                "peak_note": "FP32-pipe lane operations at 2070 MHz (152 SMs x 128 lanes)"}
-    return {"bound": "alu", "kernel": name, "achieved": None, "peak": peak_ops / 1e12,
-            "unit": "Tops/s", "frac": None, "traffic": None, "launches": cnt,
-            "kernel_ms_per_step": ms / steps}
+        work_ops = pr * OPS_PER_PAIR[base] * steps
+    if work_ops is not None:
+        achieved = work_ops / (ms / 1e3)
+        entry.update(achieved=achieved / 1e12, frac=achieved / peak_ops)
+    return entry
+
+
+def _measured_peaks():
+    """The machine's measured peaks (HBM copy GB/s, bf16 TFLOP/s), if the file is present."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _stages(r, steps):
+    """Per-stage roofline figures of the kernels with a defined algorithmic work: the 3D FoF
+    link pass against the measured HBM copy bandwidth (28 B per particle: position, id,
+    label), the pair kernels against the FP32-pipe lane rate (brute force: pairs x operations;
+    pruned: tallied d6 evaluations and box tests; blocked potential: pairs of the nodes above
+    384 members x 7 operations)."""
+    prof, out = r["prof"], {}
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2070e6
+    hbm = _measured_peaks().get("hbm_gbs")
+
+    def ms(k):
+        return prof[k][0] / steps / 1e3 if k in prof and prof[k][0] > 0 else None
+
+    if ms("k_fof_link") and hbm:
+        gbs = r["n"] * 28.0 / ms("k_fof_link") / 1e9
+        out["k_fof_link"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                             "frac": gbs / hbm, "note": "latency-bound union-find; HBM is not its limit"}
+    alu = {}
+    if ms("k_potential_blocked") and r.get("form") != "surrogate":
+        alu["k_potential_blocked"] = r["pairs_big"] * OPS_PER_PAIR["k_potential"]
+    for k in ("k_nn6d", "k_link6d"):
+        if ms(k):
+            alu[k] = r["pairs"] * OPS_PER_PAIR[k] / (2.0 if k == "k_link6d" else 1.0)
+    w = r.get("work")
+    if w:
+        for k, key in (("k_nn6d_pruned", "nn"), ("k_link6d_pruned", "link")):
+            if ms(k):
+                alu[k] = (w[f"{key}_d6"] + w[f"{key}_box"]) * OPS_PER_PAIR["k_nn6d"]
+    for k, ops in alu.items():
+        a = ops / ms(k)
+        out[k] = {"bound": "alu", "achieved": a / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                  "frac": a / peak_ops, "ms_per_step": ms(k) * 1e3}
+    return out
 
 
 TRAIN_SAMPLES = 1_000_000
@@ -344,14 +406,15 @@ def run_ours(args):
                        "form": head, "nodes": int(ctx.n_nodes), "members": int(ctx.n_members),
                        "pairs": r["pairs"], "l2": "inputs and hierarchy larger than L2 (no flush)",
                        "parallelism": f"independent snapshots x{ws}"},
-            "roofline": _roofline(r["prof"], r["pairs"], args.steps), "cpu_baseline": cpu,
+            "roofline": _roofline(r["prof"], r["pairs"], args.steps, r["work"]), "cpu_baseline": cpu,
             "e2e": {"value": e_units / e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": r["launches"], "clocks": r["clocks"], "surrogate_training": training,
             "forms": {f: {"value": v["value"], "ms_per_step": v["ms_per_step"],
                           "gpu_launches": v["launches"], "fallback_members": v["fallback"],
                           "kernels_ms_per_step": {k: t[0] / args.steps for k, t in v["prof"].items()},
-                          "roofline": _roofline(v["prof"], v["pairs"], args.steps),
+                          "roofline": _roofline(v["prof"], v["pairs"], args.steps, v["work"]),
+                          "stages": _stages(dict(v, form=f), args.steps),
                           "clocks": v["clocks"],
                           "surrogate_stats": v.get("surrogate_stats")}
                       for f, v in res.items()},

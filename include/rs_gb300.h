@@ -265,6 +265,16 @@ int rs_sort_pairs(rs_ctx* ctx, int64_t n, int nbits, uint64_t* keys, uint32_t* v
  * buffer of name_cap bytes), summed milliseconds and launch count (host). Waits for the
  * recorded events. Errors: RS_ERR_CAPACITY when index is past the last entry. */
 int rs_profile(rs_ctx* ctx, int enable);
+
+/* Work counting of the batched form's pruned 6D kernels (instrumentation, not part of the
+ * method): while enabled, k_nn6d_pruned and k_link6d_pruned run a variant that tallies, per
+ * query lane, the d6 evaluations it performs and the box lower bounds it computes (bucket,
+ * sub-bucket and superbucket tests; box-box tests counted once per warp); the results are
+ * unchanged. rs_count_work(ctx, 1, NULL) clears the tallies and enables counting;
+ * rs_count_work(ctx, 0, counts) disables it. counts_out (host int64 [4], may be NULL) receives,
+ * after a device synchronisation: NN d6 evaluations, NN box tests, link d6 evaluations, link
+ * box tests, accumulated since the last enable. Errors: RS_ERR_OOM, RS_ERR_CUDA. */
+int rs_count_work(rs_ctx* ctx, int enable, int64_t* counts_out);
 int rs_profile_get(rs_ctx* ctx, int index, char* name, int name_cap, double* total_ms,
                    int64_t* launches);
 

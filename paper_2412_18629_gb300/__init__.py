@@ -86,11 +86,12 @@ def load_library():
             getattr(lib, name).restype = i32
         lib.rs_cro_sum_noalloc.argtypes = [i64, P, P, P]
         lib.rs_profile.argtypes = [P, ctypes.c_int]
+        lib.rs_count_work.argtypes = [P, ctypes.c_int, P]
         lib.rs_profile_get.argtypes = [P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_fof3d", "rs_fof6d", "rs_fof6d_copy",
                      "rs_fof6d_node_params", "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile",
-                     "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc"):
+                     "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -162,6 +163,17 @@ class Context:
     def profile(self, enable=True):
         """Start (clearing totals) or stop CUDA-event timing of the dominant kernels."""
         self.check(self.lib.rs_profile(self.handle, 1 if enable else 0))
+
+    def count_work(self, enable=True):
+        """Enable (clearing) or disable the counting variants of the pruned 6D kernels; on
+        disable returns {nn_d6, nn_box, link_d6, link_box} accumulated since the enable."""
+        import numpy as np
+        out = np.zeros(4, np.int64)
+        self.check(self.lib.rs_count_work(self.handle, 1 if enable else 0,
+                                          None if enable else out.ctypes.data))
+        if not enable:
+            return dict(zip(("nn_d6", "nn_box", "link_d6", "link_box"), map(int, out)))
+        return None
 
     def profile_totals(self):
         """{kernel: (total_ms, launches)} recorded since profile(True)."""

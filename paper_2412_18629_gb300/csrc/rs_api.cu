@@ -74,6 +74,23 @@ extern "C" int rs_profile_get(rs_ctx* ctx, int index, char* name, int name_cap, 
   return RS_OK;
 }
 
+extern "C" int rs_count_work(rs_ctx* ctx, int enable, int64_t* counts_out) {
+  if (!ctx) return RS_ERR_INVALID_ARG;
+  ctx->err[0] = 0;
+  RS_CUDA(ctx, cudaSetDevice(ctx->device));
+  unsigned long long* w = scratch_t<unsigned long long>(ctx, rs::S_P_WORK, 4);
+  if (!w) return RS_ERR_OOM;
+  if (counts_out) {
+    RS_CUDA(ctx, cudaDeviceSynchronize());
+    unsigned long long h[4];
+    RS_CUDA(ctx, cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i) counts_out[i] = int64_t(h[i]);
+  }
+  if (enable) RS_CUDA(ctx, cudaMemset(w, 0, 4 * sizeof(unsigned long long)));
+  ctx->count_work = enable != 0;
+  return RS_OK;
+}
+
 extern "C" int rs_ctx_destroy(rs_ctx* ctx) {
   if (!ctx) return RS_OK;
   cudaSetDevice(ctx->device);

@@ -36,7 +36,7 @@ enum Slot : int {
   S_U_TILEPERM, S_U_OKEY_A, S_U_OKEY_B, S_U_OVAL_A, S_U_OVAL_B,
   // batched form: pruned 6D searches
   S_P_MEANU, S_P_MEANV, S_P_US, S_P_VS, S_P_SP, S_P_BOFF, S_P_BUCKET, S_P_BOX, S_P_SUB,
-  S_P_SBOFF, S_P_SBOX, S_P_ORDER, S_P_QCTR,
+  S_P_SBOFF, S_P_SBOX, S_P_ORDER, S_P_QCTR, S_P_WORK,
   // surrogate MLP
   S_MLP_DEV, S_MLP_W, S_MLP_PART, S_MLP_SSE, S_MLP_M, S_MLP_G, S_MLP_IDX, S_MLP_BIDX, S_MLP_XH,
   S_MLP_YH,
@@ -85,6 +85,7 @@ struct rs_ctx {
   int64_t sur_stats[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
   bool profile = false;
+  bool count_work = false;  // counting variants of the pruned 6D kernels (rs_count_work)
   struct ProfRec {
     std::string name;
     cudaEvent_t a, b;

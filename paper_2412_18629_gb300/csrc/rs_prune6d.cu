@@ -264,14 +264,22 @@ struct NNArgs {
   const uint32_t* sp;
   const float4* inv;
   unsigned long long* counter;
+  unsigned long long* work;  // [4]: NN d6, NN box tests, link d6, link box tests (counting variant)
+};
+
+// Per-lane tallies of the counting variant (evaluated d6 and box tests).
+struct Tally {
+  unsigned long long d6 = 0, box = 0;
 };
 
 // Evaluate target bucket b for the warp's query lanes (nearest-neighbour search).
+template <bool kCount>
 __device__ __forceinline__ void nn_bucket(const NNArgs& A, int64_t a, int64_t b, bool valid, float4 ui,
                                           float4 vi, float isx, float isv, float& best, int lane,
-                                          float4 (&su)[32], float4 (&sv)[32]) {
+                                          float4 (&su)[32], float4 (&sv)[32], Tally& T) {
   const Box B = A.box[b];
   const bool need = valid && lb_point_box(ui, vi, B, isx, isv) <= best;
+  if (kCount) T.box += valid;
   if (!__any_sync(0xffffffffu, need)) return;
   const Bucket Bb = A.bk[b];
   __syncwarp();
@@ -284,9 +292,11 @@ __device__ __forceinline__ void nn_bucket(const NNArgs& A, int64_t a, int64_t b,
   for (uint32_t s0 = 0; s0 < Bb.count; s0 += 8) {
     const Box Sb = A.sub[4 * b + (s0 >> 3)];
     const bool sneed = need && lb_point_box(ui, vi, Sb, isx, isv) <= best;
+    if (kCount) T.box += need;
     if (!__any_sync(0xffffffffu, sneed)) continue;
     if (sneed) {
       const uint32_t s1 = min(s0 + 8, Bb.count);
+      if (kCount) T.d6 += s1 - s0;
       for (uint32_t j = s0; j < s1; ++j) {
         if (j == self) continue;
         best = fminf(best, d6(ui, vi, su[j], sv[j], isx, isv));
@@ -295,10 +305,27 @@ __device__ __forceinline__ void nn_bucket(const NNArgs& A, int64_t a, int64_t b,
   }
 }
 
+template <bool kCount>
+__device__ __forceinline__ void flush_tally(const Tally& T, unsigned long long* work, int lane) {
+  if (!kCount) return;
+  unsigned long long d = T.d6, b = T.box;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    d += __shfl_xor_sync(0xffffffffu, d, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+  }
+  if (lane == 0) {
+    atomicAdd(work, d);
+    atomicAdd(work + 1, b);
+  }
+}
+
+template <bool kCount>
 __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict__ nn2) {
   __shared__ float4 su[kWarpsPerBlock][32], sv[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int64_t nbk = *A.nbuckets;
+  Tally T;
   while (true) {
     const int64_t w = next_work(A.counter, lane);
     if (w >= nbk) break;
@@ -316,6 +343,7 @@ __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict_
       if (s < 0 || s >= nsb) continue;
       const Box SB = A.sbox[Aq.sbfirst + s];
       const bool need = valid && lb_point_box(ui, vi, SB, isx, isv) <= best;
+      if (kCount) T.box += valid;
       if (!__any_sync(0xffffffffu, need)) continue;
       const int64_t b_lo = int64_t(Aq.first) + 32 * s;
       const int64_t b_hi = rsd::min64(b_lo + 32, int64_t(Aq.last) + 1);
@@ -323,29 +351,34 @@ __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict_
         for (int64_t t2 = 0; t2 <= 2 * 32; ++t2) {
           const int64_t b = outward(a, t2);
           if (b < b_lo || b >= b_hi) continue;
-          nn_bucket(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb]);
+          nn_bucket<kCount>(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb], T);
         }
       } else if (s > own) {
         for (int64_t b = b_lo; b < b_hi; ++b)
-          nn_bucket(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb]);
+          nn_bucket<kCount>(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb], T);
       } else {
         for (int64_t b = b_hi - 1; b >= b_lo; --b)
-          nn_bucket(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb]);
+          nn_bucket<kCount>(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb], T);
       }
     }
     if (valid) nn2[A.sp[si]] = best;
   }
+  flush_tally<kCount>(T, A.work, lane);
 }
 
 // Link pairs of query bucket a (box Abox) with target bucket b >= a.
+template <bool kCount>
 __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t b, const Box& Abox,
                                             bool active, float4 ui, float4 vi, uint32_t pi,
                                             float isx, float isv, float l2, const float* nn2,
                                             uint32_t* uf, int lane, float4 (&su)[32],
-                                            float4 (&sv)[32], uint32_t (&sj)[32], float (&snn)[32]) {
+                                            float4 (&sv)[32], uint32_t (&sj)[32], float (&snn)[32],
+                                            Tally& T) {
   const Box B = A.box[b];
+  if (kCount) T.box += (lane == 0);
   if (lb_box_box(Abox, B, isx, isv) > l2) return;
   const bool need = active && lb_point_box(ui, vi, B, isx, isv) <= l2;
+  if (kCount) T.box += active;
   if (!__any_sync(0xffffffffu, need)) return;
   const Bucket Bb = A.bk[b];
   __syncwarp();
@@ -359,11 +392,14 @@ __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t 
   const uint32_t j0 = (b == a) ? uint32_t(lane) + 1 : 0u;
   for (uint32_t s0 = 0; s0 < Bb.count; s0 += 8) {
     const Box Sb = A.sub[4 * b + (s0 >> 3)];
+    if (kCount) T.box += (lane == 0);
     if (lb_box_box(Abox, Sb, isx, isv) > l2) continue;
     const bool sneed = need && lb_point_box(ui, vi, Sb, isx, isv) <= l2;
+    if (kCount) T.box += need;
     if (!__any_sync(0xffffffffu, sneed)) continue;
     if (sneed) {
       const uint32_t s1 = min(s0 + 8, Bb.count);
+      if (kCount) T.d6 += s1 > max(s0, j0) ? s1 - max(s0, j0) : 0u;
       for (uint32_t j = max(s0, j0); j < s1; ++j) {
         if (snn[j] > l2) continue;
         if (d6(ui, vi, su[j], sv[j], isx, isv) <= l2) rsd::uf_unite(uf, pi, sj[j]);
@@ -372,8 +408,10 @@ __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t 
   }
 }
 
+template <bool kCount>
 __global__ void __launch_bounds__(kT)
 k_link6d_pruned(NNArgs A, const float* __restrict__ nn2, uint32_t* __restrict__ uf) {
+  Tally T;
   __shared__ float4 su[kWarpsPerBlock][32], sv[kWarpsPerBlock][32];
   __shared__ uint32_t sj[kWarpsPerBlock][32];
   __shared__ float snn[kWarpsPerBlock][32];
@@ -396,16 +434,19 @@ k_link6d_pruned(NNArgs A, const float* __restrict__ nn2, uint32_t* __restrict__ 
     const int64_t own = (a - int64_t(Aq.first)) >> 5, nsb = Aq.sbcount;
     for (int64_t s = own; s < nsb; ++s) {
       const Box SB = A.sbox[Aq.sbfirst + s];
+      if (kCount) T.box += (lane == 0);
       if (lb_box_box(Abox, SB, isx, isv) > l2) continue;
       const bool need = active && lb_point_box(ui, vi, SB, isx, isv) <= l2;
+      if (kCount) T.box += active;
       if (!__any_sync(0xffffffffu, need)) continue;
       const int64_t b_lo = rsd::min64(int64_t(Aq.first) + 32 * s, int64_t(Aq.last) + 1);
       const int64_t b_hi = rsd::min64(int64_t(Aq.first) + 32 * s + 32, int64_t(Aq.last) + 1);
       for (int64_t b = (s == own ? a : b_lo); b < b_hi; ++b)
-        link_bucket(A, a, b, Abox, active, ui, vi, pi, isx, isv, l2, nn2, uf, lane, su[wb], sv[wb],
-                    sj[wb], snn[wb]);
+        link_bucket<kCount>(A, a, b, Abox, active, ui, vi, pi, isx, isv, l2, nn2, uf, lane, su[wb], sv[wb],
+                            sj[wb], snn[wb], T);
     }
   }
+  flush_tally<kCount>(T, A.work + 2, lane);
 }
 
 int bits_for(uint64_t v) {
@@ -428,6 +469,7 @@ NNArgs nn_args(rs_ctx* ctx, int64_t nn) {
   A.sp = static_cast<const uint32_t*>(ctx->buf[S_P_SP].ptr);
   A.inv = h.inv;
   A.counter = static_cast<unsigned long long*>(ctx->buf[S_P_QCTR].ptr);
+  A.work = static_cast<unsigned long long*>(ctx->buf[S_P_WORK].ptr);
   return A;
 }
 
@@ -453,6 +495,7 @@ int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t
   Box* sub = scratch_t<Box>(ctx, S_P_SUB, size_t(nbk_ub) * 4);
   Box* sbox = scratch_t<Box>(ctx, S_P_SBOX, size_t(nsb_ub));
   unsigned long long* qctr = scratch_t<unsigned long long>(ctx, S_P_QCTR, 2);
+  if (!scratch_t<unsigned long long>(ctx, S_P_WORK, 4)) return RS_ERR_OOM;
   if (!mean_u || !ka || !kb || !va || !vb || !Us || !Vs || !sp || !boff || !sboff || !bk || !box ||
       !sub || !sbox || !qctr)
     return RS_ERR_OOM;
@@ -497,9 +540,11 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
   const int64_t nbk_ub = nn + m / 32 + 1;
   const unsigned grid = unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 8));
   RS_CUDA(ctx, cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st));
-  {
+  if (ctx->count_work) {
+    k_nn6d_pruned<true><<<grid, kT, 0, st>>>(A, nn2);
+  } else {
     ProfScope prof_(ctx, "k_nn6d_pruned", st);
-    k_nn6d_pruned<<<grid, kT, 0, st>>>(A, nn2);
+    k_nn6d_pruned<false><<<grid, kT, 0, st>>>(A, nn2);
   }
   RS_LAUNCHED(ctx, "k_nn6d_pruned");
   return RS_OK;
@@ -514,9 +559,11 @@ int rs::prune6d_link(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m,
   const int64_t nbk_ub = nn + m / 32 + 1;
   const unsigned grid = unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 8));
   RS_CUDA(ctx, cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st));
-  {
+  if (ctx->count_work) {
+    k_link6d_pruned<true><<<grid, kT, 0, st>>>(A, nn2, uf);
+  } else {
     ProfScope prof_(ctx, "k_link6d_pruned", st);
-    k_link6d_pruned<<<grid, kT, 0, st>>>(A, nn2, uf);
+    k_link6d_pruned<false><<<grid, kT, 0, st>>>(A, nn2, uf);
   }
   RS_LAUNCHED(ctx, "k_link6d_pruned");
   return RS_OK;

@@ -66,3 +66,23 @@ def test_plain_and_batched_identical_on_large_groups():
     assert a["hier"]["size"].max() > 5000
     o = oracle.hierarchy(s["pos"], s["vel"], s["ids"], a["labels"], s["box"])
     assert_hier_equal(b["hier"], o)
+
+
+def test_work_counting_variant_gives_the_same_hierarchy():
+    """The counting variants of the pruned kernels (instrumentation for the roofline) leave the
+    hierarchy unchanged and tally fewer d6 evaluations than the brute-force pair count."""
+    import paper_2412_18629_gb300 as rs
+    from helpers import gpu_ctx, to_dev
+    s = small_snapshot(1 << 16, 40.0, 23, n_max=12000)
+    ref = gpu_pipeline(s, stages=("fof3d", "fof6d"), mode="batched")
+    ctx = gpu_ctx(s, mode="batched")
+    pos, vel, ids = to_dev(s)
+    ctx.count_work(True)
+    lab, _ = rs.rs_fof3d(ctx, pos, ids)
+    rs.rs_fof6d(ctx, pos, vel, ids, lab)
+    w = ctx.count_work(False)
+    got = {k: v.cpu().numpy() for k, v in rs.rs_fof6d_copy(ctx).items()}
+    assert_hier_equal(got, ref["hier"])
+    sizes = got["size"].astype(np.float64)
+    assert 0 < w["nn_d6"] < (sizes * (sizes - 1)).sum()
+    assert w["nn_box"] > 0 and w["link_d6"] > 0 and w["link_box"] > 0
