@@ -33,10 +33,10 @@ enum Slot : int {
   S_H_NODE_MOM,
   // rs_unbind / rs_halo_props state
   S_U_PHI, S_U_BOUND, S_U_NB, S_U_VBULK, S_U_AMBIG, S_U_FLAGS, S_U_TILEBIG,
-  S_U_TILEPERM, S_U_OKEY_A, S_U_OKEY_B, S_U_OVAL_A, S_U_OVAL_B,
+  S_U_TILEPERM, S_U_OKEY_A, S_U_OKEY_B, S_U_OVAL_A, S_U_OVAL_B, S_U_FBMAX, S_U_FBCHUNK,
   // batched form: pruned 6D searches
   S_P_MEANU, S_P_MEANV, S_P_US, S_P_VS, S_P_SP, S_P_BOFF, S_P_BUCKET, S_P_BOX, S_P_SUB,
-  S_P_SBOFF, S_P_SBOX, S_P_ORDER, S_P_QCTR, S_P_WORK,
+  S_P_SBOFF, S_P_SBOX, S_P_ORDER, S_P_QCTR, S_P_WORK, S_P_NN2S,
   // surrogate MLP
   S_MLP_DEV, S_MLP_W, S_MLP_PART, S_MLP_SSE, S_MLP_M, S_MLP_G, S_MLP_IDX, S_MLP_BIDX, S_MLP_XH,
   S_MLP_YH,

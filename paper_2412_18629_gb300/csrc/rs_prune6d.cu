@@ -102,6 +102,12 @@ __global__ void k_gather_sorted(int64_t mb, int64_t m, const uint32_t* __restric
   sp[s] = p;
 }
 
+__global__ void k_gather_nn2(int64_t m, const uint32_t* __restrict__ sp, const float* __restrict__ nn2,
+                             float* __restrict__ nn2s) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s < m) nn2s[s] = nn2[sp[s]];
+}
+
 __global__ void k_bucket_counts(int64_t nb, int64_t nn, const int64_t* __restrict__ node_size,
                                 int64_t* __restrict__ bcnt, int64_t* __restrict__ sbcnt) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -133,6 +139,14 @@ __device__ __forceinline__ Box make_box(const float (&lo)[6], const float (&hi)[
              make_float4(lo[3], lo[4], lo[5], 0.f), make_float4(hi[3], hi[4], hi[5], 0.f)};
 }
 
+// Node size class for the work queue: 8 * floor(log2 g) + the next 3 bits of g (monotone in
+// g, 0..254 for g < 2^31), so one 8-bit radix pass orders the buckets largest node first.
+__device__ __forceinline__ uint32_t size_class(int64_t g) {
+  const int L = 63 - __clzll(uint64_t(g));
+  const uint32_t f = L >= 3 ? uint32_t((uint64_t(g) >> (L - 3)) & 7u) : uint32_t((uint64_t(g) << (3 - L)) & 7u);
+  return uint32_t(min(L, 31)) * 8u + f > 254u ? 254u : uint32_t(min(L, 31)) * 8u + f;
+}
+
 // One warp per bucket (padding warps write a queue key that sorts last): bucket table entry,
 // box, four 8-member sub-boxes (an empty sub-bucket gets lo = +inf, hi = -inf, so every gap to
 // it is +inf), and the work-queue key (largest node first).
@@ -147,7 +161,7 @@ k_buckets(int64_t nb, int64_t nn, int64_t mb, int64_t nbk_ub, const int64_t* __r
   if (w >= nbk_ub) return;
   if (w >= bucket_off[nn]) {
     if (lane == 0) {
-      qkey[w] = 0xffffffffull;
+      qkey[w] = 255u;  // after every real bucket (their keys are < 255: nodes have >= 2 members)
       qval[w] = uint32_t(w);
     }
     return;
@@ -176,7 +190,7 @@ k_buckets(int64_t nb, int64_t nn, int64_t mb, int64_t nbk_ub, const int64_t* __r
     b.pad = 0;
     bk[w] = b;
     box[w] = make_box(lo, hi);
-    qkey[w] = 0xfffffffeull - uint64_t(node_size[q]);
+    qkey[w] = 255u - size_class(node_size[q]);
     qval[w] = uint32_t(w);
   }
 }
@@ -265,6 +279,7 @@ struct NNArgs {
   const float4* inv;
   unsigned long long* counter;
   unsigned long long* work;  // [4]: NN d6, NN box tests, link d6, link box tests (counting variant)
+  const float* nn2s;         // nearest-neighbour d6 in sorted member order (link pass)
 };
 
 // Per-lane tallies of the counting variant (evaluated d6 and box tests).
@@ -386,7 +401,7 @@ __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t 
     su[lane] = A.Us[Bb.start + lane];
     sv[lane] = A.Vs[Bb.start + lane];
     sj[lane] = A.sp[Bb.start + lane];
-    snn[lane] = nn2[A.sp[Bb.start + lane]];
+    snn[lane] = A.nn2s[Bb.start + lane];
   }
   __syncwarp();
   const uint32_t j0 = (b == a) ? uint32_t(lane) + 1 : 0u;
@@ -428,7 +443,7 @@ k_link6d_pruned(NNArgs A, const float* __restrict__ nn2, uint32_t* __restrict__ 
     const uint32_t si = Aq.start + (valid ? lane : 0);
     const float4 ui = A.Us[si], vi = A.Vs[si];
     const uint32_t pi = A.sp[si];
-    const bool active = valid && nn2[pi] <= l2;
+    const bool active = valid && A.nn2s[si] <= l2;
     if (!__any_sync(0xffffffffu, active)) continue;
     const Box Abox = A.box[a];
     const int64_t own = (a - int64_t(Aq.first)) >> 5, nsb = Aq.sbcount;
@@ -470,6 +485,7 @@ NNArgs nn_args(rs_ctx* ctx, int64_t nn) {
   A.inv = h.inv;
   A.counter = static_cast<unsigned long long*>(ctx->buf[S_P_QCTR].ptr);
   A.work = static_cast<unsigned long long*>(ctx->buf[S_P_WORK].ptr);
+  A.nn2s = nullptr;
   return A;
 }
 
@@ -525,7 +541,7 @@ int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t
   RS_LAUNCHED(ctx, "k_superboxes");
   uint64_t* qk_out;
   uint32_t* qv_out;
-  RS_TRY(radix_sort_u64(ctx, nbk_ub, 32, qk, qv, qk2, qv2, &qk_out, &qv_out, st));
+  RS_TRY(radix_sort_u64(ctx, nbk_ub, 8, qk, qv, qk2, qv2, &qk_out, &qv_out, st));
   uint32_t* qorder = scratch_t<uint32_t>(ctx, S_P_ORDER, size_t(nbk_ub));
   if (!qorder) return RS_ERR_OOM;
   RS_CUDA(ctx, cudaMemcpyAsync(qorder, qv_out, sizeof(uint32_t) * nbk_ub, cudaMemcpyDeviceToDevice, st));
@@ -556,6 +572,11 @@ int rs::prune6d_link(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m,
   (void)mb;
   NNArgs A = nn_args(ctx, nn);
   A.counter += 1;
+  float* nn2s = scratch_t<float>(ctx, S_P_NN2S, size_t(std::max<int64_t>(m, 1)));
+  if (!nn2s) return RS_ERR_OOM;
+  k_gather_nn2<<<grid_for(m, kT), kT, 0, st>>>(m, A.sp, nn2, nn2s);
+  RS_LAUNCHED(ctx, "k_gather_nn2");
+  A.nn2s = nn2s;
   const int64_t nbk_ub = nn + m / 32 + 1;
   const unsigned grid = unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 8));
   RS_CUDA(ctx, cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st));

@@ -680,12 +680,12 @@ int bits_for(uint64_t v) {
   return b;
 }
 
-// k_fallback of rs_unbind.cu (float64 canonical-order potential of queued members)
+// The float64 canonical-order potential of queued members (rs_unbind.cu)
 }  // namespace
 
 namespace rs {
 int unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
-                    const double* vbulk, uint8_t* bound, cudaStream_t st);
+                    const double* vbulk, uint8_t* bound, cudaStream_t st, float* phi_out = nullptr);
 int unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t* bound,
                  uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st);
 

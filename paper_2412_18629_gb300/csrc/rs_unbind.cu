@@ -7,8 +7,9 @@
 //   k_flags       float64 kinetic energy against the node's bulk velocity (canonical-order sum),
 //                 E = KE + phi~. |E| > 2 B |phi~| decides the flag; otherwise the member is queued
 //                 for the exact float64 potential.
-//   k_fallback    one warp per queued member: the float64 potential in the canonical reduction
-//                 order, bit-identical to the definition, then the exact flag.
+//   k_fallback_*  the float64 potential of each queued member in the canonical reduction order,
+//                 bit-identical to the definition (one warp per 1024-term chunk, chunk totals
+//                 combined by the pairwise tree), then the exact flag.
 //   k_halo        bound count, halo decision, bound mass per node.
 // Properties (rs_halo_props): canonical-order sums over bound members (unbound contribute 0).
 #include <cmath>
@@ -21,7 +22,7 @@ int gather_members(rs_ctx* ctx, int64_t mb, int64_t me, int64_t nb, int64_t ne, 
 int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned long long* counters,
                      cudaStream_t st);
 int unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
-                    const double* vbulk, uint8_t* bound, cudaStream_t st);
+                    const double* vbulk, uint8_t* bound, cudaStream_t st, float* phi_out = nullptr);
 int unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t* bound,
                  uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st);
 }  // namespace rs
@@ -275,51 +276,71 @@ __global__ void k_flags(int64_t m, const uint32_t* __restrict__ mnode, const int
   }
 }
 
-// Exact float64 potential of queued members, canonical reduction order over j in member order
-// with the self term 0.0; one warp per member.
-__global__ void __launch_bounds__(kT)
-k_fallback(const unsigned long long* __restrict__ n_ambig, const uint32_t* __restrict__ ambig,
-           const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_off,
-           const int64_t* __restrict__ node_size, const float4* __restrict__ U,
-           const float4* __restrict__ V, const double* __restrict__ vbulk, double eps2, double Gm,
-           uint8_t* __restrict__ bound, float* __restrict__ phi_out) {
-  const int lane = threadIdx.x & 31;
+// Exact float64 potential of queued members: the canonical reduction order over j in member
+// order with the self term 0.0, spread over the GPU because the float64 pipe runs 2 lanes per
+// clock per SM on this part: one warp per chunk of 1024 terms (blocks of 8 chunks of member
+// w0 + blockIdx.y) writes the chunk total to chunk_tot[w][c]; k_fallback_finish combines them
+// with the pairwise tree and takes the flag.
+__global__ void k_fallback_max_chunks(const unsigned long long* __restrict__ n_ambig,
+                                      const uint32_t* __restrict__ ambig, const uint32_t* __restrict__ mnode,
+                                      const int64_t* __restrict__ node_size,
+                                      unsigned long long* __restrict__ out) {
   const unsigned long long total = *n_ambig;
-  for (unsigned long long w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < total;
-       w += (int64_t(gridDim.x) * blockDim.x) >> 5) {
-    const uint32_t p = ambig[w];
-    const uint32_t q = mnode[p];
-    const int64_t base = node_off[q], g = node_size[q];
-    const int64_t i = int64_t(p) - base;
-    const float4 ui = U[p];
-    const double xi = ui.x, yi = ui.y, zi = ui.z;
-    rsd::CroTree tree;
-    for (int64_t c = 0; c * 1024 < g; ++c) {
-      double acc = 0.0;
-      for (int k = 0; k < 32; ++k) {
-        const int64_t j = c * 1024 + lane + 32 * k;
-        if (j < g) {
-          double term = 0.0;
-          if (j != i) {
-            const float4 uj = U[base + j];
-            const double dx = __dsub_rn(double(uj.x), xi);
-            const double dy = __dsub_rn(double(uj.y), yi);
-            const double dz = __dsub_rn(double(uj.z), zi);
-            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            term = __ddiv_rn(1.0, __dsqrt_rn(__dadd_rn(r2, eps2)));
-          }
-          acc = __dadd_rn(acc, term);
-        }
+  for (unsigned long long w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < total;
+       w += int64_t(gridDim.x) * blockDim.x)
+    atomicMax(out, (unsigned long long)((node_size[mnode[ambig[w]]] + 1023) / 1024));
+}
+
+__global__ void __launch_bounds__(kT)
+k_fallback_chunks(int64_t w0, const uint32_t* __restrict__ ambig, const uint32_t* __restrict__ mnode,
+                  const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
+                  const float4* __restrict__ U, double eps2, int64_t max_chunks,
+                  double* __restrict__ chunk_tot) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = w0 + blockIdx.y;
+  const int64_t c = int64_t(blockIdx.x) * (kT / 32) + (threadIdx.x >> 5);
+  const uint32_t p = ambig[w];
+  const uint32_t q = mnode[p];
+  const int64_t base = node_off[q], g = node_size[q];
+  if (c * 1024 >= g) return;
+  const int64_t i = int64_t(p) - base;
+  const float4 ui = U[p];
+  const double xi = ui.x, yi = ui.y, zi = ui.z;
+  double acc = 0.0;
+  for (int k = 0; k < 32; ++k) {
+    const int64_t j = c * 1024 + lane + 32 * k;
+    if (j < g) {
+      double term = 0.0;
+      if (j != i) {
+        const float4 uj = U[base + j];
+        const double dx = __dsub_rn(double(uj.x), xi);
+        const double dy = __dsub_rn(double(uj.y), yi);
+        const double dz = __dsub_rn(double(uj.z), zi);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        term = __ddiv_rn(1.0, __dsqrt_rn(__dadd_rn(r2, eps2)));
       }
-      tree.push(rsd::warp_cro_combine(acc));
-    }
-    if (lane == 0) {
-      const double ph = -__dmul_rn(Gm, tree.result());
-      const double ke = kinetic(V[p], vbulk + 3 * int64_t(q));
-      bound[p] = __dadd_rn(ke, ph) < 0.0 ? 1 : 0;
-      if (phi_out) phi_out[p] = __double2float_rn(ph);
+      acc = __dadd_rn(acc, term);
     }
   }
+  acc = rsd::warp_cro_combine(acc);
+  if (lane == 0) chunk_tot[w * max_chunks + c] = acc;
+}
+
+__global__ void k_fallback_finish(int64_t n, const uint32_t* __restrict__ ambig,
+                                  const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_size,
+                                  const float4* __restrict__ V, const double* __restrict__ vbulk, double Gm,
+                                  int64_t max_chunks, const double* __restrict__ chunk_tot,
+                                  uint8_t* __restrict__ bound, float* __restrict__ phi_out) {
+  const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w >= n) return;
+  const uint32_t p = ambig[w], q = mnode[p];
+  const int64_t nc = (node_size[q] + 1023) / 1024;
+  rsd::CroTree tree;
+  for (int64_t c = 0; c < nc; ++c) tree.push(chunk_tot[w * max_chunks + c]);
+  const double ph = -__dmul_rn(Gm, tree.result());
+  const double ke = kinetic(V[p], vbulk + 3 * int64_t(q));
+  bound[p] = __dadd_rn(ke, ph) < 0.0 ? 1 : 0;
+  if (phi_out) phi_out[p] = __double2float_rn(ph);
 }
 
 __global__ void k_bound_count(int64_t m, const uint32_t* __restrict__ mnode, const uint8_t* __restrict__ bound,
@@ -530,12 +551,7 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vbulk, S, Gm, kCertB, bound,
                                            potential_out, ambig, n_ambig, sur_min, nullptr);
     RS_LAUNCHED(ctx, "k_flags");
-    {
-      ProfScope prof_(ctx, "k_fallback", st);
-      k_fallback<<<152 * 8, kT, 0, st>>>(n_ambig, ambig, h.mnode, h.node_off, h.node_size, h.U, h.V,
-                                         vbulk, double(eps) * double(eps), Gm, bound, potential_out);
-    }
-    RS_LAUNCHED(ctx, "k_fallback");
+    RS_TRY(unbind_fallback(ctx, n_ambig, ambig, vbulk, bound, st, potential_out));
     if (sur) RS_TRY(surrogate_unbind(ctx, vbulk, bound, counters, st));
     RS_CUDA(ctx, cudaMemsetAsync(nb, 0, 8 * nn, st));
     k_bound_count<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, bound, nb);
@@ -584,16 +600,34 @@ int rs::unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t*
 }
 
 int rs::unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
-                        const double* vbulk, uint8_t* bound, cudaStream_t st) {
+                        const double* vbulk, uint8_t* bound, cudaStream_t st, float* phi_out) {
   Hier h = hier_of(ctx);
   const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
   const double eps = ctx->cfg.softening;
+  unsigned long long* mc = scratch_t<unsigned long long>(ctx, S_U_FBMAX, 1);
+  if (!mc) return RS_ERR_OOM;
+  RS_CUDA(ctx, cudaMemsetAsync(mc, 0, sizeof(unsigned long long), st));
+  k_fallback_max_chunks<<<152, kT, 0, st>>>(n_ambig, ambig, h.mnode, h.node_size, mc);
+  RS_LAUNCHED(ctx, "k_fallback_max_chunks");
+  RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box, n_ambig, 8, cudaMemcpyDeviceToHost, st));
+  RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box + 1, mc, 8, cudaMemcpyDeviceToHost, st));
+  RS_CUDA(ctx, cudaStreamSynchronize(st));
+  const int64_t n = ctx->host_box[0], max_chunks = ctx->host_box[1];
+  if (n == 0) return RS_OK;
+  double* chunk_tot = scratch_t<double>(ctx, S_U_FBCHUNK, size_t(n) * size_t(max_chunks));
+  if (!chunk_tot) return RS_ERR_OOM;
   {
     ProfScope prof_(ctx, "k_fallback", st);
-    k_fallback<<<152 * 8, kT, 0, st>>>(n_ambig, ambig, h.mnode, h.node_off, h.node_size, h.U, h.V, vbulk,
-                                       eps * eps, Gm, bound, nullptr);
+    for (int64_t w0 = 0; w0 < n; w0 += 65535) {
+      const dim3 grid(unsigned((max_chunks + kT / 32 - 1) / (kT / 32)), unsigned(std::min<int64_t>(65535, n - w0)));
+      k_fallback_chunks<<<grid, kT, 0, st>>>(w0, ambig, h.mnode, h.node_off, h.node_size, h.U, eps * eps,
+                                              max_chunks, chunk_tot);
+    }
   }
-  RS_LAUNCHED(ctx, "k_fallback");
+  RS_LAUNCHED(ctx, "k_fallback_chunks");
+  k_fallback_finish<<<grid_for(n, kT), kT, 0, st>>>(n, ambig, h.mnode, h.node_size, h.V, vbulk, Gm, max_chunks,
+                                                   chunk_tot, bound, phi_out);
+  RS_LAUNCHED(ctx, "k_fallback_finish");
   return RS_OK;
 }
 
