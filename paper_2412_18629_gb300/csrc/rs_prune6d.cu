@@ -41,8 +41,13 @@ struct Bucket {
   uint32_t pad;
 };
 
+// 6D box, stored for the packed float32x2 bounds: (position, velocity) pairs per axis, the
+// lower corner and the NEGATED upper corner (so both gaps are additions).
 struct Box {
-  float4 ulo, uhi, vlo, vhi;
+  float4 lo01;   // (x, vx, y, vy)
+  float4 nhi01;  // -(x, vx, y, vy) of the upper corner
+  float2 lo2;    // (z, vz)
+  float2 nhi2;
 };
 
 __device__ __forceinline__ uint32_t spread10(uint32_t x) {
@@ -134,9 +139,10 @@ __device__ __forceinline__ void warp_box(const float (&a)[6], bool valid, int lo
   }
 }
 
+// lo, hi indexed (x, y, z, vx, vy, vz).
 __device__ __forceinline__ Box make_box(const float (&lo)[6], const float (&hi)[6]) {
-  return Box{make_float4(lo[0], lo[1], lo[2], 0.f), make_float4(hi[0], hi[1], hi[2], 0.f),
-             make_float4(lo[3], lo[4], lo[5], 0.f), make_float4(hi[3], hi[4], hi[5], 0.f)};
+  return Box{make_float4(lo[0], lo[3], lo[1], lo[4]), make_float4(-hi[0], -hi[3], -hi[1], -hi[4]),
+             make_float2(lo[2], lo[5]), make_float2(-hi[2], -hi[5])};
 }
 
 // Node size class for the work queue: 8 * floor(log2 g) + the next 3 bits of g (monotone in
@@ -208,8 +214,8 @@ k_superboxes(int64_t nn, const int64_t* __restrict__ bucket_off, const int64_t* 
   const bool valid = b0 + lane < b1;
   const Box B = box[valid ? b0 + lane : b0];
   const float inf = __int_as_float(0x7f800000);
-  float lo[6] = {B.ulo.x, B.ulo.y, B.ulo.z, B.vlo.x, B.vlo.y, B.vlo.z};
-  float hi[6] = {B.uhi.x, B.uhi.y, B.uhi.z, B.vhi.x, B.vhi.y, B.vhi.z};
+  float lo[6] = {B.lo01.x, B.lo01.z, B.lo2.x, B.lo01.y, B.lo01.w, B.lo2.y};
+  float hi[6] = {-B.nhi01.x, -B.nhi01.z, -B.nhi2.x, -B.nhi01.y, -B.nhi01.w, -B.nhi2.y};
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     lo[d] = valid ? lo[d] : inf;
@@ -223,34 +229,132 @@ k_superboxes(int64_t nn, const int64_t* __restrict__ bucket_off, const int64_t* 
   if (lane == 0) sbox[w] = make_box(lo, hi);
 }
 
-// Gap from x to [lo, hi] rounded like the d6 differences (monotone: never above |fl(y - x)| for
-// any y in the interval).
-__device__ __forceinline__ float gap1(float x, float lo, float hi) {
-  return x < lo ? __fsub_rn(lo, x) : (x > hi ? __fsub_rn(x, hi) : 0.f);
+// Packed float32x2 add and multiply, each half rounded exactly like __fadd_rn / __fmul_rn. The
+// float2 intrinsics let the compiler fuse a multiply into a following add (an FMA: one rounding
+// instead of two, which changes d6 in the last bit); inline PTX with the product taken as an
+// fma with a +0 addend keeps every rounding (fl(a b + 0) = fl(a b) for the non-negative
+// products used here).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
 }
 
-__device__ __forceinline__ float gap2(float alo, float ahi, float blo, float bhi) {
-  return blo > ahi ? __fsub_rn(blo, ahi) : (alo > bhi ? __fsub_rn(alo, bhi) : 0.f);
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rz, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rz, 0;\n\tfma.rn.f32x2 rd, ra, rb, rz;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
 }
 
-__device__ __forceinline__ float lb_point_box(float4 u, float4 v, const Box& b, float isx, float isv) {
-  const float rx = rsd::sq3(gap1(u.x, b.ulo.x, b.uhi.x), gap1(u.y, b.ulo.y, b.uhi.y), gap1(u.z, b.ulo.z, b.uhi.z));
-  const float rv = rsd::sq3(gap1(v.x, b.vlo.x, b.vhi.x), gap1(v.y, b.vlo.y, b.vhi.y), gap1(v.z, b.vlo.z, b.vhi.z));
-  return __fadd_rn(__fmul_rn(rx, isx), __fmul_rn(rv, isv));
+// A query lane's coordinates, packed for the float32x2 arithmetic: (position, velocity)
+// pairs per axis and their negations for the box bounds; each coordinate negated and
+// duplicated for the distances to two targets at once; the metric scales.
+struct Query {
+  float2 qa, qb, qc, na, nb, nc;
+  float2 nux, nuy, nuz, nvx, nvy, nvz;
+  float2 s;         // (inv_sx2, inv_sv2)
+  float2 sx2, sv2;  // (inv_sx2, inv_sx2), (inv_sv2, inv_sv2)
+};
+
+__device__ __forceinline__ Query make_query(float4 u, float4 v, float isx, float isv) {
+  Query Q;
+  Q.qa = make_float2(u.x, v.x);
+  Q.qb = make_float2(u.y, v.y);
+  Q.qc = make_float2(u.z, v.z);
+  Q.na = make_float2(-u.x, -v.x);
+  Q.nb = make_float2(-u.y, -v.y);
+  Q.nc = make_float2(-u.z, -v.z);
+  Q.nux = make_float2(-u.x, -u.x);
+  Q.nuy = make_float2(-u.y, -u.y);
+  Q.nuz = make_float2(-u.z, -u.z);
+  Q.nvx = make_float2(-v.x, -v.x);
+  Q.nvy = make_float2(-v.y, -v.y);
+  Q.nvz = make_float2(-v.z, -v.z);
+  Q.s = make_float2(isx, isv);
+  Q.sx2 = make_float2(isx, isx);
+  Q.sv2 = make_float2(isv, isv);
+  return Q;
 }
 
-__device__ __forceinline__ float lb_box_box(const Box& a, const Box& b, float isx, float isv) {
-  const float rx = rsd::sq3(gap2(a.ulo.x, a.uhi.x, b.ulo.x, b.uhi.x), gap2(a.ulo.y, a.uhi.y, b.ulo.y, b.uhi.y),
-                            gap2(a.ulo.z, a.uhi.z, b.ulo.z, b.uhi.z));
-  const float rv = rsd::sq3(gap2(a.vlo.x, a.vhi.x, b.vlo.x, b.vhi.x), gap2(a.vlo.y, a.vhi.y, b.vlo.y, b.vhi.y),
-                            gap2(a.vlo.z, a.vhi.z, b.vlo.z, b.vhi.z));
-  return __fadd_rn(__fmul_rn(rx, isx), __fmul_rn(rv, isv));
+__device__ __forceinline__ float2 max0(float2 a, float2 b) {
+  return make_float2(fmaxf(fmaxf(a.x, b.x), 0.f), fmaxf(fmaxf(a.y, b.y), 0.f));
 }
 
-__device__ __forceinline__ float d6(float4 ui, float4 vi, float4 uj, float4 vj, float isx, float isv) {
-  const float rx = rsd::sq3(__fsub_rn(uj.x, ui.x), __fsub_rn(uj.y, ui.y), __fsub_rn(uj.z, ui.z));
-  const float rv = rsd::sq3(__fsub_rn(vj.x, vi.x), __fsub_rn(vj.y, vi.y), __fsub_rn(vj.z, vi.z));
-  return __fadd_rn(__fmul_rn(rx, isx), __fmul_rn(rv, isv));
+// Per-axis gap from q to [lo, hi]: max(fl(lo - q), fl(q - hi), 0). When q < lo this is
+// fl(lo - q) (the other difference is negative), when q > hi it is fl(q - hi), otherwise 0:
+// rounded like the d6 differences, hence never above |fl(y - q)| for any y in the interval.
+__device__ __forceinline__ float2 gap_pt(float2 lo, float2 nhi, float2 q, float2 nq) {
+  return max0(padd(lo, nq), padd(q, nhi));
+}
+
+// Gap between two intervals: max(fl(blo - ahi), fl(alo - bhi), 0).
+__device__ __forceinline__ float2 gap_bb(float2 alo, float2 anhi, float2 blo, float2 bnhi) {
+  return max0(padd(blo, anhi), padd(alo, bnhi));
+}
+
+// fl(fl(rx * inv_sx2) + fl(rv * inv_sv2)) with (rx, rv) = ((ga^2 + gb^2) + gc^2) per half:
+// the operation order of d6.
+__device__ __forceinline__ float metric(float2 ga, float2 gb, float2 gc, float2 s) {
+  const float2 r = padd(padd(pmul(ga, ga), pmul(gb, gb)), pmul(gc, gc));
+  const float2 t = pmul(r, s);
+  return __fadd_rn(t.x, t.y);
+}
+
+__device__ __forceinline__ float lb_point_box(const Query& Q, const Box& b) {
+  return metric(gap_pt(make_float2(b.lo01.x, b.lo01.y), make_float2(b.nhi01.x, b.nhi01.y), Q.qa, Q.na),
+                gap_pt(make_float2(b.lo01.z, b.lo01.w), make_float2(b.nhi01.z, b.nhi01.w), Q.qb, Q.nb),
+                gap_pt(b.lo2, b.nhi2, Q.qc, Q.nc), Q.s);
+}
+
+__device__ __forceinline__ float lb_box_box(const Box& a, const Box& b, float2 s) {
+  return metric(gap_bb(make_float2(a.lo01.x, a.lo01.y), make_float2(a.nhi01.x, a.nhi01.y),
+                       make_float2(b.lo01.x, b.lo01.y), make_float2(b.nhi01.x, b.nhi01.y)),
+                gap_bb(make_float2(a.lo01.z, a.lo01.w), make_float2(a.nhi01.z, a.nhi01.w),
+                       make_float2(b.lo01.z, b.lo01.w), make_float2(b.nhi01.z, b.nhi01.w)),
+                gap_bb(a.lo2, a.nhi2, b.lo2, b.nhi2), s);
+}
+
+// Staged targets of one warp, structure of arrays (x, y, z, vx, vy, vz); slots past the
+// bucket's count hold NaN, whose distance is NaN: it lowers no minimum and passes no test.
+struct Stage {
+  float c[6][32];
+};
+
+// d6 of the query to targets j and j + 1 (j even): fl(fl(rx * isx) + fl(rv * isv)) with
+// rx = (dx^2 + dy^2) + dz^2, d = fl(u_j - u_i) formed as u_j + (-u_i), every operation rounded
+// separately; each half equals the scalar d6.
+__device__ __forceinline__ float2 d6_pair(const Query& Q, const Stage& S, int j) {
+  const float2 dx = padd(*reinterpret_cast<const float2*>(&S.c[0][j]), Q.nux);
+  const float2 dy = padd(*reinterpret_cast<const float2*>(&S.c[1][j]), Q.nuy);
+  const float2 dz = padd(*reinterpret_cast<const float2*>(&S.c[2][j]), Q.nuz);
+  const float2 ex = padd(*reinterpret_cast<const float2*>(&S.c[3][j]), Q.nvx);
+  const float2 ey = padd(*reinterpret_cast<const float2*>(&S.c[4][j]), Q.nvy);
+  const float2 ez = padd(*reinterpret_cast<const float2*>(&S.c[5][j]), Q.nvz);
+  const float2 rx = padd(padd(pmul(dx, dx), pmul(dy, dy)), pmul(dz, dz));
+  const float2 rv = padd(padd(pmul(ex, ex), pmul(ey, ey)), pmul(ez, ez));
+  return padd(pmul(rx, Q.sx2), pmul(rv, Q.sv2));
+}
+
+__device__ __forceinline__ void stage(Stage& S, const float4* __restrict__ Us, const float4* __restrict__ Vs,
+                                      uint32_t start, int cnt, int lane) {
+  const float nan = __int_as_float(0x7fc00000);
+  float4 u = make_float4(nan, nan, nan, nan), v = u;
+  if (lane < cnt) {
+    u = Us[start + lane];
+    v = Vs[start + lane];
+  }
+  S.c[0][lane] = u.x;
+  S.c[1][lane] = u.y;
+  S.c[2][lane] = u.z;
+  S.c[3][lane] = v.x;
+  S.c[4][lane] = v.y;
+  S.c[5][lane] = v.z;
 }
 
 // Index visited at step t of the outward walk from a: a, a+1, a-1, a+2, a-2, ...
@@ -289,32 +393,38 @@ struct Tally {
 
 // Evaluate target bucket b for the warp's query lanes (nearest-neighbour search).
 template <bool kCount>
-__device__ __forceinline__ void nn_bucket(const NNArgs& A, int64_t a, int64_t b, bool valid, float4 ui,
-                                          float4 vi, float isx, float isv, float& best, int lane,
-                                          float4 (&su)[32], float4 (&sv)[32], Tally& T) {
+__device__ __forceinline__ void nn_bucket(const NNArgs& A, int64_t a, int64_t b, bool valid, const Query& Q,
+                                          float& best, int lane, Stage& S, Tally& T) {
   const Box B = A.box[b];
-  const bool need = valid && lb_point_box(ui, vi, B, isx, isv) <= best;
+  const bool need = valid && lb_point_box(Q, B) <= best;
   if (kCount) T.box += valid;
   if (!__any_sync(0xffffffffu, need)) return;
   const Bucket Bb = A.bk[b];
   __syncwarp();
-  if (lane < int(Bb.count)) {
-    su[lane] = A.Us[Bb.start + lane];
-    sv[lane] = A.Vs[Bb.start + lane];
-  }
+  stage(S, A.Us, A.Vs, Bb.start, int(Bb.count), lane);
   __syncwarp();
-  const uint32_t self = (b == a) ? uint32_t(lane) : 0xffffffffu;
   for (uint32_t s0 = 0; s0 < Bb.count; s0 += 8) {
     const Box Sb = A.sub[4 * b + (s0 >> 3)];
-    const bool sneed = need && lb_point_box(ui, vi, Sb, isx, isv) <= best;
+    const bool sneed = need && lb_point_box(Q, Sb) <= best;
     if (kCount) T.box += need;
     if (!__any_sync(0xffffffffu, sneed)) continue;
     if (sneed) {
-      const uint32_t s1 = min(s0 + 8, Bb.count);
-      if (kCount) T.d6 += s1 - s0;
-      for (uint32_t j = s0; j < s1; ++j) {
-        if (j == self) continue;
-        best = fminf(best, d6(ui, vi, su[j], sv[j], isx, isv));
+      const int s1 = int(min(s0 + 8, Bb.count));
+      if (kCount) T.d6 += uint32_t(s1) - s0;
+      if (b == a) {
+        for (int j = int(s0); j < s1; j += 2) {
+          const float2 d = d6_pair(Q, S, j);
+          best = fminf(best, j == lane ? best : d.x);
+          best = fminf(best, j + 1 == lane ? best : d.y);
+        }
+      } else {
+#pragma unroll
+        for (int j = int(s0); j < int(s0) + 8; j += 2) {
+          if (j < s1) {
+            const float2 d = d6_pair(Q, S, j);
+            best = fminf(fminf(best, d.x), d.y);
+          }
+        }
       }
     }
   }
@@ -337,7 +447,7 @@ __device__ __forceinline__ void flush_tally(const Tally& T, unsigned long long* 
 
 template <bool kCount>
 __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict__ nn2) {
-  __shared__ float4 su[kWarpsPerBlock][32], sv[kWarpsPerBlock][32];
+  __shared__ Stage stg[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int64_t nbk = *A.nbuckets;
   Tally T;
@@ -347,17 +457,16 @@ __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict_
     const int64_t a = A.order[w];
     const Bucket Aq = A.bk[a];
     const float4 iv = A.inv[Aq.node];
-    const float isx = iv.x, isv = iv.y;
     const bool valid = lane < int(Aq.count);
     const uint32_t si = Aq.start + (valid ? lane : 0);
-    const float4 ui = A.Us[si], vi = A.Vs[si];
+    const Query Q = make_query(A.Us[si], A.Vs[si], iv.x, iv.y);
     float best = __int_as_float(0x7f800000);
     const int64_t own = (a - int64_t(Aq.first)) >> 5, nsb = Aq.sbcount;
     for (int64_t t = 0; t <= 2 * nsb; ++t) {
       const int64_t s = outward(own, t);
       if (s < 0 || s >= nsb) continue;
       const Box SB = A.sbox[Aq.sbfirst + s];
-      const bool need = valid && lb_point_box(ui, vi, SB, isx, isv) <= best;
+      const bool need = valid && lb_point_box(Q, SB) <= best;
       if (kCount) T.box += valid;
       if (!__any_sync(0xffffffffu, need)) continue;
       const int64_t b_lo = int64_t(Aq.first) + 32 * s;
@@ -366,14 +475,12 @@ __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict_
         for (int64_t t2 = 0; t2 <= 2 * 32; ++t2) {
           const int64_t b = outward(a, t2);
           if (b < b_lo || b >= b_hi) continue;
-          nn_bucket<kCount>(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb], T);
+          nn_bucket<kCount>(A, a, b, valid, Q, best, lane, stg[wb], T);
         }
       } else if (s > own) {
-        for (int64_t b = b_lo; b < b_hi; ++b)
-          nn_bucket<kCount>(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb], T);
+        for (int64_t b = b_lo; b < b_hi; ++b) nn_bucket<kCount>(A, a, b, valid, Q, best, lane, stg[wb], T);
       } else {
-        for (int64_t b = b_hi - 1; b >= b_lo; --b)
-          nn_bucket<kCount>(A, a, b, valid, ui, vi, isx, isv, best, lane, su[wb], sv[wb], T);
+        for (int64_t b = b_hi - 1; b >= b_lo; --b) nn_bucket<kCount>(A, a, b, valid, Q, best, lane, stg[wb], T);
       }
     }
     if (valid) nn2[A.sp[si]] = best;
@@ -384,40 +491,39 @@ __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict_
 // Link pairs of query bucket a (box Abox) with target bucket b >= a.
 template <bool kCount>
 __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t b, const Box& Abox,
-                                            bool active, float4 ui, float4 vi, uint32_t pi,
-                                            float isx, float isv, float l2, const float* nn2,
-                                            uint32_t* uf, int lane, float4 (&su)[32],
-                                            float4 (&sv)[32], uint32_t (&sj)[32], float (&snn)[32],
-                                            Tally& T) {
+                                            bool active, const Query& Q, uint32_t pi, float l2,
+                                            uint32_t* uf, int lane, Stage& S, uint32_t (&sj)[32],
+                                            float (&snn)[32], Tally& T) {
   const Box B = A.box[b];
   if (kCount) T.box += (lane == 0);
-  if (lb_box_box(Abox, B, isx, isv) > l2) return;
-  const bool need = active && lb_point_box(ui, vi, B, isx, isv) <= l2;
+  if (lb_box_box(Abox, B, Q.s) > l2) return;
+  const bool need = active && lb_point_box(Q, B) <= l2;
   if (kCount) T.box += active;
   if (!__any_sync(0xffffffffu, need)) return;
   const Bucket Bb = A.bk[b];
   __syncwarp();
+  stage(S, A.Us, A.Vs, Bb.start, int(Bb.count), lane);
   if (lane < int(Bb.count)) {
-    su[lane] = A.Us[Bb.start + lane];
-    sv[lane] = A.Vs[Bb.start + lane];
     sj[lane] = A.sp[Bb.start + lane];
     snn[lane] = A.nn2s[Bb.start + lane];
   }
   __syncwarp();
-  const uint32_t j0 = (b == a) ? uint32_t(lane) + 1 : 0u;
+  const int j0 = (b == a) ? lane + 1 : 0;
   for (uint32_t s0 = 0; s0 < Bb.count; s0 += 8) {
     const Box Sb = A.sub[4 * b + (s0 >> 3)];
     if (kCount) T.box += (lane == 0);
-    if (lb_box_box(Abox, Sb, isx, isv) > l2) continue;
-    const bool sneed = need && lb_point_box(ui, vi, Sb, isx, isv) <= l2;
+    if (lb_box_box(Abox, Sb, Q.s) > l2) continue;
+    const bool sneed = need && lb_point_box(Q, Sb) <= l2;
     if (kCount) T.box += need;
     if (!__any_sync(0xffffffffu, sneed)) continue;
     if (sneed) {
-      const uint32_t s1 = min(s0 + 8, Bb.count);
-      if (kCount) T.d6 += s1 > max(s0, j0) ? s1 - max(s0, j0) : 0u;
-      for (uint32_t j = max(s0, j0); j < s1; ++j) {
-        if (snn[j] > l2) continue;
-        if (d6(ui, vi, su[j], sv[j], isx, isv) <= l2) rsd::uf_unite(uf, pi, sj[j]);
+      const int s1 = int(min(s0 + 8, Bb.count));
+      if (kCount) T.d6 += s1 > max(int(s0), j0) ? uint32_t(s1 - max(int(s0), j0)) : 0u;
+      for (int j = int(s0); j < s1; j += 2) {
+        if (j + 1 < j0) continue;
+        const float2 d = d6_pair(Q, S, j);
+        if (j >= j0 && d.x <= l2 && snn[j] <= l2) rsd::uf_unite(uf, pi, sj[j]);
+        if (j + 1 >= j0 && j + 1 < s1 && d.y <= l2 && snn[j + 1] <= l2) rsd::uf_unite(uf, pi, sj[j + 1]);
       }
     }
   }
@@ -427,21 +533,22 @@ template <bool kCount>
 __global__ void __launch_bounds__(kT)
 k_link6d_pruned(NNArgs A, const float* __restrict__ nn2, uint32_t* __restrict__ uf) {
   Tally T;
-  __shared__ float4 su[kWarpsPerBlock][32], sv[kWarpsPerBlock][32];
+  __shared__ Stage stg[kWarpsPerBlock];
   __shared__ uint32_t sj[kWarpsPerBlock][32];
   __shared__ float snn[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int64_t nbk = *A.nbuckets;
+  (void)nn2;
   while (true) {
     const int64_t w = next_work(A.counter, lane);
     if (w >= nbk) break;
     const int64_t a = A.order[w];
     const Bucket Aq = A.bk[a];
     const float4 iv = A.inv[Aq.node];
-    const float isx = iv.x, isv = iv.y, l2 = iv.z;
+    const float l2 = iv.z;
     const bool valid = lane < int(Aq.count);
     const uint32_t si = Aq.start + (valid ? lane : 0);
-    const float4 ui = A.Us[si], vi = A.Vs[si];
+    const Query Q = make_query(A.Us[si], A.Vs[si], iv.x, iv.y);
     const uint32_t pi = A.sp[si];
     const bool active = valid && A.nn2s[si] <= l2;
     if (!__any_sync(0xffffffffu, active)) continue;
@@ -450,15 +557,14 @@ k_link6d_pruned(NNArgs A, const float* __restrict__ nn2, uint32_t* __restrict__ 
     for (int64_t s = own; s < nsb; ++s) {
       const Box SB = A.sbox[Aq.sbfirst + s];
       if (kCount) T.box += (lane == 0);
-      if (lb_box_box(Abox, SB, isx, isv) > l2) continue;
-      const bool need = active && lb_point_box(ui, vi, SB, isx, isv) <= l2;
+      if (lb_box_box(Abox, SB, Q.s) > l2) continue;
+      const bool need = active && lb_point_box(Q, SB) <= l2;
       if (kCount) T.box += active;
       if (!__any_sync(0xffffffffu, need)) continue;
       const int64_t b_lo = rsd::min64(int64_t(Aq.first) + 32 * s, int64_t(Aq.last) + 1);
       const int64_t b_hi = rsd::min64(int64_t(Aq.first) + 32 * s + 32, int64_t(Aq.last) + 1);
       for (int64_t b = (s == own ? a : b_lo); b < b_hi; ++b)
-        link_bucket<kCount>(A, a, b, Abox, active, ui, vi, pi, isx, isv, l2, nn2, uf, lane, su[wb], sv[wb],
-                            sj[wb], snn[wb], T);
+        link_bucket<kCount>(A, a, b, Abox, active, Q, pi, l2, uf, lane, stg[wb], sj[wb], snn[wb], T);
     }
   }
   flush_tally<kCount>(T, A.work + 2, lane);
