@@ -245,6 +245,19 @@ __device__ __forceinline__ void uf_unite(uint32_t* parent, uint32_t a, uint32_t 
   }
 }
 
+// Exact float32 -> float64 conversion on the integer pipe (the float64 pipe of this part runs
+// 2 lanes per clock per SM): for normal values the sign, the exponent rebiased by 1023 - 127 and
+// the mantissa shifted up by 29 bits; zero, subnormal, infinite and NaN values take the
+// hardware conversion. Bit-identical to double(f).
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return double(f);
+  const uint64_t bits = (uint64_t(u >> 31) << 63) | (uint64_t(e + 896u) << 52) |
+                        (uint64_t(u & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
 // Canonical-order combination of the 32 lane partial sums of a warp: halving tree
 // s[l] += s[l + off], off = 16 .. 1, realised as an xor butterfly (IEEE + commutes, so lane
 // 0 ends with exactly the halving-tree value).

@@ -166,8 +166,8 @@ struct MomentTerm {
   const float4* V;
   __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
     const float4 u = U[p], v = V[p];
-    const double a[3] = {double(u.x), double(u.y), double(u.z)};
-    const double b[3] = {double(v.x), double(v.y), double(v.z)};
+    const double a[3] = {rsd::f2d(u.x), rsd::f2d(u.y), rsd::f2d(u.z)};
+    const double b[3] = {rsd::f2d(v.x), rsd::f2d(v.y), rsd::f2d(v.z)};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       acc[d] = __dadd_rn(acc[d], a[d]);

@@ -266,9 +266,9 @@ __global__ void k_sur_targets(int64_t ns, const uint32_t* __restrict__ sur_mem,
 }
 
 __device__ __forceinline__ double kinetic(float4 v, const double* vb) {
-  const double dvx = __dsub_rn(double(v.x), vb[0]);
-  const double dvy = __dsub_rn(double(v.y), vb[1]);
-  const double dvz = __dsub_rn(double(v.z), vb[2]);
+  const double dvx = __dsub_rn(rsd::f2d(v.x), vb[0]);
+  const double dvy = __dsub_rn(rsd::f2d(v.y), vb[1]);
+  const double dvz = __dsub_rn(rsd::f2d(v.z), vb[2]);
   const double s = __dadd_rn(__dadd_rn(__dmul_rn(dvx, dvx), __dmul_rn(dvy, dvy)), __dmul_rn(dvz, dvz));
   return __dmul_rn(0.5, s);
 }

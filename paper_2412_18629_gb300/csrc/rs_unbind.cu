@@ -231,9 +231,9 @@ struct VelTerm {
   const float4* V;
   __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
     const float4 v = V[p];
-    acc[0] = __dadd_rn(acc[0], double(v.x));
-    acc[1] = __dadd_rn(acc[1], double(v.y));
-    acc[2] = __dadd_rn(acc[2], double(v.z));
+    acc[0] = __dadd_rn(acc[0], rsd::f2d(v.x));
+    acc[1] = __dadd_rn(acc[1], rsd::f2d(v.y));
+    acc[2] = __dadd_rn(acc[2], rsd::f2d(v.z));
   }
 };
 
@@ -246,9 +246,9 @@ __global__ void k_vbulk(int64_t nn, const int64_t* __restrict__ node_size, doubl
 }
 
 __device__ __forceinline__ double kinetic(float4 v, const double* vb) {
-  const double dvx = __dsub_rn(double(v.x), vb[0]);
-  const double dvy = __dsub_rn(double(v.y), vb[1]);
-  const double dvz = __dsub_rn(double(v.z), vb[2]);
+  const double dvx = __dsub_rn(rsd::f2d(v.x), vb[0]);
+  const double dvy = __dsub_rn(rsd::f2d(v.y), vb[1]);
+  const double dvz = __dsub_rn(rsd::f2d(v.z), vb[2]);
   const double s = __dadd_rn(__dadd_rn(__dmul_rn(dvx, dvx), __dmul_rn(dvy, dvy)), __dmul_rn(dvz, dvz));
   return __dmul_rn(0.5, s);
 }
@@ -313,9 +313,9 @@ k_fallback_chunks(int64_t w0, const uint32_t* __restrict__ ambig, const uint32_t
       double term = 0.0;
       if (j != i) {
         const float4 uj = U[base + j];
-        const double dx = __dsub_rn(double(uj.x), xi);
-        const double dy = __dsub_rn(double(uj.y), yi);
-        const double dz = __dsub_rn(double(uj.z), zi);
+        const double dx = __dsub_rn(rsd::f2d(uj.x), xi);
+        const double dy = __dsub_rn(rsd::f2d(uj.y), yi);
+        const double dz = __dsub_rn(rsd::f2d(uj.z), zi);
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         term = __ddiv_rn(1.0, __dsqrt_rn(__dadd_rn(r2, eps2)));
       }
@@ -367,8 +367,8 @@ struct PropTerm1 {  // bound-masked u, u^2, v, v^2
       return;
     }
     const float4 u = U[p], v = V[p];
-    const double a[3] = {double(u.x), double(u.y), double(u.z)};
-    const double b[3] = {double(v.x), double(v.y), double(v.z)};
+    const double a[3] = {rsd::f2d(u.x), rsd::f2d(u.y), rsd::f2d(u.z)};
+    const double b[3] = {rsd::f2d(v.x), rsd::f2d(v.y), rsd::f2d(v.z)};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       acc[d] = __dadd_rn(acc[d], a[d]);
@@ -391,8 +391,8 @@ struct PropTerm2 {  // bound-masked second moments about the bound mean
     }
     const float4 u = U[p];
     const double* mu = mean + 3 * q;
-    const double d[3] = {__dsub_rn(double(u.x), mu[0]), __dsub_rn(double(u.y), mu[1]),
-                         __dsub_rn(double(u.z), mu[2])};
+    const double d[3] = {__dsub_rn(rsd::f2d(u.x), mu[0]), __dsub_rn(rsd::f2d(u.y), mu[1]),
+                         __dsub_rn(rsd::f2d(u.z), mu[2])};
     acc[0] = __dadd_rn(acc[0], __dmul_rn(d[0], d[0]));
     acc[1] = __dadd_rn(acc[1], __dmul_rn(d[1], d[1]));
     acc[2] = __dadd_rn(acc[2], __dmul_rn(d[2], d[2]));
