@@ -245,6 +245,16 @@ __device__ __forceinline__ void uf_unite(uint32_t* parent, uint32_t a, uint32_t 
   }
 }
 
+// Size class of a node with g members for size-ordered work queues: 8 floor(log2 g) + the
+// next 3 bits of g (monotone in g; 8..254 for 2 <= g < 2^31), so one 8-bit radix pass on
+// 255 - class orders the work largest first.
+__device__ __forceinline__ uint32_t size_class(int64_t g) {
+  const int L = 63 - __clzll(static_cast<unsigned long long>(g));
+  const uint32_t f = L >= 3 ? uint32_t((uint64_t(g) >> (L - 3)) & 7u) : uint32_t((uint64_t(g) << (3 - L)) & 7u);
+  const uint32_t c = uint32_t(L < 31 ? L : 31) * 8u + f;
+  return c > 254u ? 254u : c;
+}
+
 // Exact float32 -> float64 conversion on the integer pipe (the float64 pipe of this part runs
 // 2 lanes per clock per SM): for normal values the sign, the exponent rebiased by 1023 - 127 and
 // the mantissa shifted up by 29 bits; zero, subnormal, infinite and NaN values take the

@@ -145,14 +145,6 @@ __device__ __forceinline__ Box make_box(const float (&lo)[6], const float (&hi)[
              make_float2(lo[2], lo[5]), make_float2(-hi[2], -hi[5])};
 }
 
-// Node size class for the work queue: 8 * floor(log2 g) + the next 3 bits of g (monotone in
-// g, 0..254 for g < 2^31), so one 8-bit radix pass orders the buckets largest node first.
-__device__ __forceinline__ uint32_t size_class(int64_t g) {
-  const int L = 63 - __clzll(uint64_t(g));
-  const uint32_t f = L >= 3 ? uint32_t((uint64_t(g) >> (L - 3)) & 7u) : uint32_t((uint64_t(g) << (3 - L)) & 7u);
-  return uint32_t(min(L, 31)) * 8u + f > 254u ? 254u : uint32_t(min(L, 31)) * 8u + f;
-}
-
 // One warp per bucket (padding warps write a queue key that sorts last): bucket table entry,
 // box, four 8-member sub-boxes (an empty sub-bucket gets lo = +inf, hi = -inf, so every gap to
 // it is +inf), and the work-queue key (largest node first).
@@ -196,7 +188,7 @@ k_buckets(int64_t nb, int64_t nn, int64_t mb, int64_t nbk_ub, const int64_t* __r
     b.pad = 0;
     bk[w] = b;
     box[w] = make_box(lo, hi);
-    qkey[w] = 255u - size_class(node_size[q]);
+    qkey[w] = 255u - rsd::size_class(node_size[q]);
     qval[w] = uint32_t(w);
   }
 }

@@ -674,6 +674,21 @@ __global__ void k_big_list(int64_t nn, const int64_t* __restrict__ node_size,
   if (q < nn && node_size[q] >= kSurMin) big_nodes[rank[q]] = q;
 }
 
+// Sort keys of the big nodes: largest size class first (stable: node order within a class).
+__global__ void k_big_keys(int64_t nbig, const int64_t* __restrict__ big_nodes,
+                           const int64_t* __restrict__ node_size, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= nbig) return;
+  keys[b] = 255u - rsd::size_class(node_size[big_nodes[b]]);
+  vals[b] = uint32_t(big_nodes[b]);
+}
+
+__global__ void k_big_store(int64_t nbig, const uint32_t* __restrict__ vals, int64_t* __restrict__ big_nodes) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b < nbig) big_nodes[b] = int64_t(vals[b]);
+}
+
 int bits_for(uint64_t v) {
   int b = 1;
   while (b < 64 && (v >> b) != 0) ++b;
@@ -728,6 +743,20 @@ static int sur_prepare(rs_ctx* ctx, const double* vbulk, int64_t* ns_out, cudaSt
   // rank holds the exclusive scan of big flags: rank of each big node
   k_big_list<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, rank, big_nodes);
   RS_LAUNCHED(ctx, "k_big_list");
+  {  // big nodes largest first, so the per-node work of the surrogate path starts with them
+    uint64_t* bka = scratch_t<uint64_t>(ctx, S_U_OKEY_A, size_t(nbig));
+    uint64_t* bkb = scratch_t<uint64_t>(ctx, S_U_OKEY_B, size_t(nbig));
+    uint32_t* bva = scratch_t<uint32_t>(ctx, S_U_OVAL_A, size_t(nbig));
+    uint32_t* bvb = scratch_t<uint32_t>(ctx, S_U_OVAL_B, size_t(nbig));
+    if (!bka || !bkb || !bva || !bvb) return RS_ERR_OOM;
+    k_big_keys<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, h.node_size, bka, bva);
+    RS_LAUNCHED(ctx, "k_big_keys");
+    uint64_t* bko;
+    uint32_t* bvo;
+    RS_TRY(radix_sort_u64(ctx, nbig, 8, bka, bva, bkb, bvb, &bko, &bvo, st));
+    k_big_store<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, bvo, big_nodes);
+    RS_LAUNCHED(ctx, "k_big_store");
+  }
   // radial order of the surrogate members inside their node
   k_big_radius<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, rank, h.U, stt, ka, va);
   RS_LAUNCHED(ctx, "k_big_radius");
