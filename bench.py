@@ -90,7 +90,14 @@ class ClockSampler:
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-        time.sleep(0.3)
+        # wait for the first sample, so nvidia-smi's start-up (driver queries) is over before
+        # the timed region begins and only its steady 200 ms polling overlaps it
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 10.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
+        time.sleep(0.25)
         return self
 
     def __exit__(self, *exc):
