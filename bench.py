@@ -227,7 +227,7 @@ def _measure(ctx, pos, vel, ids, n, args, ws, local):
     t_max, units = aggregate(elapsed, float(n) * args.steps, ws, f"cuda:{local}")
     return {"value": units / t_max, "ms_per_step": t_max / args.steps * 1e3, "launches": launches,
             "prof": prof, "pairs": pairs, "pairs_big": pairs_big, "clocks": clk.summary(),
-            "fallback": nfb, "work": work, "n": n}
+            "fallback": nfb, "work": work, "n": n, "autotune": ctx.tuning()}
 
 
 def _roofline(prof, pairs, steps, work=None):
@@ -423,6 +423,7 @@ def run_ours(args):
                           "roofline": _roofline(v["prof"], v["pairs"], args.steps, v["work"]),
                           "stages": _stages(dict(v, form=f), args.steps),
                           "clocks": v["clocks"],
+                          "autotune": v.get("autotune"),
                           "surrogate_stats": v.get("surrogate_stats")}
                       for f, v in res.items()},
         }

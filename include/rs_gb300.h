@@ -275,6 +275,16 @@ int rs_profile(rs_ctx* ctx, int enable);
  * after a device synchronisation: NN d6 evaluations, NN box tests, link d6 evaluations, link
  * box tests, accumulated since the last enable. Errors: RS_ERR_OOM, RS_ERR_CUDA. */
 int rs_count_work(rs_ctx* ctx, int enable, int64_t* counts_out);
+
+/* Autotuner choices of the context (host outputs; either may be NULL). The members per thread
+ * of the register-blocked potential sums (rs_unbind's direct sum; the surrogate path's sums for
+ * members outside its gate) are picked among 2, 4 and 8 on the first call whose input is large
+ * enough (2^20 members, resp. surrogate members): each candidate is timed with CUDA events on
+ * that call's own data (the sums are bit-identical for every candidate) and the fastest is kept
+ * for the context's later calls. choice_out int32 [2]: blocked potential, list potential (0 =
+ * not tuned yet); ms_out float [6]: the candidates' times (2, 4, 8) for each. Build-time
+ * choice, not part of the method. Errors: RS_ERR_INVALID_ARG. */
+int rs_tuning(rs_ctx* ctx, int32_t* choice_out, float* ms_out);
 int rs_profile_get(rs_ctx* ctx, int index, char* name, int name_cap, double* total_ms,
                    int64_t* launches);
 

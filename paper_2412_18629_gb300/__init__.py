@@ -87,11 +87,12 @@ def load_library():
         lib.rs_cro_sum_noalloc.argtypes = [i64, P, P, P]
         lib.rs_profile.argtypes = [P, ctypes.c_int]
         lib.rs_count_work.argtypes = [P, ctypes.c_int, P]
+        lib.rs_tuning.argtypes = [P, P, P]
         lib.rs_profile_get.argtypes = [P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_fof3d", "rs_fof6d", "rs_fof6d_copy",
                      "rs_fof6d_node_params", "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile",
-                     "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work"):
+                     "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work", "rs_tuning"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -174,6 +175,18 @@ class Context:
         if not enable:
             return dict(zip(("nn_d6", "nn_box", "link_d6", "link_box"), map(int, out)))
         return None
+
+    def tuning(self):
+        """Autotuner choices: members per thread of the blocked and list potential sums (0 =
+        not tuned yet) and the candidates' times in ms (2, 4, 8 each)."""
+        import numpy as np
+        ch = np.zeros(2, np.int32)
+        ms = np.zeros(6, np.float32)
+        self.check(self.lib.rs_tuning(self.handle, ch.ctypes.data, ms.ctypes.data))
+        return {"blocked_potential": {"members_per_thread": int(ch[0]),
+                                      "ms": dict(zip((2, 4, 8), map(float, ms[:3])))},
+                "list_potential": {"members_per_thread": int(ch[1]),
+                                   "ms": dict(zip((2, 4, 8), map(float, ms[3:])))}}
 
     def profile_totals(self):
         """{kernel: (total_ms, launches)} recorded since profile(True)."""

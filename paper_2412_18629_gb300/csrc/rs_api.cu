@@ -91,6 +91,20 @@ extern "C" int rs_count_work(rs_ctx* ctx, int enable, int64_t* counts_out) {
   return RS_OK;
 }
 
+extern "C" int rs_tuning(rs_ctx* ctx, int32_t* choice_out, float* ms_out) {
+  if (!ctx) return RS_ERR_INVALID_ARG;
+  if (choice_out) {
+    choice_out[0] = ctx->tune_blk_r;
+    choice_out[1] = ctx->tune_list_r;
+  }
+  if (ms_out)
+    for (int c = 0; c < 3; ++c) {
+      ms_out[c] = ctx->tune_blk_ms[c];
+      ms_out[3 + c] = ctx->tune_list_ms[c];
+    }
+  return RS_OK;
+}
+
 extern "C" int rs_ctx_destroy(rs_ctx* ctx) {
   if (!ctx) return RS_OK;
   cudaSetDevice(ctx->device);

@@ -86,6 +86,11 @@ struct rs_ctx {
   // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
   bool profile = false;
   bool count_work = false;  // counting variants of the pruned 6D kernels (rs_count_work)
+  // autotuner choices (0 = not tuned yet) and the timings they were chosen from
+  int tune_blk_r = 0;       // members per thread of the blocked potential (2, 4, 8)
+  float tune_blk_ms[3] = {0.f, 0.f, 0.f};
+  int tune_list_r = 0;      // members per thread of the surrogate path's list sums (2, 4, 8)
+  float tune_list_ms[3] = {0.f, 0.f, 0.f};
   struct ProfRec {
     std::string name;
     cudaEvent_t a, b;

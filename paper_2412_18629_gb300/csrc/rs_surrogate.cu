@@ -38,15 +38,15 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int64_t kSurMin = kSurrogateMinMembers;
+constexpr int64_t kTuneMinSurMembers = 1 << 20;  // the autotuner times candidates on lists this large
 constexpr double kU = 5.9604644775390625e-08;
 // per-member warp sum: per term <= 8u, 32-term lane blocks <= 31u, Kahan <= 2u, 5-level warp
 // tree <= 5u; 48u with slack.
 constexpr double kCertB2 = 48.0 * kU + 1e-12;
 
 // Blocked direct sum over the exact-path list: 128 threads x 4 members per block.
+// (members per thread kListR: a template parameter the autotuner picks among 2, 4, 8)
 constexpr int kListThreads = 128;
-constexpr int kListR = 4;
-constexpr int kListTile = kListThreads * kListR;
 
 struct NodeStat {
   float cx, cy, cz, r_vir;
@@ -375,14 +375,14 @@ __global__ void k_sur_exact_list(int64_t ns, const int64_t* __restrict__ lf, uin
 
 __global__ void k_sur_list_tiles(int64_t nbig, const int64_t* __restrict__ big_nodes,
                                  const int64_t* __restrict__ sur_off, const int64_t* __restrict__ node_size,
-                                 const int64_t* __restrict__ lf, int64_t* __restrict__ lofs,
+                                 const int64_t* __restrict__ lf, int list_tile, int64_t* __restrict__ lofs,
                                  int64_t* __restrict__ tiles) {
   const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (b >= nbig) return;
   const int64_t q = big_nodes[b];
   const int64_t a = lf[sur_off[q]], e = lf[sur_off[q] + node_size[q]];
   lofs[b] = a;
-  tiles[b] = (e - a + kListTile - 1) / kListTile;
+  tiles[b] = (e - a + list_tile - 1) / list_tile;
 }
 
 __global__ void k_sur_list_end(int64_t nbig, const int64_t* __restrict__ big_nodes,
@@ -513,6 +513,7 @@ k_pot_member(const unsigned long long* __restrict__ count, const uint32_t* __res
 // (the same per-member summation as the direct-sum kernels). Including the self term, whose
 // computed value is exactly w0 = rsqrt(eps^2), removes every per-pair index test; k_flags_list
 // subtracts it and widens the certified bound accordingly.
+template <int kListR>
 __global__ void __launch_bounds__(kListThreads)
 k_potential_list(int64_t nbig, const int64_t* __restrict__ tile_off, const int64_t* __restrict__ big_nodes,
                  const int64_t* __restrict__ lofs, const int64_t* __restrict__ lf_total_per_node_end,
@@ -526,7 +527,7 @@ k_potential_list(int64_t nbig, const int64_t* __restrict__ tile_off, const int64
   const int64_t bi = rsd::upper_bound_i64(tile_off, nbig, b) - 1;
   const int64_t q = big_nodes[bi], t = b - tile_off[bi];
   const int64_t base = node_off[q], g = node_size[q];
-  const int64_t l0 = lofs[bi] + t * kListTile, l1 = lf_total_per_node_end[bi];
+  const int64_t l0 = lofs[bi] + t * (kListThreads * kListR), l1 = lf_total_per_node_end[bi];
   float2 nx[kListR / 2], ny[kListR / 2], nz[kListR / 2];
   float S[kListR], C[kListR];
 #pragma unroll
@@ -876,18 +877,57 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
   k_sur_exact_list<<<grid_for(ns, kT), kT, 0, st>>>(ns, lf, exact_list, counters);
   RS_LAUNCHED(ctx, "k_sur_exact_list");
   if (nbig > 0) {
-    k_sur_list_tiles<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size, lf, lofs,
-                                                        ltiles);
-    RS_LAUNCHED(ctx, "k_sur_list_tiles");
     k_sur_list_end<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size, lf, lend);
     RS_LAUNCHED(ctx, "k_sur_list_end");
-    RS_TRY(exclusive_scan_i64(ctx, nbig, ltiles, ltiles + nbig, st));
-    {
-      ProfScope prof_(ctx, "k_potential_list", st);
-      k_potential_list<<<grid_for(ns / kListTile + nbig + 1, 1), kListThreads, 0, st>>>(
-          nbig, ltiles, big_nodes, lofs, lend, exact_list, sur_mem, h.node_off, h.node_size, h.U, eps * eps, Sx);
+    // members per thread: autotuned on the first call with enough surrogate members (each of
+    // 2, 4, 8 timed on this call's list; identical sums), then kept for the context
+    const bool tune = ctx->tune_list_r == 0 && ns >= kTuneMinSurMembers;
+    const int cand[3] = {2, 4, 8};
+    float best_ms = 0.f;
+    int best = 4;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (tune) {
+      RS_CUDA(ctx, cudaEventCreate(&e0));
+      RS_CUDA(ctx, cudaEventCreate(&e1));
     }
-    RS_LAUNCHED(ctx, "k_potential_list");
+    for (int c = tune ? 0 : 3; c <= 3; ++c) {
+      const int R = c < 3 ? cand[c] : (ctx->tune_list_r ? ctx->tune_list_r : 4);
+      k_sur_list_tiles<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size, lf,
+                                                          kListThreads * R, lofs, ltiles);
+      RS_LAUNCHED(ctx, "k_sur_list_tiles");
+      RS_TRY(exclusive_scan_i64(ctx, nbig, ltiles, ltiles + nbig, st));
+      const unsigned grid = grid_for(ns / (kListThreads * R) + nbig + 1, 1);
+      if (c < 3) RS_CUDA(ctx, cudaEventRecord(e0, st));
+      {
+        ProfScope prof_(ctx, c < 3 ? "k_potential_list_tune" : "k_potential_list", st);
+        if (R == 2)
+          k_potential_list<2><<<grid, kListThreads, 0, st>>>(nbig, ltiles, big_nodes, lofs, lend, exact_list,
+                                                             sur_mem, h.node_off, h.node_size, h.U, eps * eps, Sx);
+        else if (R == 8)
+          k_potential_list<8><<<grid, kListThreads, 0, st>>>(nbig, ltiles, big_nodes, lofs, lend, exact_list,
+                                                             sur_mem, h.node_off, h.node_size, h.U, eps * eps, Sx);
+        else
+          k_potential_list<4><<<grid, kListThreads, 0, st>>>(nbig, ltiles, big_nodes, lofs, lend, exact_list,
+                                                             sur_mem, h.node_off, h.node_size, h.U, eps * eps, Sx);
+      }
+      RS_LAUNCHED(ctx, "k_potential_list");
+      if (c < 3) {
+        RS_CUDA(ctx, cudaEventRecord(e1, st));
+        RS_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        RS_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        ctx->tune_list_ms[c] = ms;
+        if (c == 0 || ms < best_ms) {
+          best_ms = ms;
+          best = cand[c];
+        }
+        if (c == 2) ctx->tune_list_r = best;
+      }
+    }
+    if (tune) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
   }
   k_flags_list<<<grid_for(ns, kT), kT, 0, st>>>(counters + 0, exact_list, sur_mem, h.mnode, h.V, vbulk,
                                                eps * eps, Gm, Sx, bound, ambig, counters + 2);

@@ -100,14 +100,15 @@ k_potential(int64_t nn, const int64_t* __restrict__ tile_off, const int64_t* __r
 // holds as is. The self pair is tested only on the diagonal j-tiles. Blocks are ordered by
 // the node's size class, largest first, so the longest blocks start first.
 constexpr int kBlkThreads = 128;
-constexpr int kBlkR = 4;
-constexpr int kBlkTile = kBlkThreads * kBlkR;  // 512 members per block
+// Members per thread (kBlkR) is a template parameter chosen per context by the autotuner among
+// 2, 4 and 8 (tiles of 256, 512 or 1024 members); every choice gives bit-identical sums.
 constexpr int64_t kBlockedMin = 384;
+constexpr int64_t kTuneMinMembers = 1 << 20;  // the autotuner times candidates on inputs this large
 
 // Tiles of the two direct-sum kernels; nodes with >= sur_min members (sur_min > 0) are left to
 // the surrogate path. Also the sort key of the blocked tiles' order (size class, descending).
 __global__ void k_tiles_split(int64_t nn, const int64_t* __restrict__ node_size, int64_t sur_min,
-                              const int* __restrict__ only, int64_t* __restrict__ small,
+                              const int* __restrict__ only, int blk_tile, int64_t* __restrict__ small,
                               int64_t* __restrict__ big, uint64_t* __restrict__ okey,
                               uint32_t* __restrict__ oval) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -116,7 +117,7 @@ __global__ void k_tiles_split(int64_t nn, const int64_t* __restrict__ node_size,
   const bool skip = only ? (only[k] == 0) : (sur_min > 0 && g >= sur_min);
   const bool blocked = !skip && g > kBlockedMin;
   small[k] = (skip || g > kBlockedMin) ? 0 : (g + kPotTile - 1) / kPotTile;
-  big[k] = blocked ? (g + kBlkTile - 1) / kBlkTile : 0;
+  big[k] = blocked ? (g + blk_tile - 1) / blk_tile : 0;
   okey[k] = blocked ? uint64_t(63 - __clzll(g)) ^ 63u : 255u;
   oval[k] = uint32_t(k);
 }
@@ -136,6 +137,7 @@ __device__ __forceinline__ void pot_pair(float4 a, float2 zz, float2 nx, float2 
   w = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
 }
 
+template <int kBlkR>
 __global__ void __launch_bounds__(kBlkThreads)
 k_potential_blocked(int64_t nn, const int64_t* __restrict__ tile_off, const uint32_t* __restrict__ perm,
                     const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
@@ -152,7 +154,7 @@ k_potential_blocked(int64_t nn, const int64_t* __restrict__ tile_off, const uint
   float S[kBlkR], C[kBlkR];
 #pragma unroll
   for (int p = 0; p < kBlkR / 2; ++p) {
-    const int64_t i0 = t * kBlkTile + threadIdx.x + kBlkThreads * (2 * p);
+    const int64_t i0 = t * (kBlkThreads * kBlkR) + threadIdx.x + kBlkThreads * (2 * p);
     const int64_t i1 = i0 + kBlkThreads;
     const float4 u0 = i0 < g ? U[base + i0] : make_float4(0, 0, 0, 0);
     const float4 u1 = i1 < g ? U[base + i1] : make_float4(0, 0, 0, 0);
@@ -222,7 +224,7 @@ k_potential_blocked(int64_t nn, const int64_t* __restrict__ tile_off, const uint
   }
 #pragma unroll
   for (int k = 0; k < kBlkR; ++k) {
-    const int64_t i = t * kBlkTile + threadIdx.x + kBlkThreads * k;
+    const int64_t i = t * (kBlkThreads * kBlkR) + threadIdx.x + kBlkThreads * k;
     if (i < g) S_out[base + i] = S[k];
   }
 }
@@ -460,34 +462,89 @@ __global__ void k_halo_decide(int64_t nn, const int64_t* __restrict__ node_size,
   is_halo[q] = (c >= min_size && int64_t(bden) * c >= int64_t(bnum) * node_size[q]) ? 1 : 0;
 }
 
+// Tiles of the blocked kernel for kBlkR = R (nodes above kBlockedMin members, ordered by size
+// class, largest first) and of k_potential (the other selected nodes).
+int potential_tiles(rs_ctx* ctx, int64_t sur_min, const int* only, int R, int64_t* tile_small,
+                    int64_t* tile_perm, uint32_t** perm, cudaStream_t st) {
+  Hier h = hier_of(ctx);
+  const int64_t nn = ctx->n_nodes;
+  int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
+  uint64_t* ka = scratch_t<uint64_t>(ctx, S_U_OKEY_A, size_t(nn));
+  uint64_t* kb = scratch_t<uint64_t>(ctx, S_U_OKEY_B, size_t(nn));
+  uint32_t* va = scratch_t<uint32_t>(ctx, S_U_OVAL_A, size_t(nn));
+  uint32_t* vb = scratch_t<uint32_t>(ctx, S_U_OVAL_B, size_t(nn));
+  if (!tile_big || !ka || !kb || !va || !vb) return RS_ERR_OOM;
+  k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sur_min, only, kBlkThreads * R, tile_small,
+                                                 tile_big, ka, va);
+  RS_LAUNCHED(ctx, "k_tiles_split");
+  uint64_t* ko;
+  RS_TRY(radix_sort_u64(ctx, nn, 8, ka, va, kb, vb, &ko, perm, st));
+  k_perm_tiles<<<grid_for(nn, kT), kT, 0, st>>>(nn, *perm, tile_big, tile_perm);
+  RS_LAUNCHED(ctx, "k_perm_tiles");
+  RS_TRY(exclusive_scan_i64(ctx, nn, tile_small, tile_small + nn, st));
+  RS_TRY(exclusive_scan_i64(ctx, nn, tile_perm, tile_perm + nn, st));
+  return RS_OK;
+}
+
+int launch_blocked(rs_ctx* ctx, int R, const int64_t* tile_perm, const uint32_t* perm, float* S,
+                   cudaStream_t st) {
+  Hier h = hier_of(ctx);
+  const int64_t m = ctx->n_members, nn = ctx->n_nodes;
+  const float eps2 = ctx->cfg.softening * ctx->cfg.softening;
+  const unsigned grid = grid_for(m / (kBlockedMin + 1) + m / (kBlkThreads * R) + 1, 1);
+  if (R == 2)
+    k_potential_blocked<2><<<grid, kBlkThreads, 0, st>>>(nn, tile_perm, perm, h.node_off, h.node_size, h.U, eps2, S);
+  else if (R == 8)
+    k_potential_blocked<8><<<grid, kBlkThreads, 0, st>>>(nn, tile_perm, perm, h.node_off, h.node_size, h.U, eps2, S);
+  else
+    k_potential_blocked<4><<<grid, kBlkThreads, 0, st>>>(nn, tile_perm, perm, h.node_off, h.node_size, h.U, eps2, S);
+  RS_LAUNCHED(ctx, "k_potential_blocked");
+  return RS_OK;
+}
+
 // Float32 direct sums S_i = sum_{j != i} (|u_j - u_i|^2 + eps^2)^(-1/2) of every member of the
 // selected nodes (only[k] != 0 if `only` is given, else nodes below sur_min when sur_min > 0,
 // else all): nodes up to kBlockedMin members by k_potential, larger ones by the blocked kernel
-// with its tiles ordered by node size class, largest first.
+// with its tiles ordered by node size class, largest first. The blocked kernel's members per
+// thread come from the context's autotuner: on the first call with at least kTuneMinMembers
+// members, each of 2, 4 and 8 is timed on that call's own nodes (CUDA events; identical sums)
+// and the fastest is kept for the context.
 int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, float* S, cudaStream_t st) {
   Hier h = hier_of(ctx);
   const int64_t m = ctx->n_members, nn = ctx->n_nodes;
   const float eps = ctx->cfg.softening;
   int64_t* tile_small = scratch_t<int64_t>(ctx, S_SELECT, size_t(nn) + 1);
-  int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
   int64_t* tile_perm = scratch_t<int64_t>(ctx, S_U_TILEPERM, size_t(nn) + 1);
-  uint64_t* ka = scratch_t<uint64_t>(ctx, S_U_OKEY_A, size_t(nn));
-  uint64_t* kb = scratch_t<uint64_t>(ctx, S_U_OKEY_B, size_t(nn));
-  uint32_t* va = scratch_t<uint32_t>(ctx, S_U_OVAL_A, size_t(nn));
-  uint32_t* vb = scratch_t<uint32_t>(ctx, S_U_OVAL_B, size_t(nn));
-  if (!tile_small || !tile_big || !tile_perm || !ka || !kb || !va || !vb) return RS_ERR_OOM;
-  k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sur_min, only, tile_small, tile_big,
-                                                 ka, va);
-  RS_LAUNCHED(ctx, "k_tiles_split");
-  uint64_t* ko;
+  if (!tile_small || !tile_perm) return RS_ERR_OOM;
   uint32_t* perm;
-  RS_TRY(radix_sort_u64(ctx, nn, 8, ka, va, kb, vb, &ko, &perm, st));
-  k_perm_tiles<<<grid_for(nn, kT), kT, 0, st>>>(nn, perm, tile_big, tile_perm);
-  RS_LAUNCHED(ctx, "k_perm_tiles");
-  RS_TRY(exclusive_scan_i64(ctx, nn, tile_small, tile_small + nn, st));
-  RS_TRY(exclusive_scan_i64(ctx, nn, tile_perm, tile_perm + nn, st));
+  if (ctx->tune_blk_r == 0 && m >= kTuneMinMembers) {
+    const int cand[3] = {2, 4, 8};
+    float best_ms = 0.f;
+    int best = 4;
+    cudaEvent_t e0, e1;
+    RS_CUDA(ctx, cudaEventCreate(&e0));
+    RS_CUDA(ctx, cudaEventCreate(&e1));
+    for (int c = 0; c < 3; ++c) {
+      RS_TRY(potential_tiles(ctx, sur_min, only, cand[c], tile_small, tile_perm, &perm, st));
+      RS_CUDA(ctx, cudaEventRecord(e0, st));
+      RS_TRY(launch_blocked(ctx, cand[c], tile_perm, perm, S, st));
+      RS_CUDA(ctx, cudaEventRecord(e1, st));
+      RS_CUDA(ctx, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      RS_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+      ctx->tune_blk_ms[c] = ms;
+      if (c == 0 || ms < best_ms) {
+        best_ms = ms;
+        best = cand[c];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune_blk_r = best;
+  }
+  const int R = ctx->tune_blk_r ? ctx->tune_blk_r : 4;
+  RS_TRY(potential_tiles(ctx, sur_min, only, R, tile_small, tile_perm, &perm, st));
   const int64_t tiles_ub = nn + m / kPotTile + 1;
-  const int64_t big_ub = m / (kBlockedMin + 1) + m / kBlkTile + 1;
   {
     ProfScope prof_(ctx, "k_potential", st);
     k_potential<<<grid_for(tiles_ub, 1), kPotTile, 0, st>>>(nn, tile_small, h.node_off, h.node_size, h.U,
@@ -496,10 +553,8 @@ int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, float* S, cu
   RS_LAUNCHED(ctx, "k_potential");
   {
     ProfScope prof_(ctx, "k_potential_blocked", st);
-    k_potential_blocked<<<grid_for(big_ub, 1), kBlkThreads, 0, st>>>(nn, tile_perm, perm, h.node_off,
-                                                                    h.node_size, h.U, eps * eps, S);
+    RS_TRY(launch_blocked(ctx, R, tile_perm, perm, S, st));
   }
-  RS_LAUNCHED(ctx, "k_potential_blocked");
   return RS_OK;
 }
 

@@ -72,3 +72,23 @@ def test_energy_shifted_members_take_the_exact_path():
     o2 = oracle_pipeline(s2, labels=g["labels"])
     assert g["n_fallback"] >= len(pick) // 2
     _compare(g, o2)
+
+
+def test_autotuner_picks_a_candidate_and_keeps_the_sums():
+    """On a call with >= 2^20 members the autotuner times 2, 4 and 8 members per thread for the
+    blocked potential and keeps the fastest; the potentials of the tuning call and of a later
+    call with the kept choice are bit-identical."""
+    import paper_2412_18629_gb300 as rs
+    s = synth.generate(synth.WORKLOADS["nfw-2^21-L128-sub"])
+    ctx = gpu_ctx(s, mode="batched")
+    pos, vel, ids = to_dev(s)
+    lab, _ = rs.rs_fof3d(ctx, pos, ids)
+    rs.rs_fof6d(ctx, pos, vel, ids, lab)
+    assert ctx.n_members >= 1 << 20
+    assert ctx.tuning()["blocked_potential"]["members_per_thread"] == 0
+    phi1, b1, _ = rs.rs_unbind(ctx, pos, vel, want_potential=True)
+    t = ctx.tuning()["blocked_potential"]
+    assert t["members_per_thread"] in (2, 4, 8) and all(v > 0 for v in t["ms"].values()), t
+    phi1, b1 = phi1.cpu().numpy(), b1.cpu().numpy()
+    phi2, b2, _ = rs.rs_unbind(ctx, pos, vel, want_potential=True)
+    assert np.array_equal(phi1, phi2.cpu().numpy()) and np.array_equal(b1, b2.cpu().numpy())
