@@ -36,7 +36,8 @@ enum Slot : int {
   S_U_TILEPERM, S_U_OKEY_A, S_U_OKEY_B, S_U_OVAL_A, S_U_OVAL_B, S_U_FBMAX, S_U_FBCHUNK,
   // batched form: pruned 6D searches
   S_P_MEANU, S_P_MEANV, S_P_US, S_P_VS, S_P_SP, S_P_BOFF, S_P_BUCKET, S_P_BOX, S_P_SUB,
-  S_P_SBOFF, S_P_SBOX, S_P_ORDER, S_P_QCTR, S_P_WORK, S_P_NN2S,
+  S_P_SBOFF, S_P_SBOX, S_P_ORDER, S_P_QCTR, S_P_WORK, S_P_NSTART, S_P_NCNT, S_P_APOS,
+  S_P_USA, S_P_VSA, S_P_SPA, S_P_QKEY_A, S_P_QKEY_B, S_P_QVAL_A, S_P_QVAL_B,
   // surrogate MLP
   S_MLP_DEV, S_MLP_W, S_MLP_PART, S_MLP_SSE, S_MLP_M, S_MLP_G, S_MLP_IDX, S_MLP_BIDX, S_MLP_XH,
   S_MLP_YH,

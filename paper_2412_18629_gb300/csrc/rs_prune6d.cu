@@ -7,8 +7,11 @@
 // 32 consecutive buckets of a node form a superbucket with its own box. Persistent warps pull
 // query buckets from a queue ordered by node size (largest first) and, lane = member, visit
 // the node's superbuckets, buckets and sub-buckets, skipping any whose lower bound exceeds the
-// lane's current best (nearest neighbour) or l2 (link, upper triangle of bucket pairs).
-// Lower bounds are computed with the same round-to-nearest float32 operations as d6 on the
+// lane's current best (nearest neighbour) or l2 (link, upper triangle of bucket pairs). The
+// link pass runs on the members with a friend only (nn2 <= l2: no other member can be linked),
+// compacted in the same order and bucketed again, so its boxes are tighter and no lane idles.
+// Distances and bounds use packed float32x2 arithmetic with each half rounded like the scalar
+// operation. Lower bounds are computed with the same round-to-nearest float32 operations as d6 on the
 // per-axis gaps to the box: every step is monotone, so the bound never exceeds the computed
 // d6 of any member inside the box, and pruning cannot change the minimum or the set of links.
 // Results are therefore bit-identical to the brute-force kernels (and to the definition).
@@ -107,19 +110,56 @@ __global__ void k_gather_sorted(int64_t mb, int64_t m, const uint32_t* __restric
   sp[s] = p;
 }
 
-__global__ void k_gather_nn2(int64_t m, const uint32_t* __restrict__ sp, const float* __restrict__ nn2,
-                             float* __restrict__ nn2s) {
-  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (s < m) nn2s[s] = nn2[sp[s]];
-}
-
-__global__ void k_bucket_counts(int64_t nb, int64_t nn, const int64_t* __restrict__ node_size,
-                                int64_t* __restrict__ bcnt, int64_t* __restrict__ sbcnt) {
+// Members of each node of the level in the bucketed arrays: start (level-local sorted
+// position) and count; all members for the NN pass, the members with a friend for the link pass.
+__global__ void k_node_ranges(int64_t nb, int64_t nn, int64_t mb, const int64_t* __restrict__ node_off,
+                              const int64_t* __restrict__ node_size, int64_t* __restrict__ start,
+                              int64_t* __restrict__ cnt) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= nn) return;
-  const int64_t c = (node_size[nb + k] + 31) / 32;
+  start[k] = node_off[nb + k] - mb;
+  cnt[k] = node_size[nb + k];
+}
+
+__global__ void k_bucket_counts(int64_t nn, const int64_t* __restrict__ cnt, int64_t* __restrict__ bcnt,
+                                int64_t* __restrict__ sbcnt) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= nn) return;
+  const int64_t c = (cnt[k] + 31) / 32;
   bcnt[k] = c;
   sbcnt[k] = (c + 31) / 32;
+}
+
+// Link pass: the members with a friend (nn2 <= l2 of their node), compacted in sorted order.
+__global__ void k_active_flags(int64_t m, int64_t mb, const uint32_t* __restrict__ sp,
+                               const uint32_t* __restrict__ mnode, const float4* __restrict__ inv,
+                               const float* __restrict__ nn2, int64_t* __restrict__ flag) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= m) return;
+  const uint32_t p = sp[s];
+  flag[s] = nn2[p] <= inv[mnode[mb + p]].z ? 1 : 0;
+}
+
+__global__ void k_compact_active(int64_t m, const int64_t* __restrict__ pos, const float4* __restrict__ Us,
+                                 const float4* __restrict__ Vs, const uint32_t* __restrict__ sp,
+                                 float4* __restrict__ UsA, float4* __restrict__ VsA,
+                                 uint32_t* __restrict__ spA) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= m || pos[s + 1] == pos[s]) return;
+  const int64_t a = pos[s];
+  UsA[a] = Us[s];
+  VsA[a] = Vs[s];
+  spA[a] = sp[s];
+}
+
+__global__ void k_active_ranges(int64_t nb, int64_t nn, int64_t mb, const int64_t* __restrict__ node_off,
+                                const int64_t* __restrict__ node_size, const int64_t* __restrict__ pos,
+                                int64_t* __restrict__ start, int64_t* __restrict__ cnt) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= nn) return;
+  const int64_t s0 = node_off[nb + k] - mb;
+  start[k] = pos[s0];
+  cnt[k] = pos[s0 + node_size[nb + k]] - pos[s0];
 }
 
 __device__ __forceinline__ void warp_box(const float (&a)[6], bool valid, int lo_off, int hi_off,
@@ -149,9 +189,9 @@ __device__ __forceinline__ Box make_box(const float (&lo)[6], const float (&hi)[
 // box, four 8-member sub-boxes (an empty sub-bucket gets lo = +inf, hi = -inf, so every gap to
 // it is +inf), and the work-queue key (largest node first).
 __global__ void __launch_bounds__(kT)
-k_buckets(int64_t nb, int64_t nn, int64_t mb, int64_t nbk_ub, const int64_t* __restrict__ bucket_off,
-          const int64_t* __restrict__ sb_off, const int64_t* __restrict__ node_off,
-          const int64_t* __restrict__ node_size, const float4* __restrict__ Us,
+k_buckets(int64_t nb, int64_t nn, int64_t nbk_ub, const int64_t* __restrict__ bucket_off,
+          const int64_t* __restrict__ sb_off, const int64_t* __restrict__ nstart,
+          const int64_t* __restrict__ ncnt, const float4* __restrict__ Us,
           const float4* __restrict__ Vs, Bucket* __restrict__ bk, Box* __restrict__ box,
           Box* __restrict__ sub, uint64_t* __restrict__ qkey, uint32_t* __restrict__ qval) {
   const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -159,7 +199,7 @@ k_buckets(int64_t nb, int64_t nn, int64_t mb, int64_t nbk_ub, const int64_t* __r
   if (w >= nbk_ub) return;
   if (w >= bucket_off[nn]) {
     if (lane == 0) {
-      qkey[w] = 255u;  // after every real bucket (their keys are < 255: nodes have >= 2 members)
+      qkey[w] = 255u;  // the largest key: after every real bucket (stable sort, higher indices)
       qval[w] = uint32_t(w);
     }
     return;
@@ -167,8 +207,8 @@ k_buckets(int64_t nb, int64_t nn, int64_t mb, int64_t nbk_ub, const int64_t* __r
   const int64_t k = rsd::upper_bound_i64(bucket_off, nn, w) - 1;
   const int64_t q = nb + k;
   const int64_t kb = w - bucket_off[k];
-  const int64_t start = node_off[q] - mb + 32 * kb;
-  const int cnt = int(rsd::min64(32, node_size[q] - 32 * kb));
+  const int64_t start = nstart[k] + 32 * kb;
+  const int cnt = int(rsd::min64(32, ncnt[k] - 32 * kb));
   const bool valid = lane < cnt;
   const float4 u = Us[start + (valid ? lane : 0)], v = Vs[start + (valid ? lane : 0)];
   const float a[6] = {u.x, u.y, u.z, v.x, v.y, v.z};
@@ -188,7 +228,7 @@ k_buckets(int64_t nb, int64_t nn, int64_t mb, int64_t nbk_ub, const int64_t* __r
     b.pad = 0;
     bk[w] = b;
     box[w] = make_box(lo, hi);
-    qkey[w] = 255u - rsd::size_class(node_size[q]);
+    qkey[w] = 255u - rsd::size_class(ncnt[k]);
     qval[w] = uint32_t(w);
   }
 }
@@ -375,7 +415,6 @@ struct NNArgs {
   const float4* inv;
   unsigned long long* counter;
   unsigned long long* work;  // [4]: NN d6, NN box tests, link d6, link box tests (counting variant)
-  const float* nn2s;         // nearest-neighbour d6 in sorted member order (link pass)
 };
 
 // Per-lane tallies of the counting variant (evaluated d6 and box tests).
@@ -485,7 +524,7 @@ template <bool kCount>
 __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t b, const Box& Abox,
                                             bool active, const Query& Q, uint32_t pi, float l2,
                                             uint32_t* uf, int lane, Stage& S, uint32_t (&sj)[32],
-                                            float (&snn)[32], Tally& T) {
+                                            Tally& T) {
   const Box B = A.box[b];
   if (kCount) T.box += (lane == 0);
   if (lb_box_box(Abox, B, Q.s) > l2) return;
@@ -495,10 +534,7 @@ __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t 
   const Bucket Bb = A.bk[b];
   __syncwarp();
   stage(S, A.Us, A.Vs, Bb.start, int(Bb.count), lane);
-  if (lane < int(Bb.count)) {
-    sj[lane] = A.sp[Bb.start + lane];
-    snn[lane] = A.nn2s[Bb.start + lane];
-  }
+  if (lane < int(Bb.count)) sj[lane] = A.sp[Bb.start + lane];
   __syncwarp();
   const int j0 = (b == a) ? lane + 1 : 0;
   for (uint32_t s0 = 0; s0 < Bb.count; s0 += 8) {
@@ -514,23 +550,22 @@ __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t 
       for (int j = int(s0); j < s1; j += 2) {
         if (j + 1 < j0) continue;
         const float2 d = d6_pair(Q, S, j);
-        if (j >= j0 && d.x <= l2 && snn[j] <= l2) rsd::uf_unite(uf, pi, sj[j]);
-        if (j + 1 >= j0 && j + 1 < s1 && d.y <= l2 && snn[j + 1] <= l2) rsd::uf_unite(uf, pi, sj[j + 1]);
+        if (j >= j0 && d.x <= l2) rsd::uf_unite(uf, pi, sj[j]);
+        if (j + 1 >= j0 && j + 1 < s1 && d.y <= l2) rsd::uf_unite(uf, pi, sj[j + 1]);
       }
     }
   }
 }
 
+// Over the buckets of the members with a friend: every valid lane is active.
 template <bool kCount>
 __global__ void __launch_bounds__(kT)
-k_link6d_pruned(NNArgs A, const float* __restrict__ nn2, uint32_t* __restrict__ uf) {
+k_link6d_pruned(NNArgs A, uint32_t* __restrict__ uf) {
   Tally T;
   __shared__ Stage stg[kWarpsPerBlock];
   __shared__ uint32_t sj[kWarpsPerBlock][32];
-  __shared__ float snn[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int64_t nbk = *A.nbuckets;
-  (void)nn2;
   while (true) {
     const int64_t w = next_work(A.counter, lane);
     if (w >= nbk) break;
@@ -542,8 +577,7 @@ k_link6d_pruned(NNArgs A, const float* __restrict__ nn2, uint32_t* __restrict__ 
     const uint32_t si = Aq.start + (valid ? lane : 0);
     const Query Q = make_query(A.Us[si], A.Vs[si], iv.x, iv.y);
     const uint32_t pi = A.sp[si];
-    const bool active = valid && A.nn2s[si] <= l2;
-    if (!__any_sync(0xffffffffu, active)) continue;
+    const bool active = valid;
     const Box Abox = A.box[a];
     const int64_t own = (a - int64_t(Aq.first)) >> 5, nsb = Aq.sbcount;
     for (int64_t s = own; s < nsb; ++s) {
@@ -556,7 +590,7 @@ k_link6d_pruned(NNArgs A, const float* __restrict__ nn2, uint32_t* __restrict__ 
       const int64_t b_lo = rsd::min64(int64_t(Aq.first) + 32 * s, int64_t(Aq.last) + 1);
       const int64_t b_hi = rsd::min64(int64_t(Aq.first) + 32 * s + 32, int64_t(Aq.last) + 1);
       for (int64_t b = (s == own ? a : b_lo); b < b_hi; ++b)
-        link_bucket<kCount>(A, a, b, Abox, active, Q, pi, l2, uf, lane, stg[wb], sj[wb], snn[wb], T);
+        link_bucket<kCount>(A, a, b, Abox, active, Q, pi, l2, uf, lane, stg[wb], sj[wb], T);
     }
   }
   flush_tally<kCount>(T, A.work + 2, lane);
@@ -583,8 +617,51 @@ NNArgs nn_args(rs_ctx* ctx, int64_t nn) {
   A.inv = h.inv;
   A.counter = static_cast<unsigned long long*>(ctx->buf[S_P_QCTR].ptr);
   A.work = static_cast<unsigned long long*>(ctx->buf[S_P_WORK].ptr);
-  A.nn2s = nullptr;
   return A;
+}
+
+}  // namespace
+
+namespace {
+
+// Bucket tables of the level over the members [start[k], start[k] + cnt[k]) of each node k in
+// the arrays Us, Vs (m entries at most): buckets of 32, boxes, sub-boxes, superboxes and the
+// work queue ordered by node size class.
+int build_buckets(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t m, const int64_t* start, const int64_t* cnt,
+                  const float4* Us, const float4* Vs, cudaStream_t st) {
+  int64_t* boff = scratch_t<int64_t>(ctx, S_P_BOFF, size_t(nn) + 1);
+  int64_t* sboff = scratch_t<int64_t>(ctx, S_P_SBOFF, size_t(nn) + 1);
+  const int64_t nbk_ub = nn + m / 32 + 1;
+  const int64_t nsb_ub = nn + nbk_ub / 32 + 1;
+  Bucket* bk = scratch_t<Bucket>(ctx, S_P_BUCKET, size_t(nbk_ub));
+  Box* box = scratch_t<Box>(ctx, S_P_BOX, size_t(nbk_ub));
+  Box* sub = scratch_t<Box>(ctx, S_P_SUB, size_t(nbk_ub) * 4);
+  Box* sbox = scratch_t<Box>(ctx, S_P_SBOX, size_t(nsb_ub));
+  uint64_t* qk = scratch_t<uint64_t>(ctx, S_P_QKEY_A, size_t(nbk_ub));
+  uint64_t* qk2 = scratch_t<uint64_t>(ctx, S_P_QKEY_B, size_t(nbk_ub));
+  uint32_t* qv = scratch_t<uint32_t>(ctx, S_P_QVAL_A, size_t(nbk_ub));
+  uint32_t* qv2 = scratch_t<uint32_t>(ctx, S_P_QVAL_B, size_t(nbk_ub));
+  uint32_t* qorder = scratch_t<uint32_t>(ctx, S_P_ORDER, size_t(nbk_ub));
+  if (!boff || !sboff || !bk || !box || !sub || !sbox || !qk || !qk2 || !qv || !qv2 || !qorder)
+    return RS_ERR_OOM;
+  k_bucket_counts<<<grid_for(nn, kT), kT, 0, st>>>(nn, cnt, boff, sboff);
+  RS_LAUNCHED(ctx, "k_bucket_counts");
+  RS_TRY(exclusive_scan_i64(ctx, nn, boff, boff + nn, st));
+  RS_TRY(exclusive_scan_i64(ctx, nn, sboff, sboff + nn, st));
+  k_buckets<<<grid_for(nbk_ub * 32, kT), kT, 0, st>>>(nb, nn, nbk_ub, boff, sboff, start, cnt, Us, Vs, bk, box,
+                                                     sub, qk, qv);
+  RS_LAUNCHED(ctx, "k_buckets");
+  k_superboxes<<<grid_for(nsb_ub * 32, kT), kT, 0, st>>>(nn, boff, sboff, box, sbox);
+  RS_LAUNCHED(ctx, "k_superboxes");
+  uint64_t* qk_out;
+  uint32_t* qv_out;
+  RS_TRY(radix_sort_u64(ctx, nbk_ub, 8, qk, qv, qk2, qv2, &qk_out, &qv_out, st));
+  RS_CUDA(ctx, cudaMemcpyAsync(qorder, qv_out, sizeof(uint32_t) * nbk_ub, cudaMemcpyDeviceToDevice, st));
+  return RS_OK;
+}
+
+unsigned persistent_grid(int64_t nbk_ub) {
+  return unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 8));
 }
 
 }  // namespace
@@ -600,19 +677,11 @@ int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t
   float4* Us = scratch_t<float4>(ctx, S_P_US, size_t(m));
   float4* Vs = scratch_t<float4>(ctx, S_P_VS, size_t(m));
   uint32_t* sp = scratch_t<uint32_t>(ctx, S_P_SP, size_t(m));
-  int64_t* boff = scratch_t<int64_t>(ctx, S_P_BOFF, size_t(nn) + 1);
-  int64_t* sboff = scratch_t<int64_t>(ctx, S_P_SBOFF, size_t(nn) + 1);
-  const int64_t nbk_ub = nn + m / 32 + 1;
-  const int64_t nsb_ub = nn + nbk_ub / 32 + 1;
-  Bucket* bk = scratch_t<Bucket>(ctx, S_P_BUCKET, size_t(nbk_ub));
-  Box* box = scratch_t<Box>(ctx, S_P_BOX, size_t(nbk_ub));
-  Box* sub = scratch_t<Box>(ctx, S_P_SUB, size_t(nbk_ub) * 4);
-  Box* sbox = scratch_t<Box>(ctx, S_P_SBOX, size_t(nsb_ub));
+  int64_t* nstart = scratch_t<int64_t>(ctx, S_P_NSTART, size_t(nn));
+  int64_t* ncnt = scratch_t<int64_t>(ctx, S_P_NCNT, size_t(nn));
   unsigned long long* qctr = scratch_t<unsigned long long>(ctx, S_P_QCTR, 2);
   if (!scratch_t<unsigned long long>(ctx, S_P_WORK, 4)) return RS_ERR_OOM;
-  if (!mean_u || !ka || !kb || !va || !vb || !Us || !Vs || !sp || !boff || !sboff || !bk || !box ||
-      !sub || !sbox || !qctr)
-    return RS_ERR_OOM;
+  if (!mean_u || !ka || !kb || !va || !vb || !Us || !Vs || !sp || !nstart || !ncnt || !qctr) return RS_ERR_OOM;
   k_node_means<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, sums, mean_u);
   RS_LAUNCHED(ctx, "k_node_means");
   k_morton3<<<grid_for(m, kT), kT, 0, st>>>(mb, m, nb, h.mnode, h.U, h.inv, mean_u, ka, va);
@@ -622,28 +691,9 @@ int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t
   RS_TRY(radix_sort_u64(ctx, m, 30 + bits_for(uint64_t(nn)), ka, va, kb, vb, &keys, &order, st));
   k_gather_sorted<<<grid_for(m, kT), kT, 0, st>>>(mb, m, order, h.U, h.V, Us, Vs, sp);
   RS_LAUNCHED(ctx, "k_gather_sorted");
-  k_bucket_counts<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, boff, sboff);
-  RS_LAUNCHED(ctx, "k_bucket_counts");
-  RS_TRY(exclusive_scan_i64(ctx, nn, boff, boff + nn, st));
-  RS_TRY(exclusive_scan_i64(ctx, nn, sboff, sboff + nn, st));
-  // bucket tables and the work queue (keys/values reuse the sort buffers: m >= buckets)
-  uint64_t* qk = scratch_t<uint64_t>(ctx, S_KEY_A, size_t(std::max(m, nbk_ub)));
-  uint64_t* qk2 = scratch_t<uint64_t>(ctx, S_KEY_B, size_t(std::max(m, nbk_ub)));
-  uint32_t* qv = scratch_t<uint32_t>(ctx, S_VAL_A, size_t(std::max(m, nbk_ub)));
-  uint32_t* qv2 = scratch_t<uint32_t>(ctx, S_VAL_B, size_t(std::max(m, nbk_ub)));
-  if (!qk || !qk2 || !qv || !qv2) return RS_ERR_OOM;
-  k_buckets<<<grid_for(nbk_ub * 32, kT), kT, 0, st>>>(nb, nn, mb, nbk_ub, boff, sboff, h.node_off,
-                                                     h.node_size, Us, Vs, bk, box, sub, qk, qv);
-  RS_LAUNCHED(ctx, "k_buckets");
-  k_superboxes<<<grid_for(nsb_ub * 32, kT), kT, 0, st>>>(nn, boff, sboff, box, sbox);
-  RS_LAUNCHED(ctx, "k_superboxes");
-  uint64_t* qk_out;
-  uint32_t* qv_out;
-  RS_TRY(radix_sort_u64(ctx, nbk_ub, 8, qk, qv, qk2, qv2, &qk_out, &qv_out, st));
-  uint32_t* qorder = scratch_t<uint32_t>(ctx, S_P_ORDER, size_t(nbk_ub));
-  if (!qorder) return RS_ERR_OOM;
-  RS_CUDA(ctx, cudaMemcpyAsync(qorder, qv_out, sizeof(uint32_t) * nbk_ub, cudaMemcpyDeviceToDevice, st));
-  return RS_OK;
+  k_node_ranges<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, mb, h.node_off, h.node_size, nstart, ncnt);
+  RS_LAUNCHED(ctx, "k_node_ranges");
+  return build_buckets(ctx, nb, nn, m, nstart, ncnt, Us, Vs, st);
 }
 
 int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, float* nn2,
@@ -651,8 +701,7 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
   (void)nb;
   (void)mb;
   NNArgs A = nn_args(ctx, nn);
-  const int64_t nbk_ub = nn + m / 32 + 1;
-  const unsigned grid = unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 8));
+  const unsigned grid = persistent_grid(nn + m / 32 + 1);
   RS_CUDA(ctx, cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st));
   if (ctx->count_work) {
     k_nn6d_pruned<true><<<grid, kT, 0, st>>>(A, nn2);
@@ -664,25 +713,41 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
   return RS_OK;
 }
 
+// The link pass runs over the members with a friend only (the others can join no link): they
+// are compacted in the sorted order and get their own, tighter buckets.
 int rs::prune6d_link(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, const float* nn2,
                      uint32_t* uf, cudaStream_t st) {
-  (void)nb;
-  (void)mb;
+  Hier h = hier_of(ctx);
+  const float4* Us = static_cast<const float4*>(ctx->buf[S_P_US].ptr);
+  const float4* Vs = static_cast<const float4*>(ctx->buf[S_P_VS].ptr);
+  const uint32_t* sp = static_cast<const uint32_t*>(ctx->buf[S_P_SP].ptr);
+  int64_t* pos = scratch_t<int64_t>(ctx, S_P_APOS, size_t(m) + 1);
+  float4* UsA = scratch_t<float4>(ctx, S_P_USA, size_t(std::max<int64_t>(m, 1)));
+  float4* VsA = scratch_t<float4>(ctx, S_P_VSA, size_t(std::max<int64_t>(m, 1)));
+  uint32_t* spA = scratch_t<uint32_t>(ctx, S_P_SPA, size_t(std::max<int64_t>(m, 1)));
+  int64_t* nstart = scratch_t<int64_t>(ctx, S_P_NSTART, size_t(nn));
+  int64_t* ncnt = scratch_t<int64_t>(ctx, S_P_NCNT, size_t(nn));
+  if (!pos || !UsA || !VsA || !spA || !nstart || !ncnt) return RS_ERR_OOM;
+  k_active_flags<<<grid_for(m, kT), kT, 0, st>>>(m, mb, sp, h.mnode, h.inv, nn2, pos);
+  RS_LAUNCHED(ctx, "k_active_flags");
+  RS_TRY(exclusive_scan_i64(ctx, m, pos, pos + m, st));
+  k_compact_active<<<grid_for(m, kT), kT, 0, st>>>(m, pos, Us, Vs, sp, UsA, VsA, spA);
+  RS_LAUNCHED(ctx, "k_compact_active");
+  k_active_ranges<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, mb, h.node_off, h.node_size, pos, nstart, ncnt);
+  RS_LAUNCHED(ctx, "k_active_ranges");
+  RS_TRY(build_buckets(ctx, nb, nn, m, nstart, ncnt, UsA, VsA, st));
   NNArgs A = nn_args(ctx, nn);
+  A.Us = UsA;
+  A.Vs = VsA;
+  A.sp = spA;
   A.counter += 1;
-  float* nn2s = scratch_t<float>(ctx, S_P_NN2S, size_t(std::max<int64_t>(m, 1)));
-  if (!nn2s) return RS_ERR_OOM;
-  k_gather_nn2<<<grid_for(m, kT), kT, 0, st>>>(m, A.sp, nn2, nn2s);
-  RS_LAUNCHED(ctx, "k_gather_nn2");
-  A.nn2s = nn2s;
-  const int64_t nbk_ub = nn + m / 32 + 1;
-  const unsigned grid = unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 8));
+  const unsigned grid = persistent_grid(nn + m / 32 + 1);
   RS_CUDA(ctx, cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st));
   if (ctx->count_work) {
-    k_link6d_pruned<true><<<grid, kT, 0, st>>>(A, nn2, uf);
+    k_link6d_pruned<true><<<grid, kT, 0, st>>>(A, uf);
   } else {
     ProfScope prof_(ctx, "k_link6d_pruned", st);
-    k_link6d_pruned<false><<<grid, kT, 0, st>>>(A, nn2, uf);
+    k_link6d_pruned<false><<<grid, kT, 0, st>>>(A, uf);
   }
   RS_LAUNCHED(ctx, "k_link6d_pruned");
   return RS_OK;
