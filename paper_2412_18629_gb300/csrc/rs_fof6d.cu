@@ -256,7 +256,69 @@ k_nn6d(int64_t nb, int64_t nn, const int64_t* __restrict__ tile_off, const int64
 }
 
 // Exact k-th smallest nn2 of each node, k = ceil(f_num g / f_den) - 1: 4 passes of 8-bit radix
-// select on the (non-negative) float bit patterns.
+// select on the (non-negative) float bit patterns. Nodes up to kSelectWarpMax members take one
+// warp each (k_select_l2_warp), larger ones a block (k_select_l2).
+constexpr int64_t kSelectWarpMax = 4096;
+
+__global__ void __launch_bounds__(kT)
+k_select_l2_warp(int64_t nb, int64_t nn, const int64_t* __restrict__ node_off,
+                 const int64_t* __restrict__ node_size, const float* __restrict__ nn2, int64_t mb,
+                 int f_num, int f_den, float4* __restrict__ inv) {
+  __shared__ uint32_t hist[kT / 32][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t k = int64_t(blockIdx.x) * (kT / 32) + w;
+  if (k >= nn) return;
+  const int64_t q = nb + k;
+  const int64_t base = node_off[q] - mb, g = node_size[q];
+  if (g > kSelectWarpMax) return;
+  uint32_t kk = uint32_t((int64_t(f_num) * g + f_den - 1) / f_den - 1);
+  uint32_t prefix = 0, mask = 0;
+  uint32_t* h = hist[w];
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    for (int d = lane; d < 256; d += 32) h[d] = 0;
+    __syncwarp();
+    for (int64_t a = lane; a < g; a += 32) {
+      const uint32_t bits = __float_as_uint(nn2[base + a]);
+      if ((bits & mask) == prefix) atomicAdd(&h[(bits >> shift) & 255u], 1u);
+    }
+    __syncwarp();
+    // digit d with cum(d) <= kk < cum(d) + h[d]: lane l owns bins 8l .. 8l + 7
+    uint32_t c[8], sum = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      c[t] = h[8 * lane + t];
+      sum += c[t];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const uint32_t excl = incl - sum;
+    const unsigned owner = __ballot_sync(0xffffffffu, excl <= kk && kk < incl);
+    const int L = __ffs(owner) - 1;
+    uint32_t d = 0, cum = excl;
+    if (lane == L) {
+      for (int t = 0; t < 8; ++t) {
+        if (cum + c[t] > kk) {
+          d = 8 * lane + t;
+          break;
+        }
+        cum += c[t];
+      }
+    }
+    d = __shfl_sync(0xffffffffu, d, L);
+    cum = __shfl_sync(0xffffffffu, cum, L);
+    kk -= cum;
+    prefix |= d << shift;
+    mask |= 255u << shift;
+    __syncwarp();
+  }
+  if (lane == 0) inv[q].z = __uint_as_float(prefix);
+}
+
 __global__ void __launch_bounds__(kT)
 k_select_l2(int64_t nb, const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
             const float* __restrict__ nn2, int64_t mb, int f_num, int f_den, float4* __restrict__ inv) {
@@ -264,6 +326,7 @@ k_select_l2(int64_t nb, const int64_t* __restrict__ node_off, const int64_t* __r
   __shared__ uint32_t s_prefix, s_k;
   const int64_t q = nb + blockIdx.x;
   const int64_t base = node_off[q] - mb, g = node_size[q];
+  if (g <= kSelectWarpMax) return;
   if (threadIdx.x == 0) {
     s_prefix = 0;
     s_k = uint32_t((int64_t(f_num) * g + f_den - 1) / f_den - 1);
@@ -661,6 +724,8 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     }
     {
       ProfScope prof_(ctx, "k_select_l2", st);
+      k_select_l2_warp<<<grid_for(nn, kT / 32), kT, 0, st>>>(nb, nn, h.node_off, h.node_size, nn2, mb, f_num,
+                                                            f_den, h.inv);
       k_select_l2<<<unsigned(nn), kT, 0, st>>>(nb, h.node_off, h.node_size, nn2, mb, f_num, f_den, h.inv);
     }
     RS_LAUNCHED(ctx, "k_select_l2");

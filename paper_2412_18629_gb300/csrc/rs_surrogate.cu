@@ -313,6 +313,7 @@ __global__ void k_sur_gate(int64_t ns, const uint32_t* __restrict__ sur_mem, con
 
 // Calibration members: kCalib per big node, evenly spaced in member order (sflag = 3).
 constexpr int kCalib = 64;
+static_assert(kCalib % 4 == 0, "k_pot_member4 groups the calibration list by 4 members of one node");
 
 __global__ void k_sur_calib_list(int64_t nbig, const int64_t* __restrict__ big_nodes,
                                  const int64_t* __restrict__ sur_off, const int64_t* __restrict__ node_size,
@@ -616,6 +617,80 @@ __global__ void k_flags_list(const unsigned long long* __restrict__ count, const
   }
 }
 
+// k_pot_member for groups of 4 consecutive list entries of the same node (the calibration
+// list: 64 per node): one warp per group shares every target load among the 4 members; each
+// member's sum has the same per-lane order as k_pot_member (bit-identical result).
+__global__ void __launch_bounds__(kT)
+k_pot_member4(const unsigned long long* __restrict__ count, const uint32_t* __restrict__ list,
+              const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
+              const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
+              const float4* __restrict__ U, const float4* __restrict__ V, const double* __restrict__ vbulk,
+              float eps2, double Gm, float* __restrict__ Sx, uint8_t* __restrict__ bound,
+              uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long total = *count / 4;
+  for (unsigned long long w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < total;
+       w += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    uint32_t k[4], p[4];
+    int64_t i[4];
+    float4 ui[4];
+    float S[4], C[4];
+    const uint32_t q = mnode[sur_mem[list[4 * w]]];
+    const int64_t base = node_off[q], g = node_size[q];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      k[r] = list[4 * w + r];
+      p[r] = sur_mem[k[r]];
+      i[r] = int64_t(p[r]) - base;
+      ui[r] = U[p[r]];
+      S[r] = 0.f;
+      C[r] = 0.f;
+    }
+    for (int64_t j0 = lane; j0 < g; j0 += 32 * 32) {
+      float blk[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+      for (int t = 0; t < 32; ++t) {
+        const int64_t j = j0 + 32 * t;
+        if (j < g) {
+          const float4 uj = U[base + j];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const float dx = __fsub_rn(uj.x, ui[r].x);
+            const float dy = __fsub_rn(uj.y, ui[r].y);
+            const float dz = __fsub_rn(uj.z, ui[r].z);
+            const float wv = rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2))));
+            blk[r] = __fadd_rn(blk[r], j == i[r] ? 0.f : wv);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float y = __fsub_rn(blk[r], C[r]);
+        const float tt = __fadd_rn(S[r], y);
+        C[r] = __fsub_rn(__fsub_rn(tt, S[r]), y);
+        S[r] = tt;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) S[r] = __fadd_rn(S[r], __shfl_xor_sync(0xffffffffu, S[r], off));
+    }
+    if (lane < 4) {
+      const float Sr = lane == 0 ? S[0] : lane == 1 ? S[1] : lane == 2 ? S[2] : S[3];
+      const uint32_t kr = k[lane], pr = p[lane];
+      Sx[kr] = Sr;
+      const double ph = -__dmul_rn(Gm, double(Sr));
+      const double e = __dadd_rn(kinetic(V[pr], vbulk + 3 * int64_t(q)), ph);
+      if (fabs(e) > __dmul_rn(2.0 * kCertB2, fabs(ph))) {
+        bound[pr] = e < 0.0 ? 1 : 0;
+      } else {
+        ambig[atomicAdd(n_ambig, 1ull)] = pr;
+      }
+    }
+  }
+}
+
 __global__ void k_sur_verdict(const unsigned long long* __restrict__ counters,
                               const uint32_t* __restrict__ check_list, const uint32_t* __restrict__ sur_mem,
                               const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_size,
@@ -846,10 +921,10 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
   RS_LAUNCHED(ctx, "k_sur_calib_list");
   {
     ProfScope prof_(ctx, "k_pot_member", st);
-    k_pot_member<<<grid, kT, 0, st>>>(counters + 9, calib_list, sur_mem, h.mnode, h.node_off, h.node_size,
-                                      h.U, h.V, vbulk, eps * eps, Gm, Sx, bound, ambig, counters + 2);
+    k_pot_member4<<<grid, kT, 0, st>>>(counters + 9, calib_list, sur_mem, h.mnode, h.node_off, h.node_size,
+                                       h.U, h.V, vbulk, eps * eps, Gm, Sx, bound, ambig, counters + 2);
   }
-  RS_LAUNCHED(ctx, "k_pot_member");
+  RS_LAUNCHED(ctx, "k_pot_member4");
   RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vbulk, bound, st));
   k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
   RS_LAUNCHED(ctx, "k_acc_counter");
