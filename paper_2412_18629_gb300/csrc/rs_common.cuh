@@ -274,6 +274,56 @@ __device__ __forceinline__ double f2d(float f) {
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// Warp-aggregated atomics for keys laid out in runs (members in node order, particles in cell
+// order): every lane of the warp calls these; a lane with `valid` false contributes nothing and
+// ends a run. Each contiguous run of valid lanes with equal keys gets an id (the number of run
+// starts up to the lane); a shuffle-down tree combines only lanes of the same run, so the
+// run's first lane holds the run's total (sum or minimum) and issues its one atomic.
+__device__ __forceinline__ uint32_t run_id(uint32_t key, bool valid, bool& head) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t kp = __shfl_up_sync(0xffffffffu, key, 1);
+  const bool vp = __shfl_up_sync(0xffffffffu, int(valid), 1) != 0;
+  const bool start = !valid || lane == 0 || !vp || kp != key;
+  head = valid && start;
+  const unsigned starts = __ballot_sync(0xffffffffu, start);
+  return uint32_t(__popc(starts & (0xffffffffu >> (31 - lane))));
+}
+
+template <class T>
+__device__ __forceinline__ void warp_run_add(T* base, uint32_t key, bool valid, T v) {
+  const int lane = threadIdx.x & 31;
+  bool head;
+  const uint32_t rid = run_id(key, valid, head);
+  v = valid ? v : T(0);
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T o = __shfl_down_sync(0xffffffffu, v, off);
+    const uint32_t ro = __shfl_down_sync(0xffffffffu, rid, off);
+    if (lane + off < 32 && ro == rid) v += o;
+  }
+  if (head && v) atomicAdd(base + key, v);
+}
+
+__device__ __forceinline__ void warp_run_min(unsigned long long* base, uint32_t key, bool valid,
+                                             unsigned long long v) {
+  const int lane = threadIdx.x & 31;
+  bool head;
+  const uint32_t rid = run_id(key, valid, head);
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long o = __shfl_down_sync(0xffffffffu, v, off);
+    const uint32_t ro = __shfl_down_sync(0xffffffffu, rid, off);
+    if (lane + off < 32 && ro == rid && o < v) v = o;
+  }
+  if (head) atomicMin(base + key, v);
+}
+
+// One atomic per warp for a count of the lanes with `pred`.
+__device__ __forceinline__ void warp_count(unsigned long long* ctr, bool pred) {
+  const unsigned b = __ballot_sync(0xffffffffu, pred);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(ctr, (unsigned long long)__popc(b));
+}
+
 // Canonical-order combination of the 32 lane partial sums of a warp: halving tree
 // s[l] += s[l + off], off = 16 .. 1, realised as an xor butterfly (IEEE + commutes, so lane
 // 0 ends with exactly the halving-tree value).

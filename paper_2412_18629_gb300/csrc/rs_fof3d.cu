@@ -211,10 +211,10 @@ k_fof_roots(int64_t n, uint32_t* __restrict__ parent, const uint32_t* __restrict
             const int64_t* __restrict__ ids, unsigned long long* __restrict__ minid,
             unsigned long long* __restrict__ counter) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t r = rsd::uf_find_ro(parent, uint32_t(i));
-  atomicMin(minid + r, (unsigned long long)ids[idx[i]]);
-  if (r == uint32_t(i)) atomicAdd(counter, 1ull);
+  const bool valid = i < n;  // every lane stays for the warp-aggregated atomics
+  const uint32_t r = valid ? rsd::uf_find_ro(parent, uint32_t(i)) : 0u;
+  rsd::warp_run_min(minid, r, valid, valid ? (unsigned long long)ids[idx[i]] : ~0ull);
+  rsd::warp_count(counter, valid && r == uint32_t(i));
 }
 
 __global__ void __launch_bounds__(kThreads)

@@ -284,31 +284,34 @@ __global__ void k_sur_gate(int64_t ns, const uint32_t* __restrict__ sur_mem, con
                            float* __restrict__ margin, unsigned int* __restrict__ gcount,
                            unsigned int* __restrict__ ecount, unsigned long long* __restrict__ counters) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= ns) return;
-  if (sflag[k] == 3) {  // calibration member: exact already
-    margin[k] = __int_as_float(0x7f800000);
-    return;
+  // every lane stays to the end for the warp-aggregated counters
+  const bool in = k < ns;
+  const bool calib = in && sflag[k] == 3;  // calibration member: exact already
+  const uint32_t p = in ? sur_mem[k] : 0u, q = in ? mnode[p] : 0u;
+  bool gated = false;
+  if (in && !calib) {
+    // predicted energy in units of G g m / r_vir, float32 (the gate's margin dwarfs its rounding)
+    const float inv_gmr = float(1.0 / st[q].gm_over_rvir);
+    const float4 v = V[p];
+    const float dvx = v.x - float(vbulk[3 * q]), dvy = v.y - float(vbulk[3 * q + 1]),
+                dvz = v.z - float(vbulk[3 * q + 2]);
+    const float e = 0.5f * (dvx * dvx + dvy * dvy + dvz * dvz) * inv_gmr + psi_hat[k];
+    const float thr = margin_factor * fmaxf(errn[q], err_floor);
+    if (fabsf(e) > thr) {
+      const uint8_t f = e < 0.f ? 1 : 0;
+      bound[p] = f;
+      sflag[k] = f;
+      margin[k] = fabsf(e) - thr;
+      gated = true;
+    } else {
+      sflag[k] = 2;
+      margin[k] = __int_as_float(0x7f800000);
+    }
   }
-  const uint32_t p = sur_mem[k], q = mnode[p];
-  // predicted energy in units of G g m / r_vir, float32 (the gate's margin dwarfs its rounding)
-  const float inv_gmr = float(1.0 / st[q].gm_over_rvir);
-  const float4 v = V[p];
-  const float dvx = v.x - float(vbulk[3 * q]), dvy = v.y - float(vbulk[3 * q + 1]),
-              dvz = v.z - float(vbulk[3 * q + 2]);
-  const float e = 0.5f * (dvx * dvx + dvy * dvy + dvz * dvz) * inv_gmr + psi_hat[k];
-  const float thr = margin_factor * fmaxf(errn[q], err_floor);
-  if (fabsf(e) > thr) {
-    const uint8_t f = e < 0.f ? 1 : 0;
-    bound[p] = f;
-    sflag[k] = f;
-    margin[k] = fabsf(e) - thr;
-    atomicAdd(gcount + q, 1u);
-    atomicAdd(counters + 5, 1ull);
-  } else {
-    sflag[k] = 2;
-    margin[k] = __int_as_float(0x7f800000);
-    atomicAdd(ecount + q, 1u);
-  }
+  if (calib) margin[k] = __int_as_float(0x7f800000);
+  rsd::warp_run_add(gcount, q, gated, 1u);
+  rsd::warp_run_add(ecount, q, in && !calib && !gated, 1u);
+  rsd::warp_count(counters + 5, gated);
 }
 
 // Calibration members: kCalib per big node, evenly spaced in member order (sflag = 3).
@@ -727,11 +730,11 @@ __global__ void k_sur_decided(int64_t ns, const uint32_t* __restrict__ sur_mem, 
                               const int* __restrict__ full, const int* __restrict__ fail,
                               unsigned long long* __restrict__ counters) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= ns) return;
-  const uint32_t q = mnode[sur_mem[k]];
-  if (full[q]) return;
-  if (sflag[k] < 2 && !checked[k] && !fail[q]) atomicAdd(counters + 10, 1ull);
-  if (sflag[k] == 3) atomicAdd(counters + 11, 1ull);
+  const bool in = k < ns;
+  const uint32_t q = in ? mnode[sur_mem[k]] : 0u;
+  const bool keep = in && !full[q];
+  rsd::warp_count(counters + 10, keep && sflag[k] < 2 && !checked[k] && !fail[q]);
+  rsd::warp_count(counters + 11, keep && sflag[k] == 3);
 }
 
 __global__ void k_count_fail(int64_t nn, const int* __restrict__ fail, unsigned long long* __restrict__ counters) {

@@ -348,7 +348,8 @@ __global__ void k_fallback_finish(int64_t n, const uint32_t* __restrict__ ambig,
 __global__ void k_bound_count(int64_t m, const uint32_t* __restrict__ mnode, const uint8_t* __restrict__ bound,
                               unsigned long long* __restrict__ nb) {
   const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p < m && bound[p]) atomicAdd(nb + mnode[p], 1ull);
+  const bool valid = p < m && bound[p];
+  rsd::warp_run_add(nb, valid ? mnode[p] : 0u, valid, 1ull);
 }
 
 __global__ void k_copy_u8(int64_t n, const uint8_t* __restrict__ a, uint8_t* __restrict__ b) {
