@@ -87,6 +87,7 @@ struct rs_ctx {
   // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
   bool profile = false;
   bool count_work = false;  // counting variants of the pruned 6D kernels (rs_count_work)
+  int sort_blocks = 0;      // radix-sort blocks resident at once on the device (0 = not known yet)
   // autotuner choices (0 = not tuned yet) and the timings they were chosen from
   int tune_blk_r = 0;       // members per thread of the blocked potential (2, 4, 8)
   float tune_blk_ms[3] = {0.f, 0.f, 0.f};

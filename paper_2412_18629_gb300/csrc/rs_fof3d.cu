@@ -10,7 +10,8 @@
 //   k_row_start   dense table of the first sorted position of every (z, y) row
 //   k_cell_bounds cell start (union-find parent = the cell's first particle: every sub-cell is a
 //                 clique) and cell end per sorted position
-//   k_fof_link    per particle, the half stencil of rows within R sub-cells; a neighbour cell is
+//   k_fof_link    per particle (particles alone in their sub-cell, then the others, in two
+//                 launches), the half stencil of rows within R sub-cells; a neighbour cell is
 //                 skipped when its root already equals the particle's root, otherwise scanned
 //                 until the first linked member (one link joins the whole clique)
 //   k_fof_roots   full path compression; smallest id per root (atomicMin); group count
@@ -171,8 +172,10 @@ __device__ __forceinline__ void scan_cells(const LinkArgs& A, uint32_t i, uint64
 __device__ __forceinline__ void scan_row(const LinkArgs& A, uint32_t i, uint64_t key_i, float4 pi,
                                          uint32_t& root_i, int zz, int yy, int xa, int xb_) {
   const int ns = A.ns;
-  zz = ((zz % ns) + ns) % ns;
-  yy = ((yy % ns) + ns) % ns;
+  // periodic wrap of offsets within one box length (|offset| <= R < ns): a compare and an add
+  // instead of an integer division
+  zz += zz < 0 ? ns : (zz >= ns ? -ns : 0);
+  yy += yy < 0 ? ns : (yy >= ns ? -ns : 0);
   if (xa < 0) {
     scan_cells(A, i, key_i, pi, root_i, zz, yy, xa + ns, ns - 1);
     scan_cells(A, i, key_i, pi, root_i, zz, yy, 0, xb_);
@@ -184,11 +187,16 @@ __device__ __forceinline__ void scan_row(const LinkArgs& A, uint32_t i, uint64_t
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_fof_link(int64_t n, LinkArgs A) {
+// Two launches: particles alone in their sub-cell (sparse regions: short scans, few links),
+// then particles of shared sub-cells (dense regions: many occupied neighbour cells). Keeping the
+// two kinds in different launches keeps a warp's lanes on similar amounts of work.
+__global__ void __launch_bounds__(kThreads) k_fof_link(int64_t n, LinkArgs A, bool alone) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const uint32_t i = uint32_t(t);
   const uint64_t key_i = A.keys[i];
+  const bool single = (i == 0 || A.keys[i - 1] != key_i) && (t + 1 == n || A.keys[i + 1] != key_i);
+  if (single != alone) return;
   const uint32_t mask = (1u << A.xb) - 1u;
   const int kx = int(key_i & mask), ky = int((key_i >> A.xb) & mask), kz = int(key_i >> (2 * A.xb));
   const float4 pi = A.posS[i];
@@ -282,9 +290,11 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
              ctx->cfg.box_L, 0.5f * ctx->cfg.box_L, ctx->cfg.link_len * ctx->cfg.link_len};
   {
     ProfScope prof_(ctx, "k_fof_link", st);
-    k_fof_link<<<grid, kThreads, 0, st>>>(n, A);
+    k_fof_link<<<grid, kThreads, 0, st>>>(n, A, true);
+    RS_LAUNCHED(ctx, "k_fof_link");
+    k_fof_link<<<grid, kThreads, 0, st>>>(n, A, false);
+    RS_LAUNCHED(ctx, "k_fof_link");
   }
-  RS_LAUNCHED(ctx, "k_fof_link");
   RS_CUDA(ctx, cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
   RS_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   k_fof_compress<<<grid, kThreads, 0, st>>>(n, parent);

@@ -25,21 +25,29 @@ constexpr int kTile6 = 128;
 // ---------------------------------------------------------------------------------------------
 // Level 0 from FoF labels.
 
-__global__ void k_max_id(int64_t n, const int64_t* __restrict__ ids, const int64_t* __restrict__ lab,
-                         unsigned long long* __restrict__ out) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256)
+k_max_id(int64_t n, const int64_t* __restrict__ ids, const int64_t* __restrict__ lab,
+         unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long wmax[8];
   unsigned long long m = 0;
-  if (i < n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t a = ids[i], b = lab[i];
-    if (a < 0 || b < 0) m = ~0ull;  // flags an invalid (negative) id or label
-    else m = (unsigned long long)(a > b ? a : b);
+    const unsigned long long v =
+        (a < 0 || b < 0) ? ~0ull : (unsigned long long)(a > b ? a : b);  // ~0 flags a negative
+    m = v > m ? v : m;
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
     const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
     m = o > m ? o : m;
   }
-  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {  // one atomic per block
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = wmax[w] > m ? wmax[w] : m;
+    atomicMax(out, m);
+  }
 }
 
 __global__ void k_group_keys(int64_t n, const int64_t* __restrict__ ids, const int64_t* __restrict__ lab,
@@ -620,7 +628,7 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     unsigned long long* mx = scratch_t<unsigned long long>(ctx, S_COUNTER, 8);
     if (!mx) return RS_ERR_OOM;
     RS_CUDA(ctx, cudaMemsetAsync(mx, 0, 8, st));
-    k_max_id<<<grid_for(n, kT), kT, 0, st>>>(n, ids, fof_label, mx);
+    k_max_id<<<std::min(grid_for(n, kT), 152u * 8u), kT, 0, st>>>(n, ids, fof_label, mx);
     RS_LAUNCHED(ctx, "k_max_id");
     RS_TRY(read_back(ctx, mx, 8, st));
     const uint64_t maxv = uint64_t(ctx->host_box[0]);

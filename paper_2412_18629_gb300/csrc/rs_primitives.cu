@@ -89,7 +89,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kKeysPerThread = 8;
 constexpr int kTile = kSortThreads * kKeysPerThread;  // 2048
-constexpr int kMaxSortBlocks = 1216;                   // 8 x 152 SMs
+constexpr int kMaxSortBlocks = 4096;                   // bound on the histogram table's rows
 
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t dmask,
@@ -283,8 +283,14 @@ int radix_sort_u64(rs_ctx* ctx, int64_t n, int nbits, uint64_t* keys_a, uint32_t
   *vals_out = vals_a;
   if (n <= 1 || nbits <= 0) return RS_OK;
   if (n >= (int64_t(1) << 32) - 1) return set_error(ctx, RS_ERR_INVALID_ARG, "sort size %lld", (long long)n);
+  if (ctx->sort_blocks == 0) {  // one wave of scatter blocks: every block holds its share of tiles
+    int dev_sms = 0, per_sm = 0;
+    RS_CUDA(ctx, cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    RS_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter, kSortThreads, 0));
+    ctx->sort_blocks = std::max(1, std::min(dev_sms * std::max(per_sm, 1), kMaxSortBlocks));
+  }
   const int64_t ntiles = (n + kTile - 1) / kTile;
-  int64_t blocks = rsd::min64(ntiles, kMaxSortBlocks);
+  int64_t blocks = rsd::min64(ntiles, ctx->sort_blocks);
   const int64_t tpb = (ntiles + blocks - 1) / blocks;
   blocks = (ntiles + tpb - 1) / tpb;
   uint32_t* hist = scratch_t<uint32_t>(ctx, S_SORT_HIST, size_t(kRadix) * (blocks + 1));
