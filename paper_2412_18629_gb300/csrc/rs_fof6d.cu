@@ -25,29 +25,100 @@ constexpr int kTile6 = 128;
 // ---------------------------------------------------------------------------------------------
 // Level 0 from FoF labels.
 
+// out[0] = max id, out[1] = max label (~0 in both when any id or label is negative).
 __global__ void __launch_bounds__(256)
 k_max_id(int64_t n, const int64_t* __restrict__ ids, const int64_t* __restrict__ lab,
          unsigned long long* __restrict__ out) {
-  __shared__ unsigned long long wmax[8];
-  unsigned long long m = 0;
+  __shared__ unsigned long long wmax[2][8];
+  unsigned long long mi = 0, ml = 0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t a = ids[i], b = lab[i];
-    const unsigned long long v =
-        (a < 0 || b < 0) ? ~0ull : (unsigned long long)(a > b ? a : b);  // ~0 flags a negative
-    m = v > m ? v : m;
+    if (a < 0 || b < 0) {
+      mi = ml = ~0ull;
+    } else {
+      mi = (unsigned long long)a > mi ? (unsigned long long)a : mi;
+      ml = (unsigned long long)b > ml ? (unsigned long long)b : ml;
+    }
   }
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
-    const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
-    m = o > m ? o : m;
+    const unsigned long long oi = __shfl_xor_sync(0xffffffffu, mi, off);
+    const unsigned long long ol = __shfl_xor_sync(0xffffffffu, ml, off);
+    mi = oi > mi ? oi : mi;
+    ml = ol > ml ? ol : ml;
   }
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  if ((threadIdx.x & 31) == 0) {
+    wmax[0][threadIdx.x >> 5] = mi;
+    wmax[1][threadIdx.x >> 5] = ml;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {  // one atomic per block
-    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = wmax[w] > m ? wmax[w] : m;
-    atomicMax(out, m);
+  if (threadIdx.x == 0) {  // one atomic per block and value
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) {
+      mi = wmax[0][w] > mi ? wmax[0][w] : mi;
+      ml = wmax[1][w] > ml ? wmax[1][w] : ml;
+    }
+    atomicMax(out, mi);
+    atomicMax(out + 1, ml);
   }
+}
+
+// ---- level 0 over a dense label range (max label < 2 n + 4096): per-label member counts, the
+// kept labels' node indices and member offsets from two scans over the label range, then one
+// sort of the kept particles only, by (node, id).
+__global__ void k_label_count(int64_t n, const int64_t* __restrict__ lab, uint32_t* __restrict__ cnt) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool valid = i < n;  // every lane stays for the warp-aggregated atomics
+  rsd::warp_run_add<uint32_t>(cnt, valid ? uint32_t(lab[i]) : 0u, valid, 1u);
+}
+
+__global__ void k_label_keep(int64_t nl, const uint32_t* __restrict__ cnt, int min_size,
+                             int64_t* __restrict__ knode, int64_t* __restrict__ ksize) {
+  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const bool keep = cnt[l] >= uint32_t(min_size);
+  knode[l] = keep ? 1 : 0;
+  ksize[l] = keep ? int64_t(cnt[l]) : 0;
+}
+
+__global__ void k_label_nodes(int64_t nl, const uint32_t* __restrict__ cnt, int min_size,
+                              const int64_t* __restrict__ knode, const int64_t* __restrict__ koff,
+                              int64_t* __restrict__ node_off, int64_t* __restrict__ node_size,
+                              int64_t* __restrict__ node_parent, int32_t* __restrict__ node_level) {
+  const int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l >= nl || cnt[l] < uint32_t(min_size)) return;
+  const int64_t q = knode[l];
+  node_off[q] = koff[l];
+  node_size[q] = cnt[l];
+  node_parent[q] = -1;
+  node_level[q] = 0;
+}
+
+// Keys (node << bid | id) of the particles of kept groups, appended with one atomic per warp.
+__global__ void k_label_keys(int64_t n, const int64_t* __restrict__ ids, const int64_t* __restrict__ lab,
+                             const uint32_t* __restrict__ cnt, int min_size,
+                             const int64_t* __restrict__ knode, int bid,
+                             unsigned long long* __restrict__ ctr, uint64_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t l = i < n ? lab[i] : 0;
+  const bool keep = i < n && cnt[l] >= uint32_t(min_size);
+  const unsigned b = __ballot_sync(0xffffffffu, keep);
+  unsigned long long base = 0;
+  if (lane == 0 && b) base = atomicAdd(ctr, (unsigned long long)__popc(b));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (!keep) return;
+  const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
+  keys[pos] = (uint64_t(knode[l]) << bid) | uint64_t(ids[i]);
+  vals[pos] = uint32_t(i);
+}
+
+__global__ void k_level0_minid(int64_t nodes, const int64_t* __restrict__ node_off,
+                               const uint32_t* __restrict__ mem, const int64_t* __restrict__ ids,
+                               int64_t* __restrict__ node_minid) {
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q < nodes) node_minid[q] = ids[mem[node_off[q]]];  // members ascend by id
 }
 
 __global__ void k_group_keys(int64_t n, const int64_t* __restrict__ ids, const int64_t* __restrict__ lab,
@@ -625,66 +696,115 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     k_fill_i64<<<grid_for(n, kT), kT, 0, st>>>(n, deep, -1);
     RS_LAUNCHED(ctx, "k_fill_i64");
     if (!deep_pos) return RS_ERR_OOM;
-    unsigned long long* mx = scratch_t<unsigned long long>(ctx, S_COUNTER, 8);
+    unsigned long long* mx = scratch_t<unsigned long long>(ctx, S_COUNTER, 16);
     if (!mx) return RS_ERR_OOM;
-    RS_CUDA(ctx, cudaMemsetAsync(mx, 0, 8, st));
+    RS_CUDA(ctx, cudaMemsetAsync(mx, 0, 16, st));
     k_max_id<<<std::min(grid_for(n, kT), 152u * 8u), kT, 0, st>>>(n, ids, fof_label, mx);
     RS_LAUNCHED(ctx, "k_max_id");
-    RS_TRY(read_back(ctx, mx, 8, st));
-    const uint64_t maxv = uint64_t(ctx->host_box[0]);
-    if (maxv == ~0ull) return set_error(ctx, RS_ERR_INVALID_ARG, "negative id or label");
+    RS_TRY(read_back(ctx, mx, 16, st));
+    const uint64_t max_id = uint64_t(ctx->host_box[0]), max_lab = uint64_t(ctx->host_box[1]);
+    if (max_id == ~0ull) return set_error(ctx, RS_ERR_INVALID_ARG, "negative id or label");
+    const uint64_t maxv = std::max(max_id, max_lab);
     const int b = bits_for(maxv);
     if (2 * b > 64)
       return set_error(ctx, RS_ERR_INVALID_ARG, "ids must be below 2^32 (max %llu)",
                        (unsigned long long)maxv);
-    uint64_t* ka = scratch_t<uint64_t>(ctx, S_KEY_A, n);
-    uint64_t* kb = scratch_t<uint64_t>(ctx, S_KEY_B, n);
-    uint32_t* va = scratch_t<uint32_t>(ctx, S_VAL_A, n);
-    uint32_t* vb = scratch_t<uint32_t>(ctx, S_VAL_B, n);
-    int64_t* head = scratch_t<int64_t>(ctx, S_GKEY_A, size_t(n) + 1);
-    int64_t* run_start = scratch_t<int64_t>(ctx, S_GKEY_B, size_t(n) + 1);
-    int64_t* rsize = scratch_t<int64_t>(ctx, S_GVAL_A, size_t(n) * 2 + 2);
-    int64_t* keep = scratch_t<int64_t>(ctx, S_GVAL_B, size_t(n) * 2 + 2);
-    if (!ka || !kb || !va || !vb || !head || !run_start || !rsize || !keep) return RS_ERR_OOM;
-    int64_t* node_of_run = rsize + n + 1;
-    int64_t* mem_off = keep + n + 1;
-    k_group_keys<<<grid_for(n, kT), kT, 0, st>>>(n, ids, fof_label, b, ka, va);
-    RS_LAUNCHED(ctx, "k_group_keys");
-    uint64_t* keys;
-    uint32_t* vals;
-    RS_TRY(radix_sort_u64(ctx, n, 2 * b, ka, va, kb, vb, &keys, &vals, st));
-    k_run_heads<<<grid_for(n, kT), kT, 0, st>>>(n, keys, b, head);
-    RS_LAUNCHED(ctx, "k_run_heads");
-    RS_TRY(exclusive_scan_i64(ctx, n, head, head + n, st));
-    RS_TRY(read_back(ctx, head + n, 8, st));
-    const int64_t nruns = ctx->host_box[0];
-    k_run_starts<<<grid_for(n, kT), kT, 0, st>>>(n, keys, b, head, run_start);
-    RS_LAUNCHED(ctx, "k_run_starts");
-    k_run_keep<<<grid_for(nruns, kT), kT, 0, st>>>(nruns, n, run_start, min_size, keep, rsize);
-    RS_LAUNCHED(ctx, "k_run_keep");
-    RS_CUDA(ctx, cudaMemcpyAsync(node_of_run, keep, sizeof(int64_t) * nruns,
-                                 cudaMemcpyDeviceToDevice, st));
-    RS_TRY(exclusive_scan_i64(ctx, nruns, node_of_run, node_of_run + nruns, st));
-    k_size_mask<<<grid_for(nruns, kT), kT, 0, st>>>(nruns, keep, rsize, mem_off);
-    RS_LAUNCHED(ctx, "k_size_mask");
-    RS_TRY(exclusive_scan_i64(ctx, nruns, mem_off, mem_off + nruns, st));
-    RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box, node_of_run + nruns, 8, cudaMemcpyDeviceToHost, st));
-    RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box + 1, mem_off + nruns, 8, cudaMemcpyDeviceToHost, st));
-    RS_CUDA(ctx, cudaStreamSynchronize(st));
-    nodes = ctx->host_box[0];
-    members = ctx->host_box[1];
-    RS_TRY(ensure_nodes(ctx, 0, std::max<int64_t>(nodes, 1) * 2, st));
-    RS_TRY(ensure_members(ctx, 0, std::max<int64_t>(members, 1) * 2, st));
-    Hier h = hier_of(ctx);
-    if (nruns > 0) {
-      k_level0_nodes<<<grid_for(nruns, kT), kT, 0, st>>>(nruns, run_start, rsize, keep, node_of_run,
-                                                       mem_off, vals, ids, h.node_off, h.node_size,
-                                                       h.node_parent, h.node_level, h.node_minid);
-      RS_LAUNCHED(ctx, "k_level0_nodes");
-      k_level0_members<<<grid_for(n, kT), kT, 0, st>>>(n, keys, b, head, run_start, keep, mem_off,
-                                                       vals, h.mem);
-      RS_LAUNCHED(ctx, "k_level0_members");
+    if (max_lab < std::min<uint64_t>(uint64_t(2 * n + 4096), uint64_t(1) << 31)) {
+      // dense label range: count per label, keep, scan, sort the kept particles only
+      const int64_t nl = int64_t(max_lab) + 1;
+      const int bid = bits_for(max_id);
+      uint32_t* cntl = scratch_t<uint32_t>(ctx, S_ROOT_CNT, size_t(nl));
+      int64_t* knode = scratch_t<int64_t>(ctx, S_GKEY_A, size_t(nl) + 1);
+      int64_t* koff = scratch_t<int64_t>(ctx, S_GKEY_B, size_t(nl) + 1);
+      if (!cntl || !knode || !koff) return RS_ERR_OOM;
+      RS_CUDA(ctx, cudaMemsetAsync(cntl, 0, sizeof(uint32_t) * nl, st));
+      k_label_count<<<grid_for(n, kT), kT, 0, st>>>(n, fof_label, cntl);
+      RS_LAUNCHED(ctx, "k_label_count");
+      k_label_keep<<<grid_for(nl, kT), kT, 0, st>>>(nl, cntl, min_size, knode, koff);
+      RS_LAUNCHED(ctx, "k_label_keep");
+      RS_TRY(exclusive_scan_i64(ctx, nl, knode, knode + nl, st));
+      RS_TRY(exclusive_scan_i64(ctx, nl, koff, koff + nl, st));
+      RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box, knode + nl, 8, cudaMemcpyDeviceToHost, st));
+      RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box + 1, koff + nl, 8, cudaMemcpyDeviceToHost, st));
+      RS_CUDA(ctx, cudaStreamSynchronize(st));
+      nodes = ctx->host_box[0];
+      members = ctx->host_box[1];
+      RS_TRY(ensure_nodes(ctx, 0, std::max<int64_t>(nodes, 1) * 2, st));
+      RS_TRY(ensure_members(ctx, 0, std::max<int64_t>(members, 1) * 2, st));
+      Hier h = hier_of(ctx);
+      if (members > 0) {
+        uint64_t* ka = scratch_t<uint64_t>(ctx, S_KEY_A, size_t(members));
+        uint64_t* kb = scratch_t<uint64_t>(ctx, S_KEY_B, size_t(members));
+        uint32_t* va = scratch_t<uint32_t>(ctx, S_VAL_A, size_t(members));
+        uint32_t* vb = scratch_t<uint32_t>(ctx, S_VAL_B, size_t(members));
+        if (!ka || !kb || !va || !vb) return RS_ERR_OOM;
+        k_label_nodes<<<grid_for(nl, kT), kT, 0, st>>>(nl, cntl, min_size, knode, koff, h.node_off,
+                                                      h.node_size, h.node_parent, h.node_level);
+        RS_LAUNCHED(ctx, "k_label_nodes");
+        RS_CUDA(ctx, cudaMemsetAsync(mx, 0, 8, st));
+        k_label_keys<<<grid_for(n, kT), kT, 0, st>>>(n, ids, fof_label, cntl, min_size, knode, bid,
+                                                    mx, ka, va);
+        RS_LAUNCHED(ctx, "k_label_keys");
+        uint64_t* keys;
+        uint32_t* vals;
+        RS_TRY(radix_sort_u64(ctx, members, bits_for(uint64_t(std::max<int64_t>(nodes - 1, 1))) + bid,
+                              ka, va, kb, vb, &keys, &vals, st));
+        k_copy_u32<<<grid_for(members, kT), kT, 0, st>>>(members, vals, h.mem);
+        RS_LAUNCHED(ctx, "k_copy_u32");
+        k_level0_minid<<<grid_for(nodes, kT), kT, 0, st>>>(nodes, h.node_off, h.mem, ids, h.node_minid);
+        RS_LAUNCHED(ctx, "k_level0_minid");
+      }
+    } else {
+      uint64_t* ka = scratch_t<uint64_t>(ctx, S_KEY_A, n);
+      uint64_t* kb = scratch_t<uint64_t>(ctx, S_KEY_B, n);
+      uint32_t* va = scratch_t<uint32_t>(ctx, S_VAL_A, n);
+      uint32_t* vb = scratch_t<uint32_t>(ctx, S_VAL_B, n);
+      int64_t* head = scratch_t<int64_t>(ctx, S_GKEY_A, size_t(n) + 1);
+      int64_t* run_start = scratch_t<int64_t>(ctx, S_GKEY_B, size_t(n) + 1);
+      int64_t* rsize = scratch_t<int64_t>(ctx, S_GVAL_A, size_t(n) * 2 + 2);
+      int64_t* keep = scratch_t<int64_t>(ctx, S_GVAL_B, size_t(n) * 2 + 2);
+      if (!ka || !kb || !va || !vb || !head || !run_start || !rsize || !keep) return RS_ERR_OOM;
+      int64_t* node_of_run = rsize + n + 1;
+      int64_t* mem_off = keep + n + 1;
+      k_group_keys<<<grid_for(n, kT), kT, 0, st>>>(n, ids, fof_label, b, ka, va);
+      RS_LAUNCHED(ctx, "k_group_keys");
+      uint64_t* keys;
+      uint32_t* vals;
+      RS_TRY(radix_sort_u64(ctx, n, 2 * b, ka, va, kb, vb, &keys, &vals, st));
+      k_run_heads<<<grid_for(n, kT), kT, 0, st>>>(n, keys, b, head);
+      RS_LAUNCHED(ctx, "k_run_heads");
+      RS_TRY(exclusive_scan_i64(ctx, n, head, head + n, st));
+      RS_TRY(read_back(ctx, head + n, 8, st));
+      const int64_t nruns = ctx->host_box[0];
+      k_run_starts<<<grid_for(n, kT), kT, 0, st>>>(n, keys, b, head, run_start);
+      RS_LAUNCHED(ctx, "k_run_starts");
+      k_run_keep<<<grid_for(nruns, kT), kT, 0, st>>>(nruns, n, run_start, min_size, keep, rsize);
+      RS_LAUNCHED(ctx, "k_run_keep");
+      RS_CUDA(ctx, cudaMemcpyAsync(node_of_run, keep, sizeof(int64_t) * nruns,
+                                   cudaMemcpyDeviceToDevice, st));
+      RS_TRY(exclusive_scan_i64(ctx, nruns, node_of_run, node_of_run + nruns, st));
+      k_size_mask<<<grid_for(nruns, kT), kT, 0, st>>>(nruns, keep, rsize, mem_off);
+      RS_LAUNCHED(ctx, "k_size_mask");
+      RS_TRY(exclusive_scan_i64(ctx, nruns, mem_off, mem_off + nruns, st));
+      RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box, node_of_run + nruns, 8, cudaMemcpyDeviceToHost, st));
+      RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box + 1, mem_off + nruns, 8, cudaMemcpyDeviceToHost, st));
+      RS_CUDA(ctx, cudaStreamSynchronize(st));
+      nodes = ctx->host_box[0];
+      members = ctx->host_box[1];
+      RS_TRY(ensure_nodes(ctx, 0, std::max<int64_t>(nodes, 1) * 2, st));
+      RS_TRY(ensure_members(ctx, 0, std::max<int64_t>(members, 1) * 2, st));
+      Hier h = hier_of(ctx);
+      if (nruns > 0) {
+        k_level0_nodes<<<grid_for(nruns, kT), kT, 0, st>>>(nruns, run_start, rsize, keep, node_of_run,
+                                                         mem_off, vals, ids, h.node_off, h.node_size,
+                                                         h.node_parent, h.node_level, h.node_minid);
+        RS_LAUNCHED(ctx, "k_level0_nodes");
+        k_level0_members<<<grid_for(n, kT), kT, 0, st>>>(n, keys, b, head, run_start, keep, mem_off,
+                                                         vals, h.mem);
+        RS_LAUNCHED(ctx, "k_level0_members");
+      }
     }
+    Hier h = hier_of(ctx);
     k_fill_i64<<<1, 1, 0, st>>>(1, h.node_off + nodes, members);
     RS_LAUNCHED(ctx, "k_fill_i64");
   }

@@ -86,3 +86,19 @@ def test_work_counting_variant_gives_the_same_hierarchy():
     sizes = got["size"].astype(np.float64)
     assert 0 < w["nn_d6"] < (sizes * (sizes - 1)).sum()
     assert w["nn_box"] > 0 and w["link_d6"] > 0 and w["link_box"] > 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_sparse_ids_give_the_same_hierarchy(mode):
+    """Level 0 groups particles by a count per label when the labels are dense (at most about
+    2 n) and by a sort of (label, id) keys otherwise; ids spread up to ~2^31 take the second
+    path, and the hierarchy must still equal the oracle's."""
+    s = small_snapshot(1 << 15, 32.0, 22, n_max=4000)
+    rng = np.random.default_rng(7)
+    s = dict(s)
+    s["ids"] = (rng.permutation(len(s["ids"])).astype(np.int64) * 65521 + 977).astype(np.int64)
+    g = gpu_pipeline(s, stages=("fof3d", "fof6d"), mode=mode)
+    lab = oracle.fof3d(s["pos"], s["ids"], s["box"], s["link_length"])
+    assert np.array_equal(g["labels"], lab)
+    assert lab.max() > 4 * len(lab)
+    assert_hier_equal(g["hier"], oracle.hierarchy(s["pos"], s["vel"], s["ids"], lab, s["box"]))
