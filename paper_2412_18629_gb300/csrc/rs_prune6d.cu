@@ -1,7 +1,7 @@
 // Pruned 6D nearest-neighbour and link searches for the batched form of rs_fof6d.
 //
 // The plain form evaluates d6 for every pair of a node. Here the members of every node of a
-// level are ordered by a 3D Morton key of their scaled position offsets (every candidate of a
+// level are ordered by a 3D Hilbert key of their scaled position offsets (every candidate of a
 // 6D search lies within sqrt(bound / inv_sx2) in position) and cut into buckets of 32
 // consecutive members; each bucket has a 6D bounding box, four 8-member sub-boxes, and every
 // 32 consecutive buckets of a node form a superbucket with its own box. Persistent warps pull
@@ -70,9 +70,39 @@ __device__ __forceinline__ uint32_t quant10(float c) {
   return uint32_t(t);
 }
 
-// 3D Morton key of each member's position offset from the node mean (scaled by the node's
+// 3D Hilbert index (10 bits per axis) of quantised coordinates, by Skilling's transform of the
+// axes into the transposed Hilbert index (J. Skilling, "Programming the Hilbert curve", AIP
+// Conf. Proc. 707, 2004): consecutive indices are face-adjacent cells, so runs of the curve
+// are more compact than runs of the Morton order (no long jumps between octants).
+__device__ __forceinline__ uint32_t hilbert3_10(uint32_t x0, uint32_t x1, uint32_t x2) {
+  uint32_t X[3] = {x0, x1, x2};
+  for (uint32_t q = 1u << 9; q > 1; q >>= 1) {
+    const uint32_t p = q - 1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (X[i] & q) {
+        X[0] ^= p;  // invert the low bits of axis 0
+      } else {      // exchange the low bits of axes 0 and i
+        const uint32_t t = (X[0] ^ X[i]) & p;
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  X[1] ^= X[0];  // Gray encode
+  X[2] ^= X[1];
+  uint32_t t = 0;
+  for (uint32_t q = 1u << 9; q > 1; q >>= 1)
+    if (X[2] & q) t ^= q - 1;
+  X[0] ^= t;
+  X[1] ^= t;
+  X[2] ^= t;
+  return spread10(X[2]) | (spread10(X[1]) << 1) | (spread10(X[0]) << 2);  // axis 0 leads
+}
+
+// 3D Hilbert key of each member's position offset from the node mean (scaled by the node's
 // sigma_x), prefixed by the node index.
-__global__ void k_morton3(int64_t mb, int64_t m, int64_t nb, const uint32_t* __restrict__ mnode,
+__global__ void k_hilbert3(int64_t mb, int64_t m, int64_t nb, const uint32_t* __restrict__ mnode,
                           const float4* __restrict__ U, const float4* __restrict__ inv,
                           const float4* __restrict__ mean_u, uint64_t* __restrict__ keys,
                           uint32_t* __restrict__ vals) {
@@ -81,9 +111,8 @@ __global__ void k_morton3(int64_t mb, int64_t m, int64_t nb, const uint32_t* __r
   const uint32_t q = mnode[mb + p];
   const float sx = sqrtf(inv[q].x);
   const float4 u = U[mb + p], mu = mean_u[q];
-  const uint32_t code = spread10(quant10((u.x - mu.x) * sx)) |
-                        (spread10(quant10((u.y - mu.y) * sx)) << 1) |
-                        (spread10(quant10((u.z - mu.z) * sx)) << 2);
+  const uint32_t code = hilbert3_10(quant10((u.x - mu.x) * sx), quant10((u.y - mu.y) * sx),
+                                    quant10((u.z - mu.z) * sx));
   keys[p] = (uint64_t(q - nb) << 30) | uint64_t(code);
   vals[p] = uint32_t(p);
 }
@@ -684,8 +713,8 @@ int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t
   if (!mean_u || !ka || !kb || !va || !vb || !Us || !Vs || !sp || !nstart || !ncnt || !qctr) return RS_ERR_OOM;
   k_node_means<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, sums, mean_u);
   RS_LAUNCHED(ctx, "k_node_means");
-  k_morton3<<<grid_for(m, kT), kT, 0, st>>>(mb, m, nb, h.mnode, h.U, h.inv, mean_u, ka, va);
-  RS_LAUNCHED(ctx, "k_morton3");
+  k_hilbert3<<<grid_for(m, kT), kT, 0, st>>>(mb, m, nb, h.mnode, h.U, h.inv, mean_u, ka, va);
+  RS_LAUNCHED(ctx, "k_hilbert3");
   uint64_t* keys;
   uint32_t* order;
   RS_TRY(radix_sort_u64(ctx, m, 30 + bits_for(uint64_t(nn)), ka, va, kb, vb, &keys, &order, st));
