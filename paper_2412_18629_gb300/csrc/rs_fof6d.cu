@@ -487,10 +487,11 @@ k_link6d(int64_t nb, int64_t nn, const int64_t* __restrict__ tile_off, const int
 // Roots (full compression) and component sizes.
 __global__ void k_comp_count(int64_t m, uint32_t* __restrict__ uf, uint32_t* __restrict__ cnt) {
   const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= m) return;
-  const uint32_t r = rsd::uf_find_ro(uf, uint32_t(p));
-  uf[p] = r;
-  atomicAdd(cnt + r, 1u);
+  const bool valid = p < m;  // every lane stays: lanes with the same root add once
+  const uint32_t r = valid ? rsd::uf_find_ro(uf, uint32_t(p)) : 0xffffffffu;
+  if (valid) uf[p] = r;
+  const unsigned peers = __match_any_sync(0xffffffffu, r);
+  if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + r, uint32_t(__popc(peers)));
 }
 
 // child flag at each root that forms a child (>= min and < its node's size).
@@ -558,11 +559,14 @@ __global__ void k_offsets_add(int64_t n, const int64_t* __restrict__ src, int64_
 }
 
 // Deepest node per particle and the particle's member position in that node.
+// Deepest node per particle and the particle's member position in that node, written once:
+// at the level where the member does not go on into a child (its root is not a child root).
 __global__ void k_deepest(int64_t mb, int64_t me, const uint32_t* __restrict__ mem,
-                          const uint32_t* __restrict__ mnode, int64_t* __restrict__ deepest,
+                          const uint32_t* __restrict__ mnode, const uint32_t* __restrict__ uf,
+                          const int64_t* __restrict__ cflag, int64_t* __restrict__ deepest,
                           uint32_t* __restrict__ deepest_pos) {
   const int64_t p = mb + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p < me) {
+  if (p < me && !cflag[uf[p - mb]]) {
     deepest[mem[p]] = mnode[p];
     deepest_pos[mem[p]] = uint32_t(p);
   }
@@ -879,7 +883,7 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     k_member_flags<<<grid_for(m, kT), kT, 0, st>>>(m, uf, cflag, mpos);
     RS_LAUNCHED(ctx, "k_member_flags");
     RS_TRY(exclusive_scan_i64(ctx, m, mpos, mpos + m, st));
-    k_deepest<<<grid_for(m, kT), kT, 0, st>>>(mb, me, h.mem, h.mnode, deep, deep_pos);
+    k_deepest<<<grid_for(m, kT), kT, 0, st>>>(mb, me, h.mem, h.mnode, uf, cflag, deep, deep_pos);
     RS_LAUNCHED(ctx, "k_deepest");
     RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box, cidx + m, 8, cudaMemcpyDeviceToHost, st));
     RS_CUDA(ctx, cudaMemcpyAsync(ctx->host_box + 1, mpos + m, 8, cudaMemcpyDeviceToHost, st));
