@@ -305,10 +305,10 @@ def _stages(r, steps):
 
 
 TRAIN_SAMPLES = 1_000_000
-TRAIN_EPOCHS = 30
+TRAIN_EPOCHS = 300
 
 
-def train_surrogate(ctx, workload, device, samples=None):
+def train_surrogate(ctx, workload, device, samples=None, epochs=None):
     """Train the context's surrogate on the GPU, outside any timed region: exact potentials of
     a snapshot drawn with the same generator and a disjoint seed (100), 10% held out."""
     import dataclasses
@@ -330,12 +330,13 @@ def train_surrogate(ctx, workload, device, samples=None):
     x, t = x[sel].contiguous(), t[sel].contiguous()
     t0 = time.perf_counter()
     rs.rs_mlp_set_params(tctx, np.zeros(rs.MLP_PARAMS, np.float32))
-    err_max, mse = rs.rs_mlp_train(tctx, x, t, epochs=TRAIN_EPOCHS, batch=4096, lr=1e-3, seed=100)
+    epochs = epochs or TRAIN_EPOCHS
+    err_max, mse = rs.rs_mlp_train(tctx, x, t, epochs=epochs, batch=4096, lr=1e-3, seed=100)
     dt = time.perf_counter() - t0
     rs.rs_mlp_set_params(ctx, rs.rs_mlp_get_params(tctx))
     rs.rs_mlp_set_err_max(ctx, err_max)
     tctx.close()
-    return {"samples": int(k), "epochs": TRAIN_EPOCHS, "err_max_psi": err_max, "last_batch_mse": mse,
+    return {"samples": int(k), "epochs": epochs, "err_max_psi": err_max, "last_batch_mse": mse,
             "train_s": dt,
             "snapshot": f"{workload} generator, seed 100"}
 
@@ -360,7 +361,8 @@ def run_ours(args):
                                 softening=snap["softening"], particle_mass=snap["particle_mass"],
                                 device=local, mode=form)
         if form == "surrogate":
-            training = train_surrogate(ctxs[form], args.workload, local, args.train_samples)
+            training = train_surrogate(ctxs[form], args.workload, local, args.train_samples,
+                                       args.train_epochs)
         res[form] = _measure(ctxs[form], pos, vel, ids, n, args, ws, local)
         if form == "surrogate":
             res[form]["surrogate_stats"] = rs.rs_surrogate_stats(ctxs[form])
@@ -472,6 +474,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", choices=("plain", "batched", "surrogate", "all"), default="all")
     ap.add_argument("--train-samples", type=int, default=1_000_000)
+    ap.add_argument("--train-epochs", type=int, default=TRAIN_EPOCHS)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
