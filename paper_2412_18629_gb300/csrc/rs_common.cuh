@@ -275,6 +275,26 @@ __device__ __forceinline__ double f2d(float f) {
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// Exact float64 square of a float32 value on the integer pipe. A float is m 2^(e-150) (m the
+// 24-bit significand with its leading bit, or the subnormal significand with e = 1), so its
+// square is the 48-bit integer m^2 times 2^(2e-300): exactly representable in float64, hence
+// equal to the rounded FP64 product f2d(f) * f2d(f); the bits are assembled from m^2's leading
+// bit position. Zero, infinite and NaN values take the FP64 multiply.
+__device__ __forceinline__ double sq_f2d(float f) {
+  const uint32_t b = __float_as_uint(f) & 0x7fffffffu;
+  uint32_t e = b >> 23, m = b & 0x7fffffu;
+  if (b == 0u || e == 0xffu) {
+    const double d = double(f);
+    return __dmul_rn(d, d);
+  }
+  if (e == 0u) e = 1u; else m |= 0x800000u;
+  const uint64_t mm = uint64_t(m) * uint64_t(m);
+  const int top = 63 - __clzll(static_cast<long long>(mm));
+  const uint64_t frac = (mm << (52 - top)) & ((uint64_t(1) << 52) - 1u);
+  const uint64_t ebits = uint64_t(int64_t(2) * (int64_t(e) - 150) + top + 1023);
+  return __longlong_as_double(static_cast<long long>((ebits << 52) | frac));
+}
+
 // Warp-aggregated atomics for keys laid out in runs (members in node order, particles in cell
 // order): every lane of the warp calls these; a lane with `valid` false contributes nothing and
 // ends a run. Each contiguous run of valid lanes with equal keys gets an id (the number of run

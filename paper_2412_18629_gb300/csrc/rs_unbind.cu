@@ -372,12 +372,13 @@ struct PropTerm1 {  // bound-masked u, u^2, v, v^2
     const float4 u = U[p], v = V[p];
     const double a[3] = {rsd::f2d(u.x), rsd::f2d(u.y), rsd::f2d(u.z)};
     const double b[3] = {rsd::f2d(v.x), rsd::f2d(v.y), rsd::f2d(v.z)};
+    const float uc[3] = {u.x, u.y, u.z}, vc[3] = {v.x, v.y, v.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       acc[d] = __dadd_rn(acc[d], a[d]);
-      acc[3 + d] = __dadd_rn(acc[3 + d], __dmul_rn(a[d], a[d]));
+      acc[3 + d] = __dadd_rn(acc[3 + d], rsd::sq_f2d(uc[d]));  // == a[d] * a[d], exactly
       acc[6 + d] = __dadd_rn(acc[6 + d], b[d]);
-      acc[9 + d] = __dadd_rn(acc[9 + d], __dmul_rn(b[d], b[d]));
+      acc[9 + d] = __dadd_rn(acc[9 + d], rsd::sq_f2d(vc[d]));
     }
   }
 };
