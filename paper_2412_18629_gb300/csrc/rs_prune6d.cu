@@ -63,20 +63,20 @@ __device__ __forceinline__ uint32_t spread10(uint32_t x) {
   return x;
 }
 
-__device__ __forceinline__ uint32_t quant10(float c) {
-  // scaled offset (in units of the node's total position sigma) in [-4, 4) -> 0..1023
-  float t = (c + 4.0f) * 128.0f;
-  t = fminf(fmaxf(t, 0.0f), 1023.0f);
+__device__ __forceinline__ uint32_t quant8(float c) {
+  // scaled offset (in units of the node's total position sigma) in [-4, 4) -> 0..255
+  float t = (c + 4.0f) * 32.0f;
+  t = fminf(fmaxf(t, 0.0f), 255.0f);
   return uint32_t(t);
 }
 
-// 3D Hilbert index (10 bits per axis) of quantised coordinates, by Skilling's transform of the
+// 3D Hilbert index (8 bits per axis) of quantised coordinates, by Skilling's transform of the
 // axes into the transposed Hilbert index (J. Skilling, "Programming the Hilbert curve", AIP
 // Conf. Proc. 707, 2004): consecutive indices are face-adjacent cells, so runs of the curve
 // are more compact than runs of the Morton order (no long jumps between octants).
-__device__ __forceinline__ uint32_t hilbert3_10(uint32_t x0, uint32_t x1, uint32_t x2) {
+__device__ __forceinline__ uint32_t hilbert3_8(uint32_t x0, uint32_t x1, uint32_t x2) {
   uint32_t X[3] = {x0, x1, x2};
-  for (uint32_t q = 1u << 9; q > 1; q >>= 1) {
+  for (uint32_t q = 1u << 7; q > 1; q >>= 1) {
     const uint32_t p = q - 1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -92,7 +92,7 @@ __device__ __forceinline__ uint32_t hilbert3_10(uint32_t x0, uint32_t x1, uint32
   X[1] ^= X[0];  // Gray encode
   X[2] ^= X[1];
   uint32_t t = 0;
-  for (uint32_t q = 1u << 9; q > 1; q >>= 1)
+  for (uint32_t q = 1u << 7; q > 1; q >>= 1)
     if (X[2] & q) t ^= q - 1;
   X[0] ^= t;
   X[1] ^= t;
@@ -111,9 +111,9 @@ __global__ void k_hilbert3(int64_t mb, int64_t m, int64_t nb, const uint32_t* __
   const uint32_t q = mnode[mb + p];
   const float sx = sqrtf(inv[q].x);
   const float4 u = U[mb + p], mu = mean_u[q];
-  const uint32_t code = hilbert3_10(quant10((u.x - mu.x) * sx), quant10((u.y - mu.y) * sx),
-                                    quant10((u.z - mu.z) * sx));
-  keys[p] = (uint64_t(q - nb) << 30) | uint64_t(code);
+  const uint32_t code = hilbert3_8(quant8((u.x - mu.x) * sx), quant8((u.y - mu.y) * sx),
+                                   quant8((u.z - mu.z) * sx));
+  keys[p] = (uint64_t(q - nb) << 24) | uint64_t(code);
   vals[p] = uint32_t(p);
 }
 
@@ -717,7 +717,7 @@ int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t
   RS_LAUNCHED(ctx, "k_hilbert3");
   uint64_t* keys;
   uint32_t* order;
-  RS_TRY(radix_sort_u64(ctx, m, 30 + bits_for(uint64_t(nn)), ka, va, kb, vb, &keys, &order, st));
+  RS_TRY(radix_sort_u64(ctx, m, 24 + bits_for(uint64_t(nn)), ka, va, kb, vb, &keys, &order, st));
   k_gather_sorted<<<grid_for(m, kT), kT, 0, st>>>(mb, m, order, h.U, h.V, Us, Vs, sp);
   RS_LAUNCHED(ctx, "k_gather_sorted");
   k_node_ranges<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, mb, h.node_off, h.node_size, nstart, ncnt);
