@@ -1,9 +1,10 @@
 // Unbinding and halo properties over every node of the 6D hierarchy.
 //
 // Potential: phi_i = -G m sum_{j != i} (|u_j - u_i|^2 + eps^2)^(-1/2) over the node's members.
-//   k_potential   float32 direct sum: block = (node, i-tile of 256), j-tiles of 256 float4 in
-//                 shared memory, FMA + rsqrt per pair, 32-term blocks added with Kahan
-//                 compensation. Certified relative error bound B (see kCertB).
+//   k_potential   float32 direct sum for nodes up to 384 members: one thread per member, the
+//                 node's members read through L1; larger nodes by the register-blocked kernel.
+//                 FMA + rsqrt per pair, 32-term blocks added with Kahan compensation.
+//                 Certified relative error bound B (see kCertB).
 //   k_flags       float64 kinetic energy against the node's bulk velocity (canonical-order sum),
 //                 E = KE + phi~. |E| > 2 B |phi~| decides the flag; otherwise the member is queued
 //                 for the exact float64 potential.
@@ -48,46 +49,40 @@ __global__ void k_tiles(int64_t nn, const int64_t* __restrict__ node_size, int t
   if (k < nn) out[k] = (node_size[k] + tile - 1) / tile;
 }
 
-__global__ void __launch_bounds__(kPotTile)
-k_potential(int64_t nn, const int64_t* __restrict__ tile_off, const int64_t* __restrict__ node_off,
-            const int64_t* __restrict__ node_size, const float4* __restrict__ U, float eps2,
-            float* __restrict__ S_out) {
-  __shared__ float4 su[kPotTile];
-  const int64_t b = blockIdx.x;
-  if (b >= tile_off[nn]) return;
-  const int64_t q = rsd::upper_bound_i64(tile_off, nn, b) - 1;
-  const int64_t t = b - tile_off[q];
+// Nodes up to kBlockedMin members: one thread per member over the flat member list (lanes of
+// a warp are consecutive members, mostly of one node), the node's members read through L1 in
+// ascending order; the same 32-term blocks and Kahan steps as the blocked kernel. A node is
+// selected when its tile count (scanned) is non-zero.
+__global__ void __launch_bounds__(kT)
+k_potential(int64_t m, const uint32_t* __restrict__ mnode, const int64_t* __restrict__ tile_off,
+            const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
+            const float4* __restrict__ U, float eps2, float* __restrict__ S_out) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  const uint32_t q = mnode[p];
+  if (tile_off[q + 1] == tile_off[q]) return;  // not selected for this kernel
   const int64_t base = node_off[q], g = node_size[q];
-  const int64_t i = t * kPotTile + threadIdx.x;
-  const bool valid = i < g;
-  const float4 ui = valid ? U[base + i] : make_float4(0, 0, 0, 0);
+  const int64_t self = p - base;
+  const float4 ui = U[p];
   float S = 0.f, C = 0.f;
-  for (int64_t j0 = 0; j0 < g; j0 += kPotTile) {
-    const int64_t j = j0 + threadIdx.x;
-    if (j < g) su[threadIdx.x] = U[base + j];
-    __syncthreads();
-    const int jn = int(rsd::min64(kPotTile, g - j0));
-    const int self = int(i - j0);  // in [0, jn) only on the diagonal tile
-    for (int jb = 0; jb < jn; jb += 32) {
-      const int je = min(jb + 32, jn);
-      float blk = 0.f;
-      for (int jj = jb; jj < je; ++jj) {
-        const float4 uj = su[jj];
-        const float dx = __fsub_rn(uj.x, ui.x);
-        const float dy = __fsub_rn(uj.y, ui.y);
-        const float dz = __fsub_rn(uj.z, ui.z);
-        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2)));
-        const float w = rsqrtf(r2);
-        blk = __fadd_rn(blk, jj == self ? 0.f : w);
-      }
-      const float y = __fsub_rn(blk, C);
-      const float tt = __fadd_rn(S, y);
-      C = __fsub_rn(__fsub_rn(tt, S), y);
-      S = tt;
+  for (int64_t jb = 0; jb < g; jb += 32) {
+    const int64_t je = rsd::min64(jb + 32, g);
+    float blk = 0.f;
+    for (int64_t jj = jb; jj < je; ++jj) {
+      const float4 uj = __ldg(U + base + jj);
+      const float dx = __fsub_rn(uj.x, ui.x);
+      const float dy = __fsub_rn(uj.y, ui.y);
+      const float dz = __fsub_rn(uj.z, ui.z);
+      const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2)));
+      const float w = rsqrtf(r2);
+      blk = __fadd_rn(blk, jj == self ? 0.f : w);
     }
-    __syncthreads();
+    const float y = __fsub_rn(blk, C);
+    const float tt = __fadd_rn(S, y);
+    C = __fsub_rn(__fsub_rn(tt, S), y);
+    S = tt;
   }
-  if (valid) S_out[base + i] = S;
+  S_out[p] = S;
 }
 
 // Register-blocked variant for nodes larger than kBlockedMin: each of the 128 threads of a
@@ -546,11 +541,10 @@ int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, float* S, cu
   }
   const int R = ctx->tune_blk_r ? ctx->tune_blk_r : 4;
   RS_TRY(potential_tiles(ctx, sur_min, only, R, tile_small, tile_perm, &perm, st));
-  const int64_t tiles_ub = nn + m / kPotTile + 1;
   {
     ProfScope prof_(ctx, "k_potential", st);
-    k_potential<<<grid_for(tiles_ub, 1), kPotTile, 0, st>>>(nn, tile_small, h.node_off, h.node_size, h.U,
-                                                           eps * eps, S);
+    k_potential<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, tile_small, h.node_off, h.node_size, h.U,
+                                               eps * eps, S);
   }
   RS_LAUNCHED(ctx, "k_potential");
   {
