@@ -124,8 +124,9 @@ extern "C" int64_t rs_kernel_launches(rs_ctx* ctx) { return ctx ? ctx->launches 
 namespace {
 struct ArrayTerm {
   const double* a;
+  template <bool kFirst>
   __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
-    acc[0] = __dadd_rn(acc[0], a[p]);
+    rsd::cro_add<kFirst>(acc[0], a[p]);
   }
 };
 

@@ -347,11 +347,24 @@ __device__ __forceinline__ void warp_count(unsigned long long* ctr, bool pred) {
 
 // Canonical-order combination of the 32 lane partial sums of a warp: halving tree
 // s[l] += s[l + off], off = 16 .. 1, realised as an xor butterfly (IEEE + commutes, so lane
-// 0 ends with exactly the halving-tree value).
-__device__ __forceinline__ double warp_cro_combine(double s) {
+// 0 ends with exactly the halving-tree value). When only lanes below 2 off0 hold terms (the
+// others hold 0.0 and no lane sum is -0.0), the steps above off0 add 0.0 to every sum they
+// touch, so starting at off0 gives lane 0 the same value.
+__device__ __forceinline__ double warp_cro_combine(double s, int off0 = 16) {
 #pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off));
+  for (int off = off0; off >= 1; off >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off));
   return s;
+}
+
+// acc <- acc + v in a canonical-order lane sum. The first add of a lane (acc = 0.0) is formed
+// without the FP64 pipe: 0.0 + v is v, except that -0.0 becomes +0.0 (so a lane sum is never
+// -0.0, and adding a lane that holds 0.0 leaves any lane sum unchanged).
+template <bool kFirst>
+__device__ __forceinline__ void cro_add(double& acc, double v) {
+  if (kFirst)
+    acc = (__double_as_longlong(v) << 1) == 0 ? 0.0 : v;
+  else
+    acc = __dadd_rn(acc, v);
 }
 
 }  // namespace rsd

@@ -47,8 +47,9 @@ __device__ __forceinline__ int64_t upper_bound_i64(const int64_t* a, int64_t n, 
   return lo;
 }
 
-// One warp per chunk of 1024 terms of one segment. Term::add(q, p, idx, acc) adds the NS terms
-// of element p (global member position; idx = position inside the segment) of segment q.
+// One warp per chunk of 1024 terms of one segment. Term::add<first>(q, p, idx, acc) adds the NS
+// terms of element p (global member position; idx = position inside the segment) of segment q
+// (first: the lane's first term, added to 0.0 by rsd::cro_add<true>).
 // chunk_off has nseg + 1 entries (the last one is the total number of chunks).
 template <int NS, class Term>
 __global__ void __launch_bounds__(256)
@@ -62,15 +63,24 @@ k_cro_chunks(int64_t nseg, const int64_t* __restrict__ chunk_off,
   const int64_t cc = w - chunk_off[q];
   const int64_t base = seg_off[q], g = seg_size[q];
   double acc[NS];
+  const int64_t i0 = cc * 1024 + lane;
+  if (i0 < g) {
+    term.template add<true>(q, base + i0, i0, acc);
+  } else {
 #pragma unroll
-  for (int s = 0; s < NS; ++s) acc[s] = 0.0;
-  for (int k = 0; k < 32; ++k) {
-    const int64_t idx = cc * 1024 + lane + 32 * k;
-    if (idx < g) term.add(q, base + idx, idx, acc);
+    for (int s = 0; s < NS; ++s) acc[s] = 0.0;
   }
+  for (int k = 1; k < 32; ++k) {
+    const int64_t idx = i0 + 32 * k;
+    if (idx < g) term.template add<false>(q, base + idx, idx, acc);
+  }
+  const int64_t cs = g - cc * 1024;  // terms in this chunk (lanes at or above cs hold 0.0)
+  int off0 = 16;
+  while (off0 > 1 && cs <= off0) off0 >>= 1;
+  if (cs <= 1) off0 = 0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    const double v = warp_cro_combine(acc[s]);
+    const double v = warp_cro_combine(acc[s], off0);
     if (lane == 0) out[w * NS + s] = v;
   }
 }

@@ -243,6 +243,7 @@ __global__ void k_node_ref(int64_t nb, int64_t ne, const uint32_t* __restrict__ 
 struct MomentTerm {
   const float4* U;
   const float4* V;
+  template <bool kFirst>
   __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
     const float4 u = U[p], v = V[p];
     const double a[3] = {rsd::f2d(u.x), rsd::f2d(u.y), rsd::f2d(u.z)};
@@ -250,10 +251,10 @@ struct MomentTerm {
     const float uc[3] = {u.x, u.y, u.z}, vc[3] = {v.x, v.y, v.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      acc[d] = __dadd_rn(acc[d], a[d]);
-      acc[3 + d] = __dadd_rn(acc[3 + d], rsd::sq_f2d(uc[d]));  // == a[d] * a[d], exactly
-      acc[6 + d] = __dadd_rn(acc[6 + d], b[d]);
-      acc[9 + d] = __dadd_rn(acc[9 + d], rsd::sq_f2d(vc[d]));
+      rsd::cro_add<kFirst>(acc[d], a[d]);
+      rsd::cro_add<kFirst>(acc[3 + d], rsd::sq_f2d(uc[d]));  // == a[d] * a[d], exactly
+      rsd::cro_add<kFirst>(acc[6 + d], b[d]);
+      rsd::cro_add<kFirst>(acc[9 + d], rsd::sq_f2d(vc[d]));
     }
   }
 };

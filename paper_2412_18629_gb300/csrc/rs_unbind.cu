@@ -226,11 +226,12 @@ k_potential_blocked(int64_t nn, const int64_t* __restrict__ tile_off, const uint
 
 struct VelTerm {
   const float4* V;
+  template <bool kFirst>
   __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
     const float4 v = V[p];
-    acc[0] = __dadd_rn(acc[0], rsd::f2d(v.x));
-    acc[1] = __dadd_rn(acc[1], rsd::f2d(v.y));
-    acc[2] = __dadd_rn(acc[2], rsd::f2d(v.z));
+    rsd::cro_add<kFirst>(acc[0], rsd::f2d(v.x));
+    rsd::cro_add<kFirst>(acc[1], rsd::f2d(v.y));
+    rsd::cro_add<kFirst>(acc[2], rsd::f2d(v.z));
   }
 };
 
@@ -358,10 +359,11 @@ struct PropTerm1 {  // bound-masked u, u^2, v, v^2
   const float4* U;
   const float4* V;
   const uint8_t* bound;
+  template <bool kFirst>
   __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
     if (!bound[p]) {
 #pragma unroll
-      for (int s = 0; s < 12; ++s) acc[s] = __dadd_rn(acc[s], 0.0);
+      for (int s = 0; s < 12; ++s) rsd::cro_add<kFirst>(acc[s], 0.0);
       return;
     }
     const float4 u = U[p], v = V[p];
@@ -370,10 +372,10 @@ struct PropTerm1 {  // bound-masked u, u^2, v, v^2
     const float uc[3] = {u.x, u.y, u.z}, vc[3] = {v.x, v.y, v.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      acc[d] = __dadd_rn(acc[d], a[d]);
-      acc[3 + d] = __dadd_rn(acc[3 + d], rsd::sq_f2d(uc[d]));  // == a[d] * a[d], exactly
-      acc[6 + d] = __dadd_rn(acc[6 + d], b[d]);
-      acc[9 + d] = __dadd_rn(acc[9 + d], rsd::sq_f2d(vc[d]));
+      rsd::cro_add<kFirst>(acc[d], a[d]);
+      rsd::cro_add<kFirst>(acc[3 + d], rsd::sq_f2d(uc[d]));  // == a[d] * a[d], exactly
+      rsd::cro_add<kFirst>(acc[6 + d], b[d]);
+      rsd::cro_add<kFirst>(acc[9 + d], rsd::sq_f2d(vc[d]));
     }
   }
 };
@@ -382,22 +384,23 @@ struct PropTerm2 {  // bound-masked second moments about the bound mean
   const float4* U;
   const uint8_t* bound;
   const double* mean;  // [node][3]
+  template <bool kFirst>
   __device__ __forceinline__ void add(int64_t q, int64_t p, int64_t, double* acc) const {
     if (!bound[p]) {
 #pragma unroll
-      for (int s = 0; s < 6; ++s) acc[s] = __dadd_rn(acc[s], 0.0);
+      for (int s = 0; s < 6; ++s) rsd::cro_add<kFirst>(acc[s], 0.0);
       return;
     }
     const float4 u = U[p];
     const double* mu = mean + 3 * q;
     const double d[3] = {__dsub_rn(rsd::f2d(u.x), mu[0]), __dsub_rn(rsd::f2d(u.y), mu[1]),
                          __dsub_rn(rsd::f2d(u.z), mu[2])};
-    acc[0] = __dadd_rn(acc[0], __dmul_rn(d[0], d[0]));
-    acc[1] = __dadd_rn(acc[1], __dmul_rn(d[1], d[1]));
-    acc[2] = __dadd_rn(acc[2], __dmul_rn(d[2], d[2]));
-    acc[3] = __dadd_rn(acc[3], __dmul_rn(d[0], d[1]));
-    acc[4] = __dadd_rn(acc[4], __dmul_rn(d[0], d[2]));
-    acc[5] = __dadd_rn(acc[5], __dmul_rn(d[1], d[2]));
+    rsd::cro_add<kFirst>(acc[0], __dmul_rn(d[0], d[0]));
+    rsd::cro_add<kFirst>(acc[1], __dmul_rn(d[1], d[1]));
+    rsd::cro_add<kFirst>(acc[2], __dmul_rn(d[2], d[2]));
+    rsd::cro_add<kFirst>(acc[3], __dmul_rn(d[0], d[1]));
+    rsd::cro_add<kFirst>(acc[4], __dmul_rn(d[0], d[2]));
+    rsd::cro_add<kFirst>(acc[5], __dmul_rn(d[1], d[2]));
   }
 };
 
