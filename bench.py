@@ -374,18 +374,34 @@ def run_ours(args):
     h2d = sum(t.numel() * t.element_size() for t in pin.values())
     e_pos, e_vel, e_ids = (torch.empty_like(pos), torch.empty_like(vel), torch.empty_like(ids))
     out_lab = torch.empty(n, dtype=torch.int64).pin_memory()
+    out_bound = torch.empty(ctx.n_members, dtype=torch.uint8).pin_memory()
+    out_props = torch.empty((ctx.n_nodes, 8 * rs.PROPS_FIELDS), dtype=torch.uint8).pin_memory()
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
 
     def e2e_step():
+        # pos and ids feed the 3D FoF; vel (needed from the 6D split on) is copied on a side
+        # stream meanwhile, and the labels go back on it while the 6D hierarchy is built
         e_pos.copy_(pin["pos"], non_blocking=True)
-        e_vel.copy_(pin["vel"], non_blocking=True)
         e_ids.copy_(pin["ids"], non_blocking=True)
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            e_vel.copy_(pin["vel"], non_blocking=True)
+            vel_ready = side.record_event()
         lab, _ = rs.rs_fof3d(ctx, e_pos, e_ids)
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            out_lab.copy_(lab, non_blocking=True)
+            lab.record_stream(side)
+        main.wait_event(vel_ready)
         rs.rs_fof6d(ctx, e_pos, e_vel, e_ids, lab)
         _, bound, _ = rs.rs_unbind(ctx, e_pos, e_vel, want_potential=False)
         props = rs.rs_halo_props(ctx)
-        out_lab.copy_(lab, non_blocking=True)
-        b_h = bound.cpu()
-        p_h = props.cpu()
+        b_h = out_bound[:bound.numel()]
+        p_h = out_props[:props.shape[0]]
+        b_h.copy_(bound, non_blocking=True)
+        p_h.copy_(props, non_blocking=True)
+        torch.cuda.synchronize()
         return b_h.numel() + p_h.numel() + out_lab.numel() * 8
 
     e2e_step()
