@@ -79,7 +79,7 @@ int read_back(rs_ctx* ctx, const void* dev, size_t bytes, cudaStream_t st) {
 // ------------------------------------------------------------------------------------------
 // Radix sort. One pass per 8-bit digit: per-block digit histograms (k_sort_hist), a scan of
 // each digit's row of the digit-major histogram table (k_sort_scan_rows), then a stable scatter
-// (k_sort_scatter) in which each block ranks its tiles with warp match masks, reorders a tile
+// (k_sort_scatter) in which each block ranks its tiles with warp vote masks, reorders a tile
 // in shared memory and writes each digit's run contiguously.
 namespace {
 
@@ -206,8 +206,16 @@ k_sort_scatter(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict_
     }
 #pragma unroll
     for (int k = 0; k < kKeysPerThread; ++k) {
-      const uint32_t peers = __match_any_sync(0xffffffffu, dig[k]);
+      // lanes with the same digit: one vote per digit bit (ALU votes instead of a match, whose
+      // shared-pipe latency dominated the scatter)
       const bool valid = dig[k] < kRadix;
+      uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int bit = 0; bit < kRadixBits; ++bit) {
+        const bool set = (dig[k] >> bit) & 1u;
+        const uint32_t vb = __ballot_sync(0xffffffffu, set);
+        peers &= set ? vb : ~vb;
+      }
       uint32_t base = valid ? wcount[warp][dig[k]] : 0u;
       rank[k] = base + __popc(peers & lt_mask);
       __syncwarp();
