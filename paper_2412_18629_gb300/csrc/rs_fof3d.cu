@@ -3,10 +3,10 @@
 //
 // Pipeline (one stream, no host round trip except the optional group count):
 //   k_cell_keys   cell key per particle on a grid of sub-cells of side sc <= 0.99 ll / sqrt(3)
-//                 (so two particles in one sub-cell are always linked) -> key (z, y, x) packed
-//                 with XB bits per axis; value = particle index
-//   radix sort    (key, index), 3*XB key bits
-//   k_gather_pos  sorted positions as float4
+//                 (so two particles in one sub-cell are always linked) -> mixed-radix key
+//                 (z ns + y) ns + x; value = particle index
+//   radix sort    (key, index), ceil(log2 ns^3) key bits (32 for ns = 1600, not 3*11)
+//   k_gather_pos  sorted positions as float4; keys re-packed (z, y, x) with XB bits per axis
 //   k_row_start   dense table of the first sorted position of every (z, y) row
 //   k_cell_bounds cell start (union-find parent = the cell's first particle: every sub-cell is a
 //                 clique) and cell end per sorted position
@@ -70,17 +70,35 @@ k_cell_keys(int64_t n, const float* __restrict__ pos, float inv_sc, int ns, int 
     k = k < 0 ? 0 : (k >= ns ? ns - 1 : k);
     c[d] = uint32_t(k);
   }
-  keys[i] = (((uint64_t(c[2]) << xb) | c[1]) << xb) | c[0];
+  keys[i] = (uint64_t(c[2]) * uint64_t(ns) + c[1]) * uint64_t(ns) + c[0];  // mixed radix
   vals[i] = uint32_t(i);
 }
 
+// Sorted positions as float4, and the sorted mixed-radix keys (z ns + y) ns + x (the fewest key
+// bits for the sort, same order) re-packed with XB bits per axis for the row and cell lookups.
 __global__ void __launch_bounds__(kThreads)
 k_gather_pos(int64_t n, const uint32_t* __restrict__ idx, const float* __restrict__ pos,
-             float4* __restrict__ posS) {
+             const uint64_t* __restrict__ mkeys, int ns, int xb, float4* __restrict__ posS,
+             uint64_t* __restrict__ keys) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t s = idx[i];
   posS[i] = make_float4(pos[3 * s], pos[3 * s + 1], pos[3 * s + 2], 0.f);
+  const uint64_t k = mkeys[i];
+  uint64_t x, y, z;
+  if (k < (uint64_t(1) << 32)) {  // 32-bit division whenever ns^3 fits (ns <= 1625)
+    const uint32_t k32 = uint32_t(k), n32 = uint32_t(ns);
+    const uint32_t yz = k32 / n32;
+    x = k32 - yz * n32;
+    z = yz / n32;
+    y = yz - uint32_t(z) * n32;
+  } else {
+    const uint64_t yz = k / uint64_t(ns);
+    x = k - yz * uint64_t(ns);
+    z = yz / uint64_t(ns);
+    y = yz - z * uint64_t(ns);
+  }
+  keys[i] = (((z << xb) | y) << xb) | x;
 }
 
 __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* __restrict__ a, uint32_t lo,
@@ -274,10 +292,14 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
   const unsigned grid = grid_for(n, kThreads);
   k_cell_keys<<<grid, kThreads, 0, st>>>(n, pos, g.inv_sc, g.ns, g.xb, ka, va);
   RS_LAUNCHED(ctx, "k_cell_keys");
-  uint64_t* keys;
+  uint64_t* mkeys;
   uint32_t* idx;
-  RS_TRY(radix_sort_u64(ctx, n, 3 * g.xb, ka, va, kb, vb, &keys, &idx, st));
-  k_gather_pos<<<grid, kThreads, 0, st>>>(n, idx, pos, posS);
+  const uint64_t ns3 = uint64_t(g.ns) * uint64_t(g.ns) * uint64_t(g.ns);
+  int kbits = 1;
+  while (kbits < 64 && ((ns3 - 1) >> kbits) != 0) ++kbits;
+  RS_TRY(radix_sort_u64(ctx, n, kbits, ka, va, kb, vb, &mkeys, &idx, st));
+  uint64_t* keys = (mkeys == ka) ? kb : ka;  // the other key buffer receives the packed keys
+  k_gather_pos<<<grid, kThreads, 0, st>>>(n, idx, pos, mkeys, g.ns, g.xb, posS, keys);
   RS_LAUNCHED(ctx, "k_gather_pos");
   k_row_start<<<grid_for(g.nrows + 1, kThreads), kThreads, 0, st>>>(n, keys, g.xb, g.nrows, row_start);
   RS_LAUNCHED(ctx, "k_row_start");

@@ -102,7 +102,7 @@ __device__ __forceinline__ float member_radius(float4 u, const NodeStat& s) {
 }
 
 // Radial sort key of every surrogate member k (surrogate order is node-grouped): the big
-// node's rank above the radius bits, so each node's members stay in their range
+// node's rank above the radius bits (31: a radius is never negative), so each node's members stay in their range
 // [sur_off[q], sur_off[q] + g) after sorting.
 __global__ void k_big_radius(int64_t ns, const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
                              const int64_t* __restrict__ big_rank, const float4* __restrict__ U,
@@ -112,17 +112,17 @@ __global__ void k_big_radius(int64_t ns, const uint32_t* __restrict__ sur_mem, c
   if (k >= ns) return;
   const uint32_t p = sur_mem[k], q = mnode[p];
   const float r = member_radius(U[p], st[q]);
-  keys[k] = (uint64_t(big_rank[q]) << 32) | uint64_t(__float_as_uint(r));
+  keys[k] = (uint64_t(big_rank[q]) << 31) | uint64_t(__float_as_uint(r));  // r >= 0: 31 bits
   vals[k] = uint32_t(k);
 }
 
 __device__ __forceinline__ int64_t count_below(const uint64_t* __restrict__ rkeys, int64_t lo, int64_t hi,
                                                float v) {
-  // members of the segment whose radius is < v (radius bits are the low 32 bits of the keys)
+  // members of the segment whose radius is < v (radius bits are the low 31 bits of the keys)
   const int64_t base = lo;
   while (lo < hi) {
     const int64_t mid = lo + ((hi - lo) >> 1);
-    if (__uint_as_float(uint32_t(rkeys[mid] & 0xffffffffull)) < v) lo = mid + 1; else hi = mid;
+    if (__uint_as_float(uint32_t(rkeys[mid] & 0x7fffffffull)) < v) lo = mid + 1; else hi = mid;
   }
   return lo - base;
 }
@@ -135,7 +135,7 @@ __global__ void k_sur_inv_r(int64_t ns, const uint64_t* __restrict__ rkeys, cons
                             float eps, int64_t* __restrict__ fix, uint32_t* __restrict__ spos) {
   const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= ns) return;
-  const float r = __uint_as_float(uint32_t(rkeys[s] & 0xffffffffull));
+  const float r = __uint_as_float(uint32_t(rkeys[s] & 0x7fffffffull));
   fix[s] = llrint(kFix / double(fmaxf(r, eps)));
   spos[rvals[s]] = uint32_t(s);
 }
@@ -841,7 +841,7 @@ static int sur_prepare(rs_ctx* ctx, const double* vbulk, int64_t* ns_out, cudaSt
   RS_LAUNCHED(ctx, "k_big_radius");
   uint64_t* rkeys;
   uint32_t* rvals;
-  RS_TRY(radix_sort_u64(ctx, ns, 32 + bits_for(uint64_t(nbig)), ka, va, kb, vb, &rkeys, &rvals, st));
+  RS_TRY(radix_sort_u64(ctx, ns, 31 + bits_for(uint64_t(nbig)), ka, va, kb, vb, &rkeys, &rvals, st));
   ctx->sur_rkeys = rkeys;
   int64_t* fix = scratch_t<int64_t>(ctx, S_SUR_FIX, size_t(ns) + 1);
   uint32_t* spos = scratch_t<uint32_t>(ctx, S_SUR_SPOS, size_t(ns));
