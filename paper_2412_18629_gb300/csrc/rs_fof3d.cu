@@ -14,7 +14,8 @@
 //                 launches), the half stencil of rows within R sub-cells; a neighbour cell is
 //                 skipped when its root already equals the particle's root, otherwise scanned
 //                 until the first linked member (one link joins the whole clique)
-//   k_fof_roots   full path compression; smallest id per root (atomicMin); group count
+//   k_fof_roots   after full path compression: each root stores its id and counts as a group;
+//                 k_fof_member_min lowers it to the smallest member id (atomicMin)
 //   k_fof_labels  label of every particle in input order
 #include <cmath>
 
@@ -232,15 +233,26 @@ __global__ void __launch_bounds__(kThreads) k_fof_link(int64_t n, LinkArgs A, bo
   }
 }
 
+// After full compression parent[i] is i's root. Each root stores its own id (a plain store:
+// most roots are single particles) and counts as a group; then every other particle lowers its
+// root's entry to its id (warp-aggregated atomicMin over runs of equal roots).
 __global__ void __launch_bounds__(kThreads)
-k_fof_roots(int64_t n, uint32_t* __restrict__ parent, const uint32_t* __restrict__ idx,
+k_fof_roots(int64_t n, const uint32_t* __restrict__ parent, const uint32_t* __restrict__ idx,
             const int64_t* __restrict__ ids, unsigned long long* __restrict__ minid,
             unsigned long long* __restrict__ counter) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const bool valid = i < n;  // every lane stays for the warp-aggregated atomics
-  const uint32_t r = valid ? rsd::uf_find_ro(parent, uint32_t(i)) : 0u;
-  rsd::warp_run_min(minid, r, valid, valid ? (unsigned long long)ids[idx[i]] : ~0ull);
-  rsd::warp_count(counter, valid && r == uint32_t(i));
+  const bool root = i < n && parent[i] == uint32_t(i);  // every lane stays for the count
+  if (root) minid[i] = (unsigned long long)ids[idx[i]];
+  rsd::warp_count(counter, root);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_fof_member_min(int64_t n, const uint32_t* __restrict__ parent, const uint32_t* __restrict__ idx,
+                 const int64_t* __restrict__ ids, unsigned long long* __restrict__ minid) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const uint32_t r = i < n ? parent[i] : 0u;
+  const bool member = i < n && r != uint32_t(i);  // every lane stays for the run reduction
+  rsd::warp_run_min(minid, r, member, member ? (unsigned long long)ids[idx[i]] : ~0ull);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -317,12 +329,13 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
     k_fof_link<<<grid, kThreads, 0, st>>>(n, A, false);
     RS_LAUNCHED(ctx, "k_fof_link");
   }
-  RS_CUDA(ctx, cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
   RS_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   k_fof_compress<<<grid, kThreads, 0, st>>>(n, parent);
   RS_LAUNCHED(ctx, "k_fof_compress");
   k_fof_roots<<<grid, kThreads, 0, st>>>(n, parent, idx, ids, minid, counter);
   RS_LAUNCHED(ctx, "k_fof_roots");
+  k_fof_member_min<<<grid, kThreads, 0, st>>>(n, parent, idx, ids, minid);
+  RS_LAUNCHED(ctx, "k_fof_member_min");
   k_fof_labels<<<grid, kThreads, 0, st>>>(n, parent, idx, minid, label_out);
   RS_LAUNCHED(ctx, "k_fof_labels");
   if (n_groups_out) {
