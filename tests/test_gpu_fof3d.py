@@ -95,3 +95,18 @@ def test_workload_2e24_full():
     want = oracle.fof3d_grid(s["pos"], s["ids"], s["box"], s["link_length"])
     assert np.array_equal(got, want)
     assert ng == len(np.unique(want))
+
+
+def test_large_grid_keys_beyond_32_bits():
+    """box / ll large enough that the sub-cell grid has more than 1625 cells per axis: the
+    mixed-radix cell keys exceed 32 bits (64-bit unpacking path) and the sort takes 33 bits."""
+    rng = np.random.default_rng(11)
+    box, ll = 200.0, 0.2
+    sc = 0.99 * ll / np.sqrt(3.0)
+    assert int(np.ceil(box / sc)) > 1625
+    centres = rng.uniform(0, box, (1500, 3))
+    pos = (np.repeat(centres, 12, axis=0) + rng.normal(0, 0.08, (18000, 3))) % box
+    pos = np.concatenate([pos, rng.uniform(0, box, (6000, 3))]).astype(np.float32)
+    pos[pos >= np.float32(box)] = 0
+    ids = rng.permutation(len(pos)).astype(np.int64)
+    _check(pos, ids, box, ll)
