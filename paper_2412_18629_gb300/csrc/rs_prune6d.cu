@@ -566,6 +566,7 @@ __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t 
   if (lane < int(Bb.count)) sj[lane] = A.sp[Bb.start + lane];
   __syncwarp();
   const int j0 = (b == a) ? lane + 1 : 0;
+  uint32_t pending = 0;  // targets of this bucket the lane links to (unions after the scan)
   for (uint32_t s0 = 0; s0 < Bb.count; s0 += 8) {
     const Box Sb = A.sub[4 * b + (s0 >> 3)];
     if (kCount) T.box += (lane == 0);
@@ -579,10 +580,18 @@ __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t 
       for (int j = int(s0); j < s1; j += 2) {
         if (j + 1 < j0) continue;
         const float2 d = d6_pair(Q, S, j);
-        if (j >= j0 && d.x <= l2) rsd::uf_unite(uf, pi, sj[j]);
-        if (j + 1 >= j0 && j + 1 < s1 && d.y <= l2) rsd::uf_unite(uf, pi, sj[j + 1]);
+        if (j >= j0 && d.x <= l2) pending |= 1u << j;
+        if (j + 1 >= j0 && j + 1 < s1 && d.y <= l2) pending |= 2u << j;
       }
     }
+  }
+  // The bucket's unions after its distances: the lanes with links run their union-find calls
+  // side by side instead of one diverging lane at a time inside the distance loop (the union
+  // order does not change the resulting components).
+  while (pending) {
+    const int j = __ffs(pending) - 1;
+    pending &= pending - 1u;
+    rsd::uf_unite(uf, pi, sj[j]);
   }
 }
 
