@@ -548,12 +548,27 @@ __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict_
   flush_tally<kCount>(T, A.work, lane);
 }
 
+// Pending unions of each lane of a warp: member indices of its friends, lane-major columns.
+struct LinkQueue {
+  uint32_t j[32][32];
+};
+
+// Union the warp's pending friends with their lanes' members, the lanes side by side (the
+// union order does not change the resulting components).
+__device__ __forceinline__ void flush_links(uint32_t* uf, uint32_t pi, const LinkQueue& LQ, int& qn,
+                                            int lane) {
+  const int mx = int(__reduce_max_sync(0xffffffffu, uint32_t(qn)));
+  for (int k = 0; k < mx; ++k)
+    if (k < qn) rsd::uf_unite(uf, pi, LQ.j[k][lane]);
+  qn = 0;
+}
+
 // Link pairs of query bucket a (box Abox) with target bucket b >= a.
 template <bool kCount>
 __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t b, const Box& Abox,
                                             bool active, const Query& Q, uint32_t pi, float l2,
                                             uint32_t* uf, int lane, Stage& S, uint32_t (&sj)[32],
-                                            Tally& T) {
+                                            LinkQueue& LQ, int& qn, Tally& T) {
   const Box B = A.box[b];
   if (kCount) T.box += (lane == 0);
   if (lb_box_box(Abox, B, Q.s) > l2) return;
@@ -585,13 +600,14 @@ __device__ __forceinline__ void link_bucket(const NNArgs& A, int64_t a, int64_t 
       }
     }
   }
-  // The bucket's unions after its distances: the lanes with links run their union-find calls
-  // side by side instead of one diverging lane at a time inside the distance loop (the union
-  // order does not change the resulting components).
+  // Friends go to the lane's queue; the queues are flushed (union-find calls of all lanes side
+  // by side) when one would overflow and at the end of the query bucket, instead of one
+  // diverging lane at a time inside the distance loop.
+  if (__any_sync(0xffffffffu, qn + __popc(pending) > 32)) flush_links(uf, pi, LQ, qn, lane);
   while (pending) {
     const int j = __ffs(pending) - 1;
     pending &= pending - 1u;
-    rsd::uf_unite(uf, pi, sj[j]);
+    LQ.j[qn++][lane] = sj[j];
   }
 }
 
@@ -602,6 +618,7 @@ k_link6d_pruned(NNArgs A, uint32_t* __restrict__ uf) {
   Tally T;
   __shared__ Stage stg[kWarpsPerBlock];
   __shared__ uint32_t sj[kWarpsPerBlock][32];
+  __shared__ LinkQueue lq[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int64_t nbk = *A.nbuckets;
   while (true) {
@@ -617,6 +634,7 @@ k_link6d_pruned(NNArgs A, uint32_t* __restrict__ uf) {
     const uint32_t pi = A.sp[si];
     const bool active = valid;
     const Box Abox = A.box[a];
+    int qn = 0;  // this lane's pending unions in lq[wb]
     const int64_t own = (a - int64_t(Aq.first)) >> 5, nsb = Aq.sbcount;
     for (int64_t s = own; s < nsb; ++s) {
       const Box SB = A.sbox[Aq.sbfirst + s];
@@ -628,8 +646,9 @@ k_link6d_pruned(NNArgs A, uint32_t* __restrict__ uf) {
       const int64_t b_lo = rsd::min64(int64_t(Aq.first) + 32 * s, int64_t(Aq.last) + 1);
       const int64_t b_hi = rsd::min64(int64_t(Aq.first) + 32 * s + 32, int64_t(Aq.last) + 1);
       for (int64_t b = (s == own ? a : b_lo); b < b_hi; ++b)
-        link_bucket<kCount>(A, a, b, Abox, active, Q, pi, l2, uf, lane, stg[wb], sj[wb], T);
+        link_bucket<kCount>(A, a, b, Abox, active, Q, pi, l2, uf, lane, stg[wb], sj[wb], lq[wb], qn, T);
     }
+    flush_links(uf, pi, lq[wb], qn, lane);
   }
   flush_tally<kCount>(T, A.work + 2, lane);
 }
