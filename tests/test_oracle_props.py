@@ -70,3 +70,61 @@ def test_no_bound_members():
     pos = _lattice(2, 0.5, [1.0, 1.0, 1.0])
     P = _props(pos, np.zeros(len(pos)))
     assert P[0] == 8 and P[1] == 0 and np.all(P[3:] == 0)
+
+
+def _sheared_case(k=4, h=0.5):
+    """A k^3 lattice sheared by the dyadic matrix A = [[1, 1/2, 1/4], [0, 1, 1/2], [0, 0, 1]]
+    with dyadic velocities v = (16 j - 24, 32 l, 8 i + 4 j) at lattice index (i, j, l).
+    The lattice coordinates are independent and uniform on {0, h, .., (k-1) h}, each with
+    variance s = h^2 (k^2 - 1) / 12, so the position covariance is s A A^T (non-zero
+    off-diagonal terms, all different) and every moment is a short dyadic fraction: the oracle's
+    float64 sums are exact and the pins below are equalities."""
+    idx = np.stack(np.meshgrid(np.arange(k), np.arange(k), np.arange(k), indexing="ij"),
+                   -1).reshape(-1, 3).astype(np.float64)
+    A = np.array([[1.0, 0.5, 0.25], [0.0, 1.0, 0.5], [0.0, 0.0, 1.0]])
+    pos = (idx * h) @ A.T + np.array([10.0, 20.0, 30.0])
+    i, j, l = idx[:, 0], idx[:, 1], idx[:, 2]
+    vel = np.stack([16 * j - 24, 32 * l, 8 * i + 4 * j], axis=1)
+    s = h * h * (k * k - 1) / 12.0
+    cov = s * (A @ A.T)
+    return pos.astype(np.float32), vel.astype(np.float32), s, cov, A
+
+
+def test_sheared_lattice_inertia_and_velocity_dispersion():
+    pos, vel, s, cov, A = _sheared_case()
+    assert np.array_equal(pos.astype(np.float64), np.asarray(pos, np.float64))  # exact in float32
+    rng = np.random.default_rng(7)
+    ids = rng.permutation(len(pos))
+    P = _props(pos, np.ones(len(pos)), vel=vel, ids=ids)
+    # centre: origin + A (mean lattice offset); mean offset is h (k - 1) / 2 = 0.75 per axis
+    centre = np.array([10.0, 20.0, 30.0]) + A @ np.full(3, 0.75)
+    assert list(P[4:7]) == list(centre)
+    # bulk velocity: (16 * 1.5 - 24, 32 * 1.5, 8 * 1.5 + 4 * 1.5)
+    assert list(P[7:10]) == [0.0, 48.0, 18.0]
+    # sigma_x^2 = trace(cov); sigma_v^2 = 256 v1 + 1024 v1 + (64 + 16) v1, v1 = var of {0..3}
+    assert P[10] == math.sqrt(np.trace(cov))
+    v1 = 15.0 / 12.0
+    assert P[11] == math.sqrt((256 + 1024 + 80) * v1)
+    # inertia xx yy zz xy xz yz = the covariance entries, each different
+    want = [cov[0, 0], cov[1, 1], cov[2, 2], cov[0, 1], cov[0, 2], cov[1, 2]]
+    assert len(set(want)) == 6
+    assert list(P[13:19]) == want
+
+
+def test_sheared_lattice_bound_subset():
+    """Only the bound half (lattice index i < 2) enters: its lattice x-coordinate takes two
+    values, variance h^2 / 4, the other two axes keep s; the covariance is A diag(h^2/4, s, s)
+    A^T and the velocity z-component loses the i-spread."""
+    pos, vel, s, cov, A = _sheared_case()
+    h = 0.5
+    idx = np.stack(np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij"),
+                   -1).reshape(-1, 3)
+    bound = (idx[:, 0] < 2).astype(np.uint8)
+    P = _props(pos, bound, vel=vel)
+    assert P[1] == 32
+    c = A @ np.diag([h * h / 4.0, s, s]) @ A.T
+    assert list(P[13:19]) == [c[0, 0], c[1, 1], c[2, 2], c[0, 1], c[0, 2], c[1, 2]]
+    v1 = 15.0 / 12.0
+    # v = (16 j - 24, 32 l, 8 i + 4 j) with i in {0, 1}: var(i) = 1/4
+    assert P[11] == math.sqrt(256 * v1 + 1024 * v1 + (64 * 0.25 + 16 * v1))
+    assert list(P[7:10]) == [0.0, 48.0, 8 * 0.5 + 4 * 1.5]
