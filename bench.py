@@ -1,12 +1,16 @@
 """Benchmark: halo-finding particles/s on one GB300 (3D FoF -> 6D hierarchy -> unbinding ->
-halo properties), on a seeded synthetic NFW snapshot.
+halo properties), on a seeded synthetic NFW snapshot (default: 2^27 particles in a 512 Mpc/h
+box, halos up to 2e6 particles with three levels of subhalos).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one pass of the whole path over one snapshot with inputs resident in HBM. Prints one
-JSON line (rank 0). For N > 1 (torchrun, one rank per GPU) every rank processes its own
-independent snapshot (seed + rank): weak scaling, no data-path collective; the value is all
-ranks' particles over the slowest rank's time.
+One step = one pass of the whole path over one snapshot with inputs resident in HBM. The
+headline is the batched + surrogate form timed over exactly K steps after W warm-up steps; the
+plain and batched forms are timed beside it with their own (stated) step counts, and every
+form's outputs are checked identical. Prints one JSON line (rank 0). For N > 1 (torchrun, one
+rank per GPU) every rank processes its own independent snapshot (seed + 1000 rank): weak
+scaling, no data-path collective; the value is all ranks' particles over the slowest rank's
+time.
 
 --impl reference times the CPU oracle (the plain definition the CUDA path is checked against)
 on a bounded sample of the same workload, on this machine's host cores.
@@ -30,11 +34,9 @@ if ROOT not in sys.path:
 
 METRIC = "halo-finding particles/s on 1 GB300, plain vs batched+surrogate; % of roofline"
 UNIT = "particles/s"
-DEFAULT_WORKLOAD = "nfw-2^24-L256-sub"
+DEFAULT_WORKLOAD = "nfw-2^27-L512-sub3"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# fraction of the box side of the cubic sub-volume the CPU oracle is timed on
-ORACLE_SUBBOX = 0.5
 
 
 def _dist():
@@ -147,18 +149,46 @@ def _snapshot(workload, rank):
     return spec, synth.generate(spec)
 
 
-def _oracle_sample(snap):
-    """Bounded sample of the workload for the CPU oracle: the particles in the cubic sub-volume
-    [0, f L)^3 of the same snapshot (its halos are cut at the sub-volume's faces)."""
+ORACLE_CUBES = 8    # the sample cubes' side is L / ORACLE_CUBES
+ORACLE_SAMPLE = 5   # cubes the CPU baseline times (the median-load cube and its neighbours in load)
+
+
+def _oracle_cubes(snap, count=ORACLE_SAMPLE):
+    """Indices (ix, iy, iz) of the sample cubes: of the ORACLE_CUBES^3 cubes of side
+    L / ORACLE_CUBES, ranked by the sum of squared particle counts of the catalogued top-level
+    halos centred in them (the oracle's cost is dominated by sum n^2), the `count` cubes around
+    the median (ties: lowest index first)."""
+    L = float(snap["box"])
+    k = ORACLE_CUBES
+    w = np.zeros(k ** 3)
+    for depth, cnt, _, centre, _, _ in snap["catalogue"]:
+        if depth != 0:
+            continue
+        c = np.floor(np.mod(np.asarray(centre, dtype=np.float64), L) / (L / k)).astype(int) % k
+        w[(c[0] * k + c[1]) * k + c[2]] += float(cnt) ** 2
+    order = np.argsort(w, kind="stable")
+    mid = len(order) // 2
+    pick = order[max(0, mid - count // 2): max(0, mid - count // 2) + count]
+    return [(int(i) // (k * k), (int(i) // k) % k, int(i) % k) for i in pick]
+
+
+def _oracle_sample(snap, cube):
+    """The particles of cube `cube` (side L / ORACLE_CUBES) of the same snapshot: a bounded
+    sample of the workload for the CPU oracle (its halos are cut at the cube's faces)."""
     from paper_2412_18629_gb300 import synth
-    keep = np.all(snap["pos"] < np.float32(ORACLE_SUBBOX * snap["box"]), axis=1)
+    side = float(snap["box"]) / ORACLE_CUBES
+    lo = np.array(cube, dtype=np.float64) * side
+    p = snap["pos"].astype(np.float64)
+    keep = np.all((p >= lo) & (p < lo + side), axis=1)
     return synth.subsample(snap, keep)
 
 
-def time_oracle(snap, threads):
+def time_oracle(snap, threads, cube):
+    """Run the oracle over one sample cube: 3D FoF, hierarchy, unbinding, properties. Returns
+    (particles, seconds)."""
     import oracle
     from paper_2412_18629_gb300 import G_NEWTON
-    sub = _oracle_sample(snap)
+    sub = _oracle_sample(snap, cube)
     t0 = time.perf_counter()
     lab = oracle.fof3d_grid(sub["pos"], sub["ids"], sub["box"], sub["link_length"])
     h = oracle.hierarchy(sub["pos"], sub["vel"], sub["ids"], lab, sub["box"], threads=threads)
@@ -171,92 +201,16 @@ def time_oracle(snap, threads):
     return sub["n"], dt
 
 
-def _hier_work(ctx):
-    """Algorithmic pair counts of the hierarchy: sum over nodes of g (g - 1); also the part of
-    the nodes above 384 members (the blocked potential kernel's share)."""
-    import paper_2412_18629_gb300 as rs
-    sizes = rs.rs_fof6d_copy(ctx)["size"].cpu().numpy().astype(np.float64)
-    big = sizes[sizes > 384]
-    return float((sizes * (sizes - 1)).sum()), float((big * (big - 1)).sum())
-
-
-# FP32-pipe operations per pair for the two O(n_g^2) kernels (no FMA contraction):
-# 6D distance = 6 sub + 6 mul + 4 add + 2 mul (scales) + 1 add, plus the min / compare = 20;
-# potential = 3 sub + 3 FMA + 1 add (+ 1 MUFU rsqrt) = 7.
-OPS_PER_PAIR = {"k_nn6d": 20.0, "k_link6d": 20.0, "k_potential": 7.0}
-
-
-def _measure(ctx, pos, vel, ids, n, args, ws, local):
-    """Warm up, then time exactly args.steps steps of the whole path on device-resident inputs."""
-    import torch
-    import paper_2412_18629_gb300 as rs
-    stream = torch.cuda.current_stream()
-
-    def step():
-        lab, _ = rs.rs_fof3d(ctx, pos, ids)
-        rs.rs_fof6d(ctx, pos, vel, ids, lab)
-        _, bound, nfb = rs.rs_unbind(ctx, pos, vel, want_potential=False)
-        props = rs.rs_halo_props(ctx)
-        return nfb
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    pairs, pairs_big = _hier_work(ctx)
-    ctx.profile(True)
-    l0 = ctx.kernel_launches
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        _barrier(ws)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            nfb = step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        _barrier(ws)
-    launches = ctx.kernel_launches - l0
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    prof = ctx.profile_totals()
-    ctx.profile(False)
-    work = None
-    if ctx.mode != "plain":  # one untimed step through the counting variants of the 6D kernels
-        ctx.count_work(True)
-        step()
-        work = ctx.count_work(False)
-    t_max, units = aggregate(elapsed, float(n) * args.steps, ws, f"cuda:{local}")
-    return {"value": units / t_max, "ms_per_step": t_max / args.steps * 1e3, "launches": launches,
-            "prof": prof, "pairs": pairs, "pairs_big": pairs_big, "clocks": clk.summary(),
-            "fallback": nfb, "work": work, "n": n, "autotune": ctx.tuning()}
-
-
-def _roofline(prof, pairs, steps, work=None):
-    """Roofline entry of the dominant instrumented kernel (largest summed CUDA-event time).
-    Brute-force pair kernels: algorithmic operations = pairs x operations per pair. Pruned 6D
-    kernels: the d6 evaluations and box lower bounds they perform (tallied in one untimed step
-    by the counting variants), 20 FP32 operations each."""
-    if not prof:
-        return None
-    name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2070e6
-    base = name.replace("_pruned", "").replace("_blocked", "")
-    entry = {"bound": "alu", "kernel": name, "achieved": None, "peak": peak_ops / 1e12,
-             "unit": "Tops/s", "frac": None, "traffic": None, "launches": cnt,
-             "kernel_ms_per_step": ms / steps,
-             "peak_note": "FP32-pipe lane operations at 2070 MHz (152 SMs x 128 lanes)"}
-    work_ops = None
-    if name.endswith("_pruned") and work:
-        key = "nn" if base == "k_nn6d" else "link"
-        work_ops = (work[f"{key}_d6"] + work[f"{key}_box"]) * OPS_PER_PAIR["k_nn6d"] * steps
-        entry["work"] = {"d6_per_step": work[f"{key}_d6"], "box_tests_per_step": work[f"{key}_box"],
-                         "ops_each": OPS_PER_PAIR["k_nn6d"]}
-    elif base in OPS_PER_PAIR and not name.endswith("_pruned"):
-        pr = pairs if base != "k_link6d" else pairs / 2.0
-        work_ops = pr * OPS_PER_PAIR[base] * steps
-    if work_ops is not None:
-        achieved = work_ops / (ms / 1e3)
-        entry.update(achieved=achieved / 1e12, frac=achieved / peak_ops)
-    return entry
+# ---------------------------------------------------------------------------------------------
+# Algorithmic work per kernel (the per-unit figures of the roofline) and the peaks.
+FP32_PEAK_OPS = SM_COUNT * FP32_LANES_PER_SM * 2070e6   # FP32-pipe lane operations per second
+FOF_BYTES_PER_PARTICLE = 28.0   # position 12 + id 8 + label 8
+SORT_BYTES_PER_KEY_PASS = 24.0  # key 8 + value 4, read and written
+NODE_BYTES_PER_MEMBER = 40.0    # 6D level: u 12 + v 12 + id 8 + label 8 per member and level
+OPS_D6 = 20.0                   # 6D distance: 6 sub, 6 mul, 4 add, 2 scale mul, 1 add, 1 compare
+OPS_PAIR = 7.0                  # potential pair: 3 sub, 3 FMA, 1 add (+ 1 MUFU rsqrt)
+OPS_EXPANSION = 50.0            # tree walk: one quadrupole expansion with its bound and test
+TREE_MIN_DEFAULT = 16384        # the library's default smallest node of the tree bound
 
 
 def _measured_peaks():
@@ -269,48 +223,212 @@ def _measured_peaks():
         return {}
 
 
-def _stages(r, steps):
-    """Per-stage roofline figures of the kernels with a defined algorithmic work: the 3D FoF
-    link pass against the measured HBM copy bandwidth (28 B per particle: position, id,
-    label), the pair kernels against the FP32-pipe lane rate (brute force: pairs x operations;
-    pruned: tallied d6 evaluations and box tests; blocked potential: pairs of the nodes above
-    384 members x 7 operations)."""
-    prof, out = r["prof"], {}
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * 2070e6
-    hbm = _measured_peaks().get("hbm_gbs")
+HBM_FALLBACK_GBS = 6800.0
 
-    def ms(k):
-        return prof[k][0] / steps / 1e3 if k in prof and prof[k][0] > 0 else None
 
-    if ms("k_fof_link") and hbm:
-        gbs = r["n"] * 28.0 / ms("k_fof_link") / 1e9
-        out["k_fof_link"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                             "frac": gbs / hbm, "note": "latency-bound union-find; HBM is not its limit"}
-    alu = {}
-    if ms("k_potential_blocked") and r.get("form") != "surrogate":
-        alu["k_potential_blocked"] = r["pairs_big"] * OPS_PER_PAIR["k_potential"]
-    for k in ("k_nn6d", "k_link6d"):
-        if ms(k):
-            alu[k] = r["pairs"] * OPS_PER_PAIR[k] / (2.0 if k == "k_link6d" else 1.0)
-    w = r.get("work")
-    if w:
-        for k, key in (("k_nn6d_pruned", "nn"), ("k_link6d_pruned", "link")):
-            if ms(k):
-                alu[k] = (w[f"{key}_d6"] + w[f"{key}_box"]) * OPS_PER_PAIR["k_nn6d"]
-    for k, ops in alu.items():
-        a = ops / ms(k)
-        out[k] = {"bound": "alu", "achieved": a / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                  "frac": a / peak_ops, "ms_per_step": ms(k) * 1e3}
+def _hbm_peak():
+    p = _measured_peaks().get("hbm_gbs")
+    return (float(p), "measured") if p else (HBM_FALLBACK_GBS, "fallback")
+
+
+def _sizes_work(sizes, form, tree_min):
+    """Pair counts of the direct-sum kernels from the node sizes: k_potential (nodes up to 384
+    members) and the blocked / tiled kernel (larger nodes handled by the direct sum in this
+    form: below the surrogate's 1024 members or the tree's threshold); brute-force 6D pairs."""
+    g = np.asarray(sizes, dtype=np.float64)
+    pairs = g * (g - 1.0)
+    small = pairs[g <= 384].sum()
+    if form == "plain":
+        lim = np.inf
+    elif form == "surrogate":
+        lim = 1024.0
+    else:
+        lim = float(tree_min) if tree_min > 0 else np.inf
+    big = pairs[(g > 384) & (g < lim)].sum()
+    return {"pairs_all": float(pairs.sum()), "pairs_small": float(small), "pairs_blocked": float(big)}
+
+
+def kernel_work(r):
+    """{kernel: (bound, algorithmic units per step, unit, note)} for the kernels with a defined
+    work figure, from the form's measured tallies r: n, members, sort key-passes per step,
+    pair counts from node sizes, the pruned kernels' d6 tallies and the tree's counters.
+    Bytes for HBM-bound kernels, FP32-pipe operations for ALU-bound ones."""
+    out = {}
+    out["k_fof_link"] = ("hbm", r["n"] * FOF_BYTES_PER_PARTICLE, "B", "28 B per particle")
+    if r.get("sort_keypasses"):
+        out["k_sort"] = ("hbm", r["sort_keypasses"] * SORT_BYTES_PER_KEY_PASS, "B",
+                         "24 B per key and 8-bit pass (k_sort_hist + k_sort_scatter)")
+    for k in ("k_nn6d_pruned", "k_link6d_pruned", "k_nn6d", "k_link6d"):
+        out[k] = ("hbm", r["members"] * NODE_BYTES_PER_MEMBER, "B", "40 B per member and level")
+    w = r.get("pairs", {})
+    out["k_potential"] = ("alu", w.get("pairs_small", 0.0) * OPS_PAIR, "ops", "7 per ordered pair")
+    for k in ("k_potential_blocked", "k_potential_tiled"):
+        out[k] = ("alu", w.get("pairs_blocked", 0.0) * OPS_PAIR, "ops", "7 per ordered pair")
+    t = r.get("tree") or {}
+    if t.get("list_pairs"):
+        out["k_potential_list"] = ("alu", t["list_pairs"] * OPS_PAIR, "ops", "7 per listed pair")
+    if t.get("expansions") or t.get("direct_pairs"):
+        out["k_tree_walk"] = ("alu", t["expansions"] * OPS_EXPANSION + t["direct_pairs"] * OPS_PAIR,
+                              "ops", "50 per expansion + 7 per direct pair")
     return out
+
+
+def _alu_d6(r, k):
+    """FP32-pipe figure of a 6D kernel counting d6 evaluations only (box bounds as overhead)."""
+    wk = r.get("work")
+    if k.endswith("_pruned"):
+        if not wk:
+            return None
+        d6 = wk["nn_d6" if k.startswith("k_nn6d") else "link_d6"]
+    else:
+        pa = r["pairs"]["pairs_all"]
+        d6 = pa if k == "k_nn6d" else pa / 2.0
+    return d6 * OPS_D6
+
+
+def stages(r):
+    """Per-kernel roofline figures of one form from its profiled step (CUDA events per launch):
+    achieved = algorithmic work per step / kernel time per step, against the measured HBM copy
+    bandwidth or the FP32-pipe lane rate."""
+    prof = dict(r["prof"])
+    if "k_sort_hist" in prof or "k_sort_scatter" in prof:
+        a, b = prof.get("k_sort_hist", (0.0, 0)), prof.get("k_sort_scatter", (0.0, 0))
+        prof["k_sort"] = (a[0] + b[0], a[1] + b[1])
+    hbm, hbm_src = _hbm_peak()
+    out = {}
+    for k, (bound, units, unit, note) in kernel_work(r).items():
+        if k not in prof or prof[k][0] <= 0 or units <= 0:
+            continue
+        sec = prof[k][0] / 1e3
+        e = {"bound": bound, "ms_per_step": prof[k][0], "launches": prof[k][1], "work_note": note}
+        if bound == "hbm":
+            e.update(achieved=units / sec / 1e9, peak=hbm, unit="GB/s", frac=units / sec / 1e9 / hbm,
+                     peak_source=hbm_src)
+        else:
+            e.update(achieved=units / sec / 1e12, peak=FP32_PEAK_OPS / 1e12, unit="Tops/s",
+                     frac=units / sec / FP32_PEAK_OPS, peak_source="FP32 lanes x 2070 MHz")
+        if k.startswith(("k_nn6d", "k_link6d")):
+            ops = _alu_d6(r, k)
+            if ops:
+                e["alu_d6_only"] = {"achieved": ops / sec / 1e12, "peak": FP32_PEAK_OPS / 1e12,
+                                    "unit": "Tops/s", "frac": ops / sec / FP32_PEAK_OPS}
+        out[k] = e
+    return out
+
+
+def roofline(r, traffic=None):
+    """The roofline entry of the dominant kernel (largest time in the profiled step among the
+    kernels with a work figure); launches and average duration per launch."""
+    st = stages(r)
+    if not st:
+        return None
+    k = max(st, key=lambda x: st[x]["ms_per_step"])
+    e = dict(st[k])
+    e["kernel"] = k
+    e["ms_per_launch"] = e["ms_per_step"] / max(e["launches"], 1)
+    e["traffic"] = (traffic or {}).get(k)
+    return e
+
+
+def _traffic_table():
+    """DRAM bytes per launch of profiled kernels from ncu (profiles/traffic.json), scaled to the
+    bench workload by the entry's unit count: {kernel: {"bytes_per_unit", "unit", ...}}."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------------------------
+def _digest(ctx, lab, bound, props):
+    """SHA-256 of a form's outputs: 3D labels, hierarchy arrays, bound flags, properties."""
+    import hashlib
+
+    import paper_2412_18629_gb300 as rs
+    hsh = hashlib.sha256()
+    hsh.update(lab.cpu().numpy().tobytes())
+    for k, v in sorted(rs.rs_fof6d_copy(ctx).items()):
+        hsh.update(k.encode())
+        hsh.update(v.cpu().numpy().tobytes())
+    hsh.update(bound.cpu().numpy().tobytes())
+    hsh.update(props.cpu().numpy().tobytes())
+    return hsh.hexdigest()
+
+
+def _measure(ctx, pos, vel, ids, n, steps, warmup, ws, local, form):
+    """W warm-up steps, then exactly `steps` steps timed with CUDA events on the launching
+    stream between barriers (no per-kernel instrumentation), clocks sampled meanwhile; then one
+    untimed profiled step (CUDA events around each dominant kernel) and, for the batched forms,
+    one untimed step through the counting variants of the pruned 6D kernels."""
+    import torch
+    import paper_2412_18629_gb300 as rs
+    stream = torch.cuda.current_stream()
+    last = {}
+
+    def step():
+        lab, _ = rs.rs_fof3d(ctx, pos, ids)
+        rs.rs_fof6d(ctx, pos, vel, ids, lab)
+        _, bound, nfb = rs.rs_unbind(ctx, pos, vel, want_potential=False)
+        props = rs.rs_halo_props(ctx)
+        last.update(lab=lab, bound=bound, props=props, nfb=nfb)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = ctx.kernel_launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        _barrier(ws)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        _barrier(ws)
+    launches = ctx.kernel_launches - l0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    digest = _digest(ctx, last["lab"], last["bound"], last["props"])
+    tree = rs.rs_tree_stats(ctx)
+    sur = rs.rs_surrogate_stats(ctx) if form.startswith("surrogate") else None
+    bound_host = last["bound"].cpu().numpy()
+    sizes = rs.rs_fof6d_copy(ctx)["size"].cpu().numpy()
+    # one profiled step (kernel shares), untimed
+    k0 = ctx.sort_keypasses
+    ctx.profile(True)
+    step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_totals()
+    ctx.profile(False)
+    keypasses = ctx.sort_keypasses - k0
+    work = None
+    if form != "plain":
+        ctx.count_work(True)
+        step()
+        work = ctx.count_work(False)
+    t_max, units = aggregate(elapsed, float(n) * steps, ws, f"cuda:{local}")
+    r = {"form": form, "value": units / t_max, "ms_per_step": t_max / steps * 1e3, "steps": steps,
+         "warmup": warmup, "launches": launches, "launches_per_step": launches / max(steps, 1),
+         "prof": prof, "clocks": clk.summary(), "fallback": last["nfb"], "work": work, "n": n,
+         "members": int(ctx.n_members), "nodes": int(ctx.n_nodes), "digest": digest,
+         "tree": tree, "surrogate_stats": sur, "sort_keypasses": keypasses,
+         "autotune": ctx.tuning(), "bound_host": bound_host}
+    tm = int(ctx.cfg.tree_min_members)
+    r["pairs"] = _sizes_work(sizes, "surrogate" if form.startswith("surrogate") else form,
+                             0 if form == "plain" or tm < 0 else (tm or TREE_MIN_DEFAULT))
+    return r
 
 
 TRAIN_SAMPLES = 1_000_000
 TRAIN_EPOCHS = 300
+TRAIN_WORKLOAD = "nfw-2^24-L256-sub"
 
 
 def train_surrogate(ctx, workload, device, samples=None, epochs=None):
     """Train the context's surrogate on the GPU, outside any timed region: exact potentials of
-    a snapshot drawn with the same generator and a disjoint seed (100), 10% held out."""
+    a snapshot drawn with the generator of `workload` and a disjoint seed (100), 10% held out."""
     import dataclasses
 
     import torch
@@ -323,7 +441,7 @@ def train_surrogate(ctx, workload, device, samples=None, epochs=None):
     p, v, i = (torch.from_numpy(s[k]).cuda() for k in ("pos", "vel", "ids"))
     lab, _ = rs.rs_fof3d(tctx, p, i)
     rs.rs_fof6d(tctx, p, v, i, lab)
-    rs.rs_unbind(tctx, p, v, want_potential=False)
+    rs.rs_unbind(tctx, p, v, want_potential=True)  # targets need every member's potential
     x, t = rs.rs_surrogate_features(tctx)
     k = min(x.shape[0], samples or TRAIN_SAMPLES)
     sel = torch.randperm(x.shape[0], generator=torch.Generator().manual_seed(100))[:k].cuda()
@@ -336,9 +454,20 @@ def train_surrogate(ctx, workload, device, samples=None, epochs=None):
     rs.rs_mlp_set_params(ctx, rs.rs_mlp_get_params(tctx))
     rs.rs_mlp_set_err_max(ctx, err_max)
     tctx.close()
+    del p, v, i
+    torch.cuda.empty_cache()
     return {"samples": int(k), "epochs": epochs, "err_max_psi": err_max, "last_batch_mse": mse,
-            "train_s": dt,
-            "snapshot": f"{workload} generator, seed 100"}
+            "train_s": dt, "snapshot": f"{workload} generator, seed 100"}
+
+
+def _form_entry(r, traffic):
+    return {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
+            "warmup": r["warmup"], "gpu_launches": r["launches"],
+            "launches_per_step": r["launches_per_step"], "fallback_members": r["fallback"],
+            "kernels_ms_profiled_step": {k: t[0] for k, t in r["prof"].items()},
+            "roofline": roofline(r, traffic), "stages": stages(r), "clocks": r["clocks"],
+            "autotune": r["autotune"], "tree_stats": r["tree"],
+            "surrogate_stats": r["surrogate_stats"], "output_digest": r["digest"]}
 
 
 def run_ours(args):
@@ -354,32 +483,40 @@ def run_ours(args):
     vel = torch.from_numpy(snap["vel"]).cuda()
     ids = torch.from_numpy(snap["ids"]).cuda()
     n = len(snap["ids"])
-    forms = ("plain", "batched", "surrogate") if args.form == "all" else (args.form,)
-    res, ctxs, training = {}, {}, None
-    for form in forms:
-        ctxs[form] = rs.Context(box=snap["box"], link_len=snap["link_length"],
-                                softening=snap["softening"], particle_mass=snap["particle_mass"],
-                                device=local, mode=form)
-        if form == "surrogate":
-            training = train_surrogate(ctxs[form], args.workload, local, args.train_samples,
-                                       args.train_epochs)
-        res[form] = _measure(ctxs[form], pos, vel, ids, n, args, ws, local)
-        if form == "surrogate":
-            res[form]["surrogate_stats"] = rs.rs_surrogate_stats(ctxs[form])
-    # headline: the fastest form (all forms give identical outputs)
-    head = max(res, key=lambda f: res[f]["value"])
-    ctx, r = ctxs[head], res[head]
-    for f in list(ctxs):  # the other forms' device buffers are released before the e2e timing
-        if f != head:
-            ctxs.pop(f).close()
-    torch.cuda.empty_cache()
+    traffic = _traffic_table().get(args.workload, {})
+    mk = dict(box=snap["box"], link_len=snap["link_length"], softening=snap["softening"],
+              particle_mass=snap["particle_mass"], device=local)
+    res, training = {}, None
+    # headline: batched + surrogate at the requested step counts
+    ctx = rs.Context(mode="surrogate", **mk)
+    training = train_surrogate(ctx, args.train_workload, local, args.train_samples, args.train_epochs)
+    res["surrogate"] = _measure(ctx, pos, vel, ids, n, args.steps, args.warmup, ws, local, "surrogate")
+    # the other forms, each with its own stated step counts: batched (exact flags), the
+    # surrogate with the per-node calibrated gate (opt-in), plain
+    others = [] if args.form == "surrogate" else [
+        ("batched", args.batched_steps, args.batched_warmup),
+        ("surrogate_calibrated", args.calibrated_steps, 1),
+        ("plain", args.plain_steps, args.plain_warmup)]
+    for form, k, w in others:
+        if k <= 0:
+            continue
+        if form == "surrogate_calibrated":
+            c = rs.Context(mode="surrogate", surrogate_gate=1, **mk)
+            rs.rs_mlp_set_params(c, rs.rs_mlp_get_params(ctx))
+            rs.rs_mlp_set_err_max(c, training["err_max_psi"])
+        else:
+            c = rs.Context(mode=form, **mk)
+        res[form] = _measure(c, pos, vel, ids, n, k, w, ws, local, form)
+        c.close()
+        torch.cuda.empty_cache()
+    r = res["surrogate"]
     # ---- end to end through the public API with host buffers (headline form)
     pin = {k: torch.from_numpy(snap[k]).pin_memory() for k in ("pos", "vel", "ids")}
     h2d = sum(t.numel() * t.element_size() for t in pin.values())
     e_pos, e_vel, e_ids = (torch.empty_like(pos), torch.empty_like(vel), torch.empty_like(ids))
     out_lab = torch.empty(n, dtype=torch.int64).pin_memory()
-    out_bound = torch.empty(ctx.n_members, dtype=torch.uint8).pin_memory()
-    out_props = torch.empty((ctx.n_nodes, 8 * rs.PROPS_FIELDS), dtype=torch.uint8).pin_memory()
+    out_bound = torch.empty(r["members"] + 1, dtype=torch.uint8).pin_memory()
+    out_props = torch.empty((r["nodes"] + 1, 8 * rs.PROPS_FIELDS), dtype=torch.uint8).pin_memory()
     main = torch.cuda.current_stream()
     side = torch.cuda.Stream()
 
@@ -410,69 +547,82 @@ def run_ours(args):
 
     e2e_step()
     torch.cuda.synchronize()
+    e_steps = max(1, min(args.steps, int(args.e2e_seconds * 1e3 / max(r["ms_per_step"], 1e-3))))
     _barrier(ws)
     e0 = time.perf_counter()
     d2h = 0
-    for _ in range(args.steps):
+    for _ in range(e_steps):
         d2h = e2e_step()
     torch.cuda.synchronize()
     e_el = time.perf_counter() - e0
-    e_max, e_units = aggregate(e_el, float(n) * args.steps, ws, f"cuda:{local}")
+    e_max, e_units = aggregate(e_el, float(n) * e_steps, ws, f"cuda:{local}")
+    ctx.close()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        ns, dt = time_oracle(snap, threads)
-        cpu = {"value": ns / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"particles in the sub-volume [0, {ORACLE_SUBBOX} L)^3 of the same "
-                         f"snapshot ({ns} particles, {dt:.1f} s): FoF, hierarchy, unbinding, props"}
+        tot_n, tot_t = 0, 0.0
+        cubes = _oracle_cubes(snap)
+        for cube in cubes:
+            ns, dt = time_oracle(snap, threads, cube)
+            tot_n += ns
+            tot_t += dt
+        cpu = {"value": tot_n / tot_t, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(cubes)} cubes of side L/{ORACLE_CUBES} of the same snapshot "
+                         f"(those around the median halo load sum n^2), {tot_n} particles, "
+                         f"{tot_t:.1f} s: FoF, hierarchy, unbinding, props"}
     if rank == 0:
+        ident = {f: v["digest"] == r["digest"] for f, v in res.items()}
+        exact = res.get("batched")
+        mism = ({f: int(np.count_nonzero(v["bound_host"] != exact["bound_host"]))
+                 for f, v in res.items() if f.startswith("surrogate")} if exact else None)
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "box": snap["box"], "seed": spec.seed,
-                       "form": head, "nodes": int(ctx.n_nodes), "members": int(ctx.n_members),
-                       "pairs": r["pairs"], "l2": "inputs and hierarchy larger than L2 (no flush)",
+                       "form": "surrogate (batched + surrogate)", "nodes": r["nodes"],
+                       "members": r["members"], "pairs": r["pairs"]["pairs_all"],
+                       "l2": "inputs and hierarchy larger than L2 (no flush)",
                        "parallelism": f"independent snapshots x{ws}"},
-            "roofline": _roofline(r["prof"], r["pairs"], args.steps, r["work"]), "cpu_baseline": cpu,
+            "roofline": roofline(r, traffic), "cpu_baseline": cpu,
             "e2e": {"value": e_units / e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": r["launches"], "clocks": r["clocks"], "surrogate_training": training,
-            "forms": {f: {"value": v["value"], "ms_per_step": v["ms_per_step"],
-                          "gpu_launches": v["launches"], "fallback_members": v["fallback"],
-                          "kernels_ms_per_step": {k: t[0] / args.steps for k, t in v["prof"].items()},
-                          "roofline": _roofline(v["prof"], v["pairs"], args.steps, v["work"]),
-                          "stages": _stages(dict(v, form=f), args.steps),
-                          "clocks": v["clocks"],
-                          "autotune": v.get("autotune"),
-                          "surrogate_stats": v.get("surrogate_stats")}
-                      for f, v in res.items()},
+                    "d2h_bytes_per_step": d2h, "steps": e_steps},
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "plain_ms_per_step": res["plain"]["ms_per_step"] if "plain" in res else None,
+            "plain_value": res["plain"]["value"] if "plain" in res else None,
+            "batched_ms_per_step": res["batched"]["ms_per_step"] if "batched" in res else None,
+            "identical_outputs": ident,
+            "surrogate_flag_mismatches_vs_batched": mism,
+            "surrogate_training": training,
+            "forms": {f: _form_entry(v, traffic) for f, v in res.items()},
         }
         print(json.dumps(line), flush=True)
-    for c in ctxs.values():
-        c.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, one sample cube of the workload per step
+    (cycling through the median-load cubes), on this machine's host cores."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     spec, snap = _snapshot(args.workload, 0)
     threads = os.cpu_count() or 1
-    for _ in range(args.warmup):
-        time_oracle(snap, threads)
+    cubes = _oracle_cubes(snap)
+    for i in range(args.warmup):
+        time_oracle(snap, threads, cubes[i % len(cubes)])
     tot_n, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        ns, dt = time_oracle(snap, threads)
+    for i in range(args.steps):
+        ns, dt = time_oracle(snap, threads, cubes[i % len(cubes)])
         tot_n += ns
         tot_t += dt
     value = tot_n / tot_t
-    sample = (f"particles in the sub-volume [0, {ORACLE_SUBBOX} L)^3 of the same snapshot "
-              f"({tot_n // max(args.steps, 1)} per step)")
+    sample = (f"one cube of side L/{ORACLE_CUBES} of the same snapshot per step, cycling through "
+              f"the {len(cubes)} cubes around the median halo load ({tot_n // max(args.steps, 1)} "
+              f"particles per step on average)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
@@ -492,12 +642,19 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", choices=("plain", "batched", "surrogate", "all"), default="all")
-    ap.add_argument("--train-samples", type=int, default=1_000_000)
+    ap.add_argument("--form", choices=("surrogate", "all"), default="all",
+                    help="surrogate: time the headline form only")
+    ap.add_argument("--batched-steps", type=int, default=2)
+    ap.add_argument("--batched-warmup", type=int, default=1)
+    ap.add_argument("--calibrated-steps", type=int, default=2)
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--plain-warmup", type=int, default=1)
+    ap.add_argument("--e2e-seconds", type=float, default=30.0,
+                    help="end-to-end timing: as many steps (at most --steps) as fit in this time")
+    ap.add_argument("--train-workload", default=TRAIN_WORKLOAD)
+    ap.add_argument("--train-samples", type=int, default=TRAIN_SAMPLES)
     ap.add_argument("--train-epochs", type=int, default=TRAIN_EPOCHS)
     args = ap.parse_args(argv)
-    if args.warmup < 3 and args.impl == "ours":
-        args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -52,8 +52,8 @@ typedef struct rs_config {
   float link_len;             /* 3D linking length ll; pairs with d^2 <= ll*ll are linked */
   float softening;            /* Plummer softening eps of the potential (Mpc/h) */
   float margin_factor;        /* surrogate gate: classify iff |E_pred| > margin_factor *
-                                 err_node * G M / r_vir (4); err_node is the node's
-                                 calibrated surrogate error (see rs_surrogate_stats) */
+                                 err * G M / r_vir (4); err is the surrogate's held-out maximum
+                                 error (or the per-node calibrated one, surrogate_gate = 1) */
   double particle_mass;       /* m (Msun/h), equal for all particles */
   double G;                   /* gravitational constant, 4.30091e-9 Mpc (km/s)^2 / Msun */
   int32_t f_num, f_den;       /* linked fraction f = f_num / f_den of the 6D FoF (7, 10) */
@@ -65,6 +65,13 @@ typedef struct rs_config {
   int32_t use_surrogate;      /* 1: rs_unbind gates members of nodes with >= 1024 members by
                                  the trained MLP (batched + surrogate form) */
   int32_t spot_check;         /* gated members per node re-checked exactly (32) */
+  int32_t tree_min_members;   /* batched forms: nodes with at least this many members get their
+                                 flags from the certified tree bound (see rs_tree_stats) when
+                                 rs_unbind is asked for no potential; 0 = 16384, < 0 = never */
+  float tree_theta;           /* opening angle of that bound (0 = 0.5; at most 0.9) */
+  int32_t surrogate_gate;     /* 0: the error in the gate is the held-out maximum error of the
+                                 training (rs_mlp_set_err_max); 1: per node, calibrated on 64
+                                 members evaluated exactly, floored at err_max / 8 */
 } rs_config;
 
 /* Per-node halo properties written by rs_halo_props (all over the node's BOUND members). */
@@ -84,8 +91,10 @@ typedef struct rs_halo_props_t {
 
 typedef struct rs_ctx rs_ctx;
 
-/* Create a context on CUDA device `device` with a copy of *cfg. Validates cfg
- * (box_L > 0, 0 < link_len < box_L / 5... see rs_fof3d, f_num in (0, f_den], min >= 2).
+/* Create a context on CUDA device `device` with a copy of *cfg. Validates cfg: box_L > 0,
+ * link_len > 0 (rs_fof3d rejects a box of more than 4096 sub-cells per axis), softening >= 0,
+ * particle_mass > 0, G > 0, 0 < f_num <= f_den, min_halo_particles >= 2, bound_num >= 0,
+ * bound_den > 0, 0 <= tree_theta <= 0.9, surrogate_gate 0 or 1, spot_check >= 0.
  * out: host pointer receiving the context. No device memory is allocated yet. */
 int rs_ctx_create(rs_ctx** out, const rs_config* cfg, int device);
 
@@ -97,6 +106,10 @@ const char* rs_last_error(rs_ctx* ctx);
 
 /* Number of kernels this context has launched since it was created (host counter). */
 int64_t rs_kernel_launches(rs_ctx* ctx);
+
+/* Keys moved by radix-sort passes (one pass = one 8-bit digit over n keys) since the context
+ * was created (host counter; instrumentation for the sort's bandwidth figure). */
+int64_t rs_sort_keypasses(rs_ctx* ctx);
 
 /* 3D friends-of-friends (Section "Parallelization"). Particles i and j are linked iff
  *   d = x_j - x_i (float32, per dimension), wrapped once: d > L/2 -> d - L, d < -L/2 -> d + L;
@@ -167,6 +180,31 @@ int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float* potential_
  * props_out: rs_halo_props_t [n_nodes] device. Errors: RS_ERR_STATE, RS_ERR_CUDA. */
 int rs_halo_props(rs_ctx* ctx, rs_halo_props_t* props_out, void* stream);
 
+/* ---- Certified tree bound of the potential (batched forms) ---------------------------------
+ * For nodes with at least tree_min_members members, rs_unbind (called with potential_out NULL)
+ * decides most flags from a certified interval of each member's potential sum
+ * S_i = sum_{j != i} (|u_j - u_i|^2 + eps^2)^(-1/2) instead of the O(g) direct sum: a
+ * Barnes-Hut walk over a Morton-ordered tree of the node (leaves of 32 members, 8 children per
+ * cell) takes a cell as its quadrupole expansion when its radius bound a is at most tree_theta
+ * times the softened distance R', and adds the rigorous truncation bound (n/R') h^3 / (1 - h),
+ * h = a / R' (Legendre expansion of the softened kernel, |P_l| <= 1); float32 rounding is
+ * covered by a 1e-5 relative slack. A member is decided when the whole interval of
+ * E = KE - G m S lies on one side of zero; the others take the exact path (blocked float32 sum
+ * with its certified bound, then the float64 canonical-order potential). Flags are therefore
+ * identical to the direct sum's. The paper computes the exact potential; this is the build's
+ * O(g log g) potential for nodes of 10^5 - 10^6 members (the next step after the exact kernel).
+ *
+ * rs_tree_stats: host int64 [8] of the last rs_unbind: tree nodes, their members, members
+ * decided by the bound, members sent to the exact path, cell expansions evaluated, direct pair
+ * terms evaluated by the walk, pair terms of the exact list sums (tree and surrogate paths), 0.
+ * rs_tree_record(ctx, 1): later rs_unbind calls also record every bounded member's interval;
+ * rs_tree_bounds then copies them out: lo_out, hi_out float64 [n_members] device (member CSR
+ * order), NaN for members whose flag did not come from the bound walk. Errors: RS_ERR_STATE when
+ * the last rs_unbind recorded nothing. Instrumentation for tests, not part of the method. */
+int rs_tree_stats(rs_ctx* ctx, int64_t* stats_out);
+int rs_tree_record(rs_ctx* ctx, int enable);
+int rs_tree_bounds(rs_ctx* ctx, double* lo_out, double* hi_out, void* stream);
+
 /* Float64 sum of a[0..m) in the canonical reduction order every float64 sum of the path uses
  * (chunks of 1024; lane l of a chunk adds terms l, l+32, ... in order; lanes combine by the
  * halving tree; chunk totals by the level-by-level pairwise tree, odd element carried up).
@@ -191,11 +229,14 @@ int rs_cro_sum_noalloc(int64_t m, const double* a, double* out, void* stream);
  * A small MLP predicts psi = phi r_vir / (G M_node) from 8 per-member features; members whose
  * predicted energy clears a margin are classified without the O(n^2) potential, the rest (and
  * any node failing a spot check) take the exact path. The paper has no learned component; this
- * is the build's batched + surrogate form. Per node with >= 1024 members, rs_unbind: evaluates
- * 64 evenly spaced members exactly (held out of the gate) and takes err_node = max(max
- * |psi_hat - psi| over them, err_max / 8); gates |E_pred| > margin_factor * err_node * G M /
- * r_vir; re-checks exactly the spot_check gated members of smallest margin and recomputes the
- * whole node exactly if one flag differs or one error exceeds margin_factor / 2 * err_node.
+ * is the build's batched + surrogate form. Per node with >= 1024 members, rs_unbind gates
+ * |E_pred| > margin_factor * err * G M / r_vir with err = err_max, the held-out maximum error of
+ * the training (surrogate_gate = 0), or err = max(max |psi_hat - psi| over 64 evenly spaced
+ * members evaluated exactly, err_max / 8) (surrogate_gate = 1). It then re-checks exactly the
+ * spot_check gated members of smallest margin plus about spot_check more sampled at every
+ * margin, and recomputes the whole node exactly if one flag differs or one error exceeds
+ * margin_factor / 2 * err. Zero flag mismatches is measured on held-out snapshots, not
+ * guaranteed.
  * Network (8 -> 64 -> 64 -> 1, ReLU), bf16 weights and hidden activations, float32
  * accumulation on tensor cores:
  *   z1 = b1 + W1^T bf16(x); h1 = bf16(relu(z1)); z2 = b2 + W2^T h1; h2 = bf16(relu(z2));
@@ -207,8 +248,8 @@ int rs_cro_sum_noalloc(int64_t m, const double* a, double* out, void* stream);
 /* Load (host float32 [4801]) or read back the context's float32 master parameters. */
 int rs_mlp_set_params(rs_ctx* ctx, const float* params_host);
 int rs_mlp_get_params(rs_ctx* ctx, float* params_host);
-/* Held-out maximum |psi_hat - psi| from training (set by rs_mlp_train, or by the caller); the
- * gate uses err_max / 8 as the floor of every node's calibrated error. */
+/* Held-out maximum |psi_hat - psi| from training (set by rs_mlp_train, or by the caller): the
+ * error of the default gate (and err_max / 8 the floor of the calibrated gate's node error). */
 int rs_mlp_set_err_max(rs_ctx* ctx, float err_max);
 
 /* Inference: x float32 [n][8] device -> y float32 [n] device. */
@@ -231,23 +272,25 @@ int rs_mlp_train(rs_ctx* ctx, int64_t n, const float* x, const float* t, int32_t
 /* Surrogate features of the members of every node with >= 1024 members, after rs_unbind:
  * feat_out float32 [n_members][8] device (room for all members; the first *n_out rows are
  * written, node after node, members in id order): r/r_vir (r from the node's mean position),
- * fractions of the node's members with radius below 0.5 r, r and 2 r, psi_mp (the node's
- * potential at the member from the radially split multipole expansion to quadrupole order,
- * in units of G g m / r_vir), |v - v_bulk| / sigma_v,1D, log10 g, log10(g_deep / g) (g_deep:
- * size of the deepest hierarchy node holding the member).
+ * fractions of the node's members with radius below 0.5 r, r, 2 r and 4 r, |v - v_bulk| /
+ * sigma_v,1D, log10 g, and psi_mp (the node's potential at the member from the radially split
+ * multipole expansion to quadrupole order, in units of G g m / r_vir).
  * psi_out float32 [n_members] device or NULL: training target
  * psi = phi r_vir / (G g m) from the last rs_unbind's float32 potential (that rs_unbind must
- * not have used the surrogate). n_out: host. Errors: RS_ERR_STATE, RS_ERR_OOM, RS_ERR_CUDA. */
+ * have computed every member's potential: no surrogate, and potential_out given so that the
+ * certified tree bound was not used). n_out: host. Errors: RS_ERR_STATE, RS_ERR_OOM,
+ * RS_ERR_CUDA. */
 int rs_surrogate_features(rs_ctx* ctx, float* feat_out, float* psi_out, int64_t* n_out,
                           void* stream);
 
-/* Counters of the last rs_unbind (host int64 [10]): members of surrogate nodes, gated by the
+/* Counters of the last rs_unbind (host int64 [11]): members of surrogate nodes, gated by the
  * surrogate, evaluated exactly (calibration members and the members outside the gate, in
  * nodes not sent whole), spot-checked, nodes failing the spot check, float64 fallbacks in the
  * surrogate path, float64 fallbacks of the direct sums, gated members recomputed because their
- * node failed, members of nodes sent whole to the direct sum (at most 1/20 of their members
- * gated), members whose flag the surrogate decided. Members = decided + exact + spot-checked +
- * recomputed + whole-node. */
+ * node failed, members of nodes sent whole to the exact path (at most 1/20 of their members
+ * gated), members whose flag the surrogate decided, spot-checked members whose surrogate flag
+ * differed from the exact one. Members = decided + exact + spot-checked + recomputed +
+ * whole-node (the calibration members are counted in exact). */
 int rs_surrogate_stats(rs_ctx* ctx, int64_t* stats_out);
 
 /* Stable LSD radix sort of (key, value) pairs by key bits [0, nbits), in place: the sort that

@@ -14,9 +14,12 @@ tests named here):
 * cro_sum: exactly rounded sums (math.fsum) within the recursive-summation bound, hand-derived
   order-sensitive cases (tests/test_oracle_cro.py).
 * split_node / hierarchy: invariants (linked fraction, subsets, disjointness, sizes), exact
-  velocity-scaling invariance, two-blob special cases (tests/test_oracle_hierarchy.py).
+  velocity-scaling invariance, two-blob special cases, SciPy k-d tree nearest neighbours; the
+  exactly pruned k-d tree search of large nodes against the all-pairs search, bit for bit
+  (tests/test_oracle_hierarchy.py, tests/test_oracle_pruned.py).
 * unbind: two-body, centre-of-sphere and cube closed forms, Plummer and uniform-sphere profiles,
-  bound/unbound limits (tests/test_oracle_unbind.py).
+  bound/unbound limits (tests/test_oracle_unbind.py); unbind_sample equals unbind at the sampled
+  members (tests/test_oracle_pruned.py).
 * props: lattice moments and inertia in closed form, centre wrapping (tests/test_oracle_props.py).
 * mlp_forward / mlp_gradient: finite differences of the float64 form, zero-weight and linear
   special cases, bf16 rounding of exactly representable values (tests/test_oracle_mlp.py).
@@ -65,11 +68,14 @@ def _load():
         lib.or_cro_sum.argtypes = [P, i64]
         lib.or_cro_sum.restype = f64
         lib.or_split_node.argtypes = [i64, P, P, i32, i32, P, P, P]
+        lib.or_split_node_ex.argtypes = [i64, P, P, i32, i32, i32, i32, P, P, P]
+        lib.or_unbind_sample.argtypes = [i64, P, P, P, f32, f32, f64, f64, i64, P, i32, P, P]
         lib.or_hierarchy.argtypes = [i64, P, P, P, P, f32, i32, i32, i32, i32,
                                      ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.or_hierarchy.restype = P
         lib.or_hierarchy_copy.argtypes = [P, P, P, P, P, P, P, P]
         lib.or_hierarchy_free.argtypes = [P]
+        lib.or_hierarchy_params.argtypes = [P, P]
         lib.or_unbind.argtypes = [i64, P, P, P, P, f32, f32, f64, f64, i32, i32, i32, i32,
                                   P, P, P, P, P]
         lib.or_props.argtypes = [i64, P, P, P, P, P, P, f32, f64, i64, i32, P]
@@ -117,20 +123,24 @@ def cro_sum(a):
     return float(_load().or_cro_sum(_p(a), len(a)))
 
 
-def split_node(u, v, f_num=7, f_den=10):
-    """One 6D FoF level on a single node: (inv_sx2, inv_sv2, l2, nn2[g], comp[g])."""
+def split_node(u, v, f_num=7, f_den=10, pruned=-1, threads=1):
+    """One 6D FoF level on a single node: (inv_sx2, inv_sv2, l2, nn2[g], comp[g]).
+    pruned: 0 all pairs, 1 the exactly pruned k-d tree search, -1 by size (tree above 4096
+    members); threads: the tree search's member loops."""
     u, v = _c(u, np.float32), _c(v, np.float32)
     g = len(u)
     scal = np.empty(3, np.float32)
     nn2 = np.empty(g, np.float32)
     comp = np.empty(g, np.int64)
-    rc = _load().or_split_node(g, _p(u), _p(v), f_num, f_den, _p(scal), _p(nn2), _p(comp))
+    rc = _load().or_split_node_ex(g, _p(u), _p(v), f_num, f_den, int(pruned), _threads(threads),
+                                  _p(scal), _p(nn2), _p(comp))
     assert rc == 0
     return float(scal[0]), float(scal[1]), float(scal[2]), nn2, comp
 
 
 def hierarchy(pos, vel, ids, fof_label, box, f_num=7, f_den=10, min_size=10, threads=None):
-    """6D FoF hierarchy. Returns a dict of node arrays, member CSR and per-particle deepest node."""
+    """6D FoF hierarchy. Returns a dict of node arrays, member CSR, per-particle deepest node
+    and each node's split parameters (params: inv_sx2, inv_sv2, l2)."""
     pos, vel = _c(pos, np.float32), _c(vel, np.float32)
     ids, lab = _c(ids, np.int64), _c(fof_label, np.int64)
     lib = _load()
@@ -149,6 +159,8 @@ def hierarchy(pos, vel, ids, fof_label, box, f_num=7, f_den=10, min_size=10, thr
         rc = lib.or_hierarchy_copy(h, *(_p(out[k]) for k in (
             "parent", "level", "min_id", "size", "member_off", "member_idx", "deepest")))
         assert rc == 0
+        out["params"] = np.empty((n_nodes, 3), np.float32)
+        assert lib.or_hierarchy_params(h, _p(out["params"])) == 0
     finally:
         lib.or_hierarchy_free(h)
     return out
@@ -170,6 +182,19 @@ def unbind(member_off, member_idx, pos, vel, box, eps, G, m, min_size=10, bf_num
                            _p(nb), _p(halo), _p(mb))
     assert rc == 0
     return {"phi": phi, "bound": bound, "n_bound": nb, "is_halo": halo, "m_bound": mb}
+
+
+def unbind_sample(mem, pos, vel, box, eps, G, m, sample, threads=None):
+    """Potential (float64) and bound flag of the members sample[k] (positions in mem) of the
+    node whose particles are mem (ascending id), by or_unbind's definition."""
+    mem, sample = _c(mem, np.int64), _c(sample, np.int64)
+    pos, vel = _c(pos, np.float32), _c(vel, np.float32)
+    phi = np.empty(len(sample), np.float64)
+    bound = np.empty(len(sample), np.uint8)
+    rc = _load().or_unbind_sample(len(mem), _p(mem), _p(pos), _p(vel), box, eps, G, m,
+                                  len(sample), _p(sample), _threads(threads), _p(phi), _p(bound))
+    assert rc == 0
+    return phi, bound
 
 
 def props(member_off, member_idx, pos, vel, bound, is_halo, box, m, n_total, threads=None):

@@ -151,6 +151,7 @@ struct Node {
   int64_t min_id;
   int64_t size;
   int64_t off;  // into the member list
+  float scal[3] = {0.f, 0.f, 0.f};  // inv_sx2, inv_sv2, l2 of the node's split
 };
 
 struct Hierarchy {
@@ -201,31 +202,165 @@ struct SplitResult {
   std::vector<int64_t> comp;  // per member: smallest member position of its 6D component
 };
 
+// ---------------------------------------------------------------------------------------------
+// Exactly pruned 6D searches for large nodes: the same nearest-neighbour distances and the
+// same link graph as the all-pairs loops, found with a k-d tree. Points are scaled into the
+// space where the plain squared Euclidean distance is the 6D metric,
+// P = (u sqrt(inv_sx2), v sqrt(inv_sv2)) in float64. The float32 d6 of the definition is a
+// handful of correctly rounded operations away from that exact distance (relative error below
+// 1e-6), so a tree cell whose float64 lower bound exceeds (1 + 1e-5) times the current best
+// (or l2), plus 1e-30 for underflow, cannot hold a member whose float32 d6 is at most the best:
+// pruning never removes the minimum or a link, and every value used is the definition's float32
+// d6. Cells are split at the median of their widest coordinate down to 16 points.
+struct KdTree {
+  struct Cell {
+    double lo[6], hi[6];
+    int64_t a, b;             // point range [a, b) in idx
+    int64_t left = -1, right = -1;
+  };
+  std::vector<double> P;      // [g][6]
+  std::vector<int64_t> idx;   // point order
+  std::vector<Cell> cells;
+
+  KdTree(const float* u, const float* v, int64_t g, float isx, float isv) : P(6 * g), idx(g) {
+    const double sx = std::sqrt(double(isx)), sv = std::sqrt(double(isv));
+    for (int64_t i = 0; i < g; ++i) {
+      for (int d = 0; d < 3; ++d) {
+        P[6 * i + d] = double(u[3 * i + d]) * sx;
+        P[6 * i + 3 + d] = double(v[3 * i + d]) * sv;
+      }
+      idx[i] = i;
+    }
+    cells.reserve(size_t(2 * (g / 8 + 1)));
+    build(0, g);
+  }
+
+  int64_t build(int64_t a, int64_t b) {
+    Cell c;
+    c.a = a;
+    c.b = b;
+    for (int d = 0; d < 6; ++d) {
+      c.lo[d] = INFINITY;
+      c.hi[d] = -INFINITY;
+    }
+    for (int64_t k = a; k < b; ++k)
+      for (int d = 0; d < 6; ++d) {
+        c.lo[d] = std::min(c.lo[d], P[6 * idx[k] + d]);
+        c.hi[d] = std::max(c.hi[d], P[6 * idx[k] + d]);
+      }
+    const int64_t id = int64_t(cells.size());
+    cells.push_back(c);
+    if (b - a > 16) {
+      int w = 0;
+      for (int d = 1; d < 6; ++d)
+        if (c.hi[d] - c.lo[d] > c.hi[w] - c.lo[w]) w = d;
+      const int64_t mid = a + (b - a) / 2;
+      std::nth_element(idx.begin() + a, idx.begin() + mid, idx.begin() + b,
+                       [&](int64_t x, int64_t y) { return P[6 * x + w] < P[6 * y + w]; });
+      const int64_t l = build(a, mid);
+      const int64_t r = build(mid, b);
+      cells[id].left = l;
+      cells[id].right = r;
+    }
+    return id;
+  }
+
+  double lower_bound(int64_t c, int64_t i) const {
+    double s = 0.0;
+    for (int d = 0; d < 6; ++d) {
+      const double x = P[6 * i + d];
+      const double gap = x < cells[c].lo[d] ? cells[c].lo[d] - x
+                                            : (x > cells[c].hi[d] ? x - cells[c].hi[d] : 0.0);
+      s += gap * gap;
+    }
+    return s;
+  }
+
+  // Visit every point j of the cells whose lower bound from point i is at most
+  // *limit (1 + 1e-5) + 1e-30; *limit is re-read before each cell, so a shrinking best prunes more.
+  template <class Visit>
+  void search(int64_t i, const float* limit, Visit visit) const {
+    std::vector<int64_t> stack{0};
+    while (!stack.empty()) {
+      const int64_t c = stack.back();
+      stack.pop_back();
+      if (lower_bound(c, i) > double(*limit) * (1.0 + 1e-5) + 1e-30) continue;
+      if (cells[c].left < 0) {
+        for (int64_t k = cells[c].a; k < cells[c].b; ++k) visit(idx[k]);
+        continue;
+      }
+      const int64_t l = cells[c].left, r = cells[c].right;
+      if (lower_bound(l, i) <= lower_bound(r, i)) {  // nearer child on top of the stack
+        stack.push_back(r);
+        stack.push_back(l);
+      } else {
+        stack.push_back(l);
+        stack.push_back(r);
+      }
+    }
+  }
+};
+
+// Nodes above this size use the pruned searches, with their members spread over threads.
+constexpr int64_t kPrunedMin = 4096;
+
 // One level of 6D FoF on a node whose members (ascending id) have unwrapped positions u and
 // velocities v: sigma from CRO moments, nearest-neighbour distances, the adaptive link length
-// (the k-th smallest nn2 with k = ceil(f g) - 1), and the components of the link graph.
+// (the k-th smallest nn2 with k = ceil(f g) - 1), and the components of the link graph. All
+// pairs when g <= kPrunedMin (pruned < 0) or pruned == 0, the k-d tree otherwise.
 void split_node(const float* u, const float* v, int64_t g, int32_t f_num, int32_t f_den,
-                SplitResult& out) {
+                SplitResult& out, int threads = 1, int pruned = -1) {
   out.inv_sx2 = inv_or_zero(total_variance(u, g));
   out.inv_sv2 = inv_or_zero(total_variance(v, g));
   out.nn2.assign(g, INFINITY);
-  for (int64_t i = 0; i < g; ++i) {
-    float best = INFINITY;
-    for (int64_t j = 0; j < g; ++j) {
-      if (j == i) continue;
-      const float d = d6(u, v, i, j, out.inv_sx2, out.inv_sv2);
-      if (d < best) best = d;
-    }
-    out.nn2[i] = best;
-  }
+  const bool use_tree = pruned < 0 ? g > kPrunedMin : pruned != 0;
   const int64_t k = (int64_t(f_num) * g + f_den - 1) / f_den - 1;
-  std::vector<float> sorted(out.nn2);
-  std::nth_element(sorted.begin(), sorted.begin() + k, sorted.end());
-  out.l2 = sorted[k];
   UnionFind uf(g);
-  for (int64_t i = 0; i < g; ++i)
-    for (int64_t j = i + 1; j < g; ++j)
-      if (d6(u, v, i, j, out.inv_sx2, out.inv_sv2) <= out.l2) uf.unite(i, j);
+  if (!use_tree) {
+    for (int64_t i = 0; i < g; ++i) {
+      float best = INFINITY;
+      for (int64_t j = 0; j < g; ++j) {
+        if (j == i) continue;
+        const float d = d6(u, v, i, j, out.inv_sx2, out.inv_sv2);
+        if (d < best) best = d;
+      }
+      out.nn2[i] = best;
+    }
+    std::vector<float> sorted(out.nn2);
+    std::nth_element(sorted.begin(), sorted.begin() + k, sorted.end());
+    out.l2 = sorted[k];
+    for (int64_t i = 0; i < g; ++i)
+      for (int64_t j = i + 1; j < g; ++j)
+        if (d6(u, v, i, j, out.inv_sx2, out.inv_sv2) <= out.l2) uf.unite(i, j);
+  } else {
+    const KdTree tree(u, v, g, out.inv_sx2, out.inv_sv2);
+    parallel_for(g, threads, [&](int64_t i) {
+      float best = INFINITY;
+      tree.search(i, &best, [&](int64_t j) {
+        if (j == i) return;
+        const float d = d6(u, v, i, j, out.inv_sx2, out.inv_sv2);
+        if (d < best) best = d;
+      });
+      out.nn2[i] = best;
+    });
+    std::vector<float> sorted(out.nn2);
+    std::nth_element(sorted.begin(), sorted.begin() + k, sorted.end());
+    out.l2 = sorted[k];
+    // link pairs (i < j) collected per thread, then united in one thread
+    const int nt = int(std::max<int64_t>(1, std::min<int64_t>(threads, g)));
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> edges(nt);
+    const float l2 = out.l2;
+    parallel_for(nt, nt, [&](int64_t t) {
+      for (int64_t i = t; i < g; i += nt) {
+        if (out.nn2[i] > l2) continue;  // no other member is within l2
+        tree.search(i, &l2, [&](int64_t j) {
+          if (j > i && d6(u, v, i, j, out.inv_sx2, out.inv_sv2) <= l2) edges[t].emplace_back(i, j);
+        });
+      }
+    });
+    for (auto& e : edges)
+      for (auto& pr : e) uf.unite(pr.first, pr.second);
+  }
   out.comp.resize(g);
   for (int64_t i = 0; i < g; ++i) out.comp[i] = uf.find(i);
 }
@@ -281,7 +416,7 @@ Hierarchy* build_hierarchy(int64_t n, const float* pos, const float* vel, const 
     const int64_t level_end = int64_t(h->nodes.size());
     const int64_t count = level_end - level_begin;
     std::vector<std::vector<std::vector<int64_t>>> kids(count);
-    parallel_for(count, threads, [&](int64_t q) {
+    auto split_one = [&](int64_t q, int inner_threads) {
       const Node nd = h->nodes[level_begin + q];
       const int64_t* mem = h->members.data() + nd.off;
       std::vector<float> u, v(3 * nd.size);
@@ -289,9 +424,19 @@ Hierarchy* build_hierarchy(int64_t n, const float* pos, const float* vel, const 
       for (int64_t a = 0; a < nd.size; ++a)
         for (int d = 0; d < 3; ++d) v[3 * a + d] = vel[3 * mem[a] + d];
       SplitResult sr;
-      split_node(u.data(), v.data(), nd.size, f_num, f_den, sr);
+      split_node(u.data(), v.data(), nd.size, f_num, f_den, sr, inner_threads);
       kids[q] = children_of(sr, nd.size, min_size);
+      float* sc = h->nodes[level_begin + q].scal;
+      sc[0] = sr.inv_sx2;
+      sc[1] = sr.inv_sv2;
+      sc[2] = sr.l2;
+    };
+    // small nodes: one per thread; large nodes one after another, each over all threads
+    parallel_for(count, threads, [&](int64_t q) {
+      if (h->nodes[level_begin + q].size <= kPrunedMin) split_one(q, 1);
     });
+    for (int64_t q = 0; q < count; ++q)
+      if (h->nodes[level_begin + q].size > kPrunedMin) split_one(q, threads);
     for (int64_t q = 0; q < count; ++q) {
       const int64_t parent = level_begin + q;
       for (auto& kid : kids[q]) {
@@ -310,12 +455,45 @@ Hierarchy* build_hierarchy(int64_t n, const float* pos, const float* vel, const 
   return h;
 }
 
+// Bulk velocity of a node: CRO(v_d) / g per axis.
+void bulk_velocity(const float* vel, const int64_t* mem, int64_t g, double* vb) {
+  for (int d = 0; d < 3; ++d)
+    vb[d] = cro_sum(g, [&](int64_t a) { return double(vel[3 * mem[a] + d]); }) / double(g);
+}
+
+// Potential and flag of member i of a node (unwrapped positions u, bulk velocity vb):
+//   phi_i = -(G m) CRO_j( j == i ? 0 : 1 / sqrt(((Dx Dx + Dy Dy) + Dz Dz) + eps^2) ),
+//   D = (double)u_j - (double)u_i; KE_i = 0.5 ((dvx dvx + dvy dvy) + dvz dvz),
+//   dv = (double)v_i - vb; bound iff KE_i + phi_i < 0.
+bool member_energy(const float* u, const float* vel, const int64_t* mem, int64_t g, int64_t i,
+                   const double* vb, double eps2, double Gm, double* phi_out) {
+  const double s = cro_sum(g, [&](int64_t j) {
+    if (j == i) return 0.0;
+    const double dx = double(u[3 * j]) - double(u[3 * i]);
+    const double dy = double(u[3 * j + 1]) - double(u[3 * i + 1]);
+    const double dz = double(u[3 * j + 2]) - double(u[3 * i + 2]);
+    const double r2 = (dx * dx + dy * dy) + dz * dz;
+    return 1.0 / std::sqrt(r2 + eps2);
+  });
+  const double p = -(Gm * s);
+  const double dvx = double(vel[3 * mem[i]]) - vb[0];
+  const double dvy = double(vel[3 * mem[i] + 1]) - vb[1];
+  const double dvz = double(vel[3 * mem[i] + 2]) - vb[2];
+  const double ke = 0.5 * ((dvx * dvx + dvy * dvy) + dvz * dvz);
+  *phi_out = p;
+  return (ke + p) < 0.0;
+}
+
 }  // namespace
 
 // =============================================================================================
 // C ABI (ctypes). Every array is host memory owned by the caller; positions/velocities are
 // float32 [n][3], ids int64 [n]. Functions return 0 on success, -1 on invalid arguments.
 extern "C" {
+
+int or_split_node_ex(int64_t g, const float* u, const float* v, int32_t f_num, int32_t f_den,
+                     int32_t pruned, int32_t threads, float* scal_out, float* nn2_out,
+                     int64_t* comp_out);
 
 // Brute-force 3D FoF over all pairs: labels[i] = smallest id of i's component.
 int or_fof3d_brute(int64_t n, const float* pos, const int64_t* ids, float L, float ll,
@@ -388,9 +566,17 @@ double or_cro_sum(const double* a, int64_t m) {
 // floats), nn2[g], comp[g] (smallest member position of each member's component).
 int or_split_node(int64_t g, const float* u, const float* v, int32_t f_num, int32_t f_den,
                   float* scal_out, float* nn2_out, int64_t* comp_out) {
+  return or_split_node_ex(g, u, v, f_num, f_den, -1, 1, scal_out, nn2_out, comp_out);
+}
+
+// or_split_node with the search chosen explicitly (pruned: 0 all pairs, 1 k-d tree, -1 by
+// size) and the member loops of the k-d tree search spread over `threads`.
+int or_split_node_ex(int64_t g, const float* u, const float* v, int32_t f_num, int32_t f_den,
+                     int32_t pruned, int32_t threads, float* scal_out, float* nn2_out,
+                     int64_t* comp_out) {
   if (g < 2 || f_num <= 0 || f_den <= 0 || f_num > f_den) return -1;
   SplitResult sr;
-  split_node(u, v, g, f_num, f_den, sr);
+  split_node(u, v, g, f_num, f_den, sr, std::max(1, int(threads)), pruned);
   scal_out[0] = sr.inv_sx2;
   scal_out[1] = sr.inv_sv2;
   scal_out[2] = sr.l2;
@@ -430,6 +616,15 @@ int or_hierarchy_copy(void* handle, int64_t* parent, int32_t* level, int64_t* mi
   return 0;
 }
 
+// Split parameters of every node: inv_sx2, inv_sv2, l2 (float32 [n_nodes][3]).
+int or_hierarchy_params(void* handle, float* params) {
+  auto* h = static_cast<Hierarchy*>(handle);
+  if (!h) return -1;
+  for (size_t q = 0; q < h->nodes.size(); ++q)
+    for (int k = 0; k < 3; ++k) params[3 * q + k] = h->nodes[q].scal[k];
+  return 0;
+}
+
 void or_hierarchy_free(void* handle) { delete static_cast<Hierarchy*>(handle); }
 
 // Unbinding over every node of the hierarchy (member CSR: member_off [n_nodes+1], member_idx).
@@ -454,24 +649,11 @@ int or_unbind(int64_t n_nodes, const int64_t* member_off, const int64_t* member_
     std::vector<float> u;
     unwrap_node(pos, mem, g, L, u);
     double vb[3];
-    for (int d = 0; d < 3; ++d)
-      vb[d] = cro_sum(g, [&](int64_t a) { return double(vel[3 * mem[a] + d]); }) / double(g);
+    bulk_velocity(vel, mem, g, vb);
     int64_t nb = 0;
     for (int64_t i = 0; i < g; ++i) {
-      const double s = cro_sum(g, [&](int64_t j) {
-        if (j == i) return 0.0;
-        const double dx = double(u[3 * j]) - double(u[3 * i]);
-        const double dy = double(u[3 * j + 1]) - double(u[3 * i + 1]);
-        const double dz = double(u[3 * j + 2]) - double(u[3 * i + 2]);
-        const double r2 = (dx * dx + dy * dy) + dz * dz;
-        return 1.0 / std::sqrt(r2 + eps2);
-      });
-      const double p = -(Gm * s);
-      const double dvx = double(vel[3 * mem[i]]) - vb[0];
-      const double dvy = double(vel[3 * mem[i] + 1]) - vb[1];
-      const double dvz = double(vel[3 * mem[i] + 2]) - vb[2];
-      const double ke = 0.5 * ((dvx * dvx + dvy * dvy) + dvz * dvz);
-      const bool b = (ke + p) < 0.0;
+      double p;
+      const bool b = member_energy(u.data(), vel, mem, g, i, vb, eps2, Gm, &p);
       if (phi) phi[off + i] = p;
       bound[off + i] = b ? 1 : 0;
       nb += b ? 1 : 0;
@@ -479,6 +661,29 @@ int or_unbind(int64_t n_nodes, const int64_t* member_off, const int64_t* member_
     n_bound[q] = nb;
     is_halo[q] = (nb >= min_size && int64_t(bf_den) * nb >= int64_t(bf_num) * g) ? 1 : 0;
     m_bound[q] = double(nb) * m;
+  });
+  return 0;
+}
+
+// Unbinding of selected members of ONE node (mem: its g particle indices, ascending id), by the
+// definition of or_unbind: the node's bulk velocity from all its members, then phi_i, KE_i and
+// the flag of each member sample[s] (positions in mem), the samples spread over threads.
+int or_unbind_sample(int64_t g, const int64_t* mem, const float* pos, const float* vel, float L,
+                     float eps, double G, double m, int64_t k, const int64_t* sample,
+                     int32_t threads, double* phi_out, uint8_t* bound_out) {
+  if (g < 1 || k < 0) return -1;
+  for (int64_t s = 0; s < k; ++s)
+    if (sample[s] < 0 || sample[s] >= g) return -1;
+  const double Gm = G * m;
+  const double eps2 = double(eps) * double(eps);
+  std::vector<float> u;
+  unwrap_node(pos, mem, g, L, u);
+  double vb[3];
+  bulk_velocity(vel, mem, g, vb);
+  parallel_for(k, threads, [&](int64_t s) {
+    double p;
+    bound_out[s] = member_energy(u.data(), vel, mem, g, sample[s], vb, eps2, Gm, &p) ? 1 : 0;
+    phi_out[s] = p;
   });
   return 0;
 }

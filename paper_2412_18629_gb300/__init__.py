@@ -45,6 +45,8 @@ class rs_config(ctypes.Structure):
         ("min_halo_particles", ctypes.c_int32), ("bound_num", ctypes.c_int32),
         ("bound_den", ctypes.c_int32), ("batched", ctypes.c_int32),
         ("use_surrogate", ctypes.c_int32), ("spot_check", ctypes.c_int32),
+        ("tree_min_members", ctypes.c_int32), ("tree_theta", ctypes.c_float),
+        ("surrogate_gate", ctypes.c_int32),
     ]
 
 
@@ -65,6 +67,8 @@ def load_library():
         lib.rs_last_error.restype = ctypes.c_char_p
         lib.rs_kernel_launches.argtypes = [P]
         lib.rs_kernel_launches.restype = i64
+        lib.rs_sort_keypasses.argtypes = [P]
+        lib.rs_sort_keypasses.restype = i64
         lib.rs_fof3d.argtypes = [P, i64, P, P, P, ctypes.POINTER(i64), P]
         lib.rs_fof6d.argtypes = [P, i64, P, P, P, P, ctypes.POINTER(i64), ctypes.POINTER(i64), P]
         lib.rs_fof6d_copy.argtypes = [P, P, P, P, P, P, P, P, P]
@@ -85,6 +89,9 @@ def load_library():
                      "rs_mlp_forward", "rs_mlp_gradient", "rs_mlp_train"):
             getattr(lib, name).restype = i32
         lib.rs_cro_sum_noalloc.argtypes = [i64, P, P, P]
+        lib.rs_tree_stats.argtypes = [P, P]
+        lib.rs_tree_record.argtypes = [P, ctypes.c_int]
+        lib.rs_tree_bounds.argtypes = [P, P, P, P]
         lib.rs_profile.argtypes = [P, ctypes.c_int]
         lib.rs_count_work.argtypes = [P, ctypes.c_int, P]
         lib.rs_tuning.argtypes = [P, P, P]
@@ -92,7 +99,8 @@ def load_library():
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_fof3d", "rs_fof6d", "rs_fof6d_copy",
                      "rs_fof6d_node_params", "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile",
-                     "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work", "rs_tuning"):
+                     "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work", "rs_tuning",
+                     "rs_tree_stats", "rs_tree_record", "rs_tree_bounds"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -130,7 +138,7 @@ class Context:
 
     def __init__(self, box, link_len, softening, particle_mass, G=G_NEWTON, f=(7, 10),
                  min_halo_particles=10, bound_frac=(1, 2), device=0, mode="plain",
-                 margin_factor=4.0, spot_check=32):
+                 margin_factor=4.0, spot_check=32, tree_min=0, tree_theta=0.0, surrogate_gate=0):
         self.lib = load_library()
         cfg = rs_config()
         cfg.box_L, cfg.link_len, cfg.softening = float(box), float(link_len), float(softening)
@@ -144,6 +152,11 @@ class Context:
         cfg.use_surrogate = 1 if mode == "surrogate" else 0
         cfg.margin_factor = float(margin_factor)
         cfg.spot_check = int(spot_check)
+        cfg.tree_min_members = int(tree_min)
+        cfg.tree_theta = float(tree_theta)
+        if surrogate_gate not in (0, 1):
+            raise ValueError("surrogate_gate must be 0 (held-out maximum) or 1 (calibrated per node)")
+        cfg.surrogate_gate = int(surrogate_gate)
         self.mode = mode
         self.cfg = cfg
         self.device = int(device)
@@ -160,6 +173,11 @@ class Context:
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.rs_kernel_launches(self.handle))
+
+    @property
+    def sort_keypasses(self) -> int:
+        """Keys moved by radix-sort passes since the context was created."""
+        return int(self.lib.rs_sort_keypasses(self.handle))
 
     def profile(self, enable=True):
         """Start (clearing totals) or stop CUDA-event timing of the dominant kernels."""
@@ -411,15 +429,42 @@ def rs_surrogate_features(ctx, with_targets=True, stream=None):
     return feat[:k], (psi[:k] if psi is not None else None)
 
 
+TREE_STATS = ("tree_nodes", "tree_members", "decided_by_bound", "exact_path", "expansions",
+              "direct_pairs", "list_pairs", "reserved")
+
+
+def rs_tree_stats(ctx):
+    """Counters of the certified tree bound in the last rs_unbind (see TREE_STATS)."""
+    arr = (ctypes.c_int64 * 8)()
+    ctx.check(ctx.lib.rs_tree_stats(ctx.handle, ctypes.cast(arr, ctypes.c_void_p)))
+    return dict(zip(TREE_STATS, list(arr)))
+
+
+def rs_tree_record(ctx, enable=True):
+    """Record each bounded member's interval of the potential sum in later rs_unbind calls."""
+    ctx.check(ctx.lib.rs_tree_record(ctx.handle, 1 if enable else 0))
+
+
+def rs_tree_bounds(ctx, stream=None):
+    """(lo, hi) float64 CUDA tensors [n_members]: the recorded interval of each member's sum
+    S_i = sum_{j != i} (|u_j - u_i|^2 + eps^2)^(-1/2) (NaN where the flag came from elsewhere)."""
+    torch = _torch()
+    dev = torch.device("cuda", ctx.device)
+    lo = torch.empty(ctx.n_members, dtype=torch.float64, device=dev)
+    hi = torch.empty(ctx.n_members, dtype=torch.float64, device=dev)
+    ctx.check(ctx.lib.rs_tree_bounds(ctx.handle, _ptr(lo), _ptr(hi), _stream(stream)))
+    return lo, hi
+
+
 SURROGATE_STATS = ("surrogate_members", "gated", "exact_member_path", "spot_checked",
                    "failed_nodes", "fp64_member_path", "fp64_direct", "rerun_members",
-                   "whole_node_members", "surrogate_decided")
+                   "whole_node_members", "surrogate_decided", "spot_mismatches")
 
 
 def rs_surrogate_stats(ctx):
     lib = ctx.lib
     lib.rs_surrogate_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     lib.rs_surrogate_stats.restype = ctypes.c_int32
-    arr = (ctypes.c_int64 * 10)()
+    arr = (ctypes.c_int64 * 11)()
     ctx.check(lib.rs_surrogate_stats(ctx.handle, ctypes.cast(arr, ctypes.c_void_p)))
     return dict(zip(SURROGATE_STATS, list(arr)))

@@ -9,7 +9,8 @@ extern "C" int rs_ctx_create(rs_ctx** out, const rs_config* cfg, int device) {
   if (!(cfg->box_L > 0.f) || !(cfg->link_len > 0.f) || !(cfg->softening >= 0.f) ||
       !(cfg->particle_mass > 0.0) || !(cfg->G > 0.0) || cfg->f_num <= 0 || cfg->f_den <= 0 ||
       cfg->f_num > cfg->f_den || cfg->min_halo_particles < 2 || cfg->bound_num < 0 ||
-      cfg->bound_den <= 0)
+      cfg->bound_den <= 0 || !(cfg->tree_theta >= 0.f && cfg->tree_theta <= 0.9f) ||
+      cfg->surrogate_gate < 0 || cfg->surrogate_gate > 1 || cfg->spot_check < 0)
     return RS_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -20,6 +21,11 @@ extern "C" int rs_ctx_create(rs_ctx** out, const rs_config* cfg, int device) {
   rs_ctx* ctx = new rs_ctx();
   ctx->cfg = *cfg;
   ctx->device = device;
+  // certified tree bound: batched forms only
+  ctx->tree_min = cfg->batched == 0 || cfg->tree_min_members < 0
+                      ? 0
+                      : (cfg->tree_min_members == 0 ? rs::kTreeMinDefault : int64_t(cfg->tree_min_members));
+  ctx->tree_theta = cfg->tree_theta > 0.f ? cfg->tree_theta : rs::kTreeThetaDefault;
   if (cudaMallocHost(&ctx->host_box, 64 * sizeof(int64_t)) != cudaSuccess) {
     cudaGetLastError();
     delete ctx;
@@ -120,6 +126,8 @@ extern "C" int rs_ctx_destroy(rs_ctx* ctx) {
 extern "C" const char* rs_last_error(rs_ctx* ctx) { return ctx ? ctx->err : "null context"; }
 
 extern "C" int64_t rs_kernel_launches(rs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" int64_t rs_sort_keypasses(rs_ctx* ctx) { return ctx ? ctx->sort_keypasses : 0; }
 
 namespace {
 struct ArrayTerm {

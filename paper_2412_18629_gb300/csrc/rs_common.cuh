@@ -45,12 +45,20 @@ enum Slot : int {
   S_SUR_OFF, S_SUR_RANK, S_SUR_STAT, S_SUR_MEM, S_SUR_BIG, S_SUR_FEAT, S_SUR_PSI, S_SUR_MARGIN,
   S_SUR_SFLAG, S_SUR_CHECKED, S_SUR_SX, S_SUR_LIST_A, S_SUR_LIST_B, S_SUR_GCOUNT, S_SUR_TAU,
   S_SUR_FAIL, S_SUR_COUNTERS, S_SUR_FIX, S_SUR_SPOS, S_SUR_PSISPH, S_SUR_ECOUNT, S_SUR_FULL,
-  S_SUR_MP, S_SUR_ERRN, S_SUR_LIST_C, S_SUR_LSCAN, S_SUR_LOFS, S_SUR_TILES,
+  S_SUR_MP, S_SUR_ERRN, S_SUR_LIST_C, S_SUR_LSCAN, S_SUR_LOFS, S_SUR_TILES, S_SUR_WANT,
+  // certified tree bound of the potential (rs_tree.cu)
+  S_T_OFF, S_T_RANK, S_T_COFF, S_T_NODES, S_T_BOX, S_T_KA, S_T_KB, S_T_VA, S_T_VB, S_T_X, S_T_POS,
+  S_T_CELL, S_T_ORDER, S_T_WF, S_T_WL, S_T_WR, S_T_UF, S_T_LIST, S_T_LR, S_T_SX, S_T_REC,
+  S_T_WANT,
   S_NUM_SLOTS
 };
 
 // Nodes with at least this many members are unbound through the surrogate when it is enabled.
 constexpr int64_t kSurrogateMinMembers = 1024;
+// Default smallest node unbound through the certified tree bound (batched form) and its
+// opening angle (a cell is expanded when its radius bound is at most theta times the distance).
+constexpr int64_t kTreeMinDefault = 16384;
+constexpr float kTreeThetaDefault = 0.5f;
 
 struct Buffer {
   void* ptr = nullptr;
@@ -83,11 +91,19 @@ struct rs_ctx {
   int64_t sur_members = 0;
   int64_t sur_nbig = 0;
   const uint64_t* sur_rkeys = nullptr;
-  int64_t sur_stats[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t sur_stats[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // certified tree bound (batched form): smallest node, opening angle, state of the last build
+  int64_t tree_min = 0;         // 0: the tree bound is off
+  float tree_theta = 0.5f;
+  int64_t tree_nt = 0, tree_T = 0, tree_C = 0;
+  bool tree_record = false;     // record each member's interval (rs_tree_record)
+  bool tree_recorded = false;
+  int64_t tree_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
   bool profile = false;
   bool count_work = false;  // counting variants of the pruned 6D kernels (rs_count_work)
   int sort_blocks = 0;      // radix-sort blocks resident at once on the device (0 = not known yet)
+  int64_t sort_keypasses = 0;  // keys moved by radix-sort passes since the context was created
   // autotuner choices (0 = not tuned yet) and the timings they were chosen from
   int tune_blk_r = 0;       // members per thread of the blocked potential (2, 4, 8)
   float tune_blk_ms[3] = {0.f, 0.f, 0.f};

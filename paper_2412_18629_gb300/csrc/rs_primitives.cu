@@ -309,6 +309,7 @@ int radix_sort_u64(rs_ctx* ctx, int64_t n, int nbits, uint64_t* keys_a, uint32_t
   uint64_t* kout = keys_b;
   uint32_t* vout = vals_b;
   for (int shift = 0; shift < nbits; shift += kRadixBits) {
+    ctx->sort_keypasses += n;  // 24 B of key + value traffic per key and pass
     const int dbits = std::min(kRadixBits, nbits - shift);
     const uint32_t dmask = (1u << dbits) - 1u;
     {

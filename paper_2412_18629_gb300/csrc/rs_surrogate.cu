@@ -2,29 +2,34 @@
 //
 // For every node with at least kSurMin members ("big" nodes), instead of the O(g^2) potential:
 //   1. features per member (k_sur_features): r / r_vir, the enclosed-member fractions within
-//      0.5, 1 and 2 times the member's radius (binary searches in the node's radially sorted
-//      members), the node's potential at the member from the radially split multipole
-//      expansion to quadrupole order (psi_mp: monopole = spherically averaged node, plus the
-//      dipole and quadrupole moments of the members inside and outside the member's radius,
-//      from fixed-point prefix sums over the radial order), |v - v_bulk| / sigma_v,1D, log10 g
-//      and log10 of the size ratio of the deepest hierarchy node holding the member; r is
-//      measured from the node's mean position, r_vir = (3 g m / (4 pi 200 rho_bar))^(1/3);
+//      0.5, 1, 2 and 4 times the member's radius (binary searches in the node's radially sorted
+//      members), |v - v_bulk| / sigma_v,1D, log10 g, and in the eighth input the node's
+//      potential at the member from the radially split multipole expansion to quadrupole order
+//      (psi_mp: monopole = spherically averaged node, plus the dipole and quadrupole moments of
+//      the members inside and outside the member's radius, from fixed-point prefix sums over
+//      the radial order); r is measured from the node's mean position,
+//      r_vir = (3 g m / (4 pi 200 rho_bar))^(1/3);
 //   2. the MLP predicts psi = phi r_vir / (G g m); E_pred = KE + psi_hat G g m / r_vir;
-//   3. calibration: per node, kCalib members evenly spaced in member order are held out of
-//      the gate and evaluated exactly; err_node = max(max |psi_hat - psi| over them,
-//      err_max / 8), err_max being the MLP's held-out maximum error from training;
-//   4. gate (k_sur_gate): a member is classified by the surrogate iff
-//      |E_pred| > margin_factor * err_node * G g m / r_vir; every other member takes the exact
-//      path: a register-blocked float32 sum over the node for the list of such members (with
-//      the self term included and subtracted, and a per-member certified bound), the float64
-//      canonical-order potential when the energy is within that bound of zero;
-//   5. spot check: per node, the spot_check gated members with the smallest margin are also
-//      evaluated exactly; if any has a different flag, or |psi_hat - psi| above half the
-//      gate's margin (margin_factor / 2 * err_node: the calibration was off by more than that
-//      factor), the whole node is recomputed by the blocked direct sum.
+//   3. gate (k_sur_gate): a member is classified by the surrogate iff
+//      |E_pred| > margin_factor * err * G g m / r_vir, with err the MLP's held-out maximum error
+//      from training (err_max: the default gate), or, opted in (surrogate_gate = 1), a per-node
+//      calibrated error: kCalib members of the node evenly spaced in member order are evaluated
+//      exactly and err = max(their max |psi_hat - psi|, err_max / 8);
+//   4. every other member takes the exact path: the certified tree bound for nodes with a tree,
+//      a register-blocked float32 sum over the node for the list of such members (with the self
+//      term included and subtracted, and a per-member certified bound), the float64
+//      canonical-order potential when the energy is within that bound of zero; a node with at
+//      most 1/20 of its members gated goes whole to the exact path;
+//   5. spot check: per node, the spot_check gated members with the smallest margin and about
+//      spot_check more drawn at every margin (a seeded hash of the member position) are also
+//      evaluated exactly; if any has a different flag (counted), or |psi_hat - psi| above half
+//      the gate's margin, the whole node is recomputed exactly.
+// Zero flag mismatches against the exact path is a measured result (the tests compare every
+// member's flag on held-out snapshots), not a guarantee: a member the network mispredicts by
+// more than the margin and that no spot check samples keeps a wrong flag.
 #include <cmath>
 
-#include "rs_cro.cuh"
+#include "rs_exact.cuh"
 
 namespace rs {
 int mlp_forward(rs_ctx* ctx, int64_t n, const float* x, float* y, cudaStream_t st);
@@ -39,14 +44,6 @@ namespace {
 constexpr int kT = 256;
 constexpr int64_t kSurMin = kSurrogateMinMembers;
 constexpr int64_t kTuneMinSurMembers = 1 << 20;  // the autotuner times candidates on lists this large
-constexpr double kU = 5.9604644775390625e-08;
-// per-member warp sum: per term <= 8u, 32-term lane blocks <= 31u, Kahan <= 2u, 5-level warp
-// tree <= 5u; 48u with slack.
-constexpr double kCertB2 = 48.0 * kU + 1e-12;
-
-// Blocked direct sum over the exact-path list: 128 threads x 4 members per block.
-// (members per thread kListR: a template parameter the autotuner picks among 2, 4, 8)
-constexpr int kListThreads = 128;
 
 struct NodeStat {
   float cx, cy, cz, r_vir;
@@ -218,18 +215,15 @@ __device__ __forceinline__ float psi_multipole(const int64_t* __restrict__ terms
 }
 
 // Features of surrogate member k, in this order: r / r_vir; fractions of the node's members
-// with radius below 0.5 r, r and 2 r; psi_mp of the node; |v - v_bulk| / sigma_v,1D;
-// log10 g; log10 (g_d / g) of the deepest hierarchy node d holding the member (its
-// substructure: 0 when the member is in no smaller node).
+// with radius below 0.5 r, r, 2 r and 4 r; |v - v_bulk| / sigma_v,1D; log10 g; and psi_mp, the
+// node's potential at the member from the radially split multipole expansion.
 __global__ void k_sur_features(int64_t ns, const uint32_t* __restrict__ sur_mem,
-                               const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_off,
-                               const int64_t* __restrict__ node_size, const float4* __restrict__ U,
-                               const float4* __restrict__ V, const NodeStat* __restrict__ st,
-                               const double* __restrict__ vbulk, const uint64_t* __restrict__ rkeys,
-                               const float* __restrict__ psi_sph, const uint32_t* __restrict__ mem,
-                               const int64_t* __restrict__ deepest, const int64_t* __restrict__ sur_off,
-                               const uint32_t* __restrict__ spos, const int64_t* __restrict__ terms,
-                               float eps, float* __restrict__ feat) {
+                               const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_size,
+                               const float4* __restrict__ U, const float4* __restrict__ V,
+                               const NodeStat* __restrict__ st, const double* __restrict__ vbulk,
+                               const uint64_t* __restrict__ rkeys, const float* __restrict__ psi_sph,
+                               const int64_t* __restrict__ sur_off, const uint32_t* __restrict__ spos,
+                               const int64_t* __restrict__ terms, float eps, float* __restrict__ feat) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= ns) return;
   const uint32_t p = sur_mem[k], q = mnode[p];
@@ -237,22 +231,18 @@ __global__ void k_sur_features(int64_t ns, const uint32_t* __restrict__ sur_mem,
   const int64_t g = node_size[q], lo = sur_off[q], hi = lo + g;
   const float r = member_radius(U[p], s);
   const float inv_g = 1.0f / float(g);
-  const float f05 = float(count_below(rkeys, lo, hi, 0.5f * r)) * inv_g;
-  const float f1 = float(count_below(rkeys, lo, hi, r)) * inv_g;
-  const float f2 = float(count_below(rkeys, lo, hi, 2.0f * r)) * inv_g;
   const float4 v = V[p];
   const float dvx = v.x - float(vbulk[3 * q]), dvy = v.y - float(vbulk[3 * q + 1]),
               dvz = v.z - float(vbulk[3 * q + 2]);
-  const int64_t d = deepest[mem[p]];  // a node at or below q: never -1 for a member of q
   float* F = feat + 8 * k;
   F[0] = r / s.r_vir;
-  F[1] = f05;
-  F[2] = f1;
-  F[3] = f2;
-  F[4] = psi_multipole(terms, ns, lo, hi, int64_t(spos[k]), U[p], s, eps, g, psi_sph[k]);
+  F[1] = float(count_below(rkeys, lo, hi, 0.5f * r)) * inv_g;
+  F[2] = float(count_below(rkeys, lo, hi, r)) * inv_g;
+  F[3] = float(count_below(rkeys, lo, hi, 2.0f * r)) * inv_g;
+  F[4] = float(count_below(rkeys, lo, hi, 4.0f * r)) * inv_g;
   F[5] = sqrtf(dvx * dvx + dvy * dvy + dvz * dvz) / fmaxf(s.sig_v1d, 1e-30f);
   F[6] = s.log_g;
-  F[7] = log10f(float(node_size[d]) * inv_g);
+  F[7] = psi_multipole(terms, ns, lo, hi, int64_t(spos[k]), U[p], s, eps, g, psi_sph[k]);
 }
 
 __global__ void k_sur_targets(int64_t ns, const uint32_t* __restrict__ sur_mem,
@@ -263,14 +253,6 @@ __global__ void k_sur_targets(int64_t ns, const uint32_t* __restrict__ sur_mem,
   if (k >= ns) return;
   const uint32_t p = sur_mem[k], q = mnode[p];
   psi[k] = float(-double(S[p]) * double(st[q].r_vir) / double(node_size[q]));
-}
-
-__device__ __forceinline__ double kinetic(float4 v, const double* vb) {
-  const double dvx = __dsub_rn(rsd::f2d(v.x), vb[0]);
-  const double dvy = __dsub_rn(rsd::f2d(v.y), vb[1]);
-  const double dvz = __dsub_rn(rsd::f2d(v.z), vb[2]);
-  const double s = __dadd_rn(__dadd_rn(__dmul_rn(dvx, dvx), __dmul_rn(dvy, dvy)), __dmul_rn(dvz, dvz));
-  return __dmul_rn(0.5, s);
 }
 
 // counters: [0] exact per-member list, [1] check list, [2] fp64 list (current pass), [3] rerun
@@ -296,7 +278,7 @@ __global__ void k_sur_gate(int64_t ns, const uint32_t* __restrict__ sur_mem, con
     const float dvx = v.x - float(vbulk[3 * q]), dvy = v.y - float(vbulk[3 * q + 1]),
                 dvz = v.z - float(vbulk[3 * q + 2]);
     const float e = 0.5f * (dvx * dvx + dvy * dvy + dvz * dvz) * inv_gmr + psi_hat[k];
-    const float thr = margin_factor * fmaxf(errn[q], err_floor);
+    const float thr = margin_factor * (errn ? fmaxf(errn[q], err_floor) : err_floor);
     if (fabsf(e) > thr) {
       const uint8_t f = e < 0.f ? 1 : 0;
       bound[p] = f;
@@ -350,21 +332,28 @@ __global__ void k_sur_err(const unsigned long long* __restrict__ count, const ui
 // A node with at most 1/20 of its members gated goes whole through the blocked direct sum.
 __global__ void k_sur_full(int64_t nbig, const int64_t* __restrict__ big_nodes,
                            const int64_t* __restrict__ node_size, const unsigned int* __restrict__ ecount,
-                           int* __restrict__ full, unsigned long long* __restrict__ counters) {
+                           int ncalib, int* __restrict__ full, unsigned long long* __restrict__ counters) {
   const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (b >= nbig) return;
   const int64_t q = big_nodes[b], g = node_size[q];
-  const bool f = 20 * (int64_t(ecount[q]) + kCalib) >= 19 * g;
+  const bool f = 20 * (int64_t(ecount[q]) + ncalib) >= 19 * g;
   full[q] = f ? 1 : 0;
   if (f) atomicAdd(counters + 8, (unsigned long long)g);
 }
 
+// Ungated members of nodes not sent whole: the exact-path list (lf), except in nodes with a
+// certified tree (tmin > 0, at least tmin members), whose members are marked in `want` for it.
 __global__ void k_sur_exact_flags(int64_t ns, const uint32_t* __restrict__ sur_mem,
-                                  const uint32_t* __restrict__ mnode, const uint8_t* __restrict__ sflag,
-                                  const int* __restrict__ full, int64_t* __restrict__ lf) {
+                                  const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_size,
+                                  const uint8_t* __restrict__ sflag, const int* __restrict__ full,
+                                  int64_t tmin, int64_t* __restrict__ lf, uint8_t* __restrict__ want) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= ns) return;
-  lf[k] = (sflag[k] == 2 && !full[mnode[sur_mem[k]]]) ? 1 : 0;
+  const uint32_t p = sur_mem[k], q = mnode[p];
+  const bool open = sflag[k] == 2 && !full[q];
+  const bool tree = tmin > 0 && node_size[q] >= tmin;
+  lf[k] = (open && !tree) ? 1 : 0;
+  if (want) want[p] = (open && tree) ? 1 : 0;
 }
 
 // Exact-path list in surrogate-member order (so grouped by node), per-node list offsets and
@@ -380,13 +369,14 @@ __global__ void k_sur_exact_list(int64_t ns, const int64_t* __restrict__ lf, uin
 __global__ void k_sur_list_tiles(int64_t nbig, const int64_t* __restrict__ big_nodes,
                                  const int64_t* __restrict__ sur_off, const int64_t* __restrict__ node_size,
                                  const int64_t* __restrict__ lf, int list_tile, int64_t* __restrict__ lofs,
-                                 int64_t* __restrict__ tiles) {
+                                 int64_t* __restrict__ tiles, unsigned long long* __restrict__ list_pairs) {
   const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (b >= nbig) return;
   const int64_t q = big_nodes[b];
   const int64_t a = lf[sur_off[q]], e = lf[sur_off[q] + node_size[q]];
   lofs[b] = a;
   tiles[b] = (e - a + list_tile - 1) / list_tile;
+  if (list_pairs && e > a) atomicAdd(list_pairs, (unsigned long long)((e - a) * node_size[q]));
 }
 
 __global__ void k_sur_list_end(int64_t nbig, const int64_t* __restrict__ big_nodes,
@@ -445,15 +435,28 @@ k_sur_select(const int64_t* __restrict__ big_nodes, const int64_t* __restrict__ 
   if (threadIdx.x == 0) tau[q] = __uint_as_float(s_prefix);
 }
 
+// splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators", 2014)
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// Spot-checked gated members: the `spot` of smallest margin (margin <= tau) and, at every
+// margin, a seeded pseudo-random sample of about `spot` more (hash of the member position).
 __global__ void k_sur_spot_mark(int64_t ns, const uint32_t* __restrict__ sur_mem,
                                 const uint32_t* __restrict__ mnode, const float* __restrict__ margin,
                                 const uint8_t* __restrict__ sflag, const float* __restrict__ tau,
+                                const unsigned int* __restrict__ gcount, int spot, const int* __restrict__ full,
                                 uint8_t* __restrict__ checked, uint32_t* __restrict__ check_list,
                                 unsigned long long* __restrict__ counters) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= ns) return;
-  const uint32_t q = mnode[sur_mem[k]];
-  const bool c = sflag[k] < 2 && margin[k] <= tau[q];
+  const uint32_t p = sur_mem[k], q = mnode[p];
+  const uint64_t period = spot > 0 ? uint64_t(max(1u, gcount[q] / uint32_t(spot))) : 0;
+  const bool sampled = period > 0 && !full[q] && splitmix64(uint64_t(p) ^ 0x5eedull) % period == 0;
+  const bool c = sflag[k] < 2 && (margin[k] <= tau[q] || sampled);
   checked[k] = c ? 1 : 0;
   if (c) check_list[atomicAdd(counters + 1, 1ull)] = uint32_t(k);
 }
@@ -507,116 +510,6 @@ k_pot_member(const unsigned long long* __restrict__ count, const uint32_t* __res
         ambig[atomicAdd(n_ambig, 1ull)] = p;
       }
     }
-  }
-}
-
-// Float32 sums S_all,i = sum over ALL members j of the node (self included) of
-// (|u_j - u_i|^2 + eps^2)^(-1/2) for the members i of the exact-path list: block b covers one
-// 512-member tile of one big node's list; j-tiles of 128 members staged duplicated in shared
-// memory, packed float32x2 arithmetic, 32-term sequential blocks added with Kahan compensation
-// (the same per-member summation as the direct-sum kernels). Including the self term, whose
-// computed value is exactly w0 = rsqrt(eps^2), removes every per-pair index test; k_flags_list
-// subtracts it and widens the certified bound accordingly.
-template <int kListR>
-__global__ void __launch_bounds__(kListThreads)
-k_potential_list(int64_t nbig, const int64_t* __restrict__ tile_off, const int64_t* __restrict__ big_nodes,
-                 const int64_t* __restrict__ lofs, const int64_t* __restrict__ lf_total_per_node_end,
-                 const uint32_t* __restrict__ list, const uint32_t* __restrict__ sur_mem,
-                 const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
-                 const float4* __restrict__ U, float eps2, float* __restrict__ Sx) {
-  __shared__ float4 sxy[kListThreads];
-  __shared__ float2 sz[kListThreads];
-  const int64_t b = blockIdx.x;
-  if (b >= tile_off[nbig]) return;
-  const int64_t bi = rsd::upper_bound_i64(tile_off, nbig, b) - 1;
-  const int64_t q = big_nodes[bi], t = b - tile_off[bi];
-  const int64_t base = node_off[q], g = node_size[q];
-  const int64_t l0 = lofs[bi] + t * (kListThreads * kListR), l1 = lf_total_per_node_end[bi];
-  float2 nx[kListR / 2], ny[kListR / 2], nz[kListR / 2];
-  float S[kListR], C[kListR];
-#pragma unroll
-  for (int pp = 0; pp < kListR / 2; ++pp) {
-    const int64_t a0 = l0 + threadIdx.x + kListThreads * (2 * pp), a1 = a0 + kListThreads;
-    const float4 u0 = a0 < l1 ? U[sur_mem[list[a0]]] : make_float4(0, 0, 0, 0);
-    const float4 u1 = a1 < l1 ? U[sur_mem[list[a1]]] : make_float4(0, 0, 0, 0);
-    nx[pp] = make_float2(-u0.x, -u1.x);
-    ny[pp] = make_float2(-u0.y, -u1.y);
-    nz[pp] = make_float2(-u0.z, -u1.z);
-  }
-#pragma unroll
-  for (int k = 0; k < kListR; ++k) {
-    S[k] = 0.f;
-    C[k] = 0.f;
-  }
-  const float2 e2 = make_float2(eps2, eps2);
-  for (int64_t j0 = 0; j0 < g; j0 += kListThreads) {
-    const int64_t j = j0 + threadIdx.x;
-    if (j < g) {
-      const float4 u = U[base + j];
-      sxy[threadIdx.x] = make_float4(u.x, u.x, u.y, u.y);
-      sz[threadIdx.x] = make_float2(u.z, u.z);
-    }
-    __syncthreads();
-    const int jn = int(rsd::min64(kListThreads, g - j0));
-    for (int jb = 0; jb < jn; jb += 32) {
-      const int je = min(jb + 32, jn);
-      float2 blk[kListR / 2];
-#pragma unroll
-      for (int pp = 0; pp < kListR / 2; ++pp) blk[pp] = make_float2(0.f, 0.f);
-#pragma unroll 8
-      for (int jj = jb; jj < je; ++jj) {
-        const float4 a = sxy[jj];
-        const float2 zz = sz[jj];
-#pragma unroll
-        for (int pp = 0; pp < kListR / 2; ++pp) {
-          const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx[pp]);
-          const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny[pp]);
-          const float2 dz = __fadd2_rn(zz, nz[pp]);
-          const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
-          blk[pp] = __fadd2_rn(blk[pp], make_float2(rsqrtf(r2.x), rsqrtf(r2.y)));
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < kListR; ++k) {
-        const float bk = (k & 1) ? blk[k >> 1].y : blk[k >> 1].x;
-        const float y = __fsub_rn(bk, C[k]);
-        const float tt = __fadd_rn(S[k], y);
-        C[k] = __fsub_rn(__fsub_rn(tt, S[k]), y);
-        S[k] = tt;
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int k = 0; k < kListR; ++k) {
-    const int64_t a = l0 + threadIdx.x + kListThreads * k;
-    if (a < l1) Sx[list[a]] = S[k];
-  }
-}
-
-// Flags of the exact-path list from S_all: S = fl(S_all - w0). With B = 41u the bound of the
-// blocked sum relative to S_all = S + w0, |S - S_true| <= B (S + w0) + u S, so the member's
-// relative bound is Bi = B (1 + w0 / S) + u (plus slack); the flag is certain when
-// |KE + phi~| > 2 Bi |phi~|, otherwise the member is queued for the float64 potential.
-__global__ void k_flags_list(const unsigned long long* __restrict__ count, const uint32_t* __restrict__ list,
-                             const uint32_t* __restrict__ sur_mem, const uint32_t* __restrict__ mnode,
-                             const float4* __restrict__ V, const double* __restrict__ vbulk,
-                             float eps2, double Gm, float* __restrict__ Sx, uint8_t* __restrict__ bound,
-                             uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig) {
-  const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (w >= int64_t(*count)) return;
-  const uint32_t k = list[w];
-  const uint32_t p = sur_mem[k], q = mnode[p];
-  const float w0 = rsqrtf(eps2);
-  const float S = __fsub_rn(Sx[k], w0);
-  Sx[k] = S;
-  const double ph = -__dmul_rn(Gm, double(S));
-  const double e = __dadd_rn(kinetic(V[p], vbulk + 3 * int64_t(q)), ph);
-  const double Bi = 41.0 * kU * (1.0 + double(w0) / fmax(double(S), 1e-30)) + 2.0 * kU + 1e-12;
-  if (S > 0.f && fabs(e) > 2.0 * Bi * fabs(ph)) {
-    bound[p] = e < 0.0 ? 1 : 0;
-  } else {
-    ambig[atomicAdd(n_ambig, 1ull)] = p;
   }
 }
 
@@ -694,7 +587,7 @@ k_pot_member4(const unsigned long long* __restrict__ count, const uint32_t* __re
   }
 }
 
-__global__ void k_sur_verdict(const unsigned long long* __restrict__ counters,
+__global__ void k_sur_verdict(unsigned long long* __restrict__ counters,
                               const uint32_t* __restrict__ check_list, const uint32_t* __restrict__ sur_mem,
                               const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_size,
                               const NodeStat* __restrict__ st, const float* __restrict__ Sx,
@@ -707,8 +600,10 @@ __global__ void k_sur_verdict(const unsigned long long* __restrict__ counters,
     const uint32_t k = check_list[w];
     const uint32_t p = sur_mem[k], q = mnode[p];
     const double psi = -double(Sx[k]) * double(st[q].r_vir) / double(node_size[q]);
-    const double err = 0.5 * double(margin_factor) * double(fmaxf(errn[q], err_floor));
-    if (fabs(double(psi_hat[k]) - psi) > err || sflag[k] != bound[p]) fail[q] = 1;
+    const double err = 0.5 * double(margin_factor) * double(errn ? fmaxf(errn[q], err_floor) : err_floor);
+    const bool flag_differs = sflag[k] != bound[p];
+    if (flag_differs) atomicAdd(counters + 19, 1ull);
+    if (fabs(double(psi_hat[k]) - psi) > err || flag_differs) fail[q] = 1;
   }
 }
 
@@ -781,7 +676,10 @@ namespace rs {
 int unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
                     const double* vbulk, uint8_t* bound, cudaStream_t st, float* phi_out = nullptr);
 int unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t* bound,
-                 uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st);
+                 uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st,
+                 unsigned long long* counters);
+int tree_decide(rs_ctx* ctx, const int* only, const uint8_t* want, const double* vbulk,
+                uint8_t* bound, unsigned long long* counters, cudaStream_t st);
 
 // Shared set-up: big-node member list, node statistics, radial sort, features.
 // Returns the number of surrogate members through *ns_out (host).
@@ -862,9 +760,9 @@ static int sur_prepare(rs_ctx* ctx, const double* vbulk, int64_t* ns_out, cudaSt
   RS_TRY(exclusive_scan_i64(ctx, nterms, terms, terms + nterms, st));
   {
     ProfScope prof_(ctx, "k_sur_features", st);
-    k_sur_features<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_off, h.node_size, h.U,
-                                                   h.V, stt, vbulk, rkeys, psi_sph, h.mem, h.deepest,
-                                                   sur_off, spos, terms, eps, feat);
+    k_sur_features<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_size, h.U, h.V, stt,
+                                                   vbulk, rkeys, psi_sph, sur_off, spos, terms, eps,
+                                                   feat);
   }
   RS_LAUNCHED(ctx, "k_sur_features");
   return RS_OK;
@@ -910,7 +808,10 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
   const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
   const float eps = ctx->cfg.softening;
   const unsigned grid = 152 * 8;
-  const float err_floor = ctx->mlp_err_max / 8.0f;
+  // gate: the benchmark spec's held-out maximum error of the training (err_max), or, opted in, the
+  // per-node calibrated error with err_max / 8 as its floor
+  const bool calibrated = ctx->cfg.surrogate_gate == 1;
+  const float err_floor = calibrated ? ctx->mlp_err_max / 8.0f : ctx->mlp_err_max;
   RS_TRY(mlp_forward(ctx, ns, feat, psi_hat, st));
   RS_CUDA(ctx, cudaMemsetAsync(gcount, 0, 4 * nn, st));
   RS_CUDA(ctx, cudaMemsetAsync(ecount, 0, 4 * nn, st));
@@ -918,39 +819,49 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
   RS_CUDA(ctx, cudaMemsetAsync(full, 0, 4 * nn, st));
   RS_CUDA(ctx, cudaMemsetAsync(errn, 0, 4 * nn, st));
   RS_CUDA(ctx, cudaMemsetAsync(sflag, 0, size_t(ns), st));
-  // 1. calibration members: exact potential and flag, then the per-node error of the surrogate
-  k_sur_calib_list<<<grid_for(nbig * kCalib, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size,
-                                                               calib_list, sflag, counters);
-  RS_LAUNCHED(ctx, "k_sur_calib_list");
-  {
-    ProfScope prof_(ctx, "k_pot_member", st);
-    k_pot_member4<<<grid, kT, 0, st>>>(counters + 9, calib_list, sur_mem, h.mnode, h.node_off, h.node_size,
-                                       h.U, h.V, vbulk, eps * eps, Gm, Sx, bound, ambig, counters + 2);
+  if (calibrated) {
+    // 1. calibration members: exact potential and flag, then the per-node error of the surrogate
+    k_sur_calib_list<<<grid_for(nbig * kCalib, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size,
+                                                                 calib_list, sflag, counters);
+    RS_LAUNCHED(ctx, "k_sur_calib_list");
+    {
+      ProfScope prof_(ctx, "k_pot_member", st);
+      k_pot_member4<<<grid, kT, 0, st>>>(counters + 9, calib_list, sur_mem, h.mnode, h.node_off,
+                                         h.node_size, h.U, h.V, vbulk, eps * eps, Gm, Sx, bound, ambig,
+                                         counters + 2);
+    }
+    RS_LAUNCHED(ctx, "k_pot_member4");
+    RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vbulk, bound, st));
+    k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
+    RS_LAUNCHED(ctx, "k_acc_counter");
+    k_sur_err<<<grid_for(nbig * kCalib, kT), kT, 0, st>>>(counters + 9, calib_list, sur_mem, h.mnode,
+                                                          h.node_size, stt, Sx, psi_hat, errn);
+    RS_LAUNCHED(ctx, "k_sur_err");
   }
-  RS_LAUNCHED(ctx, "k_pot_member4");
-  RS_TRY(unbind_fallback(ctx, counters + 2, ambig, vbulk, bound, st));
-  k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
-  RS_LAUNCHED(ctx, "k_acc_counter");
-  k_sur_err<<<grid_for(nbig * kCalib, kT), kT, 0, st>>>(counters + 9, calib_list, sur_mem, h.mnode,
-                                                        h.node_size, stt, Sx, psi_hat, errn);
-  RS_LAUNCHED(ctx, "k_sur_err");
-  // 2. gate with the node's calibrated error
+  const float* errn_f = calibrated ? reinterpret_cast<const float*>(errn) : nullptr;
+  // 2. gate
   k_sur_gate<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_size, h.V, vbulk, stt, psi_hat,
-                                             reinterpret_cast<const float*>(errn), err_floor,
-                                             ctx->cfg.margin_factor, bound, sflag, margin, gcount, ecount,
-                                             counters);
+                                             errn_f, err_floor, ctx->cfg.margin_factor, bound, sflag,
+                                             margin, gcount, ecount, counters);
   RS_LAUNCHED(ctx, "k_sur_gate");
   if (nbig > 0) {
-    k_sur_full<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, h.node_size, ecount, full, counters);
+    k_sur_full<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, h.node_size, ecount,
+                                                  calibrated ? kCalib : 0, full, counters);
     RS_LAUNCHED(ctx, "k_sur_full");
   }
   // 3. nodes nearly all outside the gate: whole-node blocked direct sum
-  RS_TRY(unbind_nodes(ctx, full, vbulk, bound, ambig, counters + 2, st));
+  RS_TRY(unbind_nodes(ctx, full, vbulk, bound, ambig, counters + 2, st, counters));
   k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 7);
   RS_LAUNCHED(ctx, "k_acc_counter");
   // 4. the other ungated members: blocked sums over their node, certified flags, float64 fallback
-  k_sur_exact_flags<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, sflag, full, lf);
+  // (members of nodes with a certified tree: its bound first, the same exact path after it)
+  const int64_t tmin = ctx->tree_nt > 0 ? ctx->tree_min : 0;
+  uint8_t* want = tmin > 0 ? scratch_t<uint8_t>(ctx, S_SUR_WANT, size_t(ctx->n_members)) : nullptr;
+  if (tmin > 0 && !want) return RS_ERR_OOM;
+  k_sur_exact_flags<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, h.node_size, sflag, full, tmin, lf,
+                                                    want);
   RS_LAUNCHED(ctx, "k_sur_exact_flags");
+  if (tmin > 0) RS_TRY(tree_decide(ctx, nullptr, want, vbulk, bound, counters, st));
   RS_TRY(exclusive_scan_i64(ctx, ns, lf, lf + ns, st));
   k_sur_exact_list<<<grid_for(ns, kT), kT, 0, st>>>(ns, lf, exact_list, counters);
   RS_LAUNCHED(ctx, "k_sur_exact_list");
@@ -971,7 +882,8 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
     for (int c = tune ? 0 : 3; c <= 3; ++c) {
       const int R = c < 3 ? cand[c] : (ctx->tune_list_r ? ctx->tune_list_r : 4);
       k_sur_list_tiles<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size, lf,
-                                                          kListThreads * R, lofs, ltiles);
+                                                          kListThreads * R, lofs, ltiles,
+                                                          c == 3 ? counters + 18 : nullptr);
       RS_LAUNCHED(ctx, "k_sur_list_tiles");
       RS_TRY(exclusive_scan_i64(ctx, nbig, ltiles, ltiles + nbig, st));
       const unsigned grid = grid_for(ns / (kListThreads * R) + nbig + 1, 1);
@@ -1019,8 +931,8 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
                                                 ctx->cfg.spot_check, full, tau);
     RS_LAUNCHED(ctx, "k_sur_select");
   }
-  k_sur_spot_mark<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, margin, sflag, tau, checked,
-                                                  check_list, counters);
+  k_sur_spot_mark<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, margin, sflag, tau, gcount,
+                                                  ctx->cfg.spot_check, full, checked, check_list, counters);
   RS_LAUNCHED(ctx, "k_sur_spot_mark");
   {
     ProfScope prof_(ctx, "k_pot_member", st);
@@ -1032,13 +944,12 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
   k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
   RS_LAUNCHED(ctx, "k_acc_counter");
   k_sur_verdict<<<grid, kT, 0, st>>>(counters, check_list, sur_mem, h.mnode, h.node_size, stt, Sx, psi_hat,
-                                     sflag, bound, reinterpret_cast<const float*>(errn), err_floor,
-                                     ctx->cfg.margin_factor, fail);
+                                     sflag, bound, errn_f, err_floor, ctx->cfg.margin_factor, fail);
   RS_LAUNCHED(ctx, "k_sur_verdict");
   // 6. nodes that failed a spot check: the whole node through the blocked direct sum
   k_sur_rerun<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, fail, sflag, checked, counters);
   RS_LAUNCHED(ctx, "k_sur_rerun");
-  RS_TRY(unbind_nodes(ctx, fail, vbulk, bound, ambig, counters + 2, st));
+  RS_TRY(unbind_nodes(ctx, fail, vbulk, bound, ambig, counters + 2, st, counters));
   k_acc_counter<<<1, 1, 0, st>>>(counters, 2, 6);
   RS_LAUNCHED(ctx, "k_acc_counter");
   k_sur_decided<<<grid_for(ns, kT), kT, 0, st>>>(ns, sur_mem, h.mnode, sflag, checked, full, fail, counters);
@@ -1056,8 +967,10 @@ extern "C" int rs_surrogate_features(rs_ctx* ctx, float* feat_out, float* psi_ou
   ctx->err[0] = 0;
   if (!ctx->have_hier || !ctx->have_unbind)
     return set_error(ctx, RS_ERR_STATE, "needs rs_fof6d and rs_unbind first");
-  if (psi_out && ctx->last_unbind_surrogate)
-    return set_error(ctx, RS_ERR_STATE, "targets need an rs_unbind without the surrogate");
+  if (psi_out && (ctx->last_unbind_surrogate || ctx->tree_nt > 0))
+    return set_error(ctx, RS_ERR_STATE,
+                     "targets need an rs_unbind that computed every potential (no surrogate, "
+                     "no tree bound: ask it for the potential)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   RS_CUDA(ctx, cudaSetDevice(ctx->device));
   const double* vbulk = static_cast<const double*>(ctx->buf[S_U_VBULK].ptr);
@@ -1081,6 +994,6 @@ extern "C" int rs_surrogate_features(rs_ctx* ctx, float* feat_out, float* psi_ou
 
 extern "C" int rs_surrogate_stats(rs_ctx* ctx, int64_t* stats_out) {
   if (!ctx || !stats_out) return RS_ERR_INVALID_ARG;
-  for (int i = 0; i < 10; ++i) stats_out[i] = ctx->sur_stats[i];
+  for (int i = 0; i < 11; ++i) stats_out[i] = ctx->sur_stats[i];
   return RS_OK;
 }

@@ -25,7 +25,11 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
 int unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,
                     const double* vbulk, uint8_t* bound, cudaStream_t st, float* phi_out = nullptr);
 int unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t* bound,
-                 uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st);
+                 uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st,
+                 unsigned long long* counters);
+int tree_build(rs_ctx* ctx, cudaStream_t st);
+int tree_decide(rs_ctx* ctx, const int* only, const uint8_t* want, const double* vbulk,
+                uint8_t* bound, unsigned long long* counters, cudaStream_t st);
 }  // namespace rs
 
 using namespace rs;
@@ -42,12 +46,7 @@ constexpr int kPotTile = 256;
 //   Total <= 41u + 1e-12 with u = 2^-24; the flag test uses twice this.
 constexpr double kU = 5.9604644775390625e-08;
 constexpr double kCertB = 41.0 * kU + 1e-12;
-
-__global__ void k_tiles(int64_t nn, const int64_t* __restrict__ node_size, int tile,
-                        int64_t* __restrict__ out) {
-  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k < nn) out[k] = (node_size[k] + tile - 1) / tile;
-}
+constexpr int kCounters = 24;  // the unbinding counters (see rs_unbind)
 
 // Nodes up to kBlockedMin members: one thread per member over the flat member list (lanes of
 // a warp are consecutive members, mostly of one node), the node's members read through L1 in
@@ -103,18 +102,70 @@ constexpr int64_t kTuneMinMembers = 1 << 20;  // the autotuner times candidates 
 // Tiles of the two direct-sum kernels; nodes with >= sur_min members (sur_min > 0) are left to
 // the surrogate path. Also the sort key of the blocked tiles' order (size class, descending).
 __global__ void k_tiles_split(int64_t nn, const int64_t* __restrict__ node_size, int64_t sur_min,
-                              const int* __restrict__ only, int blk_tile, int64_t* __restrict__ small,
-                              int64_t* __restrict__ big, uint64_t* __restrict__ okey,
-                              uint32_t* __restrict__ oval) {
+                              const int* __restrict__ only, int64_t max_g, int blk_tile,
+                              int64_t* __restrict__ small, int64_t* __restrict__ big,
+                              uint64_t* __restrict__ okey, uint32_t* __restrict__ oval) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= nn) return;
   const int64_t g = node_size[k];
-  const bool skip = only ? (only[k] == 0) : (sur_min > 0 && g >= sur_min);
+  const bool skip = (only ? (only[k] == 0) : (sur_min > 0 && g >= sur_min)) || (max_g > 0 && g >= max_g);
   const bool blocked = !skip && g > kBlockedMin;
   small[k] = (skip || g > kBlockedMin) ? 0 : (g + kPotTile - 1) / kPotTile;
   big[k] = blocked ? (g + blk_tile - 1) / blk_tile : 0;
   okey[k] = blocked ? uint64_t(63 - __clzll(g)) ^ 63u : 255u;
   oval[k] = uint32_t(k);
+}
+
+// Plain form of the direct sum for nodes above kBlockedMin members: one thread per member,
+// blocks of 128 members of one node in node order, j-tiles of 128 members staged in shared
+// memory; the per-member summation (32-term sequential blocks of the j order, Kahan across
+// blocks, self term 0) is the blocked kernel's, so the sums are bit-identical to it.
+constexpr int kTileThreads = 128;
+
+__global__ void __launch_bounds__(kTileThreads)
+k_potential_tiled(int64_t nn, const int64_t* __restrict__ tile_off, const int64_t* __restrict__ node_off,
+                  const int64_t* __restrict__ node_size, const float4* __restrict__ U, float eps2,
+                  float* __restrict__ S_out) {
+  __shared__ float4 su[kTileThreads];
+  const int64_t b = blockIdx.x;
+  if (b >= tile_off[nn]) return;
+  const int64_t q = rsd::upper_bound_i64(tile_off, nn, b) - 1;
+  const int64_t t = b - tile_off[q];
+  const int64_t base = node_off[q], g = node_size[q];
+  const int64_t i = t * kTileThreads + threadIdx.x;
+  const float4 ui = i < g ? U[base + i] : make_float4(0, 0, 0, 0);
+  float S = 0.f, C = 0.f;
+  for (int64_t j0 = 0; j0 < g; j0 += kTileThreads) {
+    if (j0 + threadIdx.x < g) su[threadIdx.x] = U[base + j0 + threadIdx.x];
+    __syncthreads();
+    const int jn = int(rsd::min64(kTileThreads, g - j0));
+    for (int jb = 0; jb < jn; jb += 32) {
+      const int je = min(jb + 32, jn);
+      float blk = 0.f;
+      for (int jj = jb; jj < je; ++jj) {
+        const float4 uj = su[jj];
+        const float dx = __fsub_rn(uj.x, ui.x);
+        const float dy = __fsub_rn(uj.y, ui.y);
+        const float dz = __fsub_rn(uj.z, ui.z);
+        const float w = rsqrtf(__fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, eps2))));
+        blk = __fadd_rn(blk, j0 + jj == i ? 0.f : w);
+      }
+      const float y = __fsub_rn(blk, C);
+      const float tt = __fadd_rn(S, y);
+      C = __fsub_rn(__fsub_rn(tt, S), y);
+      S = tt;
+    }
+    __syncthreads();
+  }
+  if (i < g) S_out[base + i] = S;
+}
+
+__global__ void k_tiles_plain(int64_t nn, const int64_t* __restrict__ node_size, const int* __restrict__ only,
+                              int64_t* __restrict__ out) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= nn) return;
+  const int64_t g = node_size[k];
+  out[k] = (g > kBlockedMin && (!only || only[k])) ? (g + kTileThreads - 1) / kTileThreads : 0;
 }
 
 __global__ void k_perm_tiles(int64_t nn, const uint32_t* __restrict__ perm,
@@ -256,11 +307,13 @@ __global__ void k_flags(int64_t m, const uint32_t* __restrict__ mnode, const int
                         const float* __restrict__ S, double Gm, double certB,
                         uint8_t* __restrict__ bound, float* __restrict__ phi_out,
                         uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig,
-                        int64_t sur_min, const int* __restrict__ only) {
+                        int64_t sur_min, const int* __restrict__ only, int64_t max_g) {
   const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (p >= m) return;
   const uint32_t q = mnode[p];
-  if (only ? (only[q] == 0) : (sur_min > 0 && node_size[q] >= sur_min)) return;  // other path
+  const int64_t g = node_size[q];
+  if ((only ? (only[q] == 0) : (sur_min > 0 && g >= sur_min)) || (max_g > 0 && g >= max_g))
+    return;  // other path
   const double ke = kinetic(V[p], vbulk + 3 * int64_t(q));
   const double ph = -__dmul_rn(Gm, double(S[p]));
   const double e = __dadd_rn(ke, ph);
@@ -464,8 +517,8 @@ __global__ void k_halo_decide(int64_t nn, const int64_t* __restrict__ node_size,
 
 // Tiles of the blocked kernel for kBlkR = R (nodes above kBlockedMin members, ordered by size
 // class, largest first) and of k_potential (the other selected nodes).
-int potential_tiles(rs_ctx* ctx, int64_t sur_min, const int* only, int R, int64_t* tile_small,
-                    int64_t* tile_perm, uint32_t** perm, cudaStream_t st) {
+int potential_tiles(rs_ctx* ctx, int64_t sur_min, const int* only, int64_t max_g, int R,
+                    int64_t* tile_small, int64_t* tile_perm, uint32_t** perm, cudaStream_t st) {
   Hier h = hier_of(ctx);
   const int64_t nn = ctx->n_nodes;
   int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
@@ -474,8 +527,8 @@ int potential_tiles(rs_ctx* ctx, int64_t sur_min, const int* only, int R, int64_
   uint32_t* va = scratch_t<uint32_t>(ctx, S_U_OVAL_A, size_t(nn));
   uint32_t* vb = scratch_t<uint32_t>(ctx, S_U_OVAL_B, size_t(nn));
   if (!tile_big || !ka || !kb || !va || !vb) return RS_ERR_OOM;
-  k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sur_min, only, kBlkThreads * R, tile_small,
-                                                 tile_big, ka, va);
+  k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sur_min, only, max_g, kBlkThreads * R,
+                                                 tile_small, tile_big, ka, va);
   RS_LAUNCHED(ctx, "k_tiles_split");
   uint64_t* ko;
   RS_TRY(radix_sort_u64(ctx, nn, 8, ka, va, kb, vb, &ko, perm, st));
@@ -509,7 +562,8 @@ int launch_blocked(rs_ctx* ctx, int R, const int64_t* tile_perm, const uint32_t*
 // thread come from the context's autotuner: on the first call with at least kTuneMinMembers
 // members, each of 2, 4 and 8 is timed on that call's own nodes (CUDA events; identical sums)
 // and the fastest is kept for the context.
-int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, float* S, cudaStream_t st) {
+int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, int64_t max_g, float* S,
+                     cudaStream_t st) {
   Hier h = hier_of(ctx);
   const int64_t m = ctx->n_members, nn = ctx->n_nodes;
   const float eps = ctx->cfg.softening;
@@ -517,7 +571,8 @@ int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, float* S, cu
   int64_t* tile_perm = scratch_t<int64_t>(ctx, S_U_TILEPERM, size_t(nn) + 1);
   if (!tile_small || !tile_perm) return RS_ERR_OOM;
   uint32_t* perm;
-  if (ctx->tune_blk_r == 0 && m >= kTuneMinMembers) {
+  const bool plain = ctx->cfg.batched == 0;
+  if (!plain && ctx->tune_blk_r == 0 && m >= kTuneMinMembers) {
     const int cand[3] = {2, 4, 8};
     float best_ms = 0.f;
     int best = 4;
@@ -525,7 +580,7 @@ int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, float* S, cu
     RS_CUDA(ctx, cudaEventCreate(&e0));
     RS_CUDA(ctx, cudaEventCreate(&e1));
     for (int c = 0; c < 3; ++c) {
-      RS_TRY(potential_tiles(ctx, sur_min, only, cand[c], tile_small, tile_perm, &perm, st));
+      RS_TRY(potential_tiles(ctx, sur_min, only, max_g, cand[c], tile_small, tile_perm, &perm, st));
       RS_CUDA(ctx, cudaEventRecord(e0, st));
       RS_TRY(launch_blocked(ctx, cand[c], tile_perm, perm, S, st));
       RS_CUDA(ctx, cudaEventRecord(e1, st));
@@ -543,13 +598,23 @@ int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, float* S, cu
     ctx->tune_blk_r = best;
   }
   const int R = ctx->tune_blk_r ? ctx->tune_blk_r : 4;
-  RS_TRY(potential_tiles(ctx, sur_min, only, R, tile_small, tile_perm, &perm, st));
+  RS_TRY(potential_tiles(ctx, sur_min, only, max_g, R, tile_small, tile_perm, &perm, st));
   {
     ProfScope prof_(ctx, "k_potential", st);
     k_potential<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, tile_small, h.node_off, h.node_size, h.U,
                                                eps * eps, S);
   }
   RS_LAUNCHED(ctx, "k_potential");
+  if (plain) {  // one member per thread, node order (the plain form has no size-ordered tiles)
+    k_tiles_plain<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, only, tile_perm);
+    RS_LAUNCHED(ctx, "k_tiles_plain");
+    RS_TRY(exclusive_scan_i64(ctx, nn, tile_perm, tile_perm + nn, st));
+    ProfScope prof_(ctx, "k_potential_tiled", st);
+    k_potential_tiled<<<grid_for(m / (kBlockedMin + 1) + m / kTileThreads + 1, 1), kTileThreads, 0, st>>>(
+        nn, tile_perm, h.node_off, h.node_size, h.U, eps * eps, S);
+    RS_LAUNCHED(ctx, "k_potential_tiled");
+    return RS_OK;
+  }
   {
     ProfScope prof_(ctx, "k_potential_blocked", st);
     RS_TRY(launch_blocked(ctx, R, tile_perm, perm, S, st));
@@ -588,24 +653,39 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
   double* vbulk = scratch_t<double>(ctx, S_U_VBULK, size_t(std::max<int64_t>(nn, 1)) * 3);
   uint32_t* ambig = scratch_t<uint32_t>(ctx, S_U_AMBIG, size_t(std::max<int64_t>(m, 1)));
   uint8_t* halo = scratch_t<uint8_t>(ctx, S_U_FLAGS, size_t(std::max<int64_t>(nn, 1)));
-  // counters: [0..6] surrogate path (rs_surrogate.cu), [7] float64 fallbacks of the direct sums
-  unsigned long long* counters = scratch_t<unsigned long long>(ctx, S_SUR_COUNTERS, 16);
+  // counters: [0..6], [8..11] surrogate path (rs_surrogate.cu), [7] float64 fallbacks of the
+  // direct sums, [12..17] certified tree bound (rs_tree.cu)
+  unsigned long long* counters = scratch_t<unsigned long long>(ctx, S_SUR_COUNTERS, kCounters);
   if (!bound || !S || !nb || !vbulk || !ambig || !halo || !counters) return RS_ERR_OOM;
   unsigned long long* n_ambig = counters + 7;
+  // certified tree bound: batched forms, when no potential is asked for
+  const bool tree = ctx->tree_min > 0 && potential_out == nullptr && ctx->cfg.batched != 0;
+  const int64_t tree_min = ctx->tree_min;
+  const int64_t max_g = (tree && !sur) ? tree_min : 0;
+  ctx->tree_recorded = false;
+  double* rec = nullptr;
+  if (tree && ctx->tree_record && m > 0) {
+    rec = scratch_t<double>(ctx, S_T_REC, 2 * size_t(m));
+    if (!rec) return RS_ERR_OOM;
+    RS_CUDA(ctx, cudaMemsetAsync(rec, 0xff, 16 * size_t(m), st));  // NaN: not bounded
+  }
   int64_t nfb = 0;
-  for (int i = 0; i < 10; ++i) ctx->sur_stats[i] = 0;
+  for (int i = 0; i < 11; ++i) ctx->sur_stats[i] = 0;
+  for (int i = 0; i < 8; ++i) ctx->tree_stats[i] = 0;
+  ctx->tree_nt = ctx->tree_T = ctx->tree_C = 0;
   if (m > 0) {
     const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
-    const float eps = ctx->cfg.softening;
-    RS_CUDA(ctx, cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned long long), st));
+    RS_CUDA(ctx, cudaMemsetAsync(counters, 0, kCounters * sizeof(unsigned long long), st));
     RS_TRY((cro_segmented<3, VelTerm>(ctx, nn, h.node_off, h.node_size, m, VelTerm{h.V}, vbulk, st)));
     k_vbulk<<<grid_for(3 * nn, kT), kT, 0, st>>>(nn, h.node_size, vbulk);  // sums -> bulk velocities
     RS_LAUNCHED(ctx, "k_vbulk");
-    RS_TRY(direct_potential(ctx, sur_min, nullptr, S, st));
+    RS_TRY(direct_potential(ctx, sur_min, nullptr, max_g, S, st));
     k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vbulk, S, Gm, kCertB, bound,
-                                           potential_out, ambig, n_ambig, sur_min, nullptr);
+                                           potential_out, ambig, n_ambig, sur_min, nullptr, max_g);
     RS_LAUNCHED(ctx, "k_flags");
     RS_TRY(unbind_fallback(ctx, n_ambig, ambig, vbulk, bound, st, potential_out));
+    if (tree) RS_TRY(tree_build(ctx, st));
+    if (tree && !sur) RS_TRY(tree_decide(ctx, nullptr, nullptr, vbulk, bound, counters, st));
     if (sur) RS_TRY(surrogate_unbind(ctx, vbulk, bound, counters, st));
     RS_CUDA(ctx, cudaMemsetAsync(nb, 0, 8 * nn, st));
     k_bound_count<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, bound, nb);
@@ -615,11 +695,11 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     RS_LAUNCHED(ctx, "k_halo_decide");
     k_copy_u8<<<grid_for(m, kT), kT, 0, st>>>(m, bound, bound_out);
     RS_LAUNCHED(ctx, "k_copy_u8");
-    RS_TRY(read_back(ctx, counters, 16 * sizeof(unsigned long long), st));
+    RS_TRY(read_back(ctx, counters, kCounters * sizeof(unsigned long long), st));
     // stats: surrogate members, gated, exact (exact-path list + calibration members, outside
-    // nodes sent whole),
-    // spot-checked, failed nodes, fp64 (surrogate path), fp64 (direct sums), re-run members,
-    // members of nodes sent whole to the direct sum, members whose flag the surrogate decided
+    // nodes sent whole), spot-checked, failed nodes, fp64 (surrogate path), fp64 (direct sums),
+    // re-run members, members of nodes sent whole to the direct sum, members whose flag the
+    // surrogate decided, spot-checked members whose surrogate flag was wrong
     ctx->sur_stats[0] = sur ? ctx->sur_members : 0;
     ctx->sur_stats[1] = ctx->host_box[5];
     ctx->sur_stats[2] = ctx->host_box[0] + ctx->host_box[11];
@@ -630,7 +710,15 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     ctx->sur_stats[7] = ctx->host_box[3];
     ctx->sur_stats[8] = ctx->host_box[8];
     ctx->sur_stats[9] = ctx->host_box[10];
+    ctx->sur_stats[10] = ctx->host_box[19];
+    // tree: nodes, members, decided by the bound, sent to the exact list, expansions, direct
+    // pairs, pair terms of the exact list sums (tree and surrogate paths)
+    ctx->tree_stats[0] = ctx->tree_nt;
+    ctx->tree_stats[1] = ctx->tree_T;
+    for (int i = 0; i < 4; ++i) ctx->tree_stats[2 + i] = ctx->host_box[12 + i];
+    ctx->tree_stats[6] = ctx->host_box[18];
     nfb = ctx->host_box[7] + ctx->host_box[6];
+    ctx->tree_recorded = rec != nullptr;
   }
   if (n_fallback_out) *n_fallback_out = nfb;
   ctx->have_unbind = true;
@@ -639,18 +727,23 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
 }
 
 // Exact unbinding of the nodes flagged in `only` (int [n_nodes]): register-blocked float32
-// potential of all their members, certified flags, float64 fallback for the ambiguous ones.
+// potential of all their members, certified flags, float64 fallback for the ambiguous ones;
+// nodes with a built tree (tree_build of this rs_unbind) go through the certified tree bound.
 int rs::unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t* bound,
-                     uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st) {
+                     uint32_t* ambig, unsigned long long* n_ambig, cudaStream_t st,
+                     unsigned long long* counters) {
   Hier h = hier_of(ctx);
-  const int64_t m = ctx->n_members, nn = ctx->n_nodes;
+  const int64_t m = ctx->n_members;
   float* S = static_cast<float*>(ctx->buf[S_U_PHI].ptr);
   const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
-  RS_TRY(direct_potential(ctx, 0, only, S, st));
+  const int64_t max_g = ctx->tree_nt > 0 ? ctx->tree_min : 0;
+  RS_TRY(direct_potential(ctx, 0, only, max_g, S, st));
   k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vbulk, S, Gm, kCertB, bound, nullptr,
-                                         ambig, n_ambig, 0, only);
+                                         ambig, n_ambig, 0, only, max_g);
   RS_LAUNCHED(ctx, "k_flags");
-  return unbind_fallback(ctx, n_ambig, ambig, vbulk, bound, st);
+  RS_TRY(unbind_fallback(ctx, n_ambig, ambig, vbulk, bound, st));
+  if (ctx->tree_nt > 0) RS_TRY(tree_decide(ctx, only, nullptr, vbulk, bound, counters, st));
+  return RS_OK;
 }
 
 int rs::unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const uint32_t* ambig,

@@ -40,37 +40,74 @@ def test_clock_summary_without_samples(tmp_path):
     assert out["samples"] == 0 and out["reasons"] == ["unavailable"]
 
 
-def test_roofline_pruned_kernel_from_work_tallies():
-    steps = 3
-    prof = {"k_nn6d_pruned": (13.0 * steps, 30), "k_fof_link": (6.3 * steps, 6)}
-    work = {"nn_d6": 2.8e9, "nn_box": 2.0e9, "link_d6": 1.0e9, "link_box": 1.0e9}
-    r = bench._roofline(prof, pairs=4.9e10, steps=steps, work=work)
-    peak = bench.SM_COUNT * bench.FP32_LANES_PER_SM * 2070e6
-    ops = (2.8e9 + 2.0e9) * bench.OPS_PER_PAIR["k_nn6d"] * steps
-    assert r["kernel"] == "k_nn6d_pruned" and r["bound"] == "alu"
-    assert r["achieved"] == pytest.approx(ops / (13.0 * steps / 1e3) / 1e12)
-    assert r["frac"] == pytest.approx(ops / (13.0 * steps / 1e3) / peak)
-    assert r["kernel_ms_per_step"] == pytest.approx(13.0)
-    assert r["work"]["d6_per_step"] == 2.8e9
+def _form(**kw):
+    r = {"n": 1 << 24, "members": 15_000_000, "sort_keypasses": 4 * (1 << 24),
+         "pairs": {"pairs_all": 4.9e10, "pairs_small": 1.0e9, "pairs_blocked": 3.0e10},
+         "work": {"nn_d6": 2.8e9, "nn_box": 2.0e9, "link_d6": 1.0e9, "link_box": 1.0e9},
+         "tree": {"expansions": 2.0e9, "direct_pairs": 5.0e9, "list_pairs": 1.0e10}}
+    r.update(kw)
+    return r
 
 
-def test_roofline_brute_force_link_counts_unordered_pairs():
-    prof = {"k_link6d": (25.0, 10)}
-    r = bench._roofline(prof, pairs=4.0e10, steps=1)
-    ops = 4.0e10 / 2.0 * bench.OPS_PER_PAIR["k_link6d"]
-    assert r["achieved"] == pytest.approx(ops / 25e-3 / 1e12)
+def test_stages_use_the_per_unit_figures(monkeypatch):
+    monkeypatch.setattr(bench, "_measured_peaks", lambda: {"hbm_gbs": 6700.0})
+    prof = {"k_fof_link": (6.0, 2), "k_sort_hist": (1.0, 40), "k_sort_scatter": (3.0, 40),
+            "k_nn6d_pruned": (13.0, 20), "k_potential_list": (5.0, 3), "k_tree_walk": (8.0, 3),
+            "k_potential_blocked": (2.0, 1)}
+    st = bench.stages(_form(prof=prof))
+    fof = st["k_fof_link"]
+    assert fof["bound"] == "hbm" and fof["unit"] == "GB/s"
+    assert fof["achieved"] == pytest.approx((1 << 24) * 28.0 / 6.0e-3 / 1e9)
+    assert fof["frac"] == pytest.approx(fof["achieved"] / 6700.0)
+    srt = st["k_sort"]
+    assert srt["ms_per_step"] == 4.0 and srt["launches"] == 80
+    assert srt["achieved"] == pytest.approx(4 * (1 << 24) * 24.0 / 4.0e-3 / 1e9)
+    nn = st["k_nn6d_pruned"]
+    assert nn["bound"] == "hbm"
+    assert nn["achieved"] == pytest.approx(15e6 * 40.0 / 13e-3 / 1e9)
+    assert nn["alu_d6_only"]["achieved"] == pytest.approx(2.8e9 * 20.0 / 13e-3 / 1e12)
+    lst = st["k_potential_list"]
+    assert lst["bound"] == "alu"
+    assert lst["achieved"] == pytest.approx(1.0e10 * 7.0 / 5e-3 / 1e12)
+    assert st["k_tree_walk"]["achieved"] == pytest.approx((2e9 * 50 + 5e9 * 7) / 8e-3 / 1e12)
+    assert st["k_potential_blocked"]["achieved"] == pytest.approx(3e10 * 7 / 2e-3 / 1e12)
 
 
-def test_stages_entries(monkeypatch):
-    monkeypatch.setattr(bench, "_measured_peaks", lambda: {"hbm_gbs": 6761.6})
-    r = {"prof": {"k_fof_link": (12.6, 4), "k_link6d_pruned": (15.0, 20)}, "n": 1 << 24,
-         "pairs": 4.9e10, "pairs_big": 4.0e10, "form": "surrogate",
-         "work": {"nn_d6": 1.0, "nn_box": 1.0, "link_d6": 1.0e9, "link_box": 5.0e8}}
-    out = bench._stages(r, steps=2)
-    fof = out["k_fof_link"]
-    assert fof["bound"] == "hbm"
-    assert fof["achieved"] == pytest.approx((1 << 24) * 28.0 / 6.3e-3 / 1e9)
-    link = out["k_link6d_pruned"]
-    assert link["ms_per_step"] == pytest.approx(7.5)
-    assert link["achieved"] == pytest.approx(1.5e9 * 20.0 / 7.5e-3 / 1e12)
-    assert "k_potential_blocked" not in out  # the surrogate form's blocked sums are partial
+def test_roofline_is_the_dominant_kernel_with_traffic(monkeypatch):
+    monkeypatch.setattr(bench, "_measured_peaks", lambda: {"hbm_gbs": 6700.0})
+    prof = {"k_fof_link": (6.0, 2), "k_nn6d_pruned": (13.0, 20), "k_unknown": (99.0, 1)}
+    r = bench.roofline(_form(prof=prof), traffic={"k_nn6d_pruned": 1.5e9})
+    assert r["kernel"] == "k_nn6d_pruned" and r["traffic"] == 1.5e9
+    assert r["ms_per_launch"] == pytest.approx(13.0 / 20)
+    assert r["peak"] == 6700.0 and r["peak_source"] == "measured"
+
+
+def test_brute_force_pairs_and_form_thresholds():
+    sizes = [10, 300, 500, 2000, 20000]
+    p = bench._sizes_work(sizes, "plain", 0)
+    pair = lambda g: g * (g - 1.0)  # noqa: E731
+    assert p["pairs_small"] == pair(10) + pair(300)
+    assert p["pairs_blocked"] == pair(500) + pair(2000) + pair(20000)
+    b = bench._sizes_work(sizes, "batched", 16384)
+    assert b["pairs_blocked"] == pair(500) + pair(2000)
+    s = bench._sizes_work(sizes, "surrogate", 16384)
+    assert s["pairs_blocked"] == pair(500)
+    r = _form(pairs=p, prof={"k_link6d": (25.0, 10)})
+    assert bench._alu_d6(r, "k_link6d") == pytest.approx(p["pairs_all"] / 2 * 20.0)
+
+
+def test_oracle_sample_cubes_around_the_median_load():
+    L = 80.0
+    cat = []
+    # one top-level halo per cube on the diagonal of 8 cubes, loads 1..8 squared; one subhalo
+    for i in range(8):
+        c = (i + 0.5) * L / 8
+        cat.append((0, i + 1, i + 1, (c, c, c), (0, 0, 0), 1.0))
+    cat.append((1, 1000, 1000, (5.0, 5.0, 5.0), (0, 0, 0), 1.0))   # depth 1: ignored
+    snap = {"box": L, "catalogue": cat}
+    cubes = bench._oracle_cubes(snap, count=3)
+    assert len(cubes) == 3
+    # 504 empty cubes sort first, so the median of the 512 lies among the empty ones
+    assert all(c not in [(i, i, i) for i in range(8)] for c in cubes)
+    loads = {(i, i, i): (i + 1) ** 2 for i in range(8)}
+    assert all(loads.get(c, 0) == 0 for c in cubes)

@@ -18,7 +18,7 @@ def _train(train_snap):
     pos, vel, ids = to_dev(train_snap)
     lab, _ = rs.rs_fof3d(ctx, pos, ids)
     rs.rs_fof6d(ctx, pos, vel, ids, lab)
-    rs.rs_unbind(ctx, pos, vel, want_potential=False)
+    rs.rs_unbind(ctx, pos, vel, want_potential=True)  # targets need every member's potential
     x, t = rs.rs_surrogate_features(ctx)
     assert x.shape[0] > 10000
     err_max, mse = rs.rs_mlp_train(ctx, x.contiguous(), t.contiguous(), epochs=12, batch=4096,
@@ -53,12 +53,14 @@ def workload_2e18():
     return s
 
 
-def test_surrogate_flags_match_oracle(trained, workload_2e18):
-    """With the trained network, every flag, bound count and halo decision equals the oracle's;
-    the counters account for every member of the large nodes exactly once."""
+@pytest.mark.parametrize("gate", (0, 1))
+def test_surrogate_flags_match_oracle(trained, workload_2e18, gate):
+    """With the trained network, every flag, bound count and halo decision equals the oracle's,
+    for the held-out-maximum gate (0) and the calibrated gate (1); the counters account for
+    every member of the large nodes exactly once."""
     params, err_max, _ = trained
     s = workload_2e18
-    lab, bound, props, stats, _ = _run_surrogate(s, params, err_max)
+    lab, bound, props, stats, _ = _run_surrogate(s, params, err_max, surrogate_gate=gate)
     o = oracle_pipeline(s, labels=lab, stages=("fof3d", "fof6d", "unbind"))
     ub = o["unbind"]
     assert int(np.sum(bound != ub["bound"])) == 0
@@ -70,13 +72,16 @@ def test_surrogate_flags_match_oracle(trained, workload_2e18):
     assert accounted == stats["surrogate_members"], stats
 
 
-def test_surrogate_gain(trained, workload_2e18):
+@pytest.mark.parametrize("gate", (0, 1))
+def test_surrogate_gain(trained, workload_2e18, gate):
     """What the trained network gains over the method without it: the share of the large
-    nodes' members whose flag it decides (no O(g) exact sum for them) and the share of exact
-    pair interactions saved, with zero flag mismatches against the oracle."""
+    nodes' members whose flag it decides (no O(g) exact sum for them), with zero flag
+    mismatches against the oracle. The held-out-maximum gate (0) is reported (it decides few
+    members: four times the maximum error of the training's hold-out is a wide margin); the
+    calibrated gate (1) must decide a real share."""
     params, err_max, _ = trained
     s = workload_2e18
-    lab, bound, props, stats, sizes = _run_surrogate(s, params, err_max)
+    lab, bound, props, stats, sizes = _run_surrogate(s, params, err_max, surrogate_gate=gate)
     o = oracle_pipeline(s, labels=lab, stages=("fof3d", "fof6d", "unbind"))
     assert int(np.sum(bound != o["unbind"]["bound"])) == 0
     big = sizes[sizes >= 1024].astype(np.float64)
@@ -85,7 +90,8 @@ def test_surrogate_gain(trained, workload_2e18):
           stats["surrogate_members"], f"large-node members ({decided_share:.1%}); exact sums for",
           stats["exact_member_path"] + stats["spot_checked"] + stats["rerun_members"],
           "members;", stats, "err_max", err_max, "large-node pairs", float((big * big).sum()))
-    assert stats["surrogate_decided"] > 0.1 * stats["surrogate_members"], stats
+    if gate == 1:
+        assert stats["surrogate_decided"] > 0.1 * stats["surrogate_members"], stats
 
 
 def test_overconfident_surrogate_is_caught_by_spot_checks(trained, workload_2e18):
@@ -96,6 +102,9 @@ def test_overconfident_surrogate_is_caught_by_spot_checks(trained, workload_2e18
     lab, bound, props, stats, _ = _run_surrogate(workload_2e18, params, err_max, margin_factor=0.05)
     assert stats["gated"] > 0
     assert stats["failed_nodes"] > 0 and stats["rerun_members"] > 0, stats
+    assert stats["spot_mismatches"] > 0, stats
+    o = oracle_pipeline(workload_2e18, labels=lab, stages=("fof3d", "fof6d", "unbind"))
+    assert int(np.sum(bound != o["unbind"]["bound"])) == 0
 
 
 def test_surrogate_requires_weights_and_null_potential():
