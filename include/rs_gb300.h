@@ -17,7 +17,8 @@
  *     returns a message owned by the context (valid until the next call on it). No call throws.
  *   - Array arguments are DEVICE pointers owned by the caller, unless a comment says "host".
  *     Positions and velocities are float32 [n][3] (x, y, z contiguous per particle); ids are
- *     int64 [n], non-negative and unique.
+ *     int64 [n], non-negative and unique (any value up to 2^63 - 1; uniqueness is verified
+ *     only with rs_config.check_ids, a repeated id otherwise gives undefined groupings).
  *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = legacy default
  *     stream). Calls that return host-visible counts synchronise that stream before returning.
  *   - The context owns its scratch memory and the hierarchy built by rs_fof6d; those stay
@@ -72,6 +73,8 @@ typedef struct rs_config {
   int32_t surrogate_gate;     /* 0: the error in the gate is the held-out maximum error of the
                                  training (rs_mlp_set_err_max); 1: per node, calibrated on 64
                                  members evaluated exactly, floored at err_max / 8 */
+  int32_t check_ids;          /* 1: rs_fof3d first verifies that the ids are unique and
+                                 non-negative (one 64-bit sort), RS_ERR_INVALID_ARG otherwise */
 } rs_config;
 
 /* Per-node halo properties written by rs_halo_props (all over the node's BOUND members). */
@@ -122,7 +125,7 @@ int64_t rs_sort_keypasses(rs_ctx* ctx);
  * n_groups_out: host; number of groups (singletons included). May be NULL.
  * Synchronises `stream` when n_groups_out is not NULL.
  * Errors: RS_ERR_INVALID_ARG (null pointer with n > 0; box_L / link_len beyond the 4096-cell
- * grid), RS_ERR_OOM, RS_ERR_CUDA. */
+ * grid; with check_ids, a repeated or negative id), RS_ERR_OOM, RS_ERR_CUDA. */
 int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t* ids, int64_t* label_out,
              int64_t* n_groups_out, void* stream);
 
@@ -174,6 +177,29 @@ int rs_fof6d_node_params(rs_ctx* ctx, float* params_out, void* stream);
 int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float* potential_out,
               uint8_t* bound_out, int64_t* n_fallback_out, void* stream);
 
+/* Seed halos and the assignment of every FoF-group particle to one of them (Section
+ * "Parallelization": subhalo finding inside every FoF halo; the step after the hierarchy). The
+ * paper gives no formulas; the reading implemented (the CPU oracle's, bit for bit):
+ *   seeds: the nodes of the last rs_fof6d hierarchy without children;
+ *   frame: u = wrapped offset (rs_fof3d's wrap) from the level-0 node's smallest-id member;
+ *   seed s: centre c_s = float(double(wrapped x_{r_s} - x_{r0}) + S_u / g_s), S_u the
+ *     canonical-order sum of the offsets from s's own smallest-id member r_s; bulk velocity
+ *     w_s = float(S_v / g_s); metric scales inv_sx2_s, inv_sv2_s of s's own 6D split;
+ *   distance: fl(|u - c_s|^2 inv_sx2_s) + fl(|v - w_s|^2 inv_sv2_s) (float32, d6's order);
+ *   particle: the seed holding it when its deepest node is a seed, else the nearest seed under
+ *     its deepest node (ties: smaller node index);
+ *   host of seed s: among the other seeds of s's level-0 node ranking above s (more assigned
+ *     particles; equal counts: smaller node index), the nearest by the candidate's metric at
+ *     (c_s, w_s); -1 when none ranks above.
+ * pos, vel: the arrays given to rs_fof6d (others are re-gathered).
+ * particle_seed: int64 [n] device: node index of the particle's seed, -1 outside every node.
+ * node_host, node_count: int64 [n_nodes] device or NULL: host seed (-2 for nodes that are not
+ * seeds), particles assigned (0 for nodes that are not seeds).
+ * n_seeds_out: host, may be NULL (synchronises the stream). Errors: RS_ERR_STATE (no
+ * hierarchy), RS_ERR_INVALID_ARG, RS_ERR_OOM, RS_ERR_CUDA. */
+int rs_assign_seeds(rs_ctx* ctx, const float* pos, const float* vel, int64_t* particle_seed,
+                    int64_t* node_host, int64_t* node_count, int64_t* n_seeds_out, void* stream);
+
 /* Halo properties of every node of the hierarchy over its bound members (last rs_unbind),
  * float64 sums in the canonical reduction order over members in ascending id order with
  * unbound members contributing 0.
@@ -219,8 +245,11 @@ int rs_cro_sum(rs_ctx* ctx, int64_t m, const double* a, double* out, void* strea
  * Scratch: a file-scope device array of 65536 float64 chunk totals (512 KiB, held on every GPU
  * that loads the library until the process exits), so m is limited to 2^26 terms.
  * The first call on a device (with that device current) looks up the array's device address;
- * make that first call before any stream capture. Calls share the array and keep the last
- * call's contents: calls whose kernels overlap on the GPU race and must be serialised.
+ * make that first call before any stream capture. The address is cached per device ordinal for
+ * the life of the process: after cudaDeviceReset (or anything else that destroys and recreates
+ * the device's primary context) it is stale, so a process that resets a device must not call
+ * rs_cro_sum_noalloc on it again. Calls share the array and keep the last call's contents:
+ * calls whose kernels overlap on the GPU race and must be serialised.
  * a: float64 [m] device; out: float64 [1] device; stream: cudaStream_t as void*.
  * Errors: RS_ERR_INVALID_ARG (m < 0, null pointer), RS_ERR_CAPACITY (m > 2^26), RS_ERR_CUDA. */
 int rs_cro_sum_noalloc(int64_t m, const double* a, double* out, void* stream);

@@ -76,6 +76,7 @@ def _load():
         lib.or_hierarchy_copy.argtypes = [P, P, P, P, P, P, P, P]
         lib.or_hierarchy_free.argtypes = [P]
         lib.or_hierarchy_params.argtypes = [P, P]
+        lib.or_assign_seeds.argtypes = [i64, P, P, f32, i64, P, P, P, P, P, i32, P, P, P]
         lib.or_unbind.argtypes = [i64, P, P, P, P, f32, f32, f64, f64, i32, i32, i32, i32,
                                   P, P, P, P, P]
         lib.or_props.argtypes = [i64, P, P, P, P, P, P, f32, f64, i64, i32, P]
@@ -164,6 +165,24 @@ def hierarchy(pos, vel, ids, fof_label, box, f_num=7, f_den=10, min_size=10, thr
     finally:
         lib.or_hierarchy_free(h)
     return out
+
+
+def assign_seeds(hier, pos, vel, box, threads=None):
+    """Seed halos (nodes without children), each particle's seed and each seed's host, for a
+    hierarchy dict from hierarchy(): (particle_seed [n], node_host [n_nodes], node_count
+    [n_nodes]); -1 = no seed / no host, node_host -2 for nodes that are not seeds."""
+    pos, vel = _c(pos, np.float32), _c(vel, np.float32)
+    nn = len(hier["size"])
+    par, off = _c(hier["parent"], np.int64), _c(hier["member_off"], np.int64)
+    idx, deep = _c(hier["member_idx"], np.int64), _c(hier["deepest"], np.int64)
+    prm = _c(hier["params"], np.float32)
+    ps = np.empty(len(pos), np.int64)
+    host = np.empty(nn, np.int64)
+    cnt = np.empty(nn, np.int64)
+    rc = _load().or_assign_seeds(len(pos), _p(pos), _p(vel), box, nn, _p(par), _p(off), _p(idx),
+                                 _p(deep), _p(prm), _threads(threads), _p(ps), _p(host), _p(cnt))
+    assert rc == 0
+    return ps, host, cnt
 
 
 def unbind(member_off, member_idx, pos, vel, box, eps, G, m, min_size=10, bf_num=1, bf_den=2,

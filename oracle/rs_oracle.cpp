@@ -484,6 +484,106 @@ bool member_energy(const float* u, const float* vel, const int64_t* mem, int64_t
   return (ke + p) < 0.0;
 }
 
+// Seed halos and their particles (the step after the 6D hierarchy; the paper names it only as
+// subhalo finding inside every FoF halo, so this is a stated reading):
+//   seeds: the nodes without children (every level-0 node has at least one under it);
+//   frame: u = C1-wrapped offset from the level-0 node's reference member r0 (its smallest id);
+//   seed s: centre c_s = float(double(wrap(x_{r_s} - x_{r0})) + CRO(u^s) / g_s) with u^s the
+//     offsets from s's own reference member r_s, bulk velocity w_s = float(CRO(v) / g_s), and
+//     the metric scales inv_sx2_s, inv_sv2_s of s's own 6D split;
+//   distance to a seed: fl(|u - c_s|^2 inv_sx2_s) + fl(|v - w_s|^2 inv_sv2_s), float32 in d6's
+//     operation order;
+//   particle: the seed holding it when its deepest node is a seed, otherwise the nearest seed
+//     under its deepest node (ties: the smaller node index);
+//   host of a seed s: among the other seeds of the same level-0 node that rank above it (more
+//     assigned particles; equal counts: the smaller node index ranks above), the nearest by the
+//     candidate's metric evaluated at (c_s, w_s); -1 if none ranks above.
+// Outputs: particle_seed [n] (-1 outside every node), node_host [n_nodes] (-2 for a node that is
+// not a seed), node_count [n_nodes] (particles assigned; 0 for a node that is not a seed).
+inline float metric6(const float* a, const float* b, const float* va, const float* vb, float isx,
+                     float isv) {
+  const float rx = sq3(a[0] - b[0], a[1] - b[1], a[2] - b[2]);
+  const float rv = sq3(va[0] - vb[0], va[1] - vb[1], va[2] - vb[2]);
+  const float x = rx * isx;
+  const float y = rv * isv;
+  return x + y;
+}
+
+int assign_seeds(int64_t n, const float* pos, const float* vel, float L, int64_t nn,
+                 const int64_t* parent, const int64_t* member_off, const int64_t* member_idx,
+                 const int64_t* deepest, const float* params, int threads, int64_t* particle_seed,
+                 int64_t* node_host, int64_t* node_count) {
+  const float hL = 0.5f * L;
+  std::vector<int64_t> nkids(nn, 0), root(nn);
+  for (int64_t q = 0; q < nn; ++q) {
+    if (parent[q] >= 0) nkids[parent[q]]++;
+    root[q] = parent[q] < 0 ? q : root[parent[q]];  // parents precede their children
+  }
+  std::vector<float> cen(3 * nn, 0.f), bulk(3 * nn, 0.f);
+  std::vector<std::vector<int64_t>> under(nn);  // seeds under each node, ascending index
+  for (int64_t s = 0; s < nn; ++s) {
+    node_host[s] = -2;
+    node_count[s] = 0;
+    if (nkids[s] != 0) continue;
+    const int64_t g = member_off[s + 1] - member_off[s];
+    const int64_t* mem = member_idx + member_off[s];
+    const int64_t rs = mem[0], r0 = member_idx[member_off[root[s]]];
+    std::vector<float> u;
+    unwrap_node(pos, mem, g, L, u);
+    for (int d = 0; d < 3; ++d) {
+      const float o = wrap_diff(pos[3 * r0 + d], pos[3 * rs + d], L, hL);
+      const double su = cro_sum(g, [&](int64_t a) { return double(u[3 * a + d]); });
+      const double sv = cro_sum(g, [&](int64_t a) { return double(vel[3 * mem[a] + d]); });
+      cen[3 * s + d] = float(double(o) + su / double(g));
+      bulk[3 * s + d] = float(sv / double(g));
+    }
+    for (int64_t q = s; q >= 0; q = parent[q]) under[q].push_back(s);
+  }
+  for (auto& v : under) std::sort(v.begin(), v.end());
+  for (int64_t i = 0; i < n; ++i) particle_seed[i] = -1;
+  parallel_for(n, threads, [&](int64_t i) {
+    const int64_t dq = deepest[i];
+    if (dq < 0) return;
+    if (nkids[dq] == 0) {
+      particle_seed[i] = dq;
+      return;
+    }
+    const int64_t r0 = member_idx[member_off[root[dq]]];
+    float u[3];
+    for (int d = 0; d < 3; ++d) u[d] = wrap_diff(pos[3 * r0 + d], pos[3 * i + d], L, hL);
+    float best = INFINITY;
+    int64_t arg = -1;
+    for (int64_t s : under[dq]) {
+      const float d = metric6(u, &cen[3 * s], vel + 3 * i, &bulk[3 * s], params[3 * s], params[3 * s + 1]);
+      if (arg < 0 || d < best) {
+        best = d;
+        arg = s;
+      }
+    }
+    particle_seed[i] = arg;
+  });
+  for (int64_t i = 0; i < n; ++i)
+    if (particle_seed[i] >= 0) node_count[particle_seed[i]]++;
+  for (int64_t s = 0; s < nn; ++s) {
+    if (nkids[s] != 0) continue;
+    float best = INFINITY;
+    int64_t arg = -1;
+    for (int64_t h : under[root[s]]) {
+      if (h == s) continue;
+      const bool above = node_count[h] > node_count[s] || (node_count[h] == node_count[s] && h < s);
+      if (!above) continue;
+      const float d = metric6(&cen[3 * s], &cen[3 * h], &bulk[3 * s], &bulk[3 * h], params[3 * h],
+                              params[3 * h + 1]);
+      if (arg < 0 || d < best) {
+        best = d;
+        arg = h;
+      }
+    }
+    node_host[s] = arg;
+  }
+  return 0;
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -614,6 +714,17 @@ int or_hierarchy_copy(void* handle, int64_t* parent, int32_t* level, int64_t* mi
   std::memcpy(member_idx, h->members.data(), sizeof(int64_t) * h->members.size());
   std::memcpy(deepest, h->deepest.data(), sizeof(int64_t) * h->n);
   return 0;
+}
+
+// Seed halos, particle assignment and host relations of a hierarchy (assign_seeds above); the
+// hierarchy arrays as or_hierarchy_copy gives them, params = or_hierarchy_params.
+int or_assign_seeds(int64_t n, const float* pos, const float* vel, float L, int64_t n_nodes,
+                    const int64_t* parent, const int64_t* member_off, const int64_t* member_idx,
+                    const int64_t* deepest, const float* params, int32_t threads,
+                    int64_t* particle_seed, int64_t* node_host, int64_t* node_count) {
+  if (n < 0 || n_nodes < 0) return -1;
+  return assign_seeds(n, pos, vel, L, n_nodes, parent, member_off, member_idx, deepest, params,
+                      std::max(1, int(threads)), particle_seed, node_host, node_count);
 }
 
 // Split parameters of every node: inv_sx2, inv_sv2, l2 (float32 [n_nodes][3]).

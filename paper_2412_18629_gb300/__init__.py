@@ -46,7 +46,7 @@ class rs_config(ctypes.Structure):
         ("bound_den", ctypes.c_int32), ("batched", ctypes.c_int32),
         ("use_surrogate", ctypes.c_int32), ("spot_check", ctypes.c_int32),
         ("tree_min_members", ctypes.c_int32), ("tree_theta", ctypes.c_float),
-        ("surrogate_gate", ctypes.c_int32),
+        ("surrogate_gate", ctypes.c_int32), ("check_ids", ctypes.c_int32),
     ]
 
 
@@ -75,6 +75,7 @@ def load_library():
         lib.rs_fof6d_node_params.argtypes = [P, P, P]
         lib.rs_unbind.argtypes = [P, P, P, P, P, ctypes.POINTER(i64), P]
         lib.rs_halo_props.argtypes = [P, P, P]
+        lib.rs_assign_seeds.argtypes = [P, P, P, P, P, P, ctypes.POINTER(i64), P]
         lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
         lib.rs_sort_pairs.argtypes = [P, i64, ctypes.c_int, P, P, P]
         lib.rs_mlp_set_params.argtypes = [P, P]
@@ -100,7 +101,8 @@ def load_library():
         for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_fof3d", "rs_fof6d", "rs_fof6d_copy",
                      "rs_fof6d_node_params", "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile",
                      "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work", "rs_tuning",
-                     "rs_tree_stats", "rs_tree_record", "rs_tree_bounds"):
+                     "rs_tree_stats", "rs_tree_record", "rs_tree_bounds",
+                     "rs_assign_seeds"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -138,7 +140,8 @@ class Context:
 
     def __init__(self, box, link_len, softening, particle_mass, G=G_NEWTON, f=(7, 10),
                  min_halo_particles=10, bound_frac=(1, 2), device=0, mode="plain",
-                 margin_factor=4.0, spot_check=32, tree_min=0, tree_theta=0.0, surrogate_gate=0):
+                 margin_factor=4.0, spot_check=32, tree_min=0, tree_theta=0.0, surrogate_gate=0,
+                 check_ids=False):
         self.lib = load_library()
         cfg = rs_config()
         cfg.box_L, cfg.link_len, cfg.softening = float(box), float(link_len), float(softening)
@@ -157,6 +160,7 @@ class Context:
         if surrogate_gate not in (0, 1):
             raise ValueError("surrogate_gate must be 0 (held-out maximum) or 1 (calibrated per node)")
         cfg.surrogate_gate = int(surrogate_gate)
+        cfg.check_ids = 1 if check_ids else 0
         self.mode = mode
         self.cfg = cfg
         self.device = int(device)
@@ -300,6 +304,22 @@ def rs_unbind(ctx, pos, vel, want_potential=True, bound_out=None, stream=None):
     ctx.check(ctx.lib.rs_unbind(ctx.handle, _ptr(pos), _ptr(vel), _ptr(phi), _ptr(bound_out),
                                 ctypes.byref(nfb), _stream(stream)))
     return phi, bound_out, nfb.value
+
+
+def rs_assign_seeds(ctx, pos, vel, stream=None):
+    """Seed halos of the last rs_fof6d hierarchy: (particle_seed [n], node_host [n_nodes],
+    node_count [n_nodes]) int64 CUDA tensors and the number of seeds."""
+    torch = _torch()
+    _check_dev(pos, torch.float32, (3,), "pos")
+    _check_dev(vel, torch.float32, (3,), "vel")
+    dev = pos.device
+    ps = torch.empty(ctx.n_particles, dtype=torch.int64, device=dev)
+    host = torch.empty(ctx.n_nodes, dtype=torch.int64, device=dev)
+    cnt = torch.empty(ctx.n_nodes, dtype=torch.int64, device=dev)
+    ns = ctypes.c_int64(0)
+    ctx.check(ctx.lib.rs_assign_seeds(ctx.handle, _ptr(pos), _ptr(vel), _ptr(ps), _ptr(host),
+                                      _ptr(cnt), ctypes.byref(ns), _stream(stream)))
+    return ps, host, cnt, ns.value
 
 
 def rs_halo_props(ctx, props_out=None, stream=None):

@@ -50,6 +50,9 @@ enum Slot : int {
   S_T_OFF, S_T_RANK, S_T_COFF, S_T_NODES, S_T_BOX, S_T_KA, S_T_KB, S_T_VA, S_T_VB, S_T_X, S_T_POS,
   S_T_CELL, S_T_ORDER, S_T_WF, S_T_WL, S_T_WR, S_T_UF, S_T_LIST, S_T_LR, S_T_SX, S_T_REC,
   S_T_WANT,
+  // seed halos (rs_seeds.cu)
+  S_SEED_KIDS, S_SEED_ROOT, S_SEED_UCNT, S_SEED_UOFF, S_SEED_CEN, S_SEED_SUMS, S_SEED_SEG,
+  S_SEED_COUNT, S_SEED_LIST,
   S_NUM_SLOTS
 };
 

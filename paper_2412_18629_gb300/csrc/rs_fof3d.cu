@@ -272,6 +272,49 @@ k_fof_labels(int64_t n, const uint32_t* __restrict__ parent, const uint32_t* __r
 
 }  // namespace
 
+namespace {
+__global__ void k_ids_as_keys(int64_t n, const int64_t* __restrict__ ids, uint64_t* __restrict__ keys,
+                              uint32_t* __restrict__ vals) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = uint64_t(ids[i]);
+  vals[i] = uint32_t(i);
+}
+
+// Invalid ids among the sorted ids: a repeated value, or a negative one (sorted last as uint64).
+__global__ void k_bad_ids(int64_t n, const uint64_t* __restrict__ keys, unsigned long long* __restrict__ bad) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool b = (i > 0 && keys[i] == keys[i - 1]) || (keys[i] >> 63) != 0;
+  rsd::warp_count(bad, b);
+}
+}  // namespace
+
+// The optional check that ids are unique and non-negative (rs_config.check_ids): a 64-bit radix
+// sort of the ids and a comparison of neighbours.
+static int check_ids(rs_ctx* ctx, int64_t n, const int64_t* ids, cudaStream_t st) {
+  using namespace rs;
+  uint64_t* ka = scratch_t<uint64_t>(ctx, S_KEY_A, n);
+  uint64_t* kb = scratch_t<uint64_t>(ctx, S_KEY_B, n);
+  uint32_t* va = scratch_t<uint32_t>(ctx, S_VAL_A, n);
+  uint32_t* vb = scratch_t<uint32_t>(ctx, S_VAL_B, n);
+  unsigned long long* bad = scratch_t<unsigned long long>(ctx, S_COUNTER, 8);
+  if (!ka || !kb || !va || !vb || !bad) return RS_ERR_OOM;
+  k_ids_as_keys<<<grid_for(n, 256), 256, 0, st>>>(n, ids, ka, va);
+  RS_LAUNCHED(ctx, "k_ids_as_keys");
+  uint64_t* ks;
+  uint32_t* vs;
+  RS_TRY(radix_sort_u64(ctx, n, 64, ka, va, kb, vb, &ks, &vs, st));
+  RS_CUDA(ctx, cudaMemsetAsync(bad, 0, 8, st));
+  k_bad_ids<<<grid_for(n, 256), 256, 0, st>>>(n, ks, bad);
+  RS_LAUNCHED(ctx, "k_bad_ids");
+  RS_TRY(read_back(ctx, bad, 8, st));
+  if (ctx->host_box[0] != 0)
+    return set_error(ctx, RS_ERR_INVALID_ARG, "%lld repeated or negative ids",
+                     (long long)ctx->host_box[0]);
+  return RS_OK;
+}
+
 extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t* ids,
                         int64_t* label_out, int64_t* n_groups_out, void* stream) {
   if (!ctx) return RS_ERR_INVALID_ARG;
@@ -286,6 +329,7 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
     if (n_groups_out) *n_groups_out = 0;
     return RS_OK;
   }
+  if (ctx->cfg.check_ids) RS_TRY(check_ids(ctx, n, ids, st));
   Grid3 g;
   RS_TRY(make_grid(ctx, ctx->cfg.box_L, ctx->cfg.link_len, &g));
   using namespace rs;

@@ -121,12 +121,20 @@ __global__ void k_level0_minid(int64_t nodes, const int64_t* __restrict__ node_o
   if (q < nodes) node_minid[q] = ids[mem[node_off[q]]];  // members ascend by id
 }
 
-__global__ void k_group_keys(int64_t n, const int64_t* __restrict__ ids, const int64_t* __restrict__ lab,
-                             int b, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// Sparse labels: all particles ordered by (label, id) with two stable radix sorts, first by id
+// (k_id_keys), then by label (k_label_of: the labels of the id-sorted particles).
+__global__ void k_id_keys(int64_t n, const int64_t* __restrict__ ids, uint64_t* __restrict__ keys,
+                          uint32_t* __restrict__ vals) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  keys[i] = (uint64_t(lab[i]) << b) | uint64_t(ids[i]);
+  keys[i] = uint64_t(ids[i]);
   vals[i] = uint32_t(i);
+}
+
+__global__ void k_label_of(int64_t n, const uint32_t* __restrict__ vals, const int64_t* __restrict__ lab,
+                           uint64_t* __restrict__ keys) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < n) keys[k] = uint64_t(lab[vals[k]]);
 }
 
 // head flag per sorted position (1 where a new label starts); run index comes from a scan.
@@ -710,15 +718,12 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     RS_TRY(read_back(ctx, mx, 16, st));
     const uint64_t max_id = uint64_t(ctx->host_box[0]), max_lab = uint64_t(ctx->host_box[1]);
     if (max_id == ~0ull) return set_error(ctx, RS_ERR_INVALID_ARG, "negative id or label");
-    const uint64_t maxv = std::max(max_id, max_lab);
-    const int b = bits_for(maxv);
-    if (2 * b > 64)
-      return set_error(ctx, RS_ERR_INVALID_ARG, "ids must be below 2^32 (max %llu)",
-                       (unsigned long long)maxv);
-    if (max_lab < std::min<uint64_t>(uint64_t(2 * n + 4096), uint64_t(1) << 31)) {
+    // dense label range: (node << bid | id) keys of the kept particles; otherwise two sorts
+    const int bid = bits_for(max_id);
+    if (max_lab < std::min<uint64_t>(uint64_t(2 * n + 4096), uint64_t(1) << 31) &&
+        bits_for(max_lab + 1) + bid <= 64) {
       // dense label range: count per label, keep, scan, sort the kept particles only
       const int64_t nl = int64_t(max_lab) + 1;
-      const int bid = bits_for(max_id);
       uint32_t* cntl = scratch_t<uint32_t>(ctx, S_ROOT_CNT, size_t(nl));
       int64_t* knode = scratch_t<int64_t>(ctx, S_GKEY_A, size_t(nl) + 1);
       int64_t* koff = scratch_t<int64_t>(ctx, S_GKEY_B, size_t(nl) + 1);
@@ -772,11 +777,19 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
       if (!ka || !kb || !va || !vb || !head || !run_start || !rsize || !keep) return RS_ERR_OOM;
       int64_t* node_of_run = rsize + n + 1;
       int64_t* mem_off = keep + n + 1;
-      k_group_keys<<<grid_for(n, kT), kT, 0, st>>>(n, ids, fof_label, b, ka, va);
-      RS_LAUNCHED(ctx, "k_group_keys");
+      k_id_keys<<<grid_for(n, kT), kT, 0, st>>>(n, ids, ka, va);
+      RS_LAUNCHED(ctx, "k_id_keys");
       uint64_t* keys;
       uint32_t* vals;
-      RS_TRY(radix_sort_u64(ctx, n, 2 * b, ka, va, kb, vb, &keys, &vals, st));
+      RS_TRY(radix_sort_u64(ctx, n, bid, ka, va, kb, vb, &keys, &vals, st));
+      {
+        uint64_t* lk = keys == ka ? kb : ka;  // labels of the id-sorted particles
+        uint32_t* lv = vals == va ? vb : va;
+        k_label_of<<<grid_for(n, kT), kT, 0, st>>>(n, vals, fof_label, lk);
+        RS_LAUNCHED(ctx, "k_label_of");
+        RS_TRY(radix_sort_u64(ctx, n, bits_for(max_lab), lk, vals, keys, lv, &keys, &vals, st));
+      }
+      const int b = 0;  // keys are the labels themselves
       k_run_heads<<<grid_for(n, kT), kT, 0, st>>>(n, keys, b, head);
       RS_LAUNCHED(ctx, "k_run_heads");
       RS_TRY(exclusive_scan_i64(ctx, n, head, head + n, st));

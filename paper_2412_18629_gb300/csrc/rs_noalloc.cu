@@ -8,7 +8,9 @@
 // at most kMaxTerms terms (512 KiB). Every GPU that loads this library holds the array until the
 // process exits. Host code cannot use the array's name as a device address, so the first call
 // on each device (with that device current) looks the address up with cudaGetSymbolAddress and
-// caches it; that first call should therefore happen before any stream capture begins. All
+// caches it; that first call should therefore happen before any stream capture begins. The
+// cache is keyed by device ordinal only: cudaDeviceReset (or any other teardown of the primary
+// context) invalidates the address, and the library cannot notice that. All
 // calls share the array and it keeps the last call's contents: calls whose kernels overlap on
 // the GPU (different streams, or different host threads on one device) race on it and must be
 // serialised by the caller. Nothing needs clearing: a call writes every chunk slot it later

@@ -56,7 +56,29 @@ def test_gradient_exact_integer_case(ctx, n):
     assert sse == sse_o
 
 
+def _bf16(a):
+    """Round float64 values to bf16 (round to nearest even, through float32)."""
+    b = np.asarray(a, np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _flip_bound(x, p):
+    """Per sample, the largest output change a one-ulp change of the bf16 rounding of any hidden
+    activation can cause (2^-8 relative per value; through W2 and W3, ReLU 1-Lipschitz): where a
+    hidden value sits on a bf16 rounding boundary the float32 device and the float64 oracle may
+    round it to neighbouring values."""
+    W1, b1 = _bf16(p[:512]).reshape(8, 64), p[512:576].astype(np.float64)
+    W2, b2 = _bf16(p[576:4672]).reshape(64, 64), p[4672:4736].astype(np.float64)
+    W3 = np.abs(_bf16(p[4736:4800]))
+    h1 = _bf16(np.maximum(_bf16(x) @ W1 + b1, 0.0))
+    h2 = _bf16(np.maximum(h1 @ W2 + b2, 0.0))
+    return 2.0 ** -8 * (np.abs(h2) @ W3 + (np.abs(h1) @ np.abs(W2)) @ W3)
+
+
 def test_forward_and_gradient_random_weights(ctx):
+    """Element by element: every output within 1e-5 relative (floor 1e-2) plus its sample's
+    bf16 rounding-flip bound; every gradient entry within 1e-3 of the gradient's largest entry."""
     import torch
     import paper_2412_18629_gb300 as rs
     rng = np.random.default_rng(7)
@@ -66,15 +88,14 @@ def test_forward_and_gradient_random_weights(ctx):
     rs.rs_mlp_set_params(ctx, p)
     y = rs.rs_mlp_forward(ctx, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
     yo = oracle.mlp_forward(x, p)
-    err = np.abs(y - yo) / np.maximum(np.abs(yo), 1e-2)
-    # float32 vs float64 accumulation; a hidden value may round to the neighbouring bf16 on the
-    # two sides, which moves an output by ~2^-8 of one term: rare, so percentiles are checked.
-    assert np.quantile(err, 0.99) <= 1e-5 and err.max() <= 2e-2
+    tol = 1e-5 * np.maximum(np.abs(yo), 1e-2) + _flip_bound(x, p)
+    assert np.all(np.abs(y - yo) <= tol), np.max(np.abs(y - yo) / tol)
+    # most samples need no flip allowance at all
+    assert np.mean(np.abs(y - yo) <= 1e-5 * np.maximum(np.abs(yo), 1e-2)) >= 0.99
     g, _ = rs.rs_mlp_gradient(ctx, torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
     go, _ = oracle.mlp_gradient(x, t, p)
     g = g.cpu().numpy().astype(np.float64)
-    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
-    assert rel <= 1e-3, rel
+    assert np.all(np.abs(g - go) <= 1e-3 * np.abs(go).max()), np.abs(g - go).max() / np.abs(go).max()
 
 
 def test_training_reduces_loss_and_reports_holdout_error(ctx):

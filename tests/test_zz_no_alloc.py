@@ -54,3 +54,21 @@ def test_noalloc_limits_and_empty():
     rc = lib.rs_cro_sum_noalloc((1 << 26) + 1, ctypes.c_void_p(out.data_ptr()),
                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
     assert rc == 5                                # RS_ERR_CAPACITY, rejected before any launch
+
+
+def test_noalloc_at_the_size_limit():
+    """m = 2^26 terms, the largest accepted size, fills all 65536 chunk slots; the result still
+    equals rs_cro_sum bit for bit."""
+    import torch
+    import paper_2412_18629_gb300 as rs
+    lib = _lib()
+    ctx = rs.Context(box=10.0, link_len=0.2, softening=0.01, particle_mass=1.0)
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device="cuda").manual_seed(7)
+    a = torch.randn(1 << 26, dtype=torch.float64, device="cuda", generator=g)
+    out = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+    assert _noalloc(lib, a, out, stream) == rs.RS_OK
+    want = rs.rs_cro_sum(ctx, a)
+    torch.cuda.synchronize()
+    assert out.item() == want.item()
+    ctx.close()
