@@ -489,7 +489,14 @@ def run_ours(args):
     res, training = {}, None
     # headline: batched + surrogate at the requested step counts
     ctx = rs.Context(mode="surrogate", **mk)
-    training = train_surrogate(ctx, args.train_workload, local, args.train_samples, args.train_epochs)
+    if args.weights:
+        rs.rs_surrogate_load(ctx, args.weights)
+        training = {"loaded": args.weights}
+    else:
+        training = train_surrogate(ctx, args.train_workload, local, args.train_samples,
+                                   args.train_epochs)
+        if args.save_weights and rank == 0:
+            rs.rs_surrogate_save(ctx, args.save_weights)
     res["surrogate"] = _measure(ctx, pos, vel, ids, n, args.steps, args.warmup, ws, local, "surrogate")
     # the other forms, each with its own stated step counts: batched (exact flags), the
     # surrogate with the per-node calibrated gate (opt-in), plain
@@ -503,7 +510,7 @@ def run_ours(args):
         if form == "surrogate_calibrated":
             c = rs.Context(mode="surrogate", surrogate_gate=1, **mk)
             rs.rs_mlp_set_params(c, rs.rs_mlp_get_params(ctx))
-            rs.rs_mlp_set_err_max(c, training["err_max_psi"])
+            rs.rs_mlp_set_err_max(c, rs.rs_mlp_get_err_max(ctx))
         else:
             c = rs.Context(mode=form, **mk)
         res[form] = _measure(c, pos, vel, ids, n, k, w, ws, local, form)
@@ -652,6 +659,9 @@ def main(argv=None):
     ap.add_argument("--e2e-seconds", type=float, default=30.0,
                     help="end-to-end timing: as many steps (at most --steps) as fit in this time")
     ap.add_argument("--train-workload", default=TRAIN_WORKLOAD)
+    ap.add_argument("--weights", default=None,
+                    help="load the surrogate from this checkpoint (rs_surrogate_save) instead of training")
+    ap.add_argument("--save-weights", default=None, help="save the trained surrogate here")
     ap.add_argument("--train-samples", type=int, default=TRAIN_SAMPLES)
     ap.add_argument("--train-epochs", type=int, default=TRAIN_EPOCHS)
     args = ap.parse_args(argv)

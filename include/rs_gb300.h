@@ -280,6 +280,16 @@ int rs_mlp_get_params(rs_ctx* ctx, float* params_host);
 /* Held-out maximum |psi_hat - psi| from training (set by rs_mlp_train, or by the caller): the
  * error of the default gate (and err_max / 8 the floor of the calibrated gate's node error). */
 int rs_mlp_set_err_max(rs_ctx* ctx, float err_max);
+int rs_mlp_get_err_max(rs_ctx* ctx, float* err_max_out);
+
+/* Surrogate checkpoint (host file I/O): rs_surrogate_save writes the context's float32 master
+ * parameters and held-out maximum error to `path` (little endian: magic "RSMLPv01", uint32
+ * 4801, uint32 0, float32 err_max, float32 params[4801], uint64 FNV-1a hash of the params'
+ * bytes); rs_surrogate_load reads such a file into the context (weights and err_max), so a
+ * network trained once serves later runs. Errors: RS_ERR_INVALID_ARG (unopenable, truncated or
+ * corrupt file: bad magic, count or hash), RS_ERR_STATE (save without weights), RS_ERR_CUDA. */
+int rs_surrogate_save(rs_ctx* ctx, const char* path);
+int rs_surrogate_load(rs_ctx* ctx, const char* path);
 
 /* Inference: x float32 [n][8] device -> y float32 [n] device. */
 int rs_mlp_forward(rs_ctx* ctx, int64_t n, const float* x, float* y, void* stream);

@@ -81,12 +81,16 @@ def load_library():
         lib.rs_mlp_set_params.argtypes = [P, P]
         lib.rs_mlp_get_params.argtypes = [P, P]
         lib.rs_mlp_set_err_max.argtypes = [P, ctypes.c_float]
+        lib.rs_mlp_get_err_max.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+        lib.rs_surrogate_save.argtypes = [P, ctypes.c_char_p]
+        lib.rs_surrogate_load.argtypes = [P, ctypes.c_char_p]
         lib.rs_mlp_forward.argtypes = [P, i64, P, P, P]
         lib.rs_mlp_gradient.argtypes = [P, i64, P, P, P, ctypes.POINTER(ctypes.c_double), P]
         lib.rs_mlp_train.argtypes = [P, i64, P, P, i32, i32, ctypes.c_float, ctypes.c_uint64, i32,
                                      i32, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_double), P]
         for name in ("rs_mlp_set_params", "rs_mlp_get_params", "rs_mlp_set_err_max",
+                     "rs_surrogate_save", "rs_surrogate_load", "rs_mlp_get_err_max",
                      "rs_mlp_forward", "rs_mlp_gradient", "rs_mlp_train"):
             getattr(lib, name).restype = i32
         lib.rs_cro_sum_noalloc.argtypes = [i64, P, P, P]
@@ -396,6 +400,22 @@ def rs_mlp_get_params(ctx):
 
 def rs_mlp_set_err_max(ctx, err_max):
     ctx.check(ctx.lib.rs_mlp_set_err_max(ctx.handle, float(err_max)))
+
+
+def rs_mlp_get_err_max(ctx):
+    v = ctypes.c_float(0.0)
+    ctx.check(ctx.lib.rs_mlp_get_err_max(ctx.handle, ctypes.byref(v)))
+    return v.value
+
+
+def rs_surrogate_save(ctx, path):
+    """Write the surrogate's weights and held-out maximum error to `path`."""
+    ctx.check(ctx.lib.rs_surrogate_save(ctx.handle, os.fsencode(path)))
+
+
+def rs_surrogate_load(ctx, path):
+    """Load weights and held-out maximum error written by rs_surrogate_save."""
+    ctx.check(ctx.lib.rs_surrogate_load(ctx.handle, os.fsencode(path)))
 
 
 def rs_mlp_forward(ctx, x, stream=None):

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdio>
 
 #include "rs_cro.cuh"
 
@@ -678,5 +679,69 @@ extern "C" int rs_mlp_train(rs_ctx* ctx, int64_t n, const float* x, const float*
 extern "C" int rs_mlp_set_err_max(rs_ctx* ctx, float err_max) {
   if (!ctx || !(err_max >= 0.f)) return RS_ERR_INVALID_ARG;
   ctx->mlp_err_max = err_max;
+  return RS_OK;
+}
+
+extern "C" int rs_mlp_get_err_max(rs_ctx* ctx, float* err_max_out) {
+  if (!ctx || !err_max_out) return RS_ERR_INVALID_ARG;
+  *err_max_out = ctx->mlp_err_max;
+  return RS_OK;
+}
+
+// ---- Surrogate checkpoint: the float32 master parameters and the held-out maximum error in a
+// little-endian file: magic "RSMLPv01" (8 bytes), uint32 parameter count (4801), uint32 0,
+// float32 err_max, float32 params[4801], uint64 FNV-1a hash of the params' bytes.
+namespace {
+constexpr char kMagic[8] = {'R', 'S', 'M', 'L', 'P', 'v', '0', '1'};
+
+uint64_t fnv1a(const void* data, size_t bytes) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+}  // namespace
+
+extern "C" int rs_surrogate_save(rs_ctx* ctx, const char* path) {
+  if (!ctx || !path) return RS_ERR_INVALID_ARG;
+  ctx->err[0] = 0;
+  std::vector<float> p(kParams);
+  RS_TRY(rs_mlp_get_params(ctx, p.data()));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return set_error(ctx, RS_ERR_INVALID_ARG, "cannot open %s for writing", path);
+  const uint32_t hdr[2] = {uint32_t(kParams), 0u};
+  const float em = ctx->mlp_err_max;
+  const uint64_t h = fnv1a(p.data(), sizeof(float) * kParams);
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, 4, 2, f) == 2 &&
+            std::fwrite(&em, 4, 1, f) == 1 && std::fwrite(p.data(), 4, kParams, f) == size_t(kParams) &&
+            std::fwrite(&h, 8, 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return set_error(ctx, RS_ERR_INVALID_ARG, "short write to %s", path);
+  return RS_OK;
+}
+
+extern "C" int rs_surrogate_load(rs_ctx* ctx, const char* path) {
+  if (!ctx || !path) return RS_ERR_INVALID_ARG;
+  ctx->err[0] = 0;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error(ctx, RS_ERR_INVALID_ARG, "cannot open %s", path);
+  char magic[8];
+  uint32_t hdr[2];
+  float em = 0.f;
+  std::vector<float> p(kParams);
+  uint64_t h = 0;
+  const bool ok = std::fread(magic, 1, 8, f) == 8 && std::fread(hdr, 4, 2, f) == 2 &&
+                  std::fread(&em, 4, 1, f) == 1 && std::fread(p.data(), 4, kParams, f) == size_t(kParams) &&
+                  std::fread(&h, 8, 1, f) == 1;
+  std::fclose(f);
+  if (!ok || std::memcmp(magic, kMagic, 8) != 0 || hdr[0] != uint32_t(kParams))
+    return set_error(ctx, RS_ERR_INVALID_ARG, "%s is not a surrogate checkpoint", path);
+  if (h != fnv1a(p.data(), sizeof(float) * kParams) || !(em >= 0.f))
+    return set_error(ctx, RS_ERR_INVALID_ARG, "%s is corrupt (hash or err_max)", path);
+  RS_TRY(rs_mlp_set_params(ctx, p.data()));
+  ctx->mlp_err_max = em;
   return RS_OK;
 }

@@ -113,3 +113,30 @@ def test_training_reduces_loss_and_reports_holdout_error(ctx):
     p = rs.rs_mlp_get_params(ctx)
     yo = oracle.mlp_forward(x[:512], p)
     assert np.quantile(np.abs(y[:512] - yo), 0.99) <= 1e-4 * np.abs(t).max()
+
+
+def test_checkpoint_round_trip_and_corruption(ctx, tmp_path):
+    """rs_surrogate_save / rs_surrogate_load: weights and held-out maximum error come back bit
+    for bit in a new context (same outputs); a truncated or altered file is rejected."""
+    import torch
+    import paper_2412_18629_gb300 as rs
+    rng = np.random.default_rng(21)
+    p = rng.normal(0, 0.3, P).astype(np.float32)
+    rs.rs_mlp_set_params(ctx, p)
+    rs.rs_mlp_set_err_max(ctx, 1.25)
+    path = str(tmp_path / "w.bin")
+    rs.rs_surrogate_save(ctx, path)
+    other = rs.Context(box=10.0, link_len=0.2, softening=0.01, particle_mass=1.0, mode="surrogate")
+    rs.rs_surrogate_load(other, path)
+    assert np.array_equal(rs.rs_mlp_get_params(other), p) and rs.rs_mlp_get_err_max(other) == 1.25
+    x = torch.from_numpy(rng.normal(0, 1, (1000, 8)).astype(np.float32)).cuda()
+    assert torch.equal(rs.rs_mlp_forward(ctx, x), rs.rs_mlp_forward(other, x))
+    raw = open(path, "rb").read()
+    bad = bytearray(raw)
+    bad[100] ^= 1
+    for i, data in enumerate((raw[:-9], bytes(bad), b"XXXXXXXX" + raw[8:])):
+        q = str(tmp_path / f"bad{i}.bin")
+        open(q, "wb").write(data)
+        with pytest.raises(rs.RSError, match="RS_ERR_INVALID_ARG"):
+            rs.rs_surrogate_load(other, q)
+    other.close()
