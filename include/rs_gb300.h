@@ -69,7 +69,7 @@ typedef struct rs_config {
   int32_t tree_min_members;   /* batched forms: nodes with at least this many members get their
                                  flags from the certified tree bound (see rs_tree_stats) when
                                  rs_unbind is asked for no potential; 0 = 16384, < 0 = never */
-  float tree_theta;           /* opening angle of that bound (0 = 0.5; at most 0.9) */
+  float tree_theta;           /* opening angle of that bound (0 = 0.35; at most 0.9) */
   int32_t surrogate_gate;     /* 0: the error in the gate is the held-out maximum error of the
                                  training (rs_mlp_set_err_max); 1: per node, calibrated on 64
                                  members evaluated exactly, floored at err_max / 8 */
@@ -210,7 +210,7 @@ int rs_halo_props(rs_ctx* ctx, rs_halo_props_t* props_out, void* stream);
  * For nodes with at least tree_min_members members, rs_unbind (called with potential_out NULL)
  * decides most flags from a certified interval of each member's potential sum
  * S_i = sum_{j != i} (|u_j - u_i|^2 + eps^2)^(-1/2) instead of the O(g) direct sum: a
- * Barnes-Hut walk over a Morton-ordered tree of the node (leaves of 32 members, 8 children per
+ * Barnes-Hut walk over a Hilbert-ordered tree of the node (leaves of 32 members, 8 children per
  * cell) takes a cell as its quadrupole expansion when its radius bound a is at most tree_theta
  * times the softened distance R', and adds the rigorous truncation bound (n/R') h^3 / (1 - h),
  * h = a / R' (Legendre expansion of the softened kernel, |P_l| <= 1); float32 rounding is

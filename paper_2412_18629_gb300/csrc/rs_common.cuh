@@ -61,7 +61,7 @@ constexpr int64_t kSurrogateMinMembers = 1024;
 // Default smallest node unbound through the certified tree bound (batched form) and its
 // opening angle (a cell is expanded when its radius bound is at most theta times the distance).
 constexpr int64_t kTreeMinDefault = 16384;
-constexpr float kTreeThetaDefault = 0.5f;
+constexpr float kTreeThetaDefault = 0.35f;
 
 struct Buffer {
   void* ptr = nullptr;
@@ -384,6 +384,47 @@ __device__ __forceinline__ void cro_add(double& acc, double v) {
     acc = (__double_as_longlong(v) << 1) == 0 ? 0.0 : v;
   else
     acc = __dadd_rn(acc, v);
+}
+
+// Place the 10 low bits of x at bit positions 0, 3, 6, ..., 27.
+__device__ __forceinline__ uint32_t spread10(uint32_t x) {
+  x &= 0x3ffu;
+  x = (x | (x << 16)) & 0x030000ffu;
+  x = (x | (x << 8)) & 0x0300f00fu;
+  x = (x | (x << 4)) & 0x030c30c3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+// 3D Hilbert index (B <= 10 bits per axis) of quantised coordinates, by Skilling's transform of
+// the axes into the transposed Hilbert index (J. Skilling, "Programming the Hilbert curve", AIP
+// Conf. Proc. 707, 2004): consecutive indices are face-adjacent cells, so runs of the curve are
+// more compact than runs of the Morton order (no long jumps between octants).
+template <int B>
+__device__ __forceinline__ uint32_t hilbert3(uint32_t x0, uint32_t x1, uint32_t x2) {
+  uint32_t X[3] = {x0, x1, x2};
+  for (uint32_t q = 1u << (B - 1); q > 1; q >>= 1) {
+    const uint32_t p = q - 1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (X[i] & q) {
+        X[0] ^= p;  // invert the low bits of axis 0
+      } else {      // exchange the low bits of axes 0 and i
+        const uint32_t t = (X[0] ^ X[i]) & p;
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  X[1] ^= X[0];  // Gray encode
+  X[2] ^= X[1];
+  uint32_t t = 0;
+  for (uint32_t q = 1u << (B - 1); q > 1; q >>= 1)
+    if (X[2] & q) t ^= q - 1;
+  X[0] ^= t;
+  X[1] ^= t;
+  X[2] ^= t;
+  return spread10(X[2]) | (spread10(X[1]) << 1) | (spread10(X[0]) << 2);  // axis 0 leads
 }
 
 }  // namespace rsd

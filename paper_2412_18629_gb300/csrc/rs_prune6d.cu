@@ -53,51 +53,11 @@ struct Box {
   float2 nhi2;
 };
 
-__device__ __forceinline__ uint32_t spread10(uint32_t x) {
-  // place the 10 bits of x at positions 0, 3, 6, ..., 27
-  x &= 0x3ffu;
-  x = (x | (x << 16)) & 0x030000ffu;
-  x = (x | (x << 8)) & 0x0300f00fu;
-  x = (x | (x << 4)) & 0x030c30c3u;
-  x = (x | (x << 2)) & 0x09249249u;
-  return x;
-}
-
 __device__ __forceinline__ uint32_t quant8(float c) {
   // scaled offset (in units of the node's total position sigma) in [-4, 4) -> 0..255
   float t = (c + 4.0f) * 32.0f;
   t = fminf(fmaxf(t, 0.0f), 255.0f);
   return uint32_t(t);
-}
-
-// 3D Hilbert index (8 bits per axis) of quantised coordinates, by Skilling's transform of the
-// axes into the transposed Hilbert index (J. Skilling, "Programming the Hilbert curve", AIP
-// Conf. Proc. 707, 2004): consecutive indices are face-adjacent cells, so runs of the curve
-// are more compact than runs of the Morton order (no long jumps between octants).
-__device__ __forceinline__ uint32_t hilbert3_8(uint32_t x0, uint32_t x1, uint32_t x2) {
-  uint32_t X[3] = {x0, x1, x2};
-  for (uint32_t q = 1u << 7; q > 1; q >>= 1) {
-    const uint32_t p = q - 1;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      if (X[i] & q) {
-        X[0] ^= p;  // invert the low bits of axis 0
-      } else {      // exchange the low bits of axes 0 and i
-        const uint32_t t = (X[0] ^ X[i]) & p;
-        X[0] ^= t;
-        X[i] ^= t;
-      }
-    }
-  }
-  X[1] ^= X[0];  // Gray encode
-  X[2] ^= X[1];
-  uint32_t t = 0;
-  for (uint32_t q = 1u << 7; q > 1; q >>= 1)
-    if (X[2] & q) t ^= q - 1;
-  X[0] ^= t;
-  X[1] ^= t;
-  X[2] ^= t;
-  return spread10(X[2]) | (spread10(X[1]) << 1) | (spread10(X[0]) << 2);  // axis 0 leads
 }
 
 // 3D Hilbert key of each member's position offset from the node mean (scaled by the node's
@@ -111,7 +71,7 @@ __global__ void k_hilbert3(int64_t mb, int64_t m, int64_t nb, const uint32_t* __
   const uint32_t q = mnode[mb + p];
   const float sx = sqrtf(inv[q].x);
   const float4 u = U[mb + p], mu = mean_u[q];
-  const uint32_t code = hilbert3_8(quant8((u.x - mu.x) * sx), quant8((u.y - mu.y) * sx),
+  const uint32_t code = rsd::hilbert3<8>(quant8((u.x - mu.x) * sx), quant8((u.y - mu.y) * sx),
                                    quant8((u.z - mu.z) * sx));
   keys[p] = (uint64_t(q - nb) << 24) | uint64_t(code);
   vals[p] = uint32_t(p);

@@ -8,7 +8,7 @@
 // float64 canonical-order potential). The flags are therefore identical to the direct sum's.
 //
 // Interval (a Barnes-Hut walk with a rigorous truncation bound):
-//   tree    the node's members sorted by a 30-bit Morton key of their offset u inside the
+//   tree    the node's members sorted by a 30-bit Hilbert key of their offset u inside the
 //           node's bounding box; leaf cells are runs of 32 consecutive members, every level up
 //           groups 8 consecutive cells; per cell: centre c (the member mean, rounded to float32),
 //           count n, dipole p = sum (x_j - c) (small: c is rounded), second moments
@@ -89,15 +89,6 @@ __device__ __forceinline__ float unord(uint32_t o) {
   return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
-__device__ __forceinline__ uint32_t spread10(uint32_t x) {
-  x &= 0x3ffu;
-  x = (x | (x << 16)) & 0x030000ffu;
-  x = (x | (x << 8)) & 0x0300f00fu;
-  x = (x | (x << 4)) & 0x030c30c3u;
-  x = (x | (x << 2)) & 0x09249249u;
-  return x;
-}
-
 // Tree nodes: g >= tmin. Per node q: member count, selection flag and cell count (scanned into
 // member offsets, ranks and cell offsets).
 __global__ void k_tree_sel(int64_t nn, const int64_t* __restrict__ node_size, int64_t tmin,
@@ -144,8 +135,8 @@ __global__ void k_tree_bbox(int64_t m, const uint32_t* __restrict__ mnode, const
   }
 }
 
-// Sort keys of the tree members: tree rank above a 30-bit Morton key of the position inside the
-// node's bounding cube (10 bits per axis).
+// Sort keys of the tree members: tree rank above a 30-bit Hilbert key of the position inside
+// the node's bounding cube (10 bits per axis; runs of the curve make compact cells).
 __global__ void k_tree_keys(int64_t m, const uint32_t* __restrict__ mnode, const int64_t* __restrict__ node_off,
                             const int64_t* __restrict__ node_size, int64_t tmin,
                             const int64_t* __restrict__ toff, const int64_t* __restrict__ rank,
@@ -165,7 +156,7 @@ __global__ void k_tree_keys(int64_t m, const uint32_t* __restrict__ mnode, const
   uint32_t qc[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) qc[d] = uint32_t(fminf(fmaxf((c[d] - lo[d]) * sc, 0.f), 1023.f));
-  const uint32_t code = (spread10(qc[0]) << 2) | (spread10(qc[1]) << 1) | spread10(qc[2]);
+  const uint32_t code = rsd::hilbert3<10>(qc[0], qc[1], qc[2]);
   const int64_t k = toff[q] + (p - node_off[q]);
   keys[k] = (uint64_t(rank[q]) << 30) | uint64_t(code);
   vals[k] = uint32_t(p);
