@@ -466,7 +466,8 @@ def _form_entry(r, traffic):
             "launches_per_step": r["launches_per_step"], "fallback_members": r["fallback"],
             "kernels_ms_profiled_step": {k: t[0] for k, t in r["prof"].items()},
             "roofline": roofline(r, traffic), "stages": stages(r), "clocks": r["clocks"],
-            "autotune": r["autotune"], "tree_stats": r["tree"],
+            "autotune": r["autotune"], "tree_stats": r["tree"], "work_tallies": r["work"],
+            "sort_keypasses_per_step": r["sort_keypasses"],
             "surrogate_stats": r["surrogate_stats"], "output_digest": r["digest"]}
 
 

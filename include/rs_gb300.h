@@ -200,6 +200,24 @@ int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float* potential_
 int rs_assign_seeds(rs_ctx* ctx, const float* pos, const float* vel, int64_t* particle_seed,
                     int64_t* node_host, int64_t* node_count, int64_t* n_seeds_out, void* stream);
 
+/* Temporal tracking of seed halos between two snapshots of the same particles (the paper's
+ * Summary names temporal tracking among Rockstar's features; the reading, the CPU oracle's bit
+ * for bit): particles are matched by id; the progenitor of a seed h2 of the later snapshot is
+ * the seed h1 of the earlier one holding the most of h2's particles (ties: the smaller index;
+ * -1 when none is in a seed earlier); the descendant of h1 is the seed h2 receiving the most of
+ * h1's particles (ties: the smaller index). Particles missing from one snapshot or in no seed
+ * are ignored; ids must be unique and non-negative within each snapshot.
+ * n1, ids1, seed1: the earlier snapshot (int64 [n1] device; seed1 = rs_assign_seeds'
+ * particle_seed, node indices or -1); n_nodes1 its node count; likewise n2, ids2, seed2,
+ * n_nodes2 for the later one.
+ * progenitor, prog_shared: int64 [n_nodes2] device (-1 / 0 for nodes without progenitor);
+ * descendant, desc_shared: int64 [n_nodes1] device. Work on `stream`; synchronises it.
+ * Errors: RS_ERR_INVALID_ARG (sizes >= 2^32 - 1, null pointers), RS_ERR_OOM, RS_ERR_CUDA. */
+int rs_track(rs_ctx* ctx, int64_t n1, const int64_t* ids1, const int64_t* seed1, int64_t n_nodes1,
+             int64_t n2, const int64_t* ids2, const int64_t* seed2, int64_t n_nodes2,
+             int64_t* progenitor, int64_t* prog_shared, int64_t* descendant,
+             int64_t* desc_shared, void* stream);
+
 /* Halo properties of every node of the hierarchy over its bound members (last rs_unbind),
  * float64 sums in the canonical reduction order over members in ascending id order with
  * unbound members contributing 0.

@@ -77,6 +77,7 @@ def _load():
         lib.or_hierarchy_free.argtypes = [P]
         lib.or_hierarchy_params.argtypes = [P, P]
         lib.or_assign_seeds.argtypes = [i64, P, P, f32, i64, P, P, P, P, P, i32, P, P, P]
+        lib.or_track.argtypes = [i64, P, P, i64, i64, P, P, i64, P, P, P, P]
         lib.or_unbind.argtypes = [i64, P, P, P, P, f32, f32, f64, f64, i32, i32, i32, i32,
                                   P, P, P, P, P]
         lib.or_props.argtypes = [i64, P, P, P, P, P, P, f32, f64, i64, i32, P]
@@ -183,6 +184,19 @@ def assign_seeds(hier, pos, vel, box, threads=None):
                                  _p(deep), _p(prm), _threads(threads), _p(ps), _p(host), _p(cnt))
     assert rc == 0
     return ps, host, cnt
+
+
+def track(ids1, seed1, nn1, ids2, seed2, nn2):
+    """Progenitors and descendants of seed halos between two snapshots matched by id:
+    (prog [nn2], prog_shared [nn2], desc [nn1], desc_shared [nn1])."""
+    ids1, seed1 = _c(ids1, np.int64), _c(seed1, np.int64)
+    ids2, seed2 = _c(ids2, np.int64), _c(seed2, np.int64)
+    prog, ps = np.empty(nn2, np.int64), np.empty(nn2, np.int64)
+    desc, ds = np.empty(nn1, np.int64), np.empty(nn1, np.int64)
+    rc = _load().or_track(len(ids1), _p(ids1), _p(seed1), nn1, len(ids2), _p(ids2), _p(seed2), nn2,
+                          _p(prog), _p(ps), _p(desc), _p(ds))
+    assert rc == 0
+    return prog, ps, desc, ds
 
 
 def unbind(member_off, member_idx, pos, vel, box, eps, G, m, min_size=10, bf_num=1, bf_den=2,

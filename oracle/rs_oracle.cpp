@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <thread>
 #include <unordered_map>
@@ -725,6 +726,53 @@ int or_assign_seeds(int64_t n, const float* pos, const float* vel, float L, int6
   if (n < 0 || n_nodes < 0) return -1;
   return assign_seeds(n, pos, vel, L, n_nodes, parent, member_off, member_idx, deepest, params,
                       std::max(1, int(threads)), particle_seed, node_host, node_count);
+}
+
+// Temporal tracking of seed halos between two snapshots of the same particles (matched by id;
+// the paper's Summary names temporal tracking, the method is a stated reading): the progenitor
+// of a seed h2 of the later snapshot is the seed h1 of the earlier one holding the most of h2's
+// particles (ties: the smaller index; -1 when none of h2's particles is in a seed of the earlier
+// snapshot); the descendant of h1 is the seed h2 receiving the most of h1's particles (ties:
+// the smaller index). Shared counts are returned beside them. Particles absent from one snapshot
+// or in no seed are ignored. seed1 / seed2: per particle, a node index or -1 (as or_assign_seeds
+// gives them); nn1 / nn2: node counts (outputs are per node, -1 / 0 for nodes that are no seed).
+int or_track(int64_t n1, const int64_t* ids1, const int64_t* seed1, int64_t nn1, int64_t n2,
+             const int64_t* ids2, const int64_t* seed2, int64_t nn2, int64_t* prog,
+             int64_t* prog_shared, int64_t* desc, int64_t* desc_shared) {
+  if (n1 < 0 || n2 < 0 || nn1 < 0 || nn2 < 0) return -1;
+  std::unordered_map<int64_t, int64_t> where;
+  where.reserve(size_t(n1) * 2 + 1);
+  for (int64_t i = 0; i < n1; ++i) where[ids1[i]] = seed1[i];
+  std::map<std::pair<int64_t, int64_t>, int64_t> shared;  // (h2, h1) -> particles
+  for (int64_t j = 0; j < n2; ++j) {
+    if (seed2[j] < 0) continue;
+    auto it = where.find(ids2[j]);
+    if (it == where.end() || it->second < 0) continue;
+    shared[{seed2[j], it->second}]++;
+  }
+  for (int64_t q = 0; q < nn2; ++q) {
+    prog[q] = -1;
+    prog_shared[q] = 0;
+  }
+  for (int64_t q = 0; q < nn1; ++q) {
+    desc[q] = -1;
+    desc_shared[q] = 0;
+  }
+  for (const auto& kv : shared) {  // ascending (h2, h1): the first maximum has the smaller h1
+    const int64_t h2 = kv.first.first, h1 = kv.first.second, c = kv.second;
+    if (c > prog_shared[h2]) {
+      prog_shared[h2] = c;
+      prog[h2] = h1;
+    }
+  }
+  for (const auto& kv : shared) {
+    const int64_t h2 = kv.first.first, h1 = kv.first.second, c = kv.second;
+    if (c > desc_shared[h1] || (c == desc_shared[h1] && h2 < desc[h1])) {
+      desc_shared[h1] = c;
+      desc[h1] = h2;
+    }
+  }
+  return 0;
 }
 
 // Split parameters of every node: inv_sx2, inv_sv2, l2 (float32 [n_nodes][3]).

@@ -76,6 +76,7 @@ def load_library():
         lib.rs_unbind.argtypes = [P, P, P, P, P, ctypes.POINTER(i64), P]
         lib.rs_halo_props.argtypes = [P, P, P]
         lib.rs_assign_seeds.argtypes = [P, P, P, P, P, P, ctypes.POINTER(i64), P]
+        lib.rs_track.argtypes = [P, i64, P, P, i64, i64, P, P, i64, P, P, P, P, P]
         lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
         lib.rs_sort_pairs.argtypes = [P, i64, ctypes.c_int, P, P, P]
         lib.rs_mlp_set_params.argtypes = [P, P]
@@ -106,7 +107,7 @@ def load_library():
                      "rs_fof6d_node_params", "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile",
                      "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work", "rs_tuning",
                      "rs_tree_stats", "rs_tree_record", "rs_tree_bounds",
-                     "rs_assign_seeds"):
+                     "rs_assign_seeds", "rs_track"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -324,6 +325,23 @@ def rs_assign_seeds(ctx, pos, vel, stream=None):
     ctx.check(ctx.lib.rs_assign_seeds(ctx.handle, _ptr(pos), _ptr(vel), _ptr(ps), _ptr(host),
                                       _ptr(cnt), ctypes.byref(ns), _stream(stream)))
     return ps, host, cnt, ns.value
+
+
+def rs_track(ctx, ids1, seed1, n_nodes1, ids2, seed2, n_nodes2, stream=None):
+    """Progenitors (and shared counts) of the later snapshot's seeds, descendants (and shared
+    counts) of the earlier snapshot's seeds: four int64 CUDA tensors."""
+    torch = _torch()
+    for t, nm in ((ids1, "ids1"), (seed1, "seed1"), (ids2, "ids2"), (seed2, "seed2")):
+        _check_dev(t, torch.int64, None, nm)
+    dev = ids2.device
+    prog = torch.empty(n_nodes2, dtype=torch.int64, device=dev)
+    ps = torch.empty(n_nodes2, dtype=torch.int64, device=dev)
+    desc = torch.empty(n_nodes1, dtype=torch.int64, device=dev)
+    ds = torch.empty(n_nodes1, dtype=torch.int64, device=dev)
+    ctx.check(ctx.lib.rs_track(ctx.handle, ids1.numel(), _ptr(ids1), _ptr(seed1), int(n_nodes1),
+                               ids2.numel(), _ptr(ids2), _ptr(seed2), int(n_nodes2), _ptr(prog),
+                               _ptr(ps), _ptr(desc), _ptr(ds), _stream(stream)))
+    return prog, ps, desc, ds
 
 
 def rs_halo_props(ctx, props_out=None, stream=None):

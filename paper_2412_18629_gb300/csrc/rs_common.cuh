@@ -23,7 +23,7 @@ namespace rs {
 enum Slot : int {
   // rs_fof3d
   S_KEY_A, S_KEY_B, S_VAL_A, S_VAL_B, S_SORT_HIST, S_POS_SORTED, S_ROW_START, S_CELL_END,
-  S_PARENT, S_MINID, S_COUNTER,
+  S_PARENT, S_MINID, S_COUNTER, S_OCC,
   // rs_fof6d (level work)
   S_GKEY_A, S_GKEY_B, S_GVAL_A, S_GVAL_B, S_NN2, S_UF, S_ROOT_CNT, S_CHILD_IDX, S_FLAGS,
   S_SCAN_TMP, S_CHUNK_OFF, S_CHUNK_SUM, S_NODE_TMP, S_SELECT,
@@ -53,6 +53,9 @@ enum Slot : int {
   // seed halos (rs_seeds.cu)
   S_SEED_KIDS, S_SEED_ROOT, S_SEED_UCNT, S_SEED_UOFF, S_SEED_CEN, S_SEED_SUMS, S_SEED_SEG,
   S_SEED_COUNT, S_SEED_LIST,
+  // temporal tracking (rs_track.cu)
+  S_TRK_HEAD, S_TRK_RSTART, S_TRK_RKEY, S_TRK_KA, S_TRK_KB, S_TRK_VA, S_TRK_VB, S_TRK_H1,
+  S_TRK_FLAG,
   S_NUM_SLOTS
 };
 

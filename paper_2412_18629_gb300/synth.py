@@ -186,6 +186,29 @@ def generate(spec: SnapshotSpec) -> dict:
     }
 
 
+MPC_PER_GYR_PER_KMS = 1.0227  # 1 km/s sustained for 1 Gyr covers 1.0227 Mpc
+
+
+def evolve(snap: dict, dt_gyr: float, seed: int, kick_kms: float = 5.0) -> dict:
+    """The same particles a short time later, for temporal tracking: positions drifted
+    ballistically by v dt (no forces; h taken as 1 in the unit conversion), wrapped into the box;
+    velocities given a Gaussian kick of kick_kms per component; particle order reshuffled (each
+    id follows its particle). A stand-in for the next output of a simulation."""
+    rng = np.random.default_rng(seed)
+    L = float(snap["box"])
+    pos64 = snap["pos"].astype(np.float64) + snap["vel"].astype(np.float64) * (MPC_PER_GYR_PER_KMS * dt_gyr)
+    pos64 = np.mod(pos64, L)
+    pos = pos64.astype(np.float32)
+    pos[pos >= np.float32(L)] = 0.0
+    vel = (snap["vel"].astype(np.float64) + rng.normal(0.0, kick_kms, snap["vel"].shape)).astype(np.float32)
+    order = rng.permutation(len(pos))
+    out = dict(snap)
+    out["pos"] = np.ascontiguousarray(pos[order])
+    out["vel"] = np.ascontiguousarray(vel[order])
+    out["ids"] = np.ascontiguousarray(snap["ids"][order])
+    return out
+
+
 def subsample(snap: dict, keep: np.ndarray) -> dict:
     """A snapshot restricted to the particles selected by the boolean mask `keep`."""
     out = dict(snap)
