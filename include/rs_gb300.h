@@ -75,6 +75,8 @@ typedef struct rs_config {
                                  members evaluated exactly, floored at err_max / 8 */
   int32_t check_ids;          /* 1: rs_fof3d first verifies that the ids are unique and
                                  non-negative (one 64-bit sort), RS_ERR_INVALID_ARG otherwise */
+  int32_t unbind_passes;      /* 0 or 1: one unbinding pass; P > 1: iterative unbinding, up to P
+                                 passes (see rs_unbind); plain and batched forms only */
 } rs_config;
 
 /* Per-node halo properties written by rs_halo_props (all over the node's BOUND members). */
@@ -97,7 +99,8 @@ typedef struct rs_ctx rs_ctx;
 /* Create a context on CUDA device `device` with a copy of *cfg. Validates cfg: box_L > 0,
  * link_len > 0 (rs_fof3d rejects a box of more than 4096 sub-cells per axis), softening >= 0,
  * particle_mass > 0, G > 0, 0 < f_num <= f_den, min_halo_particles >= 2, bound_num >= 0,
- * bound_den > 0, 0 <= tree_theta <= 0.9, surrogate_gate 0 or 1, spot_check >= 0.
+ * bound_den > 0, 0 <= tree_theta <= 0.9, surrogate_gate 0 or 1, spot_check >= 0,
+ * unbind_passes >= 0.
  * out: host pointer receiving the context. No device memory is allocated yet. */
 int rs_ctx_create(rs_ctx** out, const rs_config* cfg, int device);
 
@@ -169,13 +172,24 @@ int rs_fof6d_node_params(rs_ctx* ctx, float* params_out, void* stream);
  * N_bound >= min_halo_particles and bound_den * N_bound >= bound_num * n.
  * The potential is computed in float32 with a certified error bound; members whose energy
  * is within that bound of zero are recomputed exactly in float64, so flags are exact.
- * potential_out: float32 [n_members] device (member CSR order) or NULL.
+ * Iterative unbinding (rs_config.unbind_passes = P > 1; the paper's Rockstar unbinds in
+ * passes, the build offers it as an option): pass p > 1 recomputes v_bulk (canonical-order sum
+ * over the members still bound, the others contributing 0.0, divided by their count) and the
+ * potential of every member still bound over the members still bound only (the others
+ * contributing 0.0 like the self term), re-flags them and leaves the others unbound; it stops
+ * after P passes or when a pass removes nobody (rs_unbind_passes tells how many ran). Every
+ * pass's flags are exact. Not with the surrogate (RS_ERR_INVALID_ARG).
+ * potential_out: float32 [n_members] device (member CSR order) or NULL; with passes, each
+ * member's potential from the last pass that evaluated it.
  * bound_out:     uint8 [n_members] device (member CSR order), 1 = bound.
  * n_fallback_out: host, may be NULL: members recomputed in float64.
  * Synchronises `stream`. Errors: RS_ERR_STATE (no hierarchy), RS_ERR_INVALID_ARG,
  * RS_ERR_CUDA. */
 int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float* potential_out,
               uint8_t* bound_out, int64_t* n_fallback_out, void* stream);
+
+/* Unbinding passes the last rs_unbind ran (1 without iterative unbinding). */
+int rs_unbind_passes(rs_ctx* ctx);
 
 /* Seed halos and the assignment of every FoF-group particle to one of them (Section
  * "Parallelization": subhalo finding inside every FoF halo; the step after the hierarchy). The

@@ -80,6 +80,8 @@ def _load():
         lib.or_track.argtypes = [i64, P, P, i64, i64, P, P, i64, P, P, P, P]
         lib.or_unbind.argtypes = [i64, P, P, P, P, f32, f32, f64, f64, i32, i32, i32, i32,
                                   P, P, P, P, P]
+        lib.or_unbind_iter.argtypes = [i64, P, P, P, P, f32, f32, f64, f64, i32, i32, i32, i32,
+                                       i32, P, P, P, P, P]
         lib.or_props.argtypes = [i64, P, P, P, P, P, P, f32, f64, i64, i32, P]
         lib.or_mlp_forward.argtypes = [i64, P, P, i32, P]
         lib.or_mlp_gradient.argtypes = [i64, P, P, P, i32, P, ctypes.POINTER(f64)]
@@ -200,8 +202,9 @@ def track(ids1, seed1, nn1, ids2, seed2, nn2):
 
 
 def unbind(member_off, member_idx, pos, vel, box, eps, G, m, min_size=10, bf_num=1, bf_den=2,
-           threads=None, want_phi=True):
-    """Potential (float64 per member), bound flags, and per-node n_bound / is_halo / m_bound."""
+           threads=None, want_phi=True, passes=1):
+    """Potential (float64 per member), bound flags, and per-node n_bound / is_halo / m_bound;
+    passes > 1: iterative unbinding over the members still bound (or_unbind_iter)."""
     off, idx = _c(member_off, np.int64), _c(member_idx, np.int64)
     pos, vel = _c(pos, np.float32), _c(vel, np.float32)
     n_nodes, n_mem = len(off) - 1, int(off[-1]) if len(off) else 0
@@ -210,9 +213,9 @@ def unbind(member_off, member_idx, pos, vel, box, eps, G, m, min_size=10, bf_num
     nb = np.empty(n_nodes, np.int64)
     halo = np.empty(n_nodes, np.uint8)
     mb = np.empty(n_nodes, np.float64)
-    rc = _load().or_unbind(n_nodes, _p(off), _p(idx), _p(pos), _p(vel), box, eps, G, m,
-                           min_size, bf_num, bf_den, _threads(threads), _p(phi), _p(bound),
-                           _p(nb), _p(halo), _p(mb))
+    rc = _load().or_unbind_iter(n_nodes, _p(off), _p(idx), _p(pos), _p(vel), box, eps, G, m,
+                                min_size, bf_num, bf_den, int(passes), _threads(threads), _p(phi),
+                                _p(bound), _p(nb), _p(halo), _p(mb))
     assert rc == 0
     return {"phi": phi, "bound": bound, "n_bound": nb, "is_halo": halo, "m_bound": mb}
 

@@ -462,14 +462,16 @@ void bulk_velocity(const float* vel, const int64_t* mem, int64_t g, double* vb) 
     vb[d] = cro_sum(g, [&](int64_t a) { return double(vel[3 * mem[a] + d]); }) / double(g);
 }
 
-// Potential and flag of member i of a node (unwrapped positions u, bulk velocity vb):
+// Potential and flag of member i of a node (unwrapped positions u, bulk velocity vb; members j
+// with in[j] == 0 contribute 0.0 when the mask `in` is given):
 //   phi_i = -(G m) CRO_j( j == i ? 0 : 1 / sqrt(((Dx Dx + Dy Dy) + Dz Dz) + eps^2) ),
 //   D = (double)u_j - (double)u_i; KE_i = 0.5 ((dvx dvx + dvy dvy) + dvz dvz),
 //   dv = (double)v_i - vb; bound iff KE_i + phi_i < 0.
 bool member_energy(const float* u, const float* vel, const int64_t* mem, int64_t g, int64_t i,
-                   const double* vb, double eps2, double Gm, double* phi_out) {
+                   const double* vb, double eps2, double Gm, double* phi_out,
+                   const uint8_t* in = nullptr) {
   const double s = cro_sum(g, [&](int64_t j) {
-    if (j == i) return 0.0;
+    if (j == i || (in && !in[j])) return 0.0;
     const double dx = double(u[3 * j]) - double(u[3 * i]);
     const double dy = double(u[3 * j + 1]) - double(u[3 * i + 1]);
     const double dz = double(u[3 * j + 2]) - double(u[3 * i + 2]);
@@ -595,6 +597,11 @@ extern "C" {
 int or_split_node_ex(int64_t g, const float* u, const float* v, int32_t f_num, int32_t f_den,
                      int32_t pruned, int32_t threads, float* scal_out, float* nn2_out,
                      int64_t* comp_out);
+int or_unbind_iter(int64_t n_nodes, const int64_t* member_off, const int64_t* member_idx,
+                   const float* pos, const float* vel, float L, float eps, double G, double m,
+                   int32_t min_size, int32_t bf_num, int32_t bf_den, int32_t passes,
+                   int32_t threads, double* phi, uint8_t* bound, int64_t* n_bound,
+                   uint8_t* is_halo, double* m_bound);
 
 // Brute-force 3D FoF over all pairs: labels[i] = smallest id of i's component.
 int or_fof3d_brute(int64_t n, const float* pos, const int64_t* ids, float L, float ll,
@@ -799,7 +806,22 @@ int or_unbind(int64_t n_nodes, const int64_t* member_off, const int64_t* member_
               const float* pos, const float* vel, float L, float eps, double G, double m,
               int32_t min_size, int32_t bf_num, int32_t bf_den, int32_t threads, double* phi,
               uint8_t* bound, int64_t* n_bound, uint8_t* is_halo, double* m_bound) {
-  if (n_nodes < 0 || bf_den <= 0) return -1;
+  return or_unbind_iter(n_nodes, member_off, member_idx, pos, vel, L, eps, G, m, min_size, bf_num,
+                        bf_den, 1, threads, phi, bound, n_bound, is_halo, m_bound);
+}
+
+// or_unbind with iterative passes: pass 1 as above; pass p > 1 recomputes the bulk velocity
+// (CRO over the members still bound, the others contributing 0.0, divided by their count) and
+// the potential of every member still bound over the members still bound (the others
+// contributing 0.0 like the self term), re-flags them, and leaves the others unbound; it stops
+// after `passes` passes or when a pass changes no flag. phi holds each member's potential from
+// the last pass that evaluated it.
+int or_unbind_iter(int64_t n_nodes, const int64_t* member_off, const int64_t* member_idx,
+                   const float* pos, const float* vel, float L, float eps, double G, double m,
+                   int32_t min_size, int32_t bf_num, int32_t bf_den, int32_t passes,
+                   int32_t threads, double* phi, uint8_t* bound, int64_t* n_bound,
+                   uint8_t* is_halo, double* m_bound) {
+  if (n_nodes < 0 || bf_den <= 0 || passes < 1) return -1;
   const double Gm = G * m;
   const double eps2 = double(eps) * double(eps);
   parallel_for(n_nodes, threads, [&](int64_t q) {
@@ -807,16 +829,31 @@ int or_unbind(int64_t n_nodes, const int64_t* member_off, const int64_t* member_
     const int64_t* mem = member_idx + off;
     std::vector<float> u;
     unwrap_node(pos, mem, g, L, u);
-    double vb[3];
-    bulk_velocity(vel, mem, g, vb);
+    std::vector<uint8_t> in(g, 1), next(g, 0);
     int64_t nb = 0;
-    for (int64_t i = 0; i < g; ++i) {
-      double p;
-      const bool b = member_energy(u.data(), vel, mem, g, i, vb, eps2, Gm, &p);
-      if (phi) phi[off + i] = p;
-      bound[off + i] = b ? 1 : 0;
-      nb += b ? 1 : 0;
+    for (int32_t pass = 0; pass < passes; ++pass) {
+      int64_t cnt = 0;
+      for (int64_t a = 0; a < g; ++a) cnt += in[a];
+      if (cnt == 0) break;
+      double vb[3];
+      for (int d = 0; d < 3; ++d)
+        vb[d] = cro_sum(g, [&](int64_t a) { return in[a] ? double(vel[3 * mem[a] + d]) : 0.0; }) / double(cnt);
+      nb = 0;
+      bool changed = false;
+      for (int64_t i = 0; i < g; ++i) {
+        next[i] = 0;
+        if (!in[i]) continue;
+        double p;
+        const bool b = member_energy(u.data(), vel, mem, g, i, vb, eps2, Gm, &p, in.data());
+        if (phi) phi[off + i] = p;
+        next[i] = b ? 1 : 0;
+        nb += b ? 1 : 0;
+        changed = changed || !b;
+      }
+      in.swap(next);
+      if (!changed) break;
     }
+    for (int64_t i = 0; i < g; ++i) bound[off + i] = in[i];
     n_bound[q] = nb;
     is_halo[q] = (nb >= min_size && int64_t(bf_den) * nb >= int64_t(bf_num) * g) ? 1 : 0;
     m_bound[q] = double(nb) * m;

@@ -47,6 +47,7 @@ class rs_config(ctypes.Structure):
         ("use_surrogate", ctypes.c_int32), ("spot_check", ctypes.c_int32),
         ("tree_min_members", ctypes.c_int32), ("tree_theta", ctypes.c_float),
         ("surrogate_gate", ctypes.c_int32), ("check_ids", ctypes.c_int32),
+        ("unbind_passes", ctypes.c_int32),
     ]
 
 
@@ -77,6 +78,7 @@ def load_library():
         lib.rs_halo_props.argtypes = [P, P, P]
         lib.rs_assign_seeds.argtypes = [P, P, P, P, P, P, ctypes.POINTER(i64), P]
         lib.rs_track.argtypes = [P, i64, P, P, i64, i64, P, P, i64, P, P, P, P, P]
+        lib.rs_unbind_passes.argtypes = [P]
         lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
         lib.rs_sort_pairs.argtypes = [P, i64, ctypes.c_int, P, P, P]
         lib.rs_mlp_set_params.argtypes = [P, P]
@@ -107,7 +109,7 @@ def load_library():
                      "rs_fof6d_node_params", "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile",
                      "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work", "rs_tuning",
                      "rs_tree_stats", "rs_tree_record", "rs_tree_bounds",
-                     "rs_assign_seeds", "rs_track"):
+                     "rs_assign_seeds", "rs_track", "rs_unbind_passes"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -146,7 +148,7 @@ class Context:
     def __init__(self, box, link_len, softening, particle_mass, G=G_NEWTON, f=(7, 10),
                  min_halo_particles=10, bound_frac=(1, 2), device=0, mode="plain",
                  margin_factor=4.0, spot_check=32, tree_min=0, tree_theta=0.0, surrogate_gate=0,
-                 check_ids=False):
+                 check_ids=False, unbind_passes=1):
         self.lib = load_library()
         cfg = rs_config()
         cfg.box_L, cfg.link_len, cfg.softening = float(box), float(link_len), float(softening)
@@ -166,6 +168,7 @@ class Context:
             raise ValueError("surrogate_gate must be 0 (held-out maximum) or 1 (calibrated per node)")
         cfg.surrogate_gate = int(surrogate_gate)
         cfg.check_ids = 1 if check_ids else 0
+        cfg.unbind_passes = int(unbind_passes)
         self.mode = mode
         self.cfg = cfg
         self.device = int(device)
@@ -342,6 +345,11 @@ def rs_track(ctx, ids1, seed1, n_nodes1, ids2, seed2, n_nodes2, stream=None):
                                ids2.numel(), _ptr(ids2), _ptr(seed2), int(n_nodes2), _ptr(prog),
                                _ptr(ps), _ptr(desc), _ptr(ds), _stream(stream)))
     return prog, ps, desc, ds
+
+
+def rs_unbind_passes(ctx):
+    """Unbinding passes the last rs_unbind ran."""
+    return int(ctx.lib.rs_unbind_passes(ctx.handle))
 
 
 def rs_halo_props(ctx, props_out=None, stream=None):

@@ -10,7 +10,8 @@ extern "C" int rs_ctx_create(rs_ctx** out, const rs_config* cfg, int device) {
       !(cfg->particle_mass > 0.0) || !(cfg->G > 0.0) || cfg->f_num <= 0 || cfg->f_den <= 0 ||
       cfg->f_num > cfg->f_den || cfg->min_halo_particles < 2 || cfg->bound_num < 0 ||
       cfg->bound_den <= 0 || !(cfg->tree_theta >= 0.f && cfg->tree_theta <= 0.9f) ||
-      cfg->surrogate_gate < 0 || cfg->surrogate_gate > 1 || cfg->spot_check < 0)
+      cfg->surrogate_gate < 0 || cfg->surrogate_gate > 1 || cfg->spot_check < 0 ||
+      cfg->unbind_passes < 0)
     return RS_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

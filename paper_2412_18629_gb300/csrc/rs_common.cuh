@@ -56,6 +56,8 @@ enum Slot : int {
   // temporal tracking (rs_track.cu)
   S_TRK_HEAD, S_TRK_RSTART, S_TRK_RKEY, S_TRK_KA, S_TRK_KB, S_TRK_VA, S_TRK_VB, S_TRK_H1,
   S_TRK_FLAG,
+  // iterative unbinding (rs_unbind.cu)
+  S_U_PREV, S_U_UM, S_U_PCNT,
   S_NUM_SLOTS
 };
 
@@ -105,6 +107,7 @@ struct rs_ctx {
   bool tree_record = false;     // record each member's interval (rs_tree_record)
   bool tree_recorded = false;
   int64_t tree_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int32_t unbind_passes_run = 0;  // passes the last rs_unbind ran (iterative unbinding)
   // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
   bool profile = false;
   bool count_work = false;  // counting variants of the pruned 6D kernels (rs_count_work)

@@ -125,8 +125,9 @@ __global__ void k_tree_bbox(int64_t m, const uint32_t* __restrict__ mnode, const
   const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool in = p < m;
   const uint32_t q = in ? mnode[p] : 0u;
-  const bool valid = in && node_size[q] >= tmin;
-  const float4 u = valid ? U[p] : make_float4(0, 0, 0, 0);
+  const float4 u = in ? U[p] : make_float4(0, 0, 0, 0);
+  // members moved to +inf (removed by an earlier unbinding pass) take no part in the tree
+  const bool valid = in && node_size[q] >= tmin && isfinite(u.x);
   const float c[3] = {u.x, u.y, u.z};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -205,8 +206,18 @@ k_tree_leaves(int64_t C, int64_t nt, const int64_t* __restrict__ tcoff, const in
   if (lev != 0) return;
   const int64_t s0 = ttoff[b] + (j << kLeafBits);
   const int cnt = int(rsd::min64(32, tg[b] - (j << kLeafBits)));
-  const bool valid = lane < cnt;
-  const float4 x = valid ? TX[s0 + lane] : make_float4(0, 0, 0, 0);
+  const float4 xr = lane < cnt ? TX[s0 + lane] : make_float4(0, 0, 0, 0);
+  // members moved to +inf (removed by an earlier unbinding pass) are left out of the moments
+  const bool valid = lane < cnt && isfinite(xr.x);
+  const int nv = __popc(__ballot_sync(0xffffffffu, valid));
+  if (nv == 0) {  // an empty cell: contributes nothing
+    if (lane == 0) {
+      const float4 z = make_float4(0, 0, 0, 0);
+      cells[c] = Cell{z, z, z, z};
+    }
+    return;
+  }
+  const float4 x = valid ? xr : make_float4(0, 0, 0, 0);
   double sx = x.x, sy = x.y, sz = x.z;
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
@@ -214,7 +225,7 @@ k_tree_leaves(int64_t C, int64_t nt, const int64_t* __restrict__ tcoff, const in
     sy += __shfl_xor_sync(0xffffffffu, sy, off);
     sz += __shfl_xor_sync(0xffffffffu, sz, off);
   }
-  const float cx = float(sx / cnt), cy = float(sy / cnt), cz = float(sz / cnt);
+  const float cx = float(sx / nv), cy = float(sy / nv), cz = float(sz / nv);
   // offsets from the float32 centre are exact in float64
   const double dx = valid ? double(x.x) - double(cx) : 0.0;
   const double dy = valid ? double(x.y) - double(cy) : 0.0;
@@ -230,7 +241,7 @@ k_tree_leaves(int64_t C, int64_t nt, const int64_t* __restrict__ tcoff, const in
   if (lane == 0) {
     Cell cl;
     cl.ca = make_float4(cx, cy, cz, round_up_f(v[9]));
-    cl.np = make_float4(float(cnt), float(v[0]), float(v[1]), float(v[2]));
+    cl.np = make_float4(float(nv), float(v[0]), float(v[1]), float(v[2]));
     cl.q0 = make_float4(float(v[3]), float(v[4]), float(v[5]), float(v[6]));
     cl.q1 = make_float4(float(v[7]), float(v[8]), float(v[3] + v[4] + v[5]), 0.f);
     cells[c] = cl;
@@ -253,15 +264,22 @@ __global__ void k_tree_up(int64_t C, int lev, int64_t nt, const int64_t* __restr
   double n = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
   for (int k = 0; k < nch; ++k) {
     const Cell ch = cells[c0 + k];
+    if (ch.np.x == 0.f) continue;  // empty child
     n += ch.np.x;
     mx += double(ch.np.x) * ch.ca.x + ch.np.y;  // sum of x_j = n c + p
     my += double(ch.np.x) * ch.ca.y + ch.np.z;
     mz += double(ch.np.x) * ch.ca.z + ch.np.w;
   }
+  if (n == 0.0) {
+    const float4 z = make_float4(0, 0, 0, 0);
+    cells[c] = Cell{z, z, z, z};
+    return;
+  }
   const float cx = float(mx / n), cy = float(my / n), cz = float(mz / n);
   double P[3] = {0.0, 0.0, 0.0}, Q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, a = 0.0;
   for (int k = 0; k < nch; ++k) {
     const Cell ch = cells[c0 + k];
+    if (ch.np.x == 0.f) continue;
     const double d[3] = {double(ch.ca.x) - cx, double(ch.ca.y) - cy, double(ch.ca.z) - cz};
     const double nc = ch.np.x;
     const double pc[3] = {ch.np.y, ch.np.z, ch.np.w};
@@ -392,6 +410,7 @@ k_tree_walk(WalkArgs A) {
     const int64_t cs = tb + (j << sh), ce = rsd::min64(cs + (int64_t(1) << sh), tb + g);
     const bool overlap = cs <= int64_t(smax) && ce > int64_t(smin);
     const Cell cl = A.cells[cb + lvo + j];
+    if (cl.np.x == 0.f) continue;  // no member left in the cell (iterative unbinding)
     const float dx = t.x - cl.ca.x, dy = t.y - cl.ca.y, dz = t.z - cl.ca.z;
     const float R2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, A.eps2)));
     const bool acc = cl.ca.w * cl.ca.w <= A.theta2 * R2;

@@ -286,6 +286,45 @@ struct VelTerm {
   }
 };
 
+// Iterative unbinding: v of the members still bound, 0.0 for the others (the oracle's order).
+struct VelTermMasked {
+  const float4* V;
+  const uint8_t* in;
+  template <bool kFirst>
+  __device__ __forceinline__ void add(int64_t, int64_t p, int64_t, double* acc) const {
+    const float4 v = V[p];
+    const bool keep = in[p] != 0;
+    rsd::cro_add<kFirst>(acc[0], keep ? rsd::f2d(v.x) : 0.0);
+    rsd::cro_add<kFirst>(acc[1], keep ? rsd::f2d(v.y) : 0.0);
+    rsd::cro_add<kFirst>(acc[2], keep ? rsd::f2d(v.z) : 0.0);
+  }
+};
+
+__global__ void k_vbulk_masked(int64_t nn, const unsigned long long* __restrict__ count,
+                               double* __restrict__ v) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= 3 * nn) return;
+  const unsigned long long c = count[k / 3];
+  v[k] = c ? __ddiv_rn(v[k], double(c)) : 0.0;
+}
+
+// Positions of the members still bound; the others moved to +inf, so every pair term with them
+// evaluates to exactly 0 (rsqrt(inf) = 1/sqrt(inf) = 0) in every potential kernel.
+__global__ void k_mask_u(int64_t m, const float4* __restrict__ U, const uint8_t* __restrict__ in,
+                         float4* __restrict__ Um) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  const float inf = __int_as_float(0x7f800000);
+  Um[p] = in[p] ? U[p] : make_float4(inf, inf, inf, 0.f);
+}
+
+// Members a pass removed (bound before, not after); the new flags become the next mask.
+__global__ void k_removed(int64_t m, const uint8_t* __restrict__ before, const uint8_t* __restrict__ after,
+                          unsigned long long* __restrict__ removed) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  rsd::warp_count(removed, p < m && before[p] && !after[p]);
+}
+
 // Bulk velocity of every node, vbulk = (canonical-order sum of v) / g, in place (one float64
 // division per node and axis instead of one per member).
 __global__ void k_vbulk(int64_t nn, const int64_t* __restrict__ node_size, double* __restrict__ v) {
@@ -307,13 +346,15 @@ __global__ void k_flags(int64_t m, const uint32_t* __restrict__ mnode, const int
                         const float* __restrict__ S, double Gm, double certB,
                         uint8_t* __restrict__ bound, float* __restrict__ phi_out,
                         uint32_t* __restrict__ ambig, unsigned long long* __restrict__ n_ambig,
-                        int64_t sur_min, const int* __restrict__ only, int64_t max_g) {
+                        int64_t sur_min, const int* __restrict__ only, int64_t max_g,
+                        const uint8_t* __restrict__ in) {
   const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (p >= m) return;
   const uint32_t q = mnode[p];
   const int64_t g = node_size[q];
   if ((only ? (only[q] == 0) : (sur_min > 0 && g >= sur_min)) || (max_g > 0 && g >= max_g))
     return;  // other path
+  if (in && !in[p]) return;  // removed by an earlier pass: stays unbound
   const double ke = kinetic(V[p], vbulk + 3 * int64_t(q));
   const double ph = -__dmul_rn(Gm, double(S[p]));
   const double e = __dadd_rn(ke, ph);
@@ -622,6 +663,56 @@ int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, int64_t max_
   return RS_OK;
 }
 
+// Passes 2.. of iterative unbinding: each recomputes the bulk velocity and the potential of the
+// members still bound over the members still bound (the others moved to +inf in a masked copy
+// of U, which the potential kernels read in place of U during the pass) and re-flags them, until
+// a pass removes nobody or `passes` passes have run. The float32 sums keep their certified
+// bounds and the float64 fallback sees the same masked copy, so every pass's flags are exact.
+int unbind_passes(rs_ctx* ctx, int passes, bool tree, int64_t max_g, double* vbulk, uint8_t* bound,
+                  float* S, float* potential_out, uint32_t* ambig, unsigned long long* counters,
+                  cudaStream_t st) {
+  Hier h = hier_of(ctx);
+  const int64_t m = ctx->n_members, nn = ctx->n_nodes;
+  const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
+  uint8_t* in = scratch_t<uint8_t>(ctx, S_U_PREV, size_t(m));
+  float4* Um = scratch_t<float4>(ctx, S_U_UM, size_t(m));
+  unsigned long long* cnt = scratch_t<unsigned long long>(ctx, S_U_PCNT, size_t(nn) + 1);
+  if (!in || !Um || !cnt) return RS_ERR_OOM;
+  unsigned long long* removed = cnt + nn;
+  for (int pass = 2; pass <= passes; ++pass) {
+    RS_CUDA(ctx, cudaMemcpyAsync(in, bound, size_t(m), cudaMemcpyDeviceToDevice, st));
+    RS_CUDA(ctx, cudaMemsetAsync(cnt, 0, 8 * (size_t(nn) + 1), st));
+    k_bound_count<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, in, cnt);
+    RS_LAUNCHED(ctx, "k_bound_count");
+    RS_TRY((cro_segmented<3, VelTermMasked>(ctx, nn, h.node_off, h.node_size, m, VelTermMasked{h.V, in},
+                                            vbulk, st)));
+    k_vbulk_masked<<<grid_for(3 * nn, kT), kT, 0, st>>>(nn, cnt, vbulk);
+    RS_LAUNCHED(ctx, "k_vbulk_masked");
+    k_mask_u<<<grid_for(m, kT), kT, 0, st>>>(m, h.U, in, Um);
+    RS_LAUNCHED(ctx, "k_mask_u");
+    std::swap(ctx->buf[S_H_U], ctx->buf[S_U_UM]);  // the pass's kernels read the masked copy
+    int rc = direct_potential(ctx, 0, nullptr, max_g, S, st);
+    Hier hm = hier_of(ctx);
+    if (rc == RS_OK) {
+      k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, hm.mnode, hm.node_size, hm.V, vbulk, S, Gm, kCertB, bound,
+                                             potential_out, ambig, counters + 7, 0, nullptr, max_g, in);
+      rc = after_launch(ctx, "k_flags");
+    }
+    if (rc == RS_OK) rc = unbind_fallback(ctx, counters + 7, ambig, vbulk, bound, st, potential_out);
+    if (rc == RS_OK && tree) rc = tree_build(ctx, st);
+    if (rc == RS_OK && tree) rc = tree_decide(ctx, nullptr, in, vbulk, bound, counters, st);
+    std::swap(ctx->buf[S_H_U], ctx->buf[S_U_UM]);
+    if (rc != RS_OK) return rc;
+    RS_CUDA(ctx, cudaMemsetAsync(removed, 0, 8, st));
+    k_removed<<<grid_for(m, kT), kT, 0, st>>>(m, in, bound, removed);
+    RS_LAUNCHED(ctx, "k_removed");
+    RS_TRY(read_back(ctx, removed, 8, st));
+    ctx->unbind_passes_run = pass;
+    if (ctx->host_box[0] == 0) break;
+  }
+  return RS_OK;
+}
+
 }  // namespace
 
 extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float* potential_out,
@@ -634,6 +725,9 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
   if (m > 0 && !bound_out) return set_error(ctx, RS_ERR_INVALID_ARG, "bound_out is NULL");
   if (m > 0 && (!pos || !vel)) return set_error(ctx, RS_ERR_INVALID_ARG, "null pos/vel");
   const bool sur = ctx->cfg.use_surrogate != 0;
+  const int passes = std::max(1, int(ctx->cfg.unbind_passes));
+  if (sur && passes > 1)
+    return set_error(ctx, RS_ERR_INVALID_ARG, "iterative unbinding runs in the plain and batched forms");
   if (sur && potential_out)
     return set_error(ctx, RS_ERR_INVALID_ARG, "potential_out must be NULL with the surrogate");
   if (sur && !ctx->have_mlp)
@@ -673,6 +767,7 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
   for (int i = 0; i < 11; ++i) ctx->sur_stats[i] = 0;
   for (int i = 0; i < 8; ++i) ctx->tree_stats[i] = 0;
   ctx->tree_nt = ctx->tree_T = ctx->tree_C = 0;
+  ctx->unbind_passes_run = 1;
   if (m > 0) {
     const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
     RS_CUDA(ctx, cudaMemsetAsync(counters, 0, kCounters * sizeof(unsigned long long), st));
@@ -681,12 +776,15 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     RS_LAUNCHED(ctx, "k_vbulk");
     RS_TRY(direct_potential(ctx, sur_min, nullptr, max_g, S, st));
     k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vbulk, S, Gm, kCertB, bound,
-                                           potential_out, ambig, n_ambig, sur_min, nullptr, max_g);
+                                           potential_out, ambig, n_ambig, sur_min, nullptr, max_g,
+                                           nullptr);
     RS_LAUNCHED(ctx, "k_flags");
     RS_TRY(unbind_fallback(ctx, n_ambig, ambig, vbulk, bound, st, potential_out));
     if (tree) RS_TRY(tree_build(ctx, st));
     if (tree && !sur) RS_TRY(tree_decide(ctx, nullptr, nullptr, vbulk, bound, counters, st));
     if (sur) RS_TRY(surrogate_unbind(ctx, vbulk, bound, counters, st));
+    if (passes > 1) RS_TRY(unbind_passes(ctx, passes, tree, max_g, vbulk, bound, S, potential_out, ambig,
+                                         counters, st));
     RS_CUDA(ctx, cudaMemsetAsync(nb, 0, 8 * nn, st));
     k_bound_count<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, bound, nb);
     RS_LAUNCHED(ctx, "k_bound_count");
@@ -739,7 +837,7 @@ int rs::unbind_nodes(rs_ctx* ctx, const int* only, const double* vbulk, uint8_t*
   const int64_t max_g = ctx->tree_nt > 0 ? ctx->tree_min : 0;
   RS_TRY(direct_potential(ctx, 0, only, max_g, S, st));
   k_flags<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, h.node_size, h.V, vbulk, S, Gm, kCertB, bound, nullptr,
-                                         ambig, n_ambig, 0, only, max_g);
+                                         ambig, n_ambig, 0, only, max_g, nullptr);
   RS_LAUNCHED(ctx, "k_flags");
   RS_TRY(unbind_fallback(ctx, n_ambig, ambig, vbulk, bound, st));
   if (ctx->tree_nt > 0) RS_TRY(tree_decide(ctx, only, nullptr, vbulk, bound, counters, st));
@@ -777,6 +875,8 @@ int rs::unbind_fallback(rs_ctx* ctx, const unsigned long long* n_ambig, const ui
   RS_LAUNCHED(ctx, "k_fallback_finish");
   return RS_OK;
 }
+
+extern "C" int rs_unbind_passes(rs_ctx* ctx) { return ctx ? ctx->unbind_passes_run : 0; }
 
 extern "C" int rs_halo_props(rs_ctx* ctx, rs_halo_props_t* props_out, void* stream) {
   if (!ctx) return RS_ERR_INVALID_ARG;

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_2412_18629_gb300 import G_NEWTON
 
 G = 4.30091e-9
 M = 1.0e10
@@ -122,3 +123,44 @@ def test_bulk_velocity_is_subtracted():
     moving[:, 2] = 5e5                     # uniform drift: no kinetic energy in the node's frame
     out = _one_node(pos, moving)
     assert out["bound"].all()
+
+
+def test_iterative_unbinding_hand_case():
+    """Four particles, G m = 43.0091 (m = 1e10): A = (0,0,0), B = (0.1,0,0) at rest, C = (10,0,0)
+    at v = (100,0,0), D = (10.1,0,0) at v = (0,10,0); eps = 0.
+    Pass 1 (bulk (25, 2.5, 0)): A, B: KE 315.6 < 438.6 = |phi|; C: KE 2815.6 > 438.7; D: KE 340.6 <
+    438.6 (C's term 430.1 keeps it bound). Pass 2 over {A, B, D} (bulk (0, 10/3, 0)): A, B: KE 5.6
+    < 434.4; D: KE 22.2 > 43.0091 (1/10 + 1/10.1) = 8.56, unbound. Pass 3 over {A, B}: both bound
+    at rest. So one pass leaves {A, B, D}, iteration {A, B}."""
+    import oracle
+    pos = np.array([[0, 0, 0], [0.1, 0, 0], [10, 0, 0], [10.1, 0, 0]], np.float32) + 20
+    vel = np.array([[0, 0, 0], [0, 0, 0], [100, 0, 0], [0, 10, 0]], np.float32)
+    off = np.array([0, 4], np.int64)
+    idx = np.arange(4, dtype=np.int64)
+    one = oracle.unbind(off, idx, pos, vel, 64.0, 0.0, G_NEWTON, 1e10, min_size=2)
+    assert list(one["bound"]) == [1, 1, 0, 1]
+    it = oracle.unbind(off, idx, pos, vel, 64.0, 0.0, G_NEWTON, 1e10, min_size=2, passes=5)
+    assert list(it["bound"]) == [1, 1, 0, 0] and it["n_bound"][0] == 2
+    two = oracle.unbind(off, idx, pos, vel, 64.0, 0.0, G_NEWTON, 1e10, min_size=2, passes=2)
+    assert list(two["bound"]) == [1, 1, 0, 0]
+    # pass 2's potential of D: only A and B contribute (positions are float32: 1e-5)
+    np.testing.assert_allclose(it["phi"][3], -G_NEWTON * 1e10 * (1 / 10.0 + 1 / 10.1), rtol=1e-5)
+    # A's last potential is pass 3's: B alone
+    np.testing.assert_allclose(it["phi"][0], -G_NEWTON * 1e10 / 0.1, rtol=1e-5)  # float32 offsets
+
+
+def test_iterative_unbinding_is_monotone_and_stops():
+    import oracle
+    from helpers import small_snapshot
+    s = small_snapshot(1 << 14, 25.0, 35, n_max=3000)
+    lab = oracle.fof3d(s["pos"], s["ids"], s["box"], s["link_length"])
+    h = oracle.hierarchy(s["pos"], s["vel"], s["ids"], lab, s["box"])
+    args = (h["member_off"], h["member_idx"], s["pos"], s["vel"], s["box"], s["softening"],
+            G_NEWTON, s["particle_mass"])
+    b1 = oracle.unbind(*args, want_phi=False)["bound"]
+    b3 = oracle.unbind(*args, want_phi=False, passes=3)["bound"]
+    b20 = oracle.unbind(*args, want_phi=False, passes=20)["bound"]
+    b21 = oracle.unbind(*args, want_phi=False, passes=21)["bound"]
+    assert np.all(b3 <= b1) and np.all(b20 <= b3)        # a removed member never comes back
+    assert np.array_equal(b20, b21)                       # converged: more passes change nothing
+    assert (b1 != b20).sum() > 0                          # iteration matters on this snapshot
