@@ -23,9 +23,11 @@
 //           expansion when a <= theta R' for every lane and it holds none of the warp's
 //           targets, a leaf is summed directly (self excluded), otherwise its children are
 //           visited;
-//   slack   float32 evaluation and summation (per term <= ~8u, 32-term leaf blocks <= 31u,
-//           expansions <= ~20u, Kahan across visits <= 2u) stay below 1e-5 relative, and the
-//           truncation terms are summed in float32 and widened by 0.1%:
+//   slack   float32 evaluation and summation (per direct term <= ~8u, 32-term leaf blocks
+//           summed as two packed halves <= 31u, the target's own term rsqrt(eps^2) taken out of
+//           its leaf once <= u of the leaf sum, expansions with FMAs <= ~20u of n/R', Kahan across
+//           visits <= 2u) stay below 1e-5 relative; the truncation terms (fast division, <= 2
+//           ulp) are summed in float32 and widened by 0.1%:
 //           S_lo = S~ (1 - 1e-5) - 1.001 B, S_hi = S~ (1 + 1e-5) + 1.001 B;
 //           the float64 sum differs from the exact one by < g 2^-53 relative.
 //   decide  bound iff KE - G m S_lo < -tol, unbound iff KE - G m S_hi > tol (tol = 1e-12 G m
@@ -415,14 +417,18 @@ k_tree_walk(WalkArgs A) {
     const float R2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, A.eps2)));
     const bool acc = cl.ca.w * cl.ca.w <= A.theta2 * R2;
     if (!overlap && __all_sync(0xffffffffu, acc)) {
+      // quadrupole expansion and its truncation bound; explicit FMAs (the evaluation only has
+      // to stay inside the 1e-5 slack, and the library is compiled without contraction)
       const float ri = rsqrtf(R2);
       const float ri2 = ri * ri, ri3 = ri2 * ri;
-      const float dqd = cl.q0.x * dx * dx + cl.q0.y * dy * dy + cl.q0.z * dz * dz +
-                        2.f * (cl.q0.w * dx * dy + cl.q1.x * dx * dz + cl.q1.y * dy * dz);
-      const float val = cl.np.x * ri + (cl.np.y * dx + cl.np.z * dy + cl.np.w * dz) * ri3 +
-                        0.5f * (3.f * dqd * ri2 - cl.q1.z) * ri3;
+      const float ax = __fmaf_rn(cl.q1.x + cl.q1.x, dz, __fmaf_rn(cl.q0.w + cl.q0.w, dy, cl.q0.x * dx));
+      const float ay = __fmaf_rn(cl.q1.y + cl.q1.y, dz, cl.q0.y * dy);
+      const float dqd = __fmaf_rn(ax, dx, __fmaf_rn(ay, dy, cl.q0.z * dz * dz));
+      const float pd = __fmaf_rn(cl.np.y, dx, __fmaf_rn(cl.np.z, dy, cl.np.w * dz));
+      const float quad = __fmaf_rn(1.5f * dqd, ri2, -0.5f * cl.q1.z);
+      const float val = __fmaf_rn(cl.np.x, ri, ri3 * (pd + quad));
       const float h = cl.ca.w * ri;
-      const float bnd = cl.np.x * ri * (h * h * h) / (1.f - h);
+      const float bnd = __fdividef(cl.np.x * ri * (h * h * h), 1.f - h);
       const float y = __fsub_rn(val, Cc);
       const float tt = __fadd_rn(S, y);
       Cc = __fsub_rn(__fsub_rn(tt, S), y);
@@ -430,15 +436,37 @@ k_tree_walk(WalkArgs A) {
       Bt += bnd;
       ++n_exp;
     } else if (lev == 0) {
+      // direct sum over the leaf's members, two per packed float32x2 step; slots past the leaf's
+      // count hold +inf, whose term is exactly 0; the target's own term rsqrt(eps^2) is taken
+      // out once (or, without softening, skipped per pair)
       const int cnt = int(ce - cs);
-      if (lane < cnt) leaf[lane] = A.TX[cs + lane];
+      const float inf = __int_as_float(0x7f800000);
+      leaf[lane] = lane < cnt ? A.TX[cs + lane] : make_float4(inf, inf, inf, 0.f);
       __syncwarp();
-      float blk = 0.f;
-      for (int k = 0; k < cnt; ++k) {
-        const float4 x = leaf[k];
-        const float ex = __fsub_rn(x.x, t.x), ey = __fsub_rn(x.y, t.y), ez = __fsub_rn(x.z, t.z);
-        const float wv = rsqrtf(__fmaf_rn(ex, ex, __fmaf_rn(ey, ey, __fmaf_rn(ez, ez, A.eps2))));
-        blk = __fadd_rn(blk, cs + k == int64_t(s_self) ? 0.f : wv);
+      float blk;
+      if (A.eps2 > 0.f) {
+        const float2 ntx = make_float2(-t.x, -t.x), nty = make_float2(-t.y, -t.y),
+                     ntz = make_float2(-t.z, -t.z), e2 = make_float2(A.eps2, A.eps2);
+        float2 acc2 = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int k = 0; k < 32; k += 2) {
+          const float4 xa = leaf[k], xb = leaf[k + 1];
+          const float2 ex = __fadd2_rn(make_float2(xa.x, xb.x), ntx);
+          const float2 ey = __fadd2_rn(make_float2(xa.y, xb.y), nty);
+          const float2 ez = __fadd2_rn(make_float2(xa.z, xb.z), ntz);
+          const float2 r2 = __ffma2_rn(ex, ex, __ffma2_rn(ey, ey, __ffma2_rn(ez, ez, e2)));
+          acc2 = __fadd2_rn(acc2, make_float2(rsqrtf(r2.x), rsqrtf(r2.y)));
+        }
+        blk = __fadd_rn(acc2.x, acc2.y);
+        if (cs <= int64_t(s_self) && int64_t(s_self) < ce) blk = __fsub_rn(blk, rsqrtf(A.eps2));
+      } else {
+        blk = 0.f;
+        for (int k = 0; k < cnt; ++k) {
+          const float4 x = leaf[k];
+          const float ex = __fsub_rn(x.x, t.x), ey = __fsub_rn(x.y, t.y), ez = __fsub_rn(x.z, t.z);
+          const float wv = rsqrtf(__fmaf_rn(ex, ex, __fmaf_rn(ey, ey, __fmaf_rn(ez, ez, A.eps2))));
+          blk = __fadd_rn(blk, cs + k == int64_t(s_self) ? 0.f : wv);
+        }
       }
       __syncwarp();
       const float y = __fsub_rn(blk, Cc);
