@@ -18,6 +18,7 @@ on a bounded sample of the same workload, on this machine's host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -344,8 +345,6 @@ def _traffic_table():
 # ---------------------------------------------------------------------------------------------
 def _digest(ctx, lab, bound, props):
     """SHA-256 of a form's outputs: 3D labels, hierarchy arrays, bound flags, properties."""
-    import hashlib
-
     import paper_2412_18629_gb300 as rs
     hsh = hashlib.sha256()
     hsh.update(lab.cpu().numpy().tobytes())
@@ -403,6 +402,7 @@ def _measure(ctx, pos, vel, ids, n, steps, warmup, ws, local, form):
     prof = ctx.profile_totals()
     ctx.profile(False)
     keypasses = ctx.sort_keypasses - k0
+    pot_pairs = rs.rs_potential_pairs(ctx)
     work = None
     if form != "plain":
         ctx.count_work(True)
@@ -418,6 +418,9 @@ def _measure(ctx, pos, vel, ids, n, steps, warmup, ws, local, form):
     tm = int(ctx.cfg.tree_min_members)
     r["pairs"] = _sizes_work(sizes, "surrogate" if form.startswith("surrogate") else form,
                              0 if form == "plain" or tm < 0 else (tm or TREE_MIN_DEFAULT))
+    # the direct sums' own pair tallies (they include the nodes the surrogate sends whole to
+    # the exact sum, which node sizes alone do not show)
+    r["pairs"]["pairs_small"], r["pairs"]["pairs_blocked"] = map(float, pot_pairs)
     return r
 
 
@@ -458,6 +461,111 @@ def train_surrogate(ctx, workload, device, samples=None, epochs=None):
     torch.cuda.empty_cache()
     return {"samples": int(k), "epochs": epochs, "err_max_psi": err_max, "last_batch_mse": mse,
             "train_s": dt, "snapshot": f"{workload} generator, seed 100"}
+
+
+STREAM_BASE = "nfw-2^24-L256-sub"   # the batched stream: this snapshot plus STREAM_COUNT others
+STREAM_COUNT = 64
+
+
+def _gen_stream(k):
+    """Snapshot k of the stream (k = -1: the base snapshot); runs in a spawned worker."""
+    from paper_2412_18629_gb300 import synth
+    spec = synth.WORKLOADS[STREAM_BASE] if k < 0 else synth.stream_spec(k)
+    s = synth.generate(spec)
+    return {key: s[key] for key in ("pos", "vel", "ids", "box", "link_length", "softening",
+                                    "particle_mass")}
+
+
+def _stream_snapshots(count):
+    import multiprocessing as mp
+    ks = [-1] + list(range(count))
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        return pool.map(_gen_stream, ks, chunksize=1)
+
+
+def measure_stream(args, local):
+    """The batched form over the stream of independent snapshots (the 2^24 snapshot plus 64 of
+    2^18..2^22 particles at unit spacing): one context running the four calls snapshot after
+    snapshot, against rs_run_batched's concurrent lanes; identical outputs required."""
+    import torch
+    import paper_2412_18629_gb300 as rs
+    t0 = time.perf_counter()
+    host = _stream_snapshots(args.stream_count)
+    gen_s = time.perf_counter() - t0
+    dev = [dict(pos=torch.from_numpy(h["pos"]).cuda(), vel=torch.from_numpy(h["vel"]).cuda(),
+                ids=torch.from_numpy(h["ids"]).cuda(), box=h["box"], link_length=h["link_length"],
+                softening=h["softening"]) for h in host]
+    sizes = [h["pos"].shape[0] for h in host]
+    n_tot = int(sum(sizes))
+    mk = dict(softening=host[0]["softening"], particle_mass=host[0]["particle_mass"], device=local,
+              mode="batched")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+    # sequential: the four calls snapshot after snapshot on one stream, one context per box
+    # (the box is part of a context's configuration)
+    by_box = {}
+    for d in dev:
+        key = (d["box"], d["link_length"])
+        if key not in by_box:
+            by_box[key] = rs.Context(box=d["box"], link_len=d["link_length"], **mk)
+    seq_ctx = list(by_box.values())
+    ctx_of = [by_box[(d["box"], d["link_length"])] for d in dev]
+    seq_out = {}
+
+    def sequential():
+        for k, (c, d) in enumerate(zip(ctx_of, dev)):
+            lab, _ = rs.rs_fof3d(c, d["pos"], d["ids"])
+            rs.rs_fof6d(c, d["pos"], d["vel"], d["ids"], lab)
+            rs.rs_unbind(c, d["pos"], d["vel"], want_potential=False)
+            seq_out[k] = (lab, rs.rs_halo_props(c))
+
+    l0 = sum(c.kernel_launches for c in seq_ctx)
+    t_seq = timed(sequential, args.stream_steps, 1)
+    seq_launches = (sum(c.kernel_launches for c in seq_ctx) - l0) / (args.stream_steps + 1)
+    seq_digest = hashlib.sha256()
+    for k in range(len(dev)):
+        seq_digest.update(seq_out[k][0].cpu().numpy().tobytes())
+        seq_digest.update(seq_out[k][1].cpu().numpy().tobytes())
+    for c in seq_ctx:
+        c.close()
+    torch.cuda.empty_cache()
+    bctx = rs.Context(box=dev[0]["box"], link_len=dev[0]["link_length"], **mk)
+    cap = [max(n // 4, 16) for n in sizes]
+    out = rs.BatchOutputs(sizes, cap, local, deepest=False)
+    counts = rs.rs_run_batched(bctx, dev, out, lanes=args.stream_lanes)   # sizes the lanes
+    l0 = bctx.kernel_launches
+    t_bat = timed(lambda: rs.rs_run_batched(bctx, dev, out, lanes=args.stream_lanes),
+                  args.stream_steps, 1)
+    bat_launches = (bctx.kernel_launches - l0) / (args.stream_steps + 1)
+    bat_digest = hashlib.sha256()
+    for k in range(len(dev)):
+        bat_digest.update(out.labels[k].cpu().numpy().tobytes())
+        bat_digest.update(out.props[k][:counts[k][1]].cpu().numpy().tobytes())
+    bctx.close()
+    del dev, out
+    torch.cuda.empty_cache()
+    return {"workload": f"{STREAM_BASE} + {args.stream_count} snapshots of 2^18..2^22 "
+                        "(n = 2^(18 + seed mod 5), unit spacing, seeds 0..)",
+            "snapshots": len(sizes), "particles": n_tot, "form": "batched",
+            "sequential": {"value": n_tot / t_seq, "ms_per_pass": t_seq * 1e3,
+                           "launches_per_pass": seq_launches},
+            "lanes": {"value": n_tot / t_bat, "ms_per_pass": t_bat * 1e3, "lanes": args.stream_lanes,
+                      "launches_per_pass": bat_launches},
+            "unit": UNIT, "steps": args.stream_steps, "warmup": 1,
+            "identical_outputs": seq_digest.hexdigest() == bat_digest.hexdigest(),
+            "nodes": int(counts[:, 1].sum()), "generation_s": gen_s}
 
 
 def _form_entry(r, traffic):
@@ -565,6 +673,9 @@ def run_ours(args):
     e_el = time.perf_counter() - e0
     e_max, e_units = aggregate(e_el, float(n) * e_steps, ws, f"cuda:{local}")
     ctx.close()
+    del e_pos, e_vel, e_ids
+    torch.cuda.empty_cache()
+    stream_res = measure_stream(args, local) if args.stream_steps > 0 else None
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -603,6 +714,7 @@ def run_ours(args):
             "identical_outputs": ident,
             "surrogate_flag_mismatches_vs_batched": mism,
             "surrogate_training": training,
+            "stream": stream_res,
             "forms": {f: _form_entry(v, traffic) for f, v in res.items()},
         }
         print(json.dumps(line), flush=True)
@@ -659,6 +771,10 @@ def main(argv=None):
     ap.add_argument("--plain-warmup", type=int, default=1)
     ap.add_argument("--e2e-seconds", type=float, default=30.0,
                     help="end-to-end timing: as many steps (at most --steps) as fit in this time")
+    ap.add_argument("--stream-steps", type=int, default=2,
+                    help="passes over the batched snapshot stream (0: skip it)")
+    ap.add_argument("--stream-count", type=int, default=STREAM_COUNT)
+    ap.add_argument("--stream-lanes", type=int, default=4)
     ap.add_argument("--train-workload", default=TRAIN_WORKLOAD)
     ap.add_argument("--weights", default=None,
                     help="load the surrogate from this checkpoint (rs_surrogate_save) instead of training")

@@ -117,6 +117,12 @@ int64_t rs_kernel_launches(rs_ctx* ctx);
  * was created (host counter; instrumentation for the sort's bandwidth figure). */
 int64_t rs_sort_keypasses(rs_ctx* ctx);
 
+/* CUDA graphs for the context's static launch sequences (1, the default) or plain launches (0);
+ * results are identical either way. A sequence is static when its launches and their
+ * arguments do not depend on values read back from the device: the surrogate's training
+ * epoch (rs_mlp_train) is captured once and replayed for every epoch. */
+int rs_use_graphs(rs_ctx* ctx, int enable);
+
 /* 3D friends-of-friends (Section "Parallelization"). Particles i and j are linked iff
  *   d = x_j - x_i (float32, per dimension), wrapped once: d > L/2 -> d - L, d < -L/2 -> d + L;
  *   (dx*dx + dy*dy) + dz*dz <= link_len*link_len, all float32, no fused multiply-add.
@@ -191,6 +197,13 @@ int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float* potential_
 /* Unbinding passes the last rs_unbind ran (1 without iterative unbinding). */
 int rs_unbind_passes(rs_ctx* ctx);
 
+/* Ordered pairs (i, j != i) the float32 direct sums of the last rs_unbind evaluated, host int64
+ * [2]: [0] nodes of at most 384 members (one-block kernel), [1] larger nodes (register-blocked
+ * or, in the plain form, tiled kernel), every node those kernels ran on counted once per pass
+ * (nodes the surrogate sends whole to the exact sum included; the tree walk and the exact list
+ * sums are counted by rs_tree_stats). Instrumentation for the kernels' work figures. */
+int rs_potential_pairs(rs_ctx* ctx, int64_t* pairs_out);
+
 /* Seed halos and the assignment of every FoF-group particle to one of them (Section
  * "Parallelization": subhalo finding inside every FoF halo; the step after the hierarchy). The
  * paper gives no formulas; the reading implemented (the CPU oracle's, bit for bit):
@@ -237,6 +250,46 @@ int rs_track(rs_ctx* ctx, int64_t n1, const int64_t* ids1, const int64_t* seed1,
  * unbound members contributing 0.
  * props_out: rs_halo_props_t [n_nodes] device. Errors: RS_ERR_STATE, RS_ERR_CUDA. */
 int rs_halo_props(rs_ctx* ctx, rs_halo_props_t* props_out, void* stream);
+
+/* ---- Batched snapshot stream ------------------------------------------------------------
+ * The whole pipeline (rs_fof3d, rs_fof6d, rs_unbind with no potential output, rs_halo_props)
+ * over many independent snapshots in one call (Section "Parallelization": independent units of
+ * work - there FoF halos over OpenMP threads - keep every core busy; here independent snapshots
+ * keep the GPU busy). Snapshots are taken largest first by `lanes` worker lanes, each a
+ * context of its own with its own CUDA stream and host thread, so one lane's kernels fill the
+ * GPU while another waits on a count it reads back. Every snapshot's outputs are identical to
+ * running the four calls on it alone with the same configuration.
+ * One snapshot of the batch; every pointer is a device pointer owned by the caller. */
+typedef struct rs_snapshot {
+  int64_t n;                  /* particles (< 2^32 - 1) */
+  float box_L;                /* this snapshot's box side, link length and softening; the */
+  float link_len;             /*   other parameters are the calling context's */
+  float softening;
+  float reserved;
+  const float* pos;           /* float32 [n][3] */
+  const float* vel;           /* float32 [n][3] */
+  const int64_t* ids;         /* int64 [n], unique, non-negative */
+  int64_t* label_out;         /* int64 [n]: 3D FoF label (smallest id of the group); required */
+  int64_t* deepest_out;       /* int64 [n] or NULL: deepest hierarchy node of each particle, -1 */
+  int64_t node_capacity;      /* entries available in node_parent_out and props_out */
+  int64_t* node_parent_out;   /* int64 [node_capacity] or NULL: parent node, -1 at level 0 */
+  rs_halo_props_t* props_out; /* [node_capacity] or NULL: rs_halo_props of every node */
+} rs_snapshot;
+
+/* Runs the pipeline over snaps[0 .. n_snap) with `lanes` lanes (1 .. 16). The lanes' contexts
+ * copy ctx's configuration (with each snapshot's box_L, link_len, softening) and, with
+ * use_surrogate, ctx's trained surrogate; they are created at the first call and kept, with
+ * their scratch memory, until rs_ctx_destroy(ctx).
+ * counts_out: host int64 [n_snap][4] or NULL: FoF groups, hierarchy nodes, hierarchy members,
+ * hierarchy levels of each snapshot.
+ * The lanes wait for the work already enqueued on `stream`; the call returns when every
+ * snapshot is done (it synchronises the lanes). Errors: RS_ERR_INVALID_ARG (a bad snapshot or
+ * lane count), RS_ERR_STATE (use_surrogate without a trained surrogate on ctx),
+ * RS_ERR_CAPACITY (a snapshot has more nodes than node_capacity while node_parent_out or
+ * props_out is given; every other snapshot is still processed and counts_out is filled, so the
+ * caller can resize), or the first error of a lane (its message in rs_last_error(ctx)). */
+int rs_run_batched(rs_ctx* ctx, int32_t n_snap, const rs_snapshot* snaps, int32_t lanes,
+                   int64_t* counts_out, void* stream);
 
 /* ---- Certified tree bound of the potential (batched forms) ---------------------------------
  * For nodes with at least tree_min_members members, rs_unbind (called with potential_out NULL)
@@ -333,7 +386,9 @@ int rs_mlp_gradient(rs_ctx* ctx, int64_t n, const float* x, const float* t, floa
 
 /* Train from a seeded He-uniform start with Adam (beta 0.9/0.999, eps 1e-8) on float32 masters:
  * samples x float32 [n][8], t float32 [n] (device); a seeded permutation holds out the last
- * holdout_num/holdout_den; minibatches of `batch`; `epochs` passes. Outputs (host, may be NULL):
+ * holdout_num/holdout_den; minibatches of `batch` (a partial last batch is left out of the
+ * epoch); `epochs` passes, each reshuffled; with graphs on (rs_use_graphs) one epoch's
+ * launches are a CUDA graph replayed every epoch. Outputs (host, may be NULL):
  * held-out max |y - t| (also stored as the gate's error) and the last batch's mean squared
  * error. Errors: RS_ERR_INVALID_ARG, RS_ERR_OOM, RS_ERR_CUDA. */
 int rs_mlp_train(rs_ctx* ctx, int64_t n, const float* x, const float* t, int32_t epochs,

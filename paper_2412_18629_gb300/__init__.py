@@ -51,6 +51,16 @@ class rs_config(ctypes.Structure):
     ]
 
 
+class rs_snapshot(ctypes.Structure):
+    """One snapshot of rs_run_batched (include/rs_gb300.h)."""
+    _fields_ = [("n", ctypes.c_int64), ("box_L", ctypes.c_float), ("link_len", ctypes.c_float),
+                ("softening", ctypes.c_float), ("reserved", ctypes.c_float),
+                ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("ids", ctypes.c_void_p),
+                ("label_out", ctypes.c_void_p), ("deepest_out", ctypes.c_void_p),
+                ("node_capacity", ctypes.c_int64), ("node_parent_out", ctypes.c_void_p),
+                ("props_out", ctypes.c_void_p)]
+
+
 def load_library():
     """Load librs_gb300.so (built by __graft_entry__.build() / build.build())."""
     global _lib
@@ -79,6 +89,9 @@ def load_library():
         lib.rs_assign_seeds.argtypes = [P, P, P, P, P, P, ctypes.POINTER(i64), P]
         lib.rs_track.argtypes = [P, i64, P, P, i64, i64, P, P, i64, P, P, P, P, P]
         lib.rs_unbind_passes.argtypes = [P]
+        lib.rs_run_batched.argtypes = [P, i32, ctypes.POINTER(rs_snapshot), i32, P, P]
+        lib.rs_use_graphs.argtypes = [P, ctypes.c_int]
+        lib.rs_potential_pairs.argtypes = [P, P]
         lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
         lib.rs_sort_pairs.argtypes = [P, i64, ctypes.c_int, P, P, P]
         lib.rs_mlp_set_params.argtypes = [P, P]
@@ -109,7 +122,8 @@ def load_library():
                      "rs_fof6d_node_params", "rs_unbind", "rs_halo_props", "rs_cro_sum", "rs_profile",
                      "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work", "rs_tuning",
                      "rs_tree_stats", "rs_tree_record", "rs_tree_bounds",
-                     "rs_assign_seeds", "rs_track", "rs_unbind_passes"):
+                     "rs_assign_seeds", "rs_track", "rs_unbind_passes", "rs_run_batched",
+                     "rs_use_graphs", "rs_potential_pairs"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -190,6 +204,10 @@ class Context:
     def sort_keypasses(self) -> int:
         """Keys moved by radix-sort passes since the context was created."""
         return int(self.lib.rs_sort_keypasses(self.handle))
+
+    def use_graphs(self, enable=True):
+        """CUDA graphs for static launch sequences (the surrogate's training epoch) on or off."""
+        self.check(self.lib.rs_use_graphs(self.handle, 1 if enable else 0))
 
     def profile(self, enable=True):
         """Start (clearing totals) or stop CUDA-event timing of the dominant kernels."""
@@ -347,6 +365,14 @@ def rs_track(ctx, ids1, seed1, n_nodes1, ids2, seed2, n_nodes2, stream=None):
     return prog, ps, desc, ds
 
 
+def rs_potential_pairs(ctx):
+    """Ordered pairs the last rs_unbind's direct sums evaluated: (small nodes, larger nodes)."""
+    import numpy as np
+    out = np.zeros(2, np.int64)
+    ctx.check(ctx.lib.rs_potential_pairs(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
+    return int(out[0]), int(out[1])
+
+
 def rs_unbind_passes(ctx):
     """Unbinding passes the last rs_unbind ran."""
     return int(ctx.lib.rs_unbind_passes(ctx.handle))
@@ -360,6 +386,56 @@ def rs_halo_props(ctx, props_out=None, stream=None):
                                 device=torch.device("cuda", ctx.device))
     ctx.check(ctx.lib.rs_halo_props(ctx.handle, _ptr(props_out), _stream(stream)))
     return props_out
+
+
+class BatchOutputs:
+    """Output buffers of rs_run_batched for a list of snapshots: per snapshot the FoF labels,
+    the deepest node of every particle, and (node_capacity rows) the parent of every node and
+    its rs_halo_props_t row; reusable across calls on snapshots of the same sizes."""
+
+    def __init__(self, sizes, node_capacity, device, deepest=True, props=True):
+        torch = _torch()
+        dev = torch.device("cuda", device)
+        self.labels = [torch.empty(n, dtype=torch.int64, device=dev) for n in sizes]
+        self.deepest = [torch.empty(n, dtype=torch.int64, device=dev) for n in sizes] if deepest else None
+        cap = [int(c) for c in node_capacity]
+        self.capacity = cap
+        self.parent = [torch.empty(c, dtype=torch.int64, device=dev) for c in cap] if props else None
+        self.props = ([torch.empty((c, 8 * PROPS_FIELDS), dtype=torch.uint8, device=dev) for c in cap]
+                      if props else None)
+
+
+def rs_run_batched(ctx, snaps, out, lanes=4, stream=None):
+    """The pipeline over every snapshot of `snaps` (dicts of CUDA tensors pos, vel, ids and
+    floats box, link_length, softening) on `lanes` concurrent lanes, writing into `out`
+    (a BatchOutputs). Returns int64 counts [n_snap, 4]: groups, nodes, members, levels.
+    Raises RSError (code RS_ERR_CAPACITY) when a snapshot has more nodes than its capacity."""
+    import numpy as np
+    torch = _torch()
+    arr = (rs_snapshot * max(len(snaps), 1))()
+    for k, sn in enumerate(snaps):
+        _check_dev(sn["pos"], torch.float32, (3,), "pos")
+        _check_dev(sn["vel"], torch.float32, (3,), "vel")
+        _check_dev(sn["ids"], torch.int64, None, "ids")
+        a = arr[k]
+        a.n = sn["pos"].shape[0]
+        a.box_L, a.link_len, a.softening = (float(sn["box"]), float(sn["link_length"]),
+                                            float(sn["softening"]))
+        a.pos, a.vel, a.ids = sn["pos"].data_ptr(), sn["vel"].data_ptr(), sn["ids"].data_ptr()
+        a.label_out = out.labels[k].data_ptr()
+        a.deepest_out = out.deepest[k].data_ptr() if out.deepest is not None else None
+        a.node_capacity = out.capacity[k]
+        if out.parent is not None:
+            a.node_parent_out = out.parent[k].data_ptr() if out.capacity[k] else None
+            a.props_out = out.props[k].data_ptr() if out.capacity[k] else None
+    counts = np.zeros((len(snaps), 4), np.int64)
+    rc = ctx.lib.rs_run_batched(ctx.handle, len(snaps), arr, int(lanes),
+                                counts.ctypes.data_as(ctypes.c_void_p), _stream(stream))
+    if rc != RS_OK:
+        err = RSError(rc, ctx.lib.rs_last_error(ctx.handle).decode(errors="replace"))
+        err.counts = counts
+        raise err
+    return counts
 
 
 def props_to_float64(raw):

@@ -115,6 +115,10 @@ extern "C" int rs_tuning(rs_ctx* ctx, int32_t* choice_out, float* ms_out) {
 extern "C" int rs_ctx_destroy(rs_ctx* ctx) {
   if (!ctx) return RS_OK;
   cudaSetDevice(ctx->device);
+  for (rs_ctx* lane : ctx->lanes) rs_ctx_destroy(lane);
+  for (void* s : ctx->lane_streams) cudaStreamDestroy(static_cast<cudaStream_t>(s));
+  if (ctx->lane_event) cudaEventDestroy(static_cast<cudaEvent_t>(ctx->lane_event));
+  if (ctx->graph_stream) cudaStreamDestroy(static_cast<cudaStream_t>(ctx->graph_stream));
   prof_resolve(ctx);
   for (auto e : ctx->prof_free) cudaEventDestroy(e);
   for (auto& b : ctx->buf)
@@ -129,6 +133,13 @@ extern "C" const char* rs_last_error(rs_ctx* ctx) { return ctx ? ctx->err : "nul
 extern "C" int64_t rs_kernel_launches(rs_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 extern "C" int64_t rs_sort_keypasses(rs_ctx* ctx) { return ctx ? ctx->sort_keypasses : 0; }
+
+extern "C" int rs_use_graphs(rs_ctx* ctx, int enable) {
+  if (!ctx) return RS_ERR_INVALID_ARG;
+  ctx->use_graphs = enable != 0;
+  for (rs_ctx* lane : ctx->lanes) lane->use_graphs = ctx->use_graphs;
+  return RS_OK;
+}
 
 namespace {
 struct ArrayTerm {

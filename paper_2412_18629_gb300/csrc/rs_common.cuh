@@ -40,7 +40,7 @@ enum Slot : int {
   S_P_USA, S_P_VSA, S_P_SPA, S_P_QKEY_A, S_P_QKEY_B, S_P_QVAL_A, S_P_QVAL_B,
   // surrogate MLP
   S_MLP_DEV, S_MLP_W, S_MLP_PART, S_MLP_SSE, S_MLP_M, S_MLP_G, S_MLP_IDX, S_MLP_BIDX, S_MLP_XH,
-  S_MLP_YH,
+  S_MLP_YH, S_MLP_CORR, S_MLP_STEP,
   // surrogate gating in rs_unbind
   S_SUR_OFF, S_SUR_RANK, S_SUR_STAT, S_SUR_MEM, S_SUR_BIG, S_SUR_FEAT, S_SUR_PSI, S_SUR_MARGIN,
   S_SUR_SFLAG, S_SUR_CHECKED, S_SUR_SX, S_SUR_LIST_A, S_SUR_LIST_B, S_SUR_GCOUNT, S_SUR_TAU,
@@ -58,6 +58,8 @@ enum Slot : int {
   S_TRK_FLAG,
   // iterative unbinding (rs_unbind.cu)
   S_U_PREV, S_U_UM, S_U_PCNT,
+  // batched snapshot stream (rs_batch.cu): a lane's bound flags
+  S_BATCH_BOUND,
   S_NUM_SLOTS
 };
 
@@ -108,6 +110,7 @@ struct rs_ctx {
   bool tree_recorded = false;
   int64_t tree_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int32_t unbind_passes_run = 0;  // passes the last rs_unbind ran (iterative unbinding)
+  int64_t pot_pairs[2] = {0, 0};  // ordered pairs the direct sums evaluated (last rs_unbind)
   // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
   bool profile = false;
   bool count_work = false;  // counting variants of the pruned 6D kernels (rs_count_work)
@@ -130,6 +133,14 @@ struct rs_ctx {
     int64_t launches;
   };
   std::vector<ProfTot> prof_tot;
+  // lanes of rs_run_batched: contexts with their own streams, created at the first call
+  std::vector<rs_ctx*> lanes;
+  std::vector<void*> lane_streams;  // cudaStream_t
+  void* lane_event = nullptr;       // cudaEvent_t: the caller's stream as the lanes start
+  // CUDA graphs for static launch sequences (rs_use_graphs): on by default; the stream graphs
+  // are captured on (the caller's may be the legacy default stream, which cannot be captured)
+  bool use_graphs = true;
+  void* graph_stream = nullptr;     // cudaStream_t
 };
 
 namespace rs {
@@ -194,6 +205,30 @@ int exclusive_scan_i64(rs_ctx* ctx, int64_t n, int64_t* data, int64_t* total_dev
 
 // Copy `bytes` device -> host mailbox and synchronise the stream.
 int read_back(rs_ctx* ctx, const void* dev, size_t bytes, cudaStream_t st);
+
+// Capture the launches `body(stream)` enqueues into an instantiated graph. Nothing runs while
+// capturing: body must only enqueue stream work (scratch already sized, no read-backs). The
+// launches it counts are returned in *launches and credited at each replay instead.
+int begin_capture(rs_ctx* ctx, cudaStream_t* cs);
+int end_capture(rs_ctx* ctx, cudaStream_t cs, int body_rc, int64_t launches0, bool profile,
+                cudaGraphExec_t* exec, int64_t* launches);
+
+template <class F>
+int capture_graph(rs_ctx* ctx, F&& body, cudaGraphExec_t* exec, int64_t* launches) {
+  cudaStream_t cs = nullptr;
+  RS_TRY(begin_capture(ctx, &cs));
+  const bool profile = ctx->profile;
+  ctx->profile = false;  // no event records inside a graph
+  const int64_t l0 = ctx->launches;
+  const int rc = body(cs);
+  return end_capture(ctx, cs, rc, l0, profile, exec, launches);
+}
+
+// Replay an instantiated graph on `st` (counted as `launches` kernel launches).
+int launch_graph(rs_ctx* ctx, cudaGraphExec_t exec, int64_t launches, cudaStream_t st);
+
+// Copy src's trained surrogate (weights and held-out maximum error) to dst (same device).
+int mlp_copy(rs_ctx* dst, rs_ctx* src, cudaStream_t st);
 
 // Device arrays of the 6D hierarchy held by a context (valid after rs_fof6d). Members are
 // stored node after node, each node's members in ascending id order.

@@ -403,11 +403,16 @@ __global__ void k_mlp_reduce(int nblk, const float* __restrict__ part, float* __
 }
 
 // Adam step on the float32 masters, then refresh the bf16 device weights.
+// Adam step number k = *step (0-based); corr[2k], corr[2k + 1] = 1 - b1^(k+1), 1 - b2^(k+1)
+// (the bias corrections, rounded on the host). The step counter lives on the device so that
+// one captured epoch replays with the right corrections.
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ grad, float lr, float b1, float b2, float eps,
-                       float c1, float c2, MlpDev* __restrict__ dev) {
+                       const float* __restrict__ corr, const int64_t* __restrict__ step) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= kParams) return;
+  const int64_t k = *step;
+  const float c1 = corr[2 * k], c2 = corr[2 * k + 1];
   const float gr = grad[p];
   const float mm = b1 * m[p] + (1.f - b1) * gr;
   const float vv = b2 * v[p] + (1.f - b2) * gr * gr;
@@ -425,8 +430,12 @@ __device__ __forceinline__ __nv_bfloat16 w2_at(const float* __restrict__ w, int 
   return __float2bfloat16_rn(w[kOffW2 + in * 64 + out]);
 }
 
-__global__ void k_pack_weights(const float* __restrict__ w, MlpDev* __restrict__ dev) {
+// bf16 copies and mma fragments of the float32 weights; advances the Adam step counter (if
+// given) once the step's update has been packed.
+__global__ void k_pack_weights(const float* __restrict__ w, MlpDev* __restrict__ dev,
+                               int64_t* __restrict__ step) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (step && p == 0) *step += 1;
   if (p < 8 * 32) {  // W1 fragments (one k-slice)
     const int nt = p / 32, lane = p % 32, g = lane >> 2, q = lane & 3;
     const int n = nt * 8 + g, k = 2 * q;
@@ -514,22 +523,33 @@ static int set_params_dev(rs_ctx* ctx, const float* w_dev_or_host, bool host, cu
   float* w = static_cast<float*>(ctx->buf[S_MLP_W].ptr);
   RS_CUDA(ctx, cudaMemcpyAsync(w, w_dev_or_host, sizeof(float) * kParams,
                                host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
-  k_pack_weights<<<(64 * 64 + 255) / 256, 256, 0, st>>>(w, static_cast<MlpDev*>(ctx->buf[S_MLP_DEV].ptr));
+  k_pack_weights<<<(64 * 64 + 255) / 256, 256, 0, st>>>(w, static_cast<MlpDev*>(ctx->buf[S_MLP_DEV].ptr),
+                                                        nullptr);
   RS_LAUNCHED(ctx, "k_pack_weights");
   ctx->have_mlp = true;
   return RS_OK;
 }
 
+int mlp_copy(rs_ctx* dst, rs_ctx* src, cudaStream_t st) {
+  if (!src->have_mlp) return set_error(dst, RS_ERR_STATE, "no surrogate weights to copy");
+  RS_TRY(set_params_dev(dst, static_cast<const float*>(src->buf[S_MLP_W].ptr), false, st));
+  dst->mlp_err_max = src->mlp_err_max;
+  return RS_OK;
+}
+
 // Full-batch gradient of L = (1/B) sum (y - t)^2 over rows idx[0..n) (or 0..n).
+// (capturing: enqueue only - scratch is already sized and the attribute set, so nothing but
+// stream work happens while a graph is being captured.)
 static int mlp_gradient(rs_ctx* ctx, int64_t n, const float* x, const float* t, const int64_t* idx,
-                        float* grad, double* sse_out, cudaStream_t st) {
+                        float* grad, double* sse_out, cudaStream_t st, bool capturing = false) {
   const int nblk = int((n + kRowsPerBlock - 1) / kRowsPerBlock);
   float* part = scratch_t<float>(ctx, S_MLP_PART, size_t(nblk) * kParams);
   double* sse = scratch_t<double>(ctx, S_MLP_SSE, size_t(nblk) + 1);
   if (!part || !sse) return RS_ERR_OOM;
   const size_t smem = grad_smem();
-  RS_CUDA(ctx, cudaFuncSetAttribute(k_mlp_grad_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    int(smem)));
+  if (!capturing)
+    RS_CUDA(ctx, cudaFuncSetAttribute(k_mlp_grad_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(smem)));
   {
     ProfScope prof_(ctx, "k_mlp_grad_block", st);
     k_mlp_grad_block<<<nblk, kThreads, smem, st>>>(n, x, t, idx, 1.0f / float(n),
@@ -622,31 +642,79 @@ extern "C" int rs_mlp_train(rs_ctx* ctx, int64_t n, const float* x, const float*
   float* w = static_cast<float*>(ctx->buf[S_MLP_W].ptr);
   MlpDev* dev = static_cast<MlpDev*>(ctx->buf[S_MLP_DEV].ptr);
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  int64_t step = 0;
-  double last_sse = 0.0;
+  const int64_t per_epoch = n_train / batch;  // full batches; the remainder is left out
+  const int64_t total = int64_t(epochs) * per_epoch;
+  // bias corrections of every step, host-rounded: 1 - b^(k+1)
+  std::vector<float> corr(size_t(2 * std::max<int64_t>(total, 1)), 1.f);
+  for (int64_t k = 0; k < total; ++k) {
+    corr[2 * k] = 1.f - std::pow(b1, float(k + 1));
+    corr[2 * k + 1] = 1.f - std::pow(b2, float(k + 1));
+  }
+  float* d_corr = scratch_t<float>(ctx, S_MLP_CORR, corr.size());
+  int64_t* d_step = scratch_t<int64_t>(ctx, S_MLP_STEP, 1);
+  int64_t* bidx = scratch_t<int64_t>(ctx, S_MLP_BIDX, size_t(std::max<int64_t>(n_train, 1)));
+  const int nblk = int((batch + kRowsPerBlock - 1) / kRowsPerBlock);
+  double* sse = scratch_t<double>(ctx, S_MLP_SSE, size_t(nblk) + 1);
+  if (!d_corr || !d_step || !bidx || !sse || !scratch_t<float>(ctx, S_MLP_PART, size_t(nblk) * kParams))
+    return RS_ERR_OOM;
+  RS_CUDA(ctx, cudaMemcpyAsync(d_corr, corr.data(), sizeof(float) * corr.size(),
+                               cudaMemcpyHostToDevice, st));
+  RS_CUDA(ctx, cudaMemsetAsync(d_step, 0, sizeof(int64_t), st));
+  RS_CUDA(ctx, cudaFuncSetAttribute(k_mlp_grad_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(grad_smem())));
+  RS_CUDA(ctx, cudaStreamSynchronize(st));
+  // One epoch's launches: gradient of each batch, Adam update, weight packing. Static (the
+  // batch order lives in bidx, the step in d_step), so with graphs on the epoch is captured
+  // once and replayed; off, the same launches are issued one by one.
+  auto epoch_body = [&](cudaStream_t s, bool capturing) -> int {
+    for (int64_t b = 0; b < per_epoch; ++b) {
+      RS_TRY(mlp_gradient(ctx, batch, x, t, bidx + b * batch, grad, nullptr, s, capturing));
+      k_adam<<<(kParams + 255) / 256, 256, 0, s>>>(w, mom, mom + kParams, grad, lr, b1, b2, eps,
+                                                   d_corr, d_step);
+      RS_LAUNCHED(ctx, "k_adam");
+      k_pack_weights<<<(64 * 64 + 255) / 256, 256, 0, s>>>(w, dev, d_step);
+      RS_LAUNCHED(ctx, "k_pack_weights");
+    }
+    return RS_OK;
+  };
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_launches = 0;
   std::vector<int64_t> order(n_train);
-  for (int e = 0; e < epochs; ++e) {
+  int rc = RS_OK;
+  for (int e = 0; e < epochs && rc == RS_OK; ++e) {
     for (int64_t i = 0; i < n_train; ++i) order[i] = perm[i];
     for (int64_t i = n_train - 1; i > 0; --i)
       std::swap(order[i], order[int64_t(splitmix(s) % uint64_t(i + 1))]);
-    int64_t* bidx = scratch_t<int64_t>(ctx, S_MLP_BIDX, size_t(n_train));
-    if (!bidx) return RS_ERR_OOM;
-    RS_CUDA(ctx, cudaMemcpyAsync(bidx, order.data(), sizeof(int64_t) * n_train, cudaMemcpyHostToDevice, st));
-    double ep_sse = 0.0;
-    for (int64_t b0 = 0; b0 + batch <= n_train; b0 += batch) {
-      double sse = 0.0;
-      const bool want = (b0 + 2 * batch > n_train);
-      RS_TRY(mlp_gradient(ctx, batch, x, t, bidx + b0, grad, want ? &sse : nullptr, st));
-      ++step;
-      const float c1 = 1.f - std::pow(b1, float(step)), c2 = 1.f - std::pow(b2, float(step));
-      k_adam<<<(kParams + 255) / 256, 256, 0, st>>>(w, mom, mom + kParams, grad, lr, b1, b2, eps, c1, c2, dev);
-      RS_LAUNCHED(ctx, "k_adam");
-      k_pack_weights<<<(64 * 64 + 255) / 256, 256, 0, st>>>(w, dev);
-      RS_LAUNCHED(ctx, "k_pack_weights");
-      if (want) ep_sse = sse / double(batch);
+    if (n_train > 0) {
+      const cudaError_t ce = cudaMemcpyAsync(bidx, order.data(), sizeof(int64_t) * n_train,
+                                             cudaMemcpyHostToDevice, st);
+      if (ce != cudaSuccess) {
+        rc = set_error(ctx, RS_ERR_CUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(ce));
+        break;
+      }
     }
-    last_sse = ep_sse;
+    if (per_epoch == 0) continue;
+    if (!ctx->use_graphs) {
+      rc = epoch_body(st, false);
+      continue;
+    }
+    if (!exec) {
+      rc = capture_graph(ctx, [&](cudaStream_t cs) { return epoch_body(cs, true); }, &exec,
+                         &graph_launches);
+      if (rc != RS_OK) break;
+    }
+    rc = launch_graph(ctx, exec, graph_launches, st);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  RS_TRY(rc);
+  // squared-error sum of the last batch trained (its per-block partials), host order
+  double last_sse = 0.0;
+  if (total > 0) {
+    std::vector<double> h(nblk);
+    RS_CUDA(ctx, cudaMemcpyAsync(h.data(), sse, sizeof(double) * nblk, cudaMemcpyDeviceToHost, st));
     RS_CUDA(ctx, cudaStreamSynchronize(st));
+    for (double v : h) last_sse += v;
+    last_sse /= double(batch);
   }
   if (train_mse_out) *train_mse_out = last_sse;
   // held-out max |y - t|

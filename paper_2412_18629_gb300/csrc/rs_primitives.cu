@@ -42,6 +42,46 @@ int after_launch(rs_ctx* ctx, const char* name) {
   return RS_OK;
 }
 
+int begin_capture(rs_ctx* ctx, cudaStream_t* cs) {
+  if (!ctx->graph_stream) {
+    cudaStream_t s;
+    RS_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    ctx->graph_stream = s;
+  }
+  *cs = static_cast<cudaStream_t>(ctx->graph_stream);
+  RS_CUDA(ctx, cudaStreamBeginCapture(*cs, cudaStreamCaptureModeThreadLocal));
+  return RS_OK;
+}
+
+int end_capture(rs_ctx* ctx, cudaStream_t cs, int body_rc, int64_t launches0, bool profile,
+                cudaGraphExec_t* exec, int64_t* launches) {
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+  ctx->profile = profile;
+  *launches = ctx->launches - launches0;
+  ctx->launches = launches0;
+  *exec = nullptr;
+  if (body_rc != RS_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (body_rc != RS_OK) return body_rc;
+    return set_error(ctx, RS_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ce));
+  }
+  const cudaError_t ie = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    *exec = nullptr;
+    return set_error(ctx, RS_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+  }
+  return RS_OK;
+}
+
+int launch_graph(rs_ctx* ctx, cudaGraphExec_t exec, int64_t launches, cudaStream_t st) {
+  RS_CUDA(ctx, cudaGraphLaunch(exec, st));
+  ctx->launches += launches;
+  return RS_OK;
+}
+
 static cudaEvent_t prof_event(rs_ctx* ctx) {
   if (!ctx->prof_free.empty()) {
     cudaEvent_t e = ctx->prof_free.back();

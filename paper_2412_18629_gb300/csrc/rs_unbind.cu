@@ -101,15 +101,30 @@ constexpr int64_t kTuneMinMembers = 1 << 20;  // the autotuner times candidates 
 
 // Tiles of the two direct-sum kernels; nodes with >= sur_min members (sur_min > 0) are left to
 // the surrogate path. Also the sort key of the blocked tiles' order (size class, descending).
+// pairs (if given): ordered pairs g (g - 1) of the selected nodes, [0] small, [1] blocked.
 __global__ void k_tiles_split(int64_t nn, const int64_t* __restrict__ node_size, int64_t sur_min,
                               const int* __restrict__ only, int64_t max_g, int blk_tile,
                               int64_t* __restrict__ small, int64_t* __restrict__ big,
-                              uint64_t* __restrict__ okey, uint32_t* __restrict__ oval) {
+                              uint64_t* __restrict__ okey, uint32_t* __restrict__ oval,
+                              unsigned long long* __restrict__ pairs) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= nn) return;
-  const int64_t g = node_size[k];
-  const bool skip = (only ? (only[k] == 0) : (sur_min > 0 && g >= sur_min)) || (max_g > 0 && g >= max_g);
+  const int64_t g = k < nn ? node_size[k] : 0;
+  const bool skip = k >= nn || (only ? (only[k] == 0) : (sur_min > 0 && g >= sur_min)) ||
+                    (max_g > 0 && g >= max_g);
   const bool blocked = !skip && g > kBlockedMin;
+  if (pairs) {  // warp sums, one atomic per warp and class
+    unsigned long long ps = (!skip && !blocked) ? (unsigned long long)(g * (g - 1)) : 0ull;
+    unsigned long long pb = blocked ? (unsigned long long)(g * (g - 1)) : 0ull;
+    for (int off = 16; off >= 1; off >>= 1) {
+      ps += __shfl_xor_sync(0xffffffffu, ps, off);
+      pb += __shfl_xor_sync(0xffffffffu, pb, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (ps) atomicAdd(pairs, ps);
+      if (pb) atomicAdd(pairs + 1, pb);
+    }
+  }
+  if (k >= nn) return;
   small[k] = (skip || g > kBlockedMin) ? 0 : (g + kPotTile - 1) / kPotTile;
   big[k] = blocked ? (g + blk_tile - 1) / blk_tile : 0;
   okey[k] = blocked ? uint64_t(63 - __clzll(g)) ^ 63u : 255u;
@@ -559,7 +574,8 @@ __global__ void k_halo_decide(int64_t nn, const int64_t* __restrict__ node_size,
 // Tiles of the blocked kernel for kBlkR = R (nodes above kBlockedMin members, ordered by size
 // class, largest first) and of k_potential (the other selected nodes).
 int potential_tiles(rs_ctx* ctx, int64_t sur_min, const int* only, int64_t max_g, int R,
-                    int64_t* tile_small, int64_t* tile_perm, uint32_t** perm, cudaStream_t st) {
+                    int64_t* tile_small, int64_t* tile_perm, uint32_t** perm, cudaStream_t st,
+                    unsigned long long* pairs) {
   Hier h = hier_of(ctx);
   const int64_t nn = ctx->n_nodes;
   int64_t* tile_big = scratch_t<int64_t>(ctx, S_U_TILEBIG, size_t(nn) + 1);
@@ -569,7 +585,7 @@ int potential_tiles(rs_ctx* ctx, int64_t sur_min, const int* only, int64_t max_g
   uint32_t* vb = scratch_t<uint32_t>(ctx, S_U_OVAL_B, size_t(nn));
   if (!tile_big || !ka || !kb || !va || !vb) return RS_ERR_OOM;
   k_tiles_split<<<grid_for(nn, kT), kT, 0, st>>>(nn, h.node_size, sur_min, only, max_g, kBlkThreads * R,
-                                                 tile_small, tile_big, ka, va);
+                                                 tile_small, tile_big, ka, va, pairs);
   RS_LAUNCHED(ctx, "k_tiles_split");
   uint64_t* ko;
   RS_TRY(radix_sort_u64(ctx, nn, 8, ka, va, kb, vb, &ko, perm, st));
@@ -621,7 +637,8 @@ int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, int64_t max_
     RS_CUDA(ctx, cudaEventCreate(&e0));
     RS_CUDA(ctx, cudaEventCreate(&e1));
     for (int c = 0; c < 3; ++c) {
-      RS_TRY(potential_tiles(ctx, sur_min, only, max_g, cand[c], tile_small, tile_perm, &perm, st));
+      RS_TRY(potential_tiles(ctx, sur_min, only, max_g, cand[c], tile_small, tile_perm, &perm, st,
+                             nullptr));
       RS_CUDA(ctx, cudaEventRecord(e0, st));
       RS_TRY(launch_blocked(ctx, cand[c], tile_perm, perm, S, st));
       RS_CUDA(ctx, cudaEventRecord(e1, st));
@@ -639,7 +656,9 @@ int direct_potential(rs_ctx* ctx, int64_t sur_min, const int* only, int64_t max_
     ctx->tune_blk_r = best;
   }
   const int R = ctx->tune_blk_r ? ctx->tune_blk_r : 4;
-  RS_TRY(potential_tiles(ctx, sur_min, only, max_g, R, tile_small, tile_perm, &perm, st));
+  // pair tallies of this rs_unbind (counters [20], [21], zeroed at its start)
+  unsigned long long* pairs = static_cast<unsigned long long*>(ctx->buf[S_SUR_COUNTERS].ptr) + 20;
+  RS_TRY(potential_tiles(ctx, sur_min, only, max_g, R, tile_small, tile_perm, &perm, st, pairs));
   {
     ProfScope prof_(ctx, "k_potential", st);
     k_potential<<<grid_for(m, kT), kT, 0, st>>>(m, h.mnode, tile_small, h.node_off, h.node_size, h.U,
@@ -747,8 +766,8 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
   double* vbulk = scratch_t<double>(ctx, S_U_VBULK, size_t(std::max<int64_t>(nn, 1)) * 3);
   uint32_t* ambig = scratch_t<uint32_t>(ctx, S_U_AMBIG, size_t(std::max<int64_t>(m, 1)));
   uint8_t* halo = scratch_t<uint8_t>(ctx, S_U_FLAGS, size_t(std::max<int64_t>(nn, 1)));
-  // counters: [0..6], [8..11] surrogate path (rs_surrogate.cu), [7] float64 fallbacks of the
-  // direct sums, [12..17] certified tree bound (rs_tree.cu)
+  // counters: [0..6], [8..11], [19] surrogate path (rs_surrogate.cu), [7] float64 fallbacks of
+  // the direct sums, [12..18] certified tree bound (rs_tree.cu), [20..21] direct-sum pairs
   unsigned long long* counters = scratch_t<unsigned long long>(ctx, S_SUR_COUNTERS, kCounters);
   if (!bound || !S || !nb || !vbulk || !ambig || !halo || !counters) return RS_ERR_OOM;
   unsigned long long* n_ambig = counters + 7;
@@ -766,6 +785,7 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
   int64_t nfb = 0;
   for (int i = 0; i < 11; ++i) ctx->sur_stats[i] = 0;
   for (int i = 0; i < 8; ++i) ctx->tree_stats[i] = 0;
+  ctx->pot_pairs[0] = ctx->pot_pairs[1] = 0;
   ctx->tree_nt = ctx->tree_T = ctx->tree_C = 0;
   ctx->unbind_passes_run = 1;
   if (m > 0) {
@@ -815,12 +835,21 @@ extern "C" int rs_unbind(rs_ctx* ctx, const float* pos, const float* vel, float*
     ctx->tree_stats[1] = ctx->tree_T;
     for (int i = 0; i < 4; ++i) ctx->tree_stats[2 + i] = ctx->host_box[12 + i];
     ctx->tree_stats[6] = ctx->host_box[18];
+    ctx->pot_pairs[0] = ctx->host_box[20];
+    ctx->pot_pairs[1] = ctx->host_box[21];
     nfb = ctx->host_box[7] + ctx->host_box[6];
     ctx->tree_recorded = rec != nullptr;
   }
   if (n_fallback_out) *n_fallback_out = nfb;
   ctx->have_unbind = true;
   ctx->last_unbind_surrogate = sur;
+  return RS_OK;
+}
+
+extern "C" int rs_potential_pairs(rs_ctx* ctx, int64_t* pairs_out) {
+  if (!ctx || !pairs_out) return RS_ERR_INVALID_ARG;
+  pairs_out[0] = ctx->pot_pairs[0];
+  pairs_out[1] = ctx->pot_pairs[1];
   return RS_OK;
 }
 

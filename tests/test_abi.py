@@ -52,3 +52,31 @@ def test_invalid_config_is_rejected(lib):
     lib.rs_ctx_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(rs.rs_config),
                                   ctypes.c_int]
     assert lib.rs_ctx_create(ctypes.byref(h), ctypes.byref(cfg), 0) == 1  # RS_ERR_INVALID_ARG
+
+
+def _c_layout(tmp_path, struct, fields):
+    """sizeof and offsetof of a header struct, from a C program compiled with gcc."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "rs_gb300.h"\n'
+                   f'int main(void) {{\n  printf("%zu\\n", sizeof({struct}));\n{body}  return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                           text=True).stdout.split()]
+    return vals[0], vals[1:]
+
+
+@pytest.mark.parametrize("name", ("rs_config", "rs_snapshot"))
+def test_ctypes_structs_match_the_header(tmp_path, name):
+    import paper_2412_18629_gb300 as rs
+    cls = getattr(rs, name)
+    fields = [f[0] for f in cls._fields_]
+    size, offs = _c_layout(tmp_path, name, fields)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offs

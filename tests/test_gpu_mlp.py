@@ -115,6 +115,30 @@ def test_training_reduces_loss_and_reports_holdout_error(ctx):
     assert np.quantile(np.abs(y[:512] - yo), 0.99) <= 1e-4 * np.abs(t).max()
 
 
+def test_graph_replayed_training_equals_plain_launches():
+    """The training epoch captured once as a CUDA graph and replayed every epoch (reshuffled
+    batch order, advancing Adam step) gives bit for bit the weights, held-out error and loss of
+    the same launches issued one by one, and counts the same kernel launches."""
+    import torch
+    import paper_2412_18629_gb300 as rs
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0, 1, (20000, 8)).astype(np.float32)
+    t = (np.sin(3 * x[:, 0]) - x[:, 2] * x[:, 7]).astype(np.float32)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    out = {}
+    for graphs in (True, False):
+        c = rs.Context(box=10.0, link_len=0.2, softening=0.01, particle_mass=1.0)
+        c.use_graphs(graphs)
+        l0 = c.kernel_launches
+        em, mse = rs.rs_mlp_train(c, xd, td, epochs=5, batch=512, lr=2e-3, seed=9)
+        out[graphs] = (rs.rs_mlp_get_params(c), em, mse, c.kernel_launches - l0)
+        c.close()
+    (pg, eg, mg, lg), (pe, ee, me, le) = out[True], out[False]
+    assert np.array_equal(pg.view(np.uint32), pe.view(np.uint32))
+    assert eg == ee and mg == me and lg == le
+    assert mg < np.var(t)                           # it did train
+
+
 def test_checkpoint_round_trip_and_corruption(ctx, tmp_path):
     """rs_surrogate_save / rs_surrogate_load: weights and held-out maximum error come back bit
     for bit in a new context (same outputs); a truncated or altered file is rejected."""

@@ -92,3 +92,24 @@ def test_autotuner_picks_a_candidate_and_keeps_the_sums():
     phi1, b1 = phi1.cpu().numpy(), b1.cpu().numpy()
     phi2, b2, _ = rs.rs_unbind(ctx, pos, vel, want_potential=True)
     assert np.array_equal(phi1, phi2.cpu().numpy()) and np.array_equal(b1, b2.cpu().numpy())
+
+
+@pytest.mark.parametrize("mode,tree_min", (("plain", 0), ("batched", 0), ("batched", 2048)))
+def test_direct_sum_pair_tallies(mode, tree_min):
+    """rs_potential_pairs counts exactly the ordered pairs g (g - 1) of the nodes each direct-sum
+    kernel ran on: nodes up to 384 members in [0], larger ones in [1] (below the tree's
+    threshold when the tree bound is on), whatever the autotuner did first."""
+    import paper_2412_18629_gb300 as rs
+    s = small_snapshot(1 << 16, 40.3, 33, n_max=8000)
+    ctx = gpu_ctx(s, mode=mode, tree_min=tree_min)
+    pos, vel, ids = to_dev(s)
+    lab, _ = rs.rs_fof3d(ctx, pos, ids)
+    rs.rs_fof6d(ctx, pos, vel, ids, lab)
+    g = rs.rs_fof6d_copy(ctx)["size"].cpu().numpy().astype(np.int64)
+    rs.rs_unbind(ctx, pos, vel, want_potential=False)
+    small, big = rs.rs_potential_pairs(ctx)
+    lim = tree_min if (mode == "batched" and tree_min > 0) else np.inf
+    p = g * (g - 1)
+    assert small == int(p[g <= 384].sum())
+    assert big == int(p[(g > 384) & (g < lim)].sum())
+    assert big > 0 and (lim == np.inf or (g >= lim).any())
