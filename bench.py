@@ -287,10 +287,11 @@ def _alu_d6(r, k):
     return d6 * OPS_D6
 
 
-def stages(r):
+def stages(r, traffic=None):
     """Per-kernel roofline figures of one form from its profiled step (CUDA events per launch):
     achieved = algorithmic work per step / kernel time per step, against the measured HBM copy
-    bandwidth or the FP32-pipe lane rate."""
+    bandwidth or the FP32-pipe lane rate; with the ncu DRAM traffic per launch where captured
+    (and, for HBM-bound kernels, the algorithmic bytes per launch beside it)."""
     prof = dict(r["prof"])
     if "k_sort_hist" in prof or "k_sort_scatter" in prof:
         a, b = prof.get("k_sort_hist", (0.0, 0)), prof.get("k_sort_scatter", (0.0, 0))
@@ -308,6 +309,10 @@ def stages(r):
         else:
             e.update(achieved=units / sec / 1e12, peak=FP32_PEAK_OPS / 1e12, unit="Tops/s",
                      frac=units / sec / FP32_PEAK_OPS, peak_source="FP32 lanes x 2070 MHz")
+        if traffic and traffic.get(k):
+            e["traffic"] = traffic[k]
+            if bound == "hbm":
+                e["algorithmic_bytes_per_launch"] = units / max(prof[k][1], 1)
         if k.startswith(("k_nn6d", "k_link6d")):
             ops = _alu_d6(r, k)
             if ops:
@@ -320,7 +325,7 @@ def stages(r):
 def roofline(r, traffic=None):
     """The roofline entry of the dominant kernel (largest time in the profiled step among the
     kernels with a work figure); launches and average duration per launch."""
-    st = stages(r)
+    st = stages(r, traffic)
     if not st:
         return None
     k = max(st, key=lambda x: st[x]["ms_per_step"])
@@ -332,14 +337,17 @@ def roofline(r, traffic=None):
 
 
 def _traffic_table():
-    """DRAM bytes per launch of profiled kernels from ncu (profiles/traffic.json), scaled to the
-    bench workload by the entry's unit count: {kernel: {"bytes_per_unit", "unit", ...}}."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes (read + write) per launch of the profiled kernels, from one ncu capture of the
+    bench command (profiles/dram_traffic.json, written from that capture; the summary beside it
+    gives the command): {workload: {kernel: bytes per launch}}. A kernel changed since its
+    capture has no entry."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
-            return json.load(f)
+            t = json.load(f)
     except (OSError, ValueError):
         return {}
+    return {w: {k: v for k, v in e.items() if not k.startswith("_")} for w, e in t.items()}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -569,11 +577,12 @@ def measure_stream(args, local):
 
 
 def _form_entry(r, traffic):
+    traffic = traffic if r["form"] == "surrogate" else None  # captured on the headline form
     return {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
             "warmup": r["warmup"], "gpu_launches": r["launches"],
             "launches_per_step": r["launches_per_step"], "fallback_members": r["fallback"],
             "kernels_ms_profiled_step": {k: t[0] for k, t in r["prof"].items()},
-            "roofline": roofline(r, traffic), "stages": stages(r), "clocks": r["clocks"],
+            "roofline": roofline(r, traffic), "stages": stages(r, traffic), "clocks": r["clocks"],
             "autotune": r["autotune"], "tree_stats": r["tree"], "work_tallies": r["work"],
             "sort_keypasses_per_step": r["sort_keypasses"],
             "surrogate_stats": r["surrogate_stats"], "output_digest": r["digest"]}

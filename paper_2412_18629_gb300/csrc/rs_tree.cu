@@ -367,10 +367,13 @@ struct WalkArgs {
   unsigned long long* counters;  // [0] decided, [1] undecided, [2] expansions, [3] direct pairs
 };
 
-// One warp per 32 wanted targets of one node: the certified walk, then the decision.
+// One warp per 32 wanted targets of one node: the certified walk, then the decision. Indices
+// inside the walk are 32-bit and relative to the node (its members are [tb, tb + g) of the
+// sorted arrays, its cells [cb, cb + cells) of the cell array); a stack entry carries the
+// cell's level, its index j within the level and its index within the node's cells.
 __global__ void __launch_bounds__(kT)
 k_tree_walk(WalkArgs A) {
-  __shared__ uint32_t s_stack[kT / 32][kStack];
+  __shared__ uint64_t s_stack[kT / 32][kStack];
   __shared__ float4 s_leaf[kT / 32][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -386,32 +389,35 @@ k_tree_walk(WalkArgs A) {
   const int64_t g = A.tg[b], tb = A.ttoff[b], cb = A.tcoff[b];
   const int nlev = levels_of(g);
   // per-level cell offsets inside the node, lane l holds level l's
-  const int64_t my_lvoff = lane < nlev ? level_off(g, lane) : 0;
-  // the warp's target range in sorted positions
-  uint32_t smin = s_self, smax = s_self;
+  const uint32_t my_lvoff = lane < nlev ? uint32_t(level_off(g, lane)) : 0u;
+  const uint32_t g32 = uint32_t(g), self_rel = s_self - uint32_t(tb);
+  // the warp's targets as a range of node-relative positions: a cell holds one of them iff
+  // its index at its level lies in [lo_rel >> sh, hi_rel >> sh]
+  uint32_t lo_rel = self_rel, hi_rel = self_rel;
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
-    smin = min(smin, __shfl_xor_sync(0xffffffffu, smin, off));
-    smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, off));
+    lo_rel = min(lo_rel, __shfl_xor_sync(0xffffffffu, lo_rel, off));
+    hi_rel = max(hi_rel, __shfl_xor_sync(0xffffffffu, hi_rel, off));
   }
-  uint32_t* stk = s_stack[wid];
+  const Cell* __restrict__ ncell = A.cells + cb;
+  const float4* __restrict__ nx = A.TX + tb;
+  uint64_t* stk = s_stack[wid];
   float4* leaf = s_leaf[wid];
   float S = 0.f, Cc = 0.f, Bt = 0.f;
-  unsigned long long n_exp = 0, n_dir = 0;
-  if (lane == 0) stk[0] = (uint32_t(nlev - 1) << 28);
+  uint32_t n_exp = 0, n_dir = 0;
+  const uint32_t root_off = __shfl_sync(0xffffffffu, my_lvoff, nlev - 1);
+  if (lane == 0) stk[0] = (uint64_t(nlev - 1) << 60) | uint64_t(root_off);
   int sp = 1;
   __syncwarp();
   while (sp > 0) {
     --sp;
-    const uint32_t e = stk[sp];
+    const uint64_t e = stk[sp];
     __syncwarp();
-    const int lev = int(e >> 28);
-    const int64_t j = int64_t(e & 0x0fffffffu);
-    const int64_t lvo = __shfl_sync(0xffffffffu, my_lvoff, lev);
+    const int lev = int(e >> 60);
+    const uint32_t j = uint32_t(e >> 32) & 0x0fffffffu;
     const int sh = kLeafBits + kBrBits * lev;
-    const int64_t cs = tb + (j << sh), ce = rsd::min64(cs + (int64_t(1) << sh), tb + g);
-    const bool overlap = cs <= int64_t(smax) && ce > int64_t(smin);
-    const Cell cl = A.cells[cb + lvo + j];
+    const bool overlap = j >= (lo_rel >> sh) && j <= (hi_rel >> sh);
+    const Cell cl = ncell[uint32_t(e)];
     if (cl.np.x == 0.f) continue;  // no member left in the cell (iterative unbinding)
     const float dx = t.x - cl.ca.x, dy = t.y - cl.ca.y, dz = t.z - cl.ca.z;
     const float R2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, A.eps2)));
@@ -439,9 +445,10 @@ k_tree_walk(WalkArgs A) {
       // direct sum over the leaf's members, two per packed float32x2 step; slots past the leaf's
       // count hold +inf, whose term is exactly 0; the target's own term rsqrt(eps^2) is taken
       // out once (or, without softening, skipped per pair)
-      const int cnt = int(ce - cs);
+      const uint32_t c0 = j << kLeafBits;
+      const int cnt = int(min(32u, g32 - c0));
       const float inf = __int_as_float(0x7f800000);
-      leaf[lane] = lane < cnt ? A.TX[cs + lane] : make_float4(inf, inf, inf, 0.f);
+      leaf[lane] = lane < cnt ? nx[c0 + lane] : make_float4(inf, inf, inf, 0.f);
       __syncwarp();
       float blk;
       if (A.eps2 > 0.f) {
@@ -458,14 +465,14 @@ k_tree_walk(WalkArgs A) {
           acc2 = __fadd2_rn(acc2, make_float2(rsqrtf(r2.x), rsqrtf(r2.y)));
         }
         blk = __fadd_rn(acc2.x, acc2.y);
-        if (cs <= int64_t(s_self) && int64_t(s_self) < ce) blk = __fsub_rn(blk, rsqrtf(A.eps2));
+        if ((self_rel >> kLeafBits) == j) blk = __fsub_rn(blk, rsqrtf(A.eps2));
       } else {
         blk = 0.f;
         for (int k = 0; k < cnt; ++k) {
           const float4 x = leaf[k];
           const float ex = __fsub_rn(x.x, t.x), ey = __fsub_rn(x.y, t.y), ez = __fsub_rn(x.z, t.z);
           const float wv = rsqrtf(__fmaf_rn(ex, ex, __fmaf_rn(ey, ey, __fmaf_rn(ez, ez, A.eps2))));
-          blk = __fadd_rn(blk, cs + k == int64_t(s_self) ? 0.f : wv);
+          blk = __fadd_rn(blk, c0 + uint32_t(k) == self_rel ? 0.f : wv);
         }
       }
       __syncwarp();
@@ -475,10 +482,13 @@ k_tree_walk(WalkArgs A) {
       S = tt;
       n_dir += uint32_t(cnt);
     } else {
-      const int64_t nchild = cells_at(g, lev - 1);
-      const int64_t j0 = j << kBrBits;
-      const int nch = int(rsd::min64(int64_t(1) << kBrBits, nchild - j0));
-      if (lane < nch) stk[sp + lane] = (uint32_t(lev - 1) << 28) | uint32_t(j0 + lane);
+      const int shc = sh - kBrBits;  // the children's level
+      const uint32_t nchild = uint32_t((uint64_t(g32) + (1ull << shc) - 1) >> shc);
+      const uint32_t j0 = j << kBrBits;
+      const int nch = int(min(1u << kBrBits, nchild - j0));
+      const uint32_t lvc = __shfl_sync(0xffffffffu, my_lvoff, lev - 1);
+      if (lane < nch)
+        stk[sp + lane] = (uint64_t(lev - 1) << 60) | (uint64_t(j0 + lane) << 32) | uint64_t(lvc + j0 + lane);
       sp += nch;
       __syncwarp();
     }
@@ -508,16 +518,17 @@ k_tree_walk(WalkArgs A) {
   }
   const unsigned dec = __ballot_sync(0xffffffffu, valid && decided);
   const unsigned und = __ballot_sync(0xffffffffu, valid && !decided);
+  unsigned long long n_exp64 = n_exp, n_dir64 = n_dir;
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
-    n_exp += __shfl_xor_sync(0xffffffffu, n_exp, off);
-    n_dir += __shfl_xor_sync(0xffffffffu, n_dir, off);
+    n_exp64 += __shfl_xor_sync(0xffffffffu, n_exp64, off);
+    n_dir64 += __shfl_xor_sync(0xffffffffu, n_dir64, off);
   }
   if (lane == 0) {
     if (dec) atomicAdd(A.counters + 0, (unsigned long long)__popc(dec));
     if (und) atomicAdd(A.counters + 1, (unsigned long long)__popc(und));
-    atomicAdd(A.counters + 2, n_exp);
-    atomicAdd(A.counters + 3, n_dir);
+    atomicAdd(A.counters + 2, n_exp64);
+    atomicAdd(A.counters + 3, n_dir64);
   }
 }
 
