@@ -12,12 +12,9 @@
 //                 clique) and cell end per sorted position
 //   k_occ_set     occupancy bits per (z, y) row, one per 8 sub-cells in x (grids whose bits fit
 //                 in 32 MB, so that they stay in L2)
-//   k_fof_single, scan, k_fof_partition
-//                 the particles alone in their sub-cell, then the others (a stable partition
-//                 of the sorted positions, so a warp holds one kind: sparse-region particles
-//                 with short scans, or dense-region ones with many occupied neighbour cells)
-//   k_fof_link    per particle in that order, the half stencil of rows within R sub-cells, a
-//                 row skipped when no occupancy bit of its x range is set; a neighbour cell is
+//   k_fof_link    per particle (particles alone in their sub-cell, then the others, in two
+//                 launches), the half stencil of rows within R sub-cells, a row skipped when no
+//                 occupancy bit of its x range is set; a neighbour cell is
 //                 skipped when its root already equals the particle's root, otherwise scanned
 //                 until the first linked member (one link joins the whole clique)
 //   k_fof_roots   after full path compression: each root stores its id and counts as a group;
@@ -239,33 +236,18 @@ __device__ __forceinline__ void scan_row(const LinkArgs& A, uint32_t i, uint64_t
   }
 }
 
-// 1 for a particle alone in its sub-cell, else 0 (int64, for the scan).
-__global__ void __launch_bounds__(kThreads)
-k_fof_single(int64_t n, const uint64_t* __restrict__ keys, int64_t* __restrict__ flag) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint64_t k = keys[i];
-  flag[i] = ((i == 0 || keys[i - 1] != k) && (i + 1 == n || keys[i + 1] != k)) ? 1 : 0;
-}
-
-// Stable partition of the sorted positions: alone particles first (at their scan offset), then
-// the others (after all alone ones). flag holds the exclusive scan and, at [n], the total.
-__global__ void __launch_bounds__(kThreads)
-k_fof_partition(int64_t n, const int64_t* __restrict__ flag, uint32_t* __restrict__ order) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t a = flag[i];
-  const bool single = flag[i + 1] != a;
-  order[single ? a : flag[n] + (i - a)] = uint32_t(i);
-}
-
-// One thread per particle, in the partitioned order.
-__global__ void __launch_bounds__(kThreads)
-k_fof_link(int64_t n, LinkArgs A, const uint32_t* __restrict__ order) {
+// Two launches: particles alone in their sub-cell (sparse regions: short scans, few links),
+// then particles of shared sub-cells (dense regions: many occupied neighbour cells). Keeping the
+// two kinds in different launches keeps a warp's lanes on similar amounts of work, and each
+// launch reads the particles in sorted order (a partition of the two kinds into one launch
+// was measured slower: its warps gather scattered particles).
+__global__ void __launch_bounds__(kThreads) k_fof_link(int64_t n, LinkArgs A, bool alone) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const uint32_t i = order[t];
+  const uint32_t i = uint32_t(t);
   const uint64_t key_i = A.keys[i];
+  const bool single = (i == 0 || A.keys[i - 1] != key_i) && (t + 1 == n || A.keys[i + 1] != key_i);
+  if (single != alone) return;
   const uint32_t mask = (1u << A.xb) - 1u;
   const int kx = int(key_i & mask), ky = int((key_i >> A.xb) & mask), kz = int(key_i >> (2 * A.xb));
   const float4 pi = A.posS[i];
@@ -400,10 +382,8 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
   const bool use_occ = !g.full && occ_full * sizeof(uint32_t) <= kOccMaxBytes;
   const size_t occ_n = use_occ ? occ_full : 1;
   uint32_t* occ = scratch_t<uint32_t>(ctx, S_OCC, occ_n);
-  int64_t* single = scratch_t<int64_t>(ctx, S_FOF_FLAG, size_t(n) + 1);
-  uint32_t* order = scratch_t<uint32_t>(ctx, S_FOF_ORDER, size_t(n));
   if (!ka || !kb || !va || !vb || !posS || !row_start || !cend || !parent || !minid || !counter ||
-      !occ || !single || !order)
+      !occ)
     return RS_ERR_OOM;
   const unsigned grid = grid_for(n, kThreads);
   k_cell_keys<<<grid, kThreads, 0, st>>>(n, pos, g.inv_sc, g.ns, g.xb, ka, va);
@@ -431,16 +411,13 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
   }
   LinkArgs A{keys, posS, row_start, cend, parent, use_occ ? occ : nullptr, occ_words, g.ns, g.xb, g.R, g.full,
              ctx->cfg.box_L, 0.5f * ctx->cfg.box_L, ctx->cfg.link_len * ctx->cfg.link_len};
-  k_fof_single<<<grid, kThreads, 0, st>>>(n, keys, single);
-  RS_LAUNCHED(ctx, "k_fof_single");
-  RS_TRY(exclusive_scan_i64(ctx, n, single, single + n, st));
-  k_fof_partition<<<grid, kThreads, 0, st>>>(n, single, order);
-  RS_LAUNCHED(ctx, "k_fof_partition");
   {
     ProfScope prof_(ctx, "k_fof_link", st);
-    k_fof_link<<<grid, kThreads, 0, st>>>(n, A, order);
+    k_fof_link<<<grid, kThreads, 0, st>>>(n, A, true);
+    RS_LAUNCHED(ctx, "k_fof_link");
+    k_fof_link<<<grid, kThreads, 0, st>>>(n, A, false);
+    RS_LAUNCHED(ctx, "k_fof_link");
   }
-  RS_LAUNCHED(ctx, "k_fof_link");
   RS_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   k_fof_compress<<<grid, kThreads, 0, st>>>(n, parent);
   RS_LAUNCHED(ctx, "k_fof_compress");
