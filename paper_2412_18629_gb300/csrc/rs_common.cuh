@@ -23,7 +23,7 @@ namespace rs {
 enum Slot : int {
   // rs_fof3d
   S_KEY_A, S_KEY_B, S_VAL_A, S_VAL_B, S_SORT_HIST, S_POS_SORTED, S_ROW_START, S_CELL_END,
-  S_PARENT, S_MINID, S_COUNTER, S_OCC,
+  S_PARENT, S_MINID, S_COUNTER,
   // rs_fof6d (level work)
   S_GKEY_A, S_GKEY_B, S_GVAL_A, S_GVAL_B, S_NN2, S_UF, S_ROOT_CNT, S_CHILD_IDX, S_FLAGS,
   S_SCAN_TMP, S_CHUNK_OFF, S_CHUNK_SUM, S_NODE_TMP, S_SELECT,

@@ -15,11 +15,8 @@ constexpr double kU = 5.9604644775390625e-08;
 constexpr double kCertB2 = 48.0 * kU + 1e-12;
 
 // Blocked direct sum over a list: 128 threads x kListR members per block (kListR: a template
-// parameter the autotuner picks among 2, 4, 8). Nodes with at most kListShortMax listed members
-// take tiles of 2 members per thread instead (a second launch): a short list in a tile of 1024
-// would leave most of its threads summing padding.
+// parameter the autotuner picks among 2, 4, 8).
 constexpr int kListThreads = 128;
-constexpr int64_t kListShortMax = 768;
 
 // 0.5 |v - v_bulk|^2 in float64, every operation rounded (the oracle's kinetic energy).
 __device__ __forceinline__ double kinetic(float4 v, const double* vb) {
@@ -138,15 +135,6 @@ __global__ void k_flags_list(const unsigned long long* __restrict__ count, const
   } else {
     ambig[atomicAdd(n_ambig, 1ull)] = p;
   }
-}
-
-
-// Tile counts of one node's list of L members: `tile` members per tile, or, when short_tiles is
-// given and L <= kListShortMax, tiles of 2 x kListThreads in the short table instead.
-__device__ __forceinline__ void list_tiles(int64_t L, int tile, int64_t* main_tiles, int64_t* short_tiles) {
-  const bool s = short_tiles && L <= kListShortMax;
-  *main_tiles = s ? 0 : (L + tile - 1) / tile;
-  if (short_tiles) *short_tiles = s ? (L + 2 * kListThreads - 1) / (2 * kListThreads) : 0;
 }
 
 }  // namespace

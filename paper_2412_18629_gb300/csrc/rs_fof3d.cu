@@ -10,11 +10,8 @@
 //   k_row_start   dense table of the first sorted position of every (z, y) row
 //   k_cell_bounds cell start (union-find parent = the cell's first particle: every sub-cell is a
 //                 clique) and cell end per sorted position
-//   k_occ_set     occupancy bits per (z, y) row, one per 8 sub-cells in x (grids whose bits fit
-//                 in 32 MB, so that they stay in L2)
 //   k_fof_link    per particle (particles alone in their sub-cell, then the others, in two
-//                 launches), the half stencil of rows within R sub-cells, a row skipped when no
-//                 occupancy bit of its x range is set; a neighbour cell is
+//                 launches), the half stencil of rows within R sub-cells; a neighbour cell is
 //                 skipped when its root already equals the particle's root, otherwise scanned
 //                 until the first linked member (one link joins the whole clique)
 //   k_fof_roots   after full path compression: each root stores its id and counts as a group;
@@ -151,42 +148,15 @@ struct LinkArgs {
   const uint32_t* row_start;
   const uint32_t* cell_end;
   uint32_t* parent;
-  const uint32_t* occ;  // occupancy bits: per (z, y) row (z ns + y), one bit per 8 sub-cells in x;
-                        // nullptr when the grid is too large for them to stay in L2
-  int occ_words;        // 32-bit words per row
   int ns, xb, R;
   bool full;
   float L, hL, ll2;
 };
 
-constexpr int kOccShift = 3;  // 8 sub-cells per occupancy bit
-constexpr size_t kOccMaxBytes = size_t(32) << 20;  // occupancy bits only up to this size
-
-// Occupancy bit of every occupied sub-cell (set by its first particle in sorted order).
-__global__ void __launch_bounds__(kThreads)
-k_occ_set(int64_t n, const uint64_t* __restrict__ keys, int xb, int ns, int words,
-          uint32_t* __restrict__ occ) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint64_t k = keys[i];
-  if (i > 0 && keys[i - 1] == k) return;
-  const uint32_t mask = (1u << xb) - 1u;
-  const uint32_t x = uint32_t(k) & mask, y = uint32_t(k >> xb) & mask;
-  const uint64_t z = k >> (2 * xb);
-  const uint32_t gx = x >> kOccShift;
-  atomicOr(occ + (z * uint64_t(ns) + y) * uint64_t(words) + (gx >> 5), 1u << (gx & 31));
-}
-
 // Scan cells with x sub-cell in [x0, x1] of row (zz, yy) against particle i.
 __device__ __forceinline__ void scan_cells(const LinkArgs& A, uint32_t i, uint64_t key_i,
                                            float4 pi, uint32_t& root_i, int zz, int yy, int x0,
                                            int x1) {
-  if (A.occ) {  // no occupied sub-cell in [x0, x1] of this row: nothing to scan
-    const uint32_t* w = A.occ + (uint64_t(zz) * uint64_t(A.ns) + uint64_t(yy)) * uint64_t(A.occ_words);
-    uint32_t any = 0;
-    for (int gg = x0 >> kOccShift; gg <= (x1 >> kOccShift); ++gg) any |= (w[gg >> 5] >> (gg & 31)) & 1u;
-    if (!any) return;
-  }
   const uint64_t row = (uint64_t(zz) << A.xb) | uint64_t(yy);
   const uint32_t a = A.row_start[row], b = A.row_start[row + 1];
   if (a == b) return;
@@ -239,8 +209,10 @@ __device__ __forceinline__ void scan_row(const LinkArgs& A, uint32_t i, uint64_t
 // Two launches: particles alone in their sub-cell (sparse regions: short scans, few links),
 // then particles of shared sub-cells (dense regions: many occupied neighbour cells). Keeping the
 // two kinds in different launches keeps a warp's lanes on similar amounts of work, and each
-// launch reads the particles in sorted order (a partition of the two kinds into one launch
-// was measured slower: its warps gather scattered particles).
+// launch reads the particles in sorted order. Measured on 2^27 particles in L = 512 Mpc/h, two
+// alternatives were slower: occupancy bits per row segment to skip empty stencil rows (their
+// random reads into a 0.5 GB bit array cost more than the row searches they save) and one
+// launch over a partition of the two kinds (its warps gather scattered particles).
 __global__ void __launch_bounds__(kThreads) k_fof_link(int64_t n, LinkArgs A, bool alone) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n) return;
@@ -375,15 +347,7 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
   uint32_t* parent = scratch_t<uint32_t>(ctx, S_PARENT, n);
   unsigned long long* minid = scratch_t<unsigned long long>(ctx, S_MINID, n);
   unsigned long long* counter = scratch_t<unsigned long long>(ctx, S_COUNTER, 8);
-  const int occ_words = ((g.ns + (1 << kOccShift) - 1) >> kOccShift) / 32 + 1;
-  // The bits pay only while they stay in L2: on larger grids each lookup is a DRAM sector of
-  // its own, dearer than the row search it saves (measured: 2^27 particles, L = 512 Mpc/h).
-  const size_t occ_full = size_t(g.ns) * size_t(g.ns) * size_t(occ_words);
-  const bool use_occ = !g.full && occ_full * sizeof(uint32_t) <= kOccMaxBytes;
-  const size_t occ_n = use_occ ? occ_full : 1;
-  uint32_t* occ = scratch_t<uint32_t>(ctx, S_OCC, occ_n);
-  if (!ka || !kb || !va || !vb || !posS || !row_start || !cend || !parent || !minid || !counter ||
-      !occ)
+  if (!ka || !kb || !va || !vb || !posS || !row_start || !cend || !parent || !minid || !counter)
     return RS_ERR_OOM;
   const unsigned grid = grid_for(n, kThreads);
   k_cell_keys<<<grid, kThreads, 0, st>>>(n, pos, g.inv_sc, g.ns, g.xb, ka, va);
@@ -404,12 +368,7 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
     k_cell_bounds<<<grid, kThreads, 0, st>>>(n, keys, row_start, g.xb, cend, parent);
   }
   RS_LAUNCHED(ctx, "k_cell_bounds");
-  if (use_occ) {
-    RS_CUDA(ctx, cudaMemsetAsync(occ, 0, sizeof(uint32_t) * occ_n, st));
-    k_occ_set<<<grid, kThreads, 0, st>>>(n, keys, g.xb, g.ns, occ_words, occ);
-    RS_LAUNCHED(ctx, "k_occ_set");
-  }
-  LinkArgs A{keys, posS, row_start, cend, parent, use_occ ? occ : nullptr, occ_words, g.ns, g.xb, g.R, g.full,
+  LinkArgs A{keys, posS, row_start, cend, parent, g.ns, g.xb, g.R, g.full,
              ctx->cfg.box_L, 0.5f * ctx->cfg.box_L, ctx->cfg.link_len * ctx->cfg.link_len};
   {
     ProfScope prof_(ctx, "k_fof_link", st);

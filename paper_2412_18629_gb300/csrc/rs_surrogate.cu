@@ -369,14 +369,13 @@ __global__ void k_sur_exact_list(int64_t ns, const int64_t* __restrict__ lf, uin
 __global__ void k_sur_list_tiles(int64_t nbig, const int64_t* __restrict__ big_nodes,
                                  const int64_t* __restrict__ sur_off, const int64_t* __restrict__ node_size,
                                  const int64_t* __restrict__ lf, int list_tile, int64_t* __restrict__ lofs,
-                                 int64_t* __restrict__ tiles, int64_t* __restrict__ short_tiles,
-                                 unsigned long long* __restrict__ list_pairs) {
+                                 int64_t* __restrict__ tiles, unsigned long long* __restrict__ list_pairs) {
   const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (b >= nbig) return;
   const int64_t q = big_nodes[b];
   const int64_t a = lf[sur_off[q]], e = lf[sur_off[q] + node_size[q]];
   lofs[b] = a;
-  list_tiles(e - a, list_tile, tiles + b, short_tiles ? short_tiles + b : nullptr);
+  tiles[b] = (e - a + list_tile - 1) / list_tile;
   if (list_pairs && e > a) atomicAdd(list_pairs, (unsigned long long)((e - a) * node_size[q]));
 }
 
@@ -803,8 +802,7 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
   uint32_t* calib_list = scratch_t<uint32_t>(ctx, S_SUR_LIST_C, size_t(nbig) * kCalib + 1);
   int64_t* lf = scratch_t<int64_t>(ctx, S_SUR_LSCAN, size_t(ns) + 1);
   int64_t* lofs = scratch_t<int64_t>(ctx, S_SUR_LOFS, size_t(nbig) * 2 + 2);
-  int64_t* ltiles = scratch_t<int64_t>(ctx, S_SUR_TILES, size_t(nbig) * 2 + 2);
-  int64_t* stiles = ltiles ? ltiles + nbig + 1 : nullptr;  // short lists (2 members per thread)
+  int64_t* ltiles = scratch_t<int64_t>(ctx, S_SUR_TILES, size_t(nbig) + 1);
   if (!errn || !calib_list || !lf || !lofs || !ltiles) return RS_ERR_OOM;
   int64_t* lend = lofs + nbig + 1;
   const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
@@ -883,14 +881,11 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
     }
     for (int c = tune ? 0 : 3; c <= 3; ++c) {
       const int R = c < 3 ? cand[c] : (ctx->tune_list_r ? ctx->tune_list_r : 4);
-      const bool split = c == 3 && R > 2;  // the timed candidates run one table each
       k_sur_list_tiles<<<grid_for(nbig, kT), kT, 0, st>>>(nbig, big_nodes, sur_off, h.node_size, lf,
                                                           kListThreads * R, lofs, ltiles,
-                                                          split ? stiles : nullptr,
                                                           c == 3 ? counters + 18 : nullptr);
       RS_LAUNCHED(ctx, "k_sur_list_tiles");
       RS_TRY(exclusive_scan_i64(ctx, nbig, ltiles, ltiles + nbig, st));
-      if (split) RS_TRY(exclusive_scan_i64(ctx, nbig, stiles, stiles + nbig, st));
       const unsigned grid = grid_for(ns / (kListThreads * R) + nbig + 1, 1);
       if (c < 3) RS_CUDA(ctx, cudaEventRecord(e0, st));
       {
@@ -904,13 +899,8 @@ int surrogate_unbind(rs_ctx* ctx, const double* vbulk, uint8_t* bound, unsigned 
         else
           k_potential_list<4><<<grid, kListThreads, 0, st>>>(nbig, ltiles, big_nodes, lofs, lend, exact_list,
                                                              sur_mem, h.node_off, h.node_size, h.U, eps * eps, Sx);
-        if (split)
-          k_potential_list<2><<<grid_for(ns / (2 * kListThreads) + nbig + 1, 1), kListThreads, 0, st>>>(
-              nbig, stiles, big_nodes, lofs, lend, exact_list, sur_mem, h.node_off, h.node_size, h.U,
-              eps * eps, Sx);
       }
       RS_LAUNCHED(ctx, "k_potential_list");
-      if (split) RS_LAUNCHED(ctx, "k_potential_list");
       if (c < 3) {
         RS_CUDA(ctx, cudaEventRecord(e1, st));
         RS_CUDA(ctx, cudaEventSynchronize(e1));

@@ -543,13 +543,13 @@ __global__ void k_tree_ulist(int64_t T, const int64_t* __restrict__ uf, uint32_t
 __global__ void k_tree_lranges(int64_t nt, const int64_t* __restrict__ ttoff, const int64_t* __restrict__ tg,
                                const int64_t* __restrict__ uf, int tile, int64_t* __restrict__ lofs,
                                int64_t* __restrict__ lend, int64_t* __restrict__ tiles,
-                               int64_t* __restrict__ short_tiles, unsigned long long* __restrict__ list_pairs) {
+                               unsigned long long* __restrict__ list_pairs) {
   const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (b >= nt) return;
   const int64_t a = uf[ttoff[b]], e = uf[ttoff[b] + tg[b]];
   lofs[b] = a;
   lend[b] = e;
-  list_tiles(e - a, tile, tiles + b, short_tiles ? short_tiles + b : nullptr);
+  tiles[b] = (e - a + tile - 1) / tile;
   if (e > a) atomicAdd(list_pairs, (unsigned long long)((e - a) * tg[b]));
 }
 
@@ -670,7 +670,7 @@ int rs::tree_decide(rs_ctx* ctx, const int* only, const uint8_t* want, const dou
   int64_t* wr = scratch_t<int64_t>(ctx, S_T_WR, size_t(nt) * 3 + 3);
   int64_t* uf = scratch_t<int64_t>(ctx, S_T_UF, size_t(T) + 1);
   uint32_t* ulist = scratch_t<uint32_t>(ctx, S_T_LIST, size_t(T));
-  int64_t* lr = scratch_t<int64_t>(ctx, S_T_LR, size_t(nt) * 4 + 4);
+  int64_t* lr = scratch_t<int64_t>(ctx, S_T_LR, size_t(nt) * 3 + 3);
   float* Sx = scratch_t<float>(ctx, S_T_SX, size_t(T));
   uint32_t* ambig = scratch_t<uint32_t>(ctx, S_U_AMBIG, size_t(ctx->n_members) + 1);
   if (!wf || !wl || !wr || !uf || !ulist || !lr || !Sx || !ambig) return RS_ERR_OOM;
@@ -721,13 +721,11 @@ int rs::tree_decide(rs_ctx* ctx, const int* only, const uint8_t* want, const dou
   k_tree_ulist<<<grid_for(T, kT), kT, 0, st>>>(T, uf, ulist, ucount);
   RS_LAUNCHED(ctx, "k_tree_ulist");
   const int R = ctx->tune_list_r ? ctx->tune_list_r : 4;
-  int64_t *lofs = lr, *lend = lr + nt, *ltiles = lr + 2 * nt, *stiles = lr + 3 * nt + 1;
-  const bool split = R > 2;  // short lists take tiles of 2 members per thread
+  int64_t *lofs = lr, *lend = lr + nt, *ltiles = lr + 2 * nt;
   k_tree_lranges<<<grid_for(nt, kT), kT, 0, st>>>(nt, ttoff, tg, uf, kListThreads * R, lofs, lend, ltiles,
-                                                  split ? stiles : nullptr, counters + 18);
+                                                  counters + 18);
   RS_LAUNCHED(ctx, "k_tree_lranges");
   RS_TRY(exclusive_scan_i64(ctx, nt, ltiles, ltiles + nt, st));
-  if (split) RS_TRY(exclusive_scan_i64(ctx, nt, stiles, stiles + nt, st));
   const float eps2 = ctx->cfg.softening * ctx->cfg.softening;
   const unsigned grid = grid_for(T / (kListThreads * R) + nt + 1, 1);
   {
@@ -741,12 +739,8 @@ int rs::tree_decide(rs_ctx* ctx, const int* only, const uint8_t* want, const dou
     else
       k_potential_list<4><<<grid, kListThreads, 0, st>>>(nt, ltiles, tnode, lofs, lend, ulist, tpos, h.node_off,
                                                          h.node_size, h.U, eps2, Sx);
-    if (split)
-      k_potential_list<2><<<grid_for(T / (2 * kListThreads) + nt + 1, 1), kListThreads, 0, st>>>(
-          nt, stiles, tnode, lofs, lend, ulist, tpos, h.node_off, h.node_size, h.U, eps2, Sx);
   }
   RS_LAUNCHED(ctx, "k_potential_list");
-  if (split) RS_LAUNCHED(ctx, "k_potential_list");
   const double Gm = ctx->cfg.G * ctx->cfg.particle_mass;
   k_flags_list<<<grid_for(T, kT), kT, 0, st>>>(ucount, ulist, tpos, h.mnode, h.V, vbulk, eps2, Gm, Sx, bound,
                                               ambig, counters + 16);
