@@ -440,10 +440,19 @@ int rs_profile(rs_ctx* ctx, int enable);
  * query lane, the d6 evaluations it performs and the box lower bounds it computes (bucket,
  * sub-bucket and superbucket tests; box-box tests counted once per warp); the results are
  * unchanged. rs_count_work(ctx, 1, NULL) clears the tallies and enables counting;
- * rs_count_work(ctx, 0, counts) disables it. counts_out (host int64 [4], may be NULL) receives,
+ * rs_count_work(ctx, 0, counts) disables it. counts_out (host int64 [6], may be NULL) receives,
  * after a device synchronisation: NN d6 evaluations, NN box tests, link d6 evaluations, link
- * box tests, accumulated since the last enable. Errors: RS_ERR_OOM, RS_ERR_CUDA. */
+ * box tests, nodes whose nearest-neighbour search ran with sampled bounds, and those of them
+ * whose l2 fell outside the bounds (searched exactly again), accumulated since the last
+ * enable. Errors: RS_ERR_OOM, RS_ERR_CUDA. */
 int rs_count_work(rs_ctx* ctx, int enable, int64_t* counts_out);
+
+/* Scale of the margin of the sampled bounds of the batched form's nearest-neighbour searches
+ * (see rs_fof6d; 1 = the default). Test instrumentation: a negative scale gives every node of
+ * at least 16384 members empty bounds, so each one fails the check after the selection and is
+ * searched again exactly; the results do not depend on the scale. Errors: RS_ERR_INVALID_ARG
+ * (NaN). */
+int rs_nn_bound_margin(rs_ctx* ctx, float scale);
 
 /* Autotuner choices of the context (host outputs; either may be NULL). The members per thread
  * of the register-blocked potential sums (rs_unbind's direct sum; the surrogate path's sums for

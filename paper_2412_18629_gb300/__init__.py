@@ -92,6 +92,7 @@ def load_library():
         lib.rs_run_batched.argtypes = [P, i32, ctypes.POINTER(rs_snapshot), i32, P, P]
         lib.rs_use_graphs.argtypes = [P, ctypes.c_int]
         lib.rs_potential_pairs.argtypes = [P, P]
+        lib.rs_nn_bound_margin.argtypes = [P, ctypes.c_float]
         lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
         lib.rs_sort_pairs.argtypes = [P, i64, ctypes.c_int, P, P, P]
         lib.rs_mlp_set_params.argtypes = [P, P]
@@ -123,7 +124,7 @@ def load_library():
                      "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work", "rs_tuning",
                      "rs_tree_stats", "rs_tree_record", "rs_tree_bounds",
                      "rs_assign_seeds", "rs_track", "rs_unbind_passes", "rs_run_batched",
-                     "rs_use_graphs", "rs_potential_pairs"):
+                     "rs_use_graphs", "rs_potential_pairs", "rs_nn_bound_margin"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -205,6 +206,10 @@ class Context:
         """Keys moved by radix-sort passes since the context was created."""
         return int(self.lib.rs_sort_keypasses(self.handle))
 
+    def nn_bound_margin(self, scale=1.0):
+        """Scale of the sampled nearest-neighbour bounds' margin (test instrumentation)."""
+        self.check(self.lib.rs_nn_bound_margin(self.handle, float(scale)))
+
     def use_graphs(self, enable=True):
         """CUDA graphs for static launch sequences (the surrogate's training epoch) on or off."""
         self.check(self.lib.rs_use_graphs(self.handle, 1 if enable else 0))
@@ -215,13 +220,15 @@ class Context:
 
     def count_work(self, enable=True):
         """Enable (clearing) or disable the counting variants of the pruned 6D kernels; on
-        disable returns {nn_d6, nn_box, link_d6, link_box} accumulated since the enable."""
+        disable returns {nn_d6, nn_box, link_d6, link_box, bounded_nodes, bound_failures}
+        accumulated since the enable."""
         import numpy as np
-        out = np.zeros(4, np.int64)
+        out = np.zeros(6, np.int64)
         self.check(self.lib.rs_count_work(self.handle, 1 if enable else 0,
                                           None if enable else out.ctypes.data))
         if not enable:
-            return dict(zip(("nn_d6", "nn_box", "link_d6", "link_box"), map(int, out)))
+            return dict(zip(("nn_d6", "nn_box", "link_d6", "link_box", "bounded_nodes",
+                             "bound_failures"), map(int, out)))
         return None
 
     def tuning(self):

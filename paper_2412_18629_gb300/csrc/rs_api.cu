@@ -85,15 +85,15 @@ extern "C" int rs_count_work(rs_ctx* ctx, int enable, int64_t* counts_out) {
   if (!ctx) return RS_ERR_INVALID_ARG;
   ctx->err[0] = 0;
   RS_CUDA(ctx, cudaSetDevice(ctx->device));
-  unsigned long long* w = scratch_t<unsigned long long>(ctx, rs::S_P_WORK, 4);
+  unsigned long long* w = scratch_t<unsigned long long>(ctx, rs::S_P_WORK, 6);
   if (!w) return RS_ERR_OOM;
   if (counts_out) {
     RS_CUDA(ctx, cudaDeviceSynchronize());
-    unsigned long long h[4];
+    unsigned long long h[6];
     RS_CUDA(ctx, cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < 4; ++i) counts_out[i] = int64_t(h[i]);
+    for (int i = 0; i < 6; ++i) counts_out[i] = int64_t(h[i]);
   }
-  if (enable) RS_CUDA(ctx, cudaMemset(w, 0, 4 * sizeof(unsigned long long)));
+  if (enable) RS_CUDA(ctx, cudaMemset(w, 0, 6 * sizeof(unsigned long long)));
   ctx->count_work = enable != 0;
   return RS_OK;
 }
@@ -133,6 +133,12 @@ extern "C" const char* rs_last_error(rs_ctx* ctx) { return ctx ? ctx->err : "nul
 extern "C" int64_t rs_kernel_launches(rs_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 extern "C" int64_t rs_sort_keypasses(rs_ctx* ctx) { return ctx ? ctx->sort_keypasses : 0; }
+
+extern "C" int rs_nn_bound_margin(rs_ctx* ctx, float scale) {
+  if (!ctx || !(scale == scale)) return RS_ERR_INVALID_ARG;
+  ctx->nn_bound_margin = scale;
+  return RS_OK;
+}
 
 extern "C" int rs_use_graphs(rs_ctx* ctx, int enable) {
   if (!ctx) return RS_ERR_INVALID_ARG;

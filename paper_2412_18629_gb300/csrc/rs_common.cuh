@@ -37,7 +37,8 @@ enum Slot : int {
   // batched form: pruned 6D searches
   S_P_MEANU, S_P_MEANV, S_P_US, S_P_VS, S_P_SP, S_P_BOFF, S_P_BUCKET, S_P_BOX, S_P_SUB,
   S_P_SBOFF, S_P_SBOX, S_P_ORDER, S_P_QCTR, S_P_WORK, S_P_NSTART, S_P_NCNT, S_P_APOS,
-  S_P_USA, S_P_VSA, S_P_SPA, S_P_QKEY_A, S_P_QKEY_B, S_P_QVAL_A, S_P_QVAL_B,
+  S_P_USA, S_P_VSA, S_P_SPA, S_P_QKEY_A, S_P_QKEY_B, S_P_QVAL_A, S_P_QVAL_B, S_P_QFS, S_P_QFR,
+  S_P_QS, S_P_QR, S_P_QCOUNT, S_P_BOUNDS, S_P_FAILED,
   // surrogate MLP
   S_MLP_DEV, S_MLP_W, S_MLP_PART, S_MLP_SSE, S_MLP_M, S_MLP_G, S_MLP_IDX, S_MLP_BIDX, S_MLP_XH,
   S_MLP_YH, S_MLP_CORR, S_MLP_STEP,
@@ -111,6 +112,7 @@ struct rs_ctx {
   int64_t tree_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int32_t unbind_passes_run = 0;  // passes the last rs_unbind ran (iterative unbinding)
   int64_t pot_pairs[2] = {0, 0};  // ordered pairs the direct sums evaluated (last rs_unbind)
+  float nn_bound_margin = 1.f;    // scale of the sampled nearest-neighbour bounds' margin
   // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
   bool profile = false;
   bool count_work = false;  // counting variants of the pruned 6D kernels (rs_count_work)

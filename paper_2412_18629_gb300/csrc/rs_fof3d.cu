@@ -370,11 +370,11 @@ extern "C" int rs_fof3d(rs_ctx* ctx, int64_t n, const float* pos, const int64_t*
   RS_LAUNCHED(ctx, "k_cell_bounds");
   LinkArgs A{keys, posS, row_start, cend, parent, g.ns, g.xb, g.R, g.full,
              ctx->cfg.box_L, 0.5f * ctx->cfg.box_L, ctx->cfg.link_len * ctx->cfg.link_len};
-  {
-    ProfScope prof_(ctx, "k_fof_link", st);
-    k_fof_link<<<grid, kThreads, 0, st>>>(n, A, true);
-    RS_LAUNCHED(ctx, "k_fof_link");
-    k_fof_link<<<grid, kThreads, 0, st>>>(n, A, false);
+  for (const bool alone : {true, false}) {
+    {
+      ProfScope prof_(ctx, "k_fof_link", st);
+      k_fof_link<<<grid, kThreads, 0, st>>>(n, A, alone);
+    }
     RS_LAUNCHED(ctx, "k_fof_link");
   }
   RS_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));

@@ -408,14 +408,16 @@ k_select_l2_warp(int64_t nb, int64_t nn, const int64_t* __restrict__ node_off,
   if (lane == 0) inv[q].z = __uint_as_float(prefix);
 }
 
+// only (if given): int [nn], the nodes to select for (the others keep their l2).
 __global__ void __launch_bounds__(kT)
 k_select_l2(int64_t nb, const int64_t* __restrict__ node_off, const int64_t* __restrict__ node_size,
-            const float* __restrict__ nn2, int64_t mb, int f_num, int f_den, float4* __restrict__ inv) {
+            const float* __restrict__ nn2, int64_t mb, int f_num, int f_den, float4* __restrict__ inv,
+            const int* __restrict__ only) {
   __shared__ uint32_t hist[256];
   __shared__ uint32_t s_prefix, s_k;
   const int64_t q = nb + blockIdx.x;
   const int64_t base = node_off[q] - mb, g = node_size[q];
-  if (g <= kSelectWarpMax) return;
+  if (g <= kSelectWarpMax || (only && !only[blockIdx.x])) return;
   if (threadIdx.x == 0) {
     s_prefix = 0;
     s_k = uint32_t((int64_t(f_num) * g + f_den - 1) / f_den - 1);
@@ -635,6 +637,8 @@ int prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m,
                     const double* sums, cudaStream_t st);
 int prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, float* nn2,
                cudaStream_t st);
+int prune6d_check(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t m, float* nn2, const int** failed_out,
+                  cudaStream_t st);
 int prune6d_link(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, const float* nn2,
                  uint32_t* uf, cudaStream_t st);
 
@@ -873,9 +877,19 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
       ProfScope prof_(ctx, "k_select_l2", st);
       k_select_l2_warp<<<grid_for(nn, kT / 32), kT, 0, st>>>(nb, nn, h.node_off, h.node_size, nn2, mb, f_num,
                                                             f_den, h.inv);
-      k_select_l2<<<unsigned(nn), kT, 0, st>>>(nb, h.node_off, h.node_size, nn2, mb, f_num, f_den, h.inv);
+      k_select_l2<<<unsigned(nn), kT, 0, st>>>(nb, h.node_off, h.node_size, nn2, mb, f_num, f_den, h.inv,
+                                               nullptr);
     }
     RS_LAUNCHED(ctx, "k_select_l2");
+    if (batched) {  // bounded searches: nodes whose l2 fell outside their bounds, exactly again
+      const int* failed = nullptr;
+      RS_TRY(prune6d_check(ctx, nb, nn, m, nn2, &failed, st));
+      h = hier_of(ctx);
+      ProfScope prof_(ctx, "k_select_l2", st);
+      k_select_l2<<<unsigned(nn), kT, 0, st>>>(nb, h.node_off, h.node_size, nn2, mb, f_num, f_den, h.inv,
+                                               failed);
+      RS_LAUNCHED(ctx, "k_select_l2");
+    }
     k_iota_u32<<<grid_for(m, kT), kT, 0, st>>>(m, uf);
     RS_LAUNCHED(ctx, "k_iota_u32");
     if (batched) {

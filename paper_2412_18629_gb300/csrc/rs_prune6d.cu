@@ -22,6 +22,8 @@ int prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m,
                     const double* sums, cudaStream_t st);
 int prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, float* nn2,
                cudaStream_t st);
+int prune6d_check(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t m, float* nn2, const int** failed_out,
+                  cudaStream_t st);
 int prune6d_link(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, const float* nn2,
                  uint32_t* uf, cudaStream_t st);
 }  // namespace rs
@@ -404,7 +406,17 @@ struct NNArgs {
   const float4* inv;
   unsigned long long* counter;
   unsigned long long* work;  // [4]: NN d6, NN box tests, link d6, link box tests (counting variant)
+  const float2* bounds;      // NN only: per node of the level (node - nb): (lo, hi), or nullptr
+  int64_t nb;
 };
+
+// Search limit of a nearest-neighbour lane with current minimum `best` and node bounds
+// [lo, hi]: boxes whose lower bound exceeds it are skipped. A lane below lo is done (-1: no
+// bound is negative); otherwise min(best, hi): a minimum above hi only needs to be known above
+// hi. With (lo, hi) = (-inf, +inf) this is best itself: the exact search.
+__device__ __forceinline__ float nn_limit(float best, float lo, float hi) {
+  return best < lo ? -1.f : fminf(best, hi);
+}
 
 // Per-lane tallies of the counting variant (evaluated d6 and box tests).
 struct Tally {
@@ -414,9 +426,9 @@ struct Tally {
 // Evaluate target bucket b for the warp's query lanes (nearest-neighbour search).
 template <bool kCount>
 __device__ __forceinline__ void nn_bucket(const NNArgs& A, int64_t a, int64_t b, bool valid, const Query& Q,
-                                          float& best, int lane, Stage& S, Tally& T) {
+                                          float& best, float lo, float hi, int lane, Stage& S, Tally& T) {
   const Box B = A.box[b];
-  const bool need = valid && lb_point_box(Q, B) <= best;
+  const bool need = valid && lb_point_box(Q, B) <= nn_limit(best, lo, hi);
   if (kCount) T.box += valid;
   if (!__any_sync(0xffffffffu, need)) return;
   const Bucket Bb = A.bk[b];
@@ -425,7 +437,7 @@ __device__ __forceinline__ void nn_bucket(const NNArgs& A, int64_t a, int64_t b,
   __syncwarp();
   for (uint32_t s0 = 0; s0 < Bb.count; s0 += 8) {
     const Box Sb = A.sub[4 * b + (s0 >> 3)];
-    const bool sneed = need && lb_point_box(Q, Sb) <= best;
+    const bool sneed = need && lb_point_box(Q, Sb) <= nn_limit(best, lo, hi);
     if (kCount) T.box += need;
     if (!__any_sync(0xffffffffu, sneed)) continue;
     if (sneed) {
@@ -481,12 +493,19 @@ __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict_
     const uint32_t si = Aq.start + (valid ? lane : 0);
     const Query Q = make_query(A.Us[si], A.Vs[si], iv.x, iv.y);
     float best = __int_as_float(0x7f800000);
+    float lo = -best, hi = best;
+    if (A.bounds) {
+      const float2 bd = A.bounds[int64_t(Aq.node) - A.nb];
+      lo = bd.x;
+      hi = bd.y;
+    }
     const int64_t own = (a - int64_t(Aq.first)) >> 5, nsb = Aq.sbcount;
     for (int64_t t = 0; t <= 2 * nsb; ++t) {
+      if (__all_sync(0xffffffffu, !valid || best < lo)) break;  // every lane known below lo
       const int64_t s = outward(own, t);
       if (s < 0 || s >= nsb) continue;
       const Box SB = A.sbox[Aq.sbfirst + s];
-      const bool need = valid && lb_point_box(Q, SB) <= best;
+      const bool need = valid && lb_point_box(Q, SB) <= nn_limit(best, lo, hi);
       if (kCount) T.box += valid;
       if (!__any_sync(0xffffffffu, need)) continue;
       const int64_t b_lo = int64_t(Aq.first) + 32 * s;
@@ -495,12 +514,14 @@ __global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict_
         for (int64_t t2 = 0; t2 <= 2 * 32; ++t2) {
           const int64_t b = outward(a, t2);
           if (b < b_lo || b >= b_hi) continue;
-          nn_bucket<kCount>(A, a, b, valid, Q, best, lane, stg[wb], T);
+          nn_bucket<kCount>(A, a, b, valid, Q, best, lo, hi, lane, stg[wb], T);
         }
       } else if (s > own) {
-        for (int64_t b = b_lo; b < b_hi; ++b) nn_bucket<kCount>(A, a, b, valid, Q, best, lane, stg[wb], T);
+        for (int64_t b = b_lo; b < b_hi; ++b)
+          nn_bucket<kCount>(A, a, b, valid, Q, best, lo, hi, lane, stg[wb], T);
       } else {
-        for (int64_t b = b_hi - 1; b >= b_lo; --b) nn_bucket<kCount>(A, a, b, valid, Q, best, lane, stg[wb], T);
+        for (int64_t b = b_hi - 1; b >= b_lo; --b)
+          nn_bucket<kCount>(A, a, b, valid, Q, best, lo, hi, lane, stg[wb], T);
       }
     }
     if (valid) nn2[A.sp[si]] = best;
@@ -634,6 +655,8 @@ NNArgs nn_args(rs_ctx* ctx, int64_t nn) {
   A.inv = h.inv;
   A.counter = static_cast<unsigned long long*>(ctx->buf[S_P_QCTR].ptr);
   A.work = static_cast<unsigned long long*>(ctx->buf[S_P_WORK].ptr);
+  A.bounds = nullptr;
+  A.nb = 0;
   return A;
 }
 
@@ -677,6 +700,172 @@ int build_buckets(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t m, const int64_t*
   return RS_OK;
 }
 
+// ---- Bounded nearest-neighbour searches for large nodes ---------------------------------------
+// The split needs each member's nn2 exactly only near the k-th smallest value (the adaptive l2)
+// and, elsewhere, only whether it lies below or above it (k_select_l2 and the link pass's
+// member filter). For nodes of at least kBoundMin members a sample of buckets (every S-th of
+// the node, about kSampleBuckets of them) is searched exactly first; the sample's order
+// statistics around rank p s (p = (k + 1/2) / g) give bounds lo <= hi; the other members are
+// searched with the limit of nn_limit: a lane stops once its minimum is below lo (its nn2 is
+// then some value below lo) and prunes with hi (a minimum above hi is kept as some value above
+// hi). Members whose nn2 lies in [lo, hi] are found exactly, so the k-th smallest of the stored
+// values equals the exact one whenever it lies in [lo, hi]; k_bounds_check verifies that per
+// node after the selection and sends every node that fails through the exact search again.
+constexpr int64_t kBoundMin = 16384;
+constexpr int64_t kSampleBuckets = 48;
+
+__device__ __forceinline__ int64_t sample_stride(int64_t nbk) {
+  return nbk / kSampleBuckets > 1 ? nbk / kSampleBuckets : 1;
+}
+
+// Queue entry w (bucket order[w]) goes to the sample queue (flag s) or the others (flag r);
+// buckets of nodes below kBoundMin go to the others and are searched exactly.
+__global__ void k_queue_flags(int64_t nbk_ub, const int64_t* __restrict__ nbk, const uint32_t* __restrict__ order,
+                              const Bucket* __restrict__ bk, const int64_t* __restrict__ node_size,
+                              int64_t* __restrict__ fs, int64_t* __restrict__ fr) {
+  const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w >= nbk_ub) return;
+  int64_t smp = 0, rest = 0;
+  if (w < *nbk) {
+    const Bucket B = bk[order[w]];
+    const int64_t nb_node = int64_t(B.last) - int64_t(B.first) + 1;
+    const bool bounded = node_size[B.node] >= kBoundMin;
+    smp = bounded && ((int64_t(order[w]) - int64_t(B.first)) % sample_stride(nb_node)) == 0;
+    rest = !smp;
+  }
+  fs[w] = smp;
+  fr[w] = rest;
+}
+
+// Stable scatter of the two queues (order preserved: largest nodes first in both); counts at
+// qcount[0] (sample) and qcount[1] (others).
+__global__ void k_queue_scatter(int64_t nbk_ub, const uint32_t* __restrict__ order, const int64_t* __restrict__ fs,
+                                const int64_t* __restrict__ fr, uint32_t* __restrict__ qs,
+                                uint32_t* __restrict__ qr, int64_t* __restrict__ qcount) {
+  const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w == 0) {
+    qcount[0] = fs[nbk_ub];
+    qcount[1] = fr[nbk_ub];
+  }
+  if (w >= nbk_ub) return;
+  if (fs[w + 1] != fs[w]) qs[fs[w]] = order[w];
+  if (fr[w + 1] != fr[w]) qr[fr[w]] = order[w];
+}
+
+// Radix select (4 passes of 8 bits over non-negative float bit patterns) of rank k among the
+// sample values of one node, read through `val(t)` for t < n (invalid entries return false).
+template <class Val>
+__device__ float block_select(Val val, int64_t n, uint32_t k, uint32_t* hist, uint32_t* s_prefix,
+                              uint32_t* s_k) {
+  if (threadIdx.x == 0) {
+    *s_prefix = 0;
+    *s_k = k;
+  }
+  uint32_t mask = 0;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d] = 0;
+    __syncthreads();
+    const uint32_t prefix = *s_prefix;
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+      float v;
+      if (!val(t, v)) continue;
+      const uint32_t bits = __float_as_uint(v);
+      if ((bits & mask) == prefix) atomicAdd(&hist[(bits >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t kk = *s_k, cum = 0;
+      int d = 0;
+      for (; d < 255; ++d) {
+        if (cum + hist[d] > kk) break;
+        cum += hist[d];
+      }
+      *s_k = kk - cum;
+      *s_prefix = prefix | (uint32_t(d) << shift);
+    }
+    mask |= 255u << shift;
+    __syncthreads();
+  }
+  return __uint_as_float(*s_prefix);
+}
+
+// One block per node of the level: bounds (lo, hi) from the sample of a node of at least
+// kBoundMin members, (-inf, +inf) (exact search) otherwise. The sample of a node is every
+// S-th of its buckets; its size s and the target rank r = p s with p = (k + 1/2) / g; the
+// bounds are the sample's order statistics at r -+ d, d = 6 sqrt(s p (1 - p)) + 8 (twice
+// three binomial standard deviations: the sampled buckets are clusters of neighbours).
+__global__ void __launch_bounds__(256)
+k_sample_bounds(int64_t nb, int64_t nn, const int64_t* __restrict__ node_size, const int64_t* __restrict__ boff,
+                const Bucket* __restrict__ bk, const uint32_t* __restrict__ sp, const float* __restrict__ nn2,
+                int f_num, int f_den, float margin, float2* __restrict__ bounds) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t s_prefix, s_k;
+  const int64_t k = blockIdx.x;
+  if (k >= nn) return;
+  const int64_t g = node_size[nb + k];
+  const float inf = __int_as_float(0x7f800000);
+  if (g < kBoundMin) {
+    if (threadIdx.x == 0) bounds[k] = make_float2(-inf, inf);
+    return;
+  }
+  const int64_t b0 = boff[k], nbk = boff[k + 1] - b0;
+  const int64_t S = sample_stride(nbk), ns = (nbk + S - 1) / S;
+  // sample members: 32 per sampled bucket except possibly the node's last bucket
+  const Bucket last = bk[b0 + nbk - 1];
+  const bool last_sampled = ((nbk - 1) % S) == 0;
+  const int64_t s = ns * 32 - (last_sampled ? 32 - int64_t(last.count) : 0);
+  const int64_t kk = (int64_t(f_num) * g + f_den - 1) / f_den - 1;
+  const double p = (double(kk) + 0.5) / double(g);
+  const double r = p * double(s);
+  const double d = double(margin) * (6.0 * sqrt(double(s) * p * (1.0 - p)) + 8.0);
+  const int64_t r_lo = int64_t(floor(r - d)), r_hi = int64_t(ceil(r + d));
+  if (r_lo > r_hi) {  // empty bounds (margin < 0: the exact fallback under test)
+    if (threadIdx.x == 0) bounds[k] = make_float2(inf, -inf);
+    return;
+  }
+  auto val = [&](int64_t t, float& v) -> bool {
+    const Bucket B = bk[b0 + (t >> 5) * S];
+    const uint32_t l = uint32_t(t & 31);
+    if (l >= B.count) return false;
+    v = nn2[sp[B.start + l]];
+    return true;
+  };
+  const float lo = r_lo <= 0 ? -inf : block_select(val, ns * 32, uint32_t(r_lo), hist, &s_prefix, &s_k);
+  __syncthreads();
+  const float hi = r_hi >= s - 1 ? inf : block_select(val, ns * 32, uint32_t(r_hi), hist, &s_prefix, &s_k);
+  if (threadIdx.x == 0) bounds[k] = make_float2(lo, hi);
+}
+
+// After the selection: a bounded node whose l2 lies outside its [lo, hi] failed (its stored
+// values are not exact there): mark it, reset its bounds to the exact search and queue all its
+// buckets again (qcount[2]; order of the queue does not matter for exact results).
+// tally (counting variant, may be null): [0] nodes searched with bounds, [1] nodes that failed.
+__global__ void k_bounds_check(int64_t nb, int64_t nn, const float4* __restrict__ inv, float2* __restrict__ bounds,
+                               int* __restrict__ failed, unsigned long long* __restrict__ tally) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= nn) return;
+  const float inf = __int_as_float(0x7f800000);
+  const float2 bd = bounds[k];
+  const float l2 = inv[nb + k].z;
+  const bool bad = !(bd.x <= l2 && l2 <= bd.y);
+  failed[k] = bad ? 1 : 0;
+  if (bad) bounds[k] = make_float2(-inf, inf);
+  if (tally && (bd.x > -inf || bd.y < inf)) {
+    atomicAdd(tally, 1ull);
+    if (bad) atomicAdd(tally + 1, 1ull);
+  }
+}
+
+__global__ void k_fail_queue(int64_t nbk_ub, const int64_t* __restrict__ nbk, const uint32_t* __restrict__ order,
+                             const Bucket* __restrict__ bk, int64_t nb, const int* __restrict__ failed,
+                             uint32_t* __restrict__ qf, unsigned long long* __restrict__ qcount) {
+  const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w >= nbk_ub || w >= *nbk) return;
+  const uint32_t a = order[w];
+  if (failed[int64_t(bk[a].node) - nb]) qf[atomicAdd(qcount, 1ull)] = a;
+}
+
 unsigned persistent_grid(int64_t nbk_ub) {
   return unsigned(std::min<int64_t>((nbk_ub + kWarpsPerBlock - 1) / kWarpsPerBlock, 152 * 8));
 }
@@ -697,7 +886,7 @@ int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t
   int64_t* nstart = scratch_t<int64_t>(ctx, S_P_NSTART, size_t(nn));
   int64_t* ncnt = scratch_t<int64_t>(ctx, S_P_NCNT, size_t(nn));
   unsigned long long* qctr = scratch_t<unsigned long long>(ctx, S_P_QCTR, 2);
-  if (!scratch_t<unsigned long long>(ctx, S_P_WORK, 4)) return RS_ERR_OOM;
+  if (!scratch_t<unsigned long long>(ctx, S_P_WORK, 6)) return RS_ERR_OOM;
   if (!mean_u || !ka || !kb || !va || !vb || !Us || !Vs || !sp || !nstart || !ncnt || !qctr) return RS_ERR_OOM;
   k_node_means<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.node_size, sums, mean_u);
   RS_LAUNCHED(ctx, "k_node_means");
@@ -713,12 +902,12 @@ int rs::prune6d_prepare(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t
   return build_buckets(ctx, nb, nn, m, nstart, ncnt, Us, Vs, st);
 }
 
-int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, float* nn2,
-                   cudaStream_t st) {
-  (void)nb;
-  (void)mb;
-  NNArgs A = nn_args(ctx, nn);
-  const unsigned grid = persistent_grid(nn + m / 32 + 1);
+// One persistent launch of the nearest-neighbour kernel over the queue (order, count).
+static int run_nn(rs_ctx* ctx, NNArgs A, const uint32_t* order, const int64_t* count, int64_t nbk_ub,
+                  float* nn2, cudaStream_t st) {
+  A.order = order;
+  A.nbuckets = count;
+  const unsigned grid = persistent_grid(nbk_ub);
   RS_CUDA(ctx, cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st));
   if (ctx->count_work) {
     k_nn6d_pruned<true><<<grid, kT, 0, st>>>(A, nn2);
@@ -727,6 +916,65 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
     k_nn6d_pruned<false><<<grid, kT, 0, st>>>(A, nn2);
   }
   RS_LAUNCHED(ctx, "k_nn6d_pruned");
+  return RS_OK;
+}
+
+// Nearest neighbours of the level: the sample of every large node exactly, its bounds, then the
+// other buckets with those bounds (nodes below kBoundMin: exactly). No host round trip: the
+// queues and their counts stay on the device.
+int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, float* nn2,
+                   cudaStream_t st) {
+  (void)mb;
+  Hier h = hier_of(ctx);
+  NNArgs A = nn_args(ctx, nn);
+  const int64_t nbk_ub = nn + m / 32 + 1;
+  int64_t* fs = scratch_t<int64_t>(ctx, S_P_QFS, size_t(nbk_ub) + 1);
+  int64_t* fr = scratch_t<int64_t>(ctx, S_P_QFR, size_t(nbk_ub) + 1);
+  uint32_t* qs = scratch_t<uint32_t>(ctx, S_P_QS, size_t(nbk_ub));
+  uint32_t* qr = scratch_t<uint32_t>(ctx, S_P_QR, size_t(nbk_ub));
+  int64_t* qcount = scratch_t<int64_t>(ctx, S_P_QCOUNT, 4);
+  float2* bounds = scratch_t<float2>(ctx, S_P_BOUNDS, size_t(std::max<int64_t>(nn, 1)));
+  if (!fs || !fr || !qs || !qr || !qcount || !bounds) return RS_ERR_OOM;
+  k_queue_flags<<<grid_for(nbk_ub, kT), kT, 0, st>>>(nbk_ub, A.nbuckets, A.order, A.bk, h.node_size, fs, fr);
+  RS_LAUNCHED(ctx, "k_queue_flags");
+  RS_TRY(exclusive_scan_i64(ctx, nbk_ub, fs, fs + nbk_ub, st));
+  RS_TRY(exclusive_scan_i64(ctx, nbk_ub, fr, fr + nbk_ub, st));
+  k_queue_scatter<<<grid_for(nbk_ub, kT), kT, 0, st>>>(nbk_ub, A.order, fs, fr, qs, qr, qcount);
+  RS_LAUNCHED(ctx, "k_queue_scatter");
+  RS_TRY(run_nn(ctx, A, qs, qcount + 0, nbk_ub, nn2, st));  // the samples, exactly
+  const int64_t* boff = static_cast<const int64_t*>(ctx->buf[S_P_BOFF].ptr);
+  k_sample_bounds<<<unsigned(std::max<int64_t>(nn, 1)), 256, 0, st>>>(nb, nn, h.node_size, boff, A.bk, A.sp, nn2,
+                                                                   ctx->cfg.f_num, ctx->cfg.f_den,
+                                                                   ctx->nn_bound_margin, bounds);
+  RS_LAUNCHED(ctx, "k_sample_bounds");
+  A.bounds = bounds;
+  A.nb = nb;
+  return run_nn(ctx, A, qr, qcount + 1, nbk_ub, nn2, st);
+}
+
+// After the selection of l2: nodes whose l2 fell outside their bounds are searched again
+// exactly (*failed_out: int [nn], 1 for those nodes, for the selection to be repeated there).
+int rs::prune6d_check(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t m, float* nn2, const int** failed_out,
+                      cudaStream_t st) {
+  Hier h = hier_of(ctx);
+  NNArgs A = nn_args(ctx, nn);
+  const int64_t nbk_ub = nn + m / 32 + 1;
+  float2* bounds = static_cast<float2*>(ctx->buf[S_P_BOUNDS].ptr);
+  int* failed = scratch_t<int>(ctx, S_P_FAILED, size_t(std::max<int64_t>(nn, 1)));
+  uint32_t* qf = scratch_t<uint32_t>(ctx, S_P_QS, size_t(nbk_ub));  // the sample queue is done
+  unsigned long long* fcount = reinterpret_cast<unsigned long long*>(
+      static_cast<int64_t*>(ctx->buf[S_P_QCOUNT].ptr) + 2);
+  if (!failed || !qf) return RS_ERR_OOM;
+  k_bounds_check<<<grid_for(nn, kT), kT, 0, st>>>(nb, nn, h.inv, bounds, failed,
+                                                  ctx->count_work ? A.work + 4 : nullptr);
+  RS_LAUNCHED(ctx, "k_bounds_check");
+  RS_CUDA(ctx, cudaMemsetAsync(fcount, 0, sizeof(unsigned long long), st));
+  k_fail_queue<<<grid_for(nbk_ub, kT), kT, 0, st>>>(nbk_ub, A.nbuckets, A.order, A.bk, nb, failed, qf, fcount);
+  RS_LAUNCHED(ctx, "k_fail_queue");
+  A.bounds = bounds;
+  A.nb = nb;
+  RS_TRY(run_nn(ctx, A, qf, reinterpret_cast<const int64_t*>(fcount), nbk_ub, nn2, st));
+  *failed_out = failed;
   return RS_OK;
 }
 
