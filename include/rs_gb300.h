@@ -447,12 +447,12 @@ int rs_profile(rs_ctx* ctx, int enable);
  * enable. Errors: RS_ERR_OOM, RS_ERR_CUDA. */
 int rs_count_work(rs_ctx* ctx, int enable, int64_t* counts_out);
 
-/* Scale of the margin of the sampled bounds of the batched form's nearest-neighbour searches
- * (see rs_fof6d; 1 = the default). Test instrumentation: a negative scale gives every node of
- * at least 16384 members empty bounds, so each one fails the check after the selection and is
- * searched again exactly; the results do not depend on the scale. Errors: RS_ERR_INVALID_ARG
- * (NaN). */
-int rs_nn_bound_margin(rs_ctx* ctx, float scale);
+/* The batched form's sampled nearest-neighbour bounds (see rs_fof6d): the scale of their
+ * margin (1 = the default) and the smallest node searched with them (0 = the default, 4096
+ * members). Tuning and test instrumentation; the results do not depend on either: a negative
+ * scale gives every such node empty bounds, so each one fails the check after the selection and
+ * is searched again exactly. Errors: RS_ERR_INVALID_ARG (NaN scale, negative size). */
+int rs_nn_bounds(rs_ctx* ctx, float margin_scale, int64_t min_members);
 
 /* Autotuner choices of the context (host outputs; either may be NULL). The members per thread
  * of the register-blocked potential sums (rs_unbind's direct sum; the surrogate path's sums for

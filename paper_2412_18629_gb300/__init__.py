@@ -92,7 +92,7 @@ def load_library():
         lib.rs_run_batched.argtypes = [P, i32, ctypes.POINTER(rs_snapshot), i32, P, P]
         lib.rs_use_graphs.argtypes = [P, ctypes.c_int]
         lib.rs_potential_pairs.argtypes = [P, P]
-        lib.rs_nn_bound_margin.argtypes = [P, ctypes.c_float]
+        lib.rs_nn_bounds.argtypes = [P, ctypes.c_float, i64]
         lib.rs_cro_sum.argtypes = [P, i64, P, P, P]
         lib.rs_sort_pairs.argtypes = [P, i64, ctypes.c_int, P, P, P]
         lib.rs_mlp_set_params.argtypes = [P, P]
@@ -124,7 +124,7 @@ def load_library():
                      "rs_profile_get", "rs_sort_pairs", "rs_cro_sum_noalloc", "rs_count_work", "rs_tuning",
                      "rs_tree_stats", "rs_tree_record", "rs_tree_bounds",
                      "rs_assign_seeds", "rs_track", "rs_unbind_passes", "rs_run_batched",
-                     "rs_use_graphs", "rs_potential_pairs", "rs_nn_bound_margin"):
+                     "rs_use_graphs", "rs_potential_pairs", "rs_nn_bounds"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -206,9 +206,10 @@ class Context:
         """Keys moved by radix-sort passes since the context was created."""
         return int(self.lib.rs_sort_keypasses(self.handle))
 
-    def nn_bound_margin(self, scale=1.0):
-        """Scale of the sampled nearest-neighbour bounds' margin (test instrumentation)."""
-        self.check(self.lib.rs_nn_bound_margin(self.handle, float(scale)))
+    def nn_bounds(self, margin_scale=1.0, min_members=0):
+        """Margin scale and smallest node of the sampled nearest-neighbour bounds (tuning and
+        test instrumentation; 0 members = the default)."""
+        self.check(self.lib.rs_nn_bounds(self.handle, float(margin_scale), int(min_members)))
 
     def use_graphs(self, enable=True):
         """CUDA graphs for static launch sequences (the surrogate's training epoch) on or off."""

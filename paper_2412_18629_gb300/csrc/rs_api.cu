@@ -134,9 +134,10 @@ extern "C" int64_t rs_kernel_launches(rs_ctx* ctx) { return ctx ? ctx->launches 
 
 extern "C" int64_t rs_sort_keypasses(rs_ctx* ctx) { return ctx ? ctx->sort_keypasses : 0; }
 
-extern "C" int rs_nn_bound_margin(rs_ctx* ctx, float scale) {
-  if (!ctx || !(scale == scale)) return RS_ERR_INVALID_ARG;
-  ctx->nn_bound_margin = scale;
+extern "C" int rs_nn_bounds(rs_ctx* ctx, float margin_scale, int64_t min_members) {
+  if (!ctx || !(margin_scale == margin_scale) || min_members < 0) return RS_ERR_INVALID_ARG;
+  ctx->nn_bound_margin = margin_scale;
+  ctx->nn_bound_min = min_members;
   return RS_OK;
 }
 

@@ -703,15 +703,15 @@ int build_buckets(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t m, const int64_t*
 // ---- Bounded nearest-neighbour searches for large nodes ---------------------------------------
 // The split needs each member's nn2 exactly only near the k-th smallest value (the adaptive l2)
 // and, elsewhere, only whether it lies below or above it (k_select_l2 and the link pass's
-// member filter). For nodes of at least kBoundMin members a sample of buckets (every S-th of
-// the node, about kSampleBuckets of them) is searched exactly first; the sample's order
+// member filter). For nodes of at least min_members (4096 by default) members a sample of
+// buckets (every S-th of the node, about kSampleBuckets of them) is searched exactly first; the sample's order
 // statistics around rank p s (p = (k + 1/2) / g) give bounds lo <= hi; the other members are
 // searched with the limit of nn_limit: a lane stops once its minimum is below lo (its nn2 is
 // then some value below lo) and prunes with hi (a minimum above hi is kept as some value above
 // hi). Members whose nn2 lies in [lo, hi] are found exactly, so the k-th smallest of the stored
 // values equals the exact one whenever it lies in [lo, hi]; k_bounds_check verifies that per
 // node after the selection and sends every node that fails through the exact search again.
-constexpr int64_t kBoundMin = 16384;
+constexpr int64_t kBoundMinDefault = 4096;
 constexpr int64_t kSampleBuckets = 48;
 
 __device__ __forceinline__ int64_t sample_stride(int64_t nbk) {
@@ -719,17 +719,17 @@ __device__ __forceinline__ int64_t sample_stride(int64_t nbk) {
 }
 
 // Queue entry w (bucket order[w]) goes to the sample queue (flag s) or the others (flag r);
-// buckets of nodes below kBoundMin go to the others and are searched exactly.
+// buckets of nodes below min_members go to the others and are searched exactly.
 __global__ void k_queue_flags(int64_t nbk_ub, const int64_t* __restrict__ nbk, const uint32_t* __restrict__ order,
                               const Bucket* __restrict__ bk, const int64_t* __restrict__ node_size,
-                              int64_t* __restrict__ fs, int64_t* __restrict__ fr) {
+                              int64_t min_members, int64_t* __restrict__ fs, int64_t* __restrict__ fr) {
   const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w >= nbk_ub) return;
   int64_t smp = 0, rest = 0;
   if (w < *nbk) {
     const Bucket B = bk[order[w]];
     const int64_t nb_node = int64_t(B.last) - int64_t(B.first) + 1;
-    const bool bounded = node_size[B.node] >= kBoundMin;
+    const bool bounded = node_size[B.node] >= min_members;
     smp = bounded && ((int64_t(order[w]) - int64_t(B.first)) % sample_stride(nb_node)) == 0;
     rest = !smp;
   }
@@ -791,21 +791,21 @@ __device__ float block_select(Val val, int64_t n, uint32_t k, uint32_t* hist, ui
 }
 
 // One block per node of the level: bounds (lo, hi) from the sample of a node of at least
-// kBoundMin members, (-inf, +inf) (exact search) otherwise. The sample of a node is every
+// min_members members, (-inf, +inf) (exact search) otherwise. The sample of a node is every
 // S-th of its buckets; its size s and the target rank r = p s with p = (k + 1/2) / g; the
 // bounds are the sample's order statistics at r -+ d, d = 6 sqrt(s p (1 - p)) + 8 (twice
 // three binomial standard deviations: the sampled buckets are clusters of neighbours).
 __global__ void __launch_bounds__(256)
 k_sample_bounds(int64_t nb, int64_t nn, const int64_t* __restrict__ node_size, const int64_t* __restrict__ boff,
                 const Bucket* __restrict__ bk, const uint32_t* __restrict__ sp, const float* __restrict__ nn2,
-                int f_num, int f_den, float margin, float2* __restrict__ bounds) {
+                int f_num, int f_den, float margin, int64_t min_members, float2* __restrict__ bounds) {
   __shared__ uint32_t hist[256];
   __shared__ uint32_t s_prefix, s_k;
   const int64_t k = blockIdx.x;
   if (k >= nn) return;
   const int64_t g = node_size[nb + k];
   const float inf = __int_as_float(0x7f800000);
-  if (g < kBoundMin) {
+  if (g < min_members) {
     if (threadIdx.x == 0) bounds[k] = make_float2(-inf, inf);
     return;
   }
@@ -920,7 +920,7 @@ static int run_nn(rs_ctx* ctx, NNArgs A, const uint32_t* order, const int64_t* c
 }
 
 // Nearest neighbours of the level: the sample of every large node exactly, its bounds, then the
-// other buckets with those bounds (nodes below kBoundMin: exactly). No host round trip: the
+// other buckets with those bounds (smaller nodes: exactly). No host round trip: the
 // queues and their counts stay on the device.
 int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, float* nn2,
                    cudaStream_t st) {
@@ -935,7 +935,9 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
   int64_t* qcount = scratch_t<int64_t>(ctx, S_P_QCOUNT, 4);
   float2* bounds = scratch_t<float2>(ctx, S_P_BOUNDS, size_t(std::max<int64_t>(nn, 1)));
   if (!fs || !fr || !qs || !qr || !qcount || !bounds) return RS_ERR_OOM;
-  k_queue_flags<<<grid_for(nbk_ub, kT), kT, 0, st>>>(nbk_ub, A.nbuckets, A.order, A.bk, h.node_size, fs, fr);
+  const int64_t bmin = ctx->nn_bound_min > 0 ? ctx->nn_bound_min : kBoundMinDefault;
+  k_queue_flags<<<grid_for(nbk_ub, kT), kT, 0, st>>>(nbk_ub, A.nbuckets, A.order, A.bk, h.node_size, bmin, fs,
+                                                     fr);
   RS_LAUNCHED(ctx, "k_queue_flags");
   RS_TRY(exclusive_scan_i64(ctx, nbk_ub, fs, fs + nbk_ub, st));
   RS_TRY(exclusive_scan_i64(ctx, nbk_ub, fr, fr + nbk_ub, st));
@@ -945,7 +947,7 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
   const int64_t* boff = static_cast<const int64_t*>(ctx->buf[S_P_BOFF].ptr);
   k_sample_bounds<<<unsigned(std::max<int64_t>(nn, 1)), 256, 0, st>>>(nb, nn, h.node_size, boff, A.bk, A.sp, nn2,
                                                                    ctx->cfg.f_num, ctx->cfg.f_den,
-                                                                   ctx->nn_bound_margin, bounds);
+                                                                   ctx->nn_bound_margin, bmin, bounds);
   RS_LAUNCHED(ctx, "k_sample_bounds");
   A.bounds = bounds;
   A.nb = nb;

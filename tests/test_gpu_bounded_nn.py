@@ -1,4 +1,4 @@
-"""Bounded nearest-neighbour searches of the batched form (nodes of at least 16384 members):
+"""Bounded nearest-neighbour searches of the batched form (nodes of at least 4096 members):
 a sample of each large node's buckets is searched exactly, its order statistics bound the
 adaptive link length, and the other members are searched only as far as those bounds need.
 The hierarchy (node table, member lists, deepest nodes, split parameters including l2) must be
@@ -15,15 +15,15 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def snap():
-    # halos up to 6e4 particles: several level-0 nodes and some subnodes above 16384 members
+    # halos up to 6e4 particles: several level-0 nodes and subnodes above 4096 members
     return small_snapshot(1 << 18, 64.0, 77, n_max=6.0e4)
 
 
-def _hierarchy(s, mode, margin=None):
+def _hierarchy(s, mode, margin=None, min_members=0):
     import paper_2412_18629_gb300 as rs
     ctx = gpu_ctx(s, mode=mode)
-    if margin is not None:
-        ctx.nn_bound_margin(margin)
+    if margin is not None or min_members:
+        ctx.nn_bounds(1.0 if margin is None else margin, min_members)
     pos, vel, ids = to_dev(s)
     lab, _ = rs.rs_fof3d(ctx, pos, ids)
     if mode != "plain":
@@ -48,7 +48,7 @@ def test_bounded_search_matches_plain_and_oracle(snap, plain):
     assert_hier_equal(h, hp)
     assert np.array_equal(params.view(np.uint32), pp.view(np.uint32))
     sizes = np.diff(h["member_off"])
-    assert (sizes >= 16384).sum() >= 2
+    assert (sizes >= 4096).sum() >= 2
     o = oracle.hierarchy(snap["pos"], snap["vel"], snap["ids"], lab, snap["box"])
     assert_hier_equal(h, o)
     assert np.array_equal(params[:, :3].view(np.uint32), o["params"][:, :3].view(np.uint32))
@@ -66,6 +66,15 @@ def test_tight_margin_still_exact(snap, plain):
     """A margin of zero (bounds at the sample's own quantile +- 8 ranks) fails more often; the
     fallback keeps every result exact whatever the sample gave."""
     lab, h, params, work = _hierarchy(snap, "batched", margin=0.0)
+    _, hp, pp, _ = plain
+    assert_hier_equal(h, hp)
+    assert np.array_equal(params.view(np.uint32), pp.view(np.uint32))
+
+
+def test_smaller_bounded_nodes(snap, plain):
+    """Bounds down to 2048-member nodes (samples of every 1st-2nd bucket there): still exact."""
+    lab, h, params, work = _hierarchy(snap, "batched", min_members=2048)
+    assert work["bounded_nodes"] > 10, work
     _, hp, pp, _ = plain
     assert_hier_equal(h, hp)
     assert np.array_equal(params.view(np.uint32), pp.view(np.uint32))
