@@ -10,11 +10,14 @@
 // lane's current best (nearest neighbour) or l2 (link, upper triangle of bucket pairs). The
 // link pass runs on the members with a friend only (nn2 <= l2: no other member can be linked),
 // compacted in the same order and bucketed again, so its boxes are tighter and no lane idles.
-// Distances and bounds use packed float32x2 arithmetic with each half rounded like the scalar
-// operation. Lower bounds are computed with the same round-to-nearest float32 operations as d6 on the
-// per-axis gaps to the box: every step is monotone, so the bound never exceeds the computed
-// d6 of any member inside the box, and pruning cannot change the minimum or the set of links.
-// Results are therefore bit-identical to the brute-force kernels (and to the definition).
+// Nodes of 4096 members or more search their nearest neighbours within bounds of l2 taken
+// from an exactly searched sample (see k_sample_bounds; a device check re-searches any node
+// whose l2 falls outside them). Distances and bounds use packed float32x2 arithmetic with each
+// half rounded like the scalar operation. Lower bounds are computed with the same
+// round-to-nearest float32 operations as d6 on the per-axis gaps to the box: every step is
+// monotone, so the bound never exceeds the computed d6 of any member inside the box, and
+// pruning cannot change the minimum or the set of links. Results are therefore bit-identical
+// to the brute-force kernels (and to the definition).
 #include "rs_cro.cuh"
 
 namespace rs {
@@ -345,7 +348,7 @@ __device__ __forceinline__ float lb_box_box(const Box& a, const Box& b, float2 s
 
 // Staged targets of one warp, structure of arrays (x, y, z, vx, vy, vz); slots past the
 // bucket's count hold NaN, whose distance is NaN: it lowers no minimum and passes no test.
-struct Stage {
+struct __align__(16) Stage {  // 16-byte aligned: pairs of slots load as float2
   float c[6][32];
 };
 
@@ -478,7 +481,7 @@ __device__ __forceinline__ void flush_tally(const Tally& T, unsigned long long* 
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(kT) k_nn6d_pruned(NNArgs A, float* __restrict__ nn2) {
+__global__ void __launch_bounds__(kT, 4) k_nn6d_pruned(NNArgs A, float* __restrict__ nn2) {
   __shared__ Stage stg[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int64_t nbk = *A.nbuckets;
@@ -704,9 +707,9 @@ int build_buckets(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t m, const int64_t*
 // The split needs each member's nn2 exactly only near the k-th smallest value (the adaptive l2)
 // and, elsewhere, only whether it lies below or above it (k_select_l2 and the link pass's
 // member filter). For nodes of at least min_members (4096 by default) members a sample of
-// buckets (every S-th of the node, about kSampleBuckets of them) is searched exactly first; the sample's order
-// statistics around rank p s (p = (k + 1/2) / g) give bounds lo <= hi; the other members are
-// searched with the limit of nn_limit: a lane stops once its minimum is below lo (its nn2 is
+// buckets (every S-th of the node, about kSampleBuckets of them) is searched exactly first;
+// the sample's order statistics around rank p s (p = (k + 1/2) / g) give bounds lo <= hi; the
+// other members are searched with the limit of nn_limit: a lane stops once its minimum is below lo (its nn2 is
 // then some value below lo) and prunes with hi (a minimum above hi is kept as some value above
 // hi). Members whose nn2 lies in [lo, hi] are found exactly, so the k-th smallest of the stored
 // values equals the exact one whenever it lies in [lo, hi]; k_bounds_check verifies that per
@@ -718,8 +721,9 @@ __device__ __forceinline__ int64_t sample_stride(int64_t nbk) {
   return nbk / kSampleBuckets > 1 ? nbk / kSampleBuckets : 1;
 }
 
-// Queue entry w (bucket order[w]) goes to the sample queue (flag s) or the others (flag r);
-// buckets of nodes below min_members go to the others and are searched exactly.
+// Queue entry w (bucket order[w]) goes to the first, exact queue (flag s: the samples of the
+// nodes searched with bounds, and every bucket of the smaller nodes, so that the first launch
+// fills the GPU) or to the second (flag r: the other buckets of the bounded nodes).
 __global__ void k_queue_flags(int64_t nbk_ub, const int64_t* __restrict__ nbk, const uint32_t* __restrict__ order,
                               const Bucket* __restrict__ bk, const int64_t* __restrict__ node_size,
                               int64_t min_members, int64_t* __restrict__ fs, int64_t* __restrict__ fr) {
@@ -730,7 +734,7 @@ __global__ void k_queue_flags(int64_t nbk_ub, const int64_t* __restrict__ nbk, c
     const Bucket B = bk[order[w]];
     const int64_t nb_node = int64_t(B.last) - int64_t(B.first) + 1;
     const bool bounded = node_size[B.node] >= min_members;
-    smp = bounded && ((int64_t(order[w]) - int64_t(B.first)) % sample_stride(nb_node)) == 0;
+    smp = !bounded || ((int64_t(order[w]) - int64_t(B.first)) % sample_stride(nb_node)) == 0;
     rest = !smp;
   }
   fs[w] = smp;
@@ -919,9 +923,9 @@ static int run_nn(rs_ctx* ctx, NNArgs A, const uint32_t* order, const int64_t* c
   return RS_OK;
 }
 
-// Nearest neighbours of the level: the sample of every large node exactly, its bounds, then the
-// other buckets with those bounds (smaller nodes: exactly). No host round trip: the
-// queues and their counts stay on the device.
+// Nearest neighbours of the level: the smaller nodes and the sample of every large node
+// exactly, the large nodes' bounds, then their other buckets with those bounds. No host round
+// trip: the queues and their counts stay on the device.
 int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, float* nn2,
                    cudaStream_t st) {
   (void)mb;
@@ -943,7 +947,7 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
   RS_TRY(exclusive_scan_i64(ctx, nbk_ub, fr, fr + nbk_ub, st));
   k_queue_scatter<<<grid_for(nbk_ub, kT), kT, 0, st>>>(nbk_ub, A.order, fs, fr, qs, qr, qcount);
   RS_LAUNCHED(ctx, "k_queue_scatter");
-  RS_TRY(run_nn(ctx, A, qs, qcount + 0, nbk_ub, nn2, st));  // the samples, exactly
+  RS_TRY(run_nn(ctx, A, qs, qcount + 0, nbk_ub, nn2, st));  // exactly
   const int64_t* boff = static_cast<const int64_t*>(ctx->buf[S_P_BOFF].ptr);
   k_sample_bounds<<<unsigned(std::max<int64_t>(nn, 1)), 256, 0, st>>>(nb, nn, h.node_size, boff, A.bk, A.sp, nn2,
                                                                    ctx->cfg.f_num, ctx->cfg.f_den,

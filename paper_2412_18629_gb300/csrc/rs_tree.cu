@@ -374,7 +374,7 @@ struct WalkArgs {
 __global__ void __launch_bounds__(kT)
 k_tree_walk(WalkArgs A) {
   __shared__ uint64_t s_stack[kT / 32][kStack];
-  __shared__ float4 s_leaf[kT / 32][32];
+  __shared__ __align__(16) float s_leaf[kT / 32][3][32];  // a leaf's members in x / y / z rows
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (w >= A.item_off[A.nt]) return;
@@ -402,7 +402,7 @@ k_tree_walk(WalkArgs A) {
   const Cell* __restrict__ ncell = A.cells + cb;
   const float4* __restrict__ nx = A.TX + tb;
   uint64_t* stk = s_stack[wid];
-  float4* leaf = s_leaf[wid];
+  float (*leaf)[32] = s_leaf[wid];
   float S = 0.f, Cc = 0.f, Bt = 0.f;
   uint32_t n_exp = 0, n_dir = 0;
   const uint32_t root_off = __shfl_sync(0xffffffffu, my_lvoff, nlev - 1);
@@ -448,7 +448,10 @@ k_tree_walk(WalkArgs A) {
       const uint32_t c0 = j << kLeafBits;
       const int cnt = int(min(32u, g32 - c0));
       const float inf = __int_as_float(0x7f800000);
-      leaf[lane] = lane < cnt ? nx[c0 + lane] : make_float4(inf, inf, inf, 0.f);
+      const float4 xm = lane < cnt ? nx[c0 + lane] : make_float4(inf, inf, inf, 0.f);
+      leaf[0][lane] = xm.x;
+      leaf[1][lane] = xm.y;
+      leaf[2][lane] = xm.z;
       __syncwarp();
       float blk;
       if (A.eps2 > 0.f) {
@@ -457,10 +460,9 @@ k_tree_walk(WalkArgs A) {
         float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int k = 0; k < 32; k += 2) {
-          const float4 xa = leaf[k], xb = leaf[k + 1];
-          const float2 ex = __fadd2_rn(make_float2(xa.x, xb.x), ntx);
-          const float2 ey = __fadd2_rn(make_float2(xa.y, xb.y), nty);
-          const float2 ez = __fadd2_rn(make_float2(xa.z, xb.z), ntz);
+          const float2 ex = __fadd2_rn(*reinterpret_cast<const float2*>(&leaf[0][k]), ntx);
+          const float2 ey = __fadd2_rn(*reinterpret_cast<const float2*>(&leaf[1][k]), nty);
+          const float2 ez = __fadd2_rn(*reinterpret_cast<const float2*>(&leaf[2][k]), ntz);
           const float2 r2 = __ffma2_rn(ex, ex, __ffma2_rn(ey, ey, __ffma2_rn(ez, ez, e2)));
           acc2 = __fadd2_rn(acc2, make_float2(rsqrtf(r2.x), rsqrtf(r2.y)));
         }
@@ -469,8 +471,8 @@ k_tree_walk(WalkArgs A) {
       } else {
         blk = 0.f;
         for (int k = 0; k < cnt; ++k) {
-          const float4 x = leaf[k];
-          const float ex = __fsub_rn(x.x, t.x), ey = __fsub_rn(x.y, t.y), ez = __fsub_rn(x.z, t.z);
+          const float ex = __fsub_rn(leaf[0][k], t.x), ey = __fsub_rn(leaf[1][k], t.y),
+                      ez = __fsub_rn(leaf[2][k], t.z);
           const float wv = rsqrtf(__fmaf_rn(ex, ex, __fmaf_rn(ey, ey, __fmaf_rn(ez, ez, A.eps2))));
           blk = __fadd_rn(blk, c0 + uint32_t(k) == self_rel ? 0.f : wv);
         }
