@@ -69,7 +69,7 @@ typedef struct rs_config {
   int32_t tree_min_members;   /* batched forms: nodes with at least this many members get their
                                  flags from the certified tree bound (see rs_tree_stats) when
                                  rs_unbind is asked for no potential; 0 = 16384, < 0 = never */
-  float tree_theta;           /* opening angle of that bound (0 = 0.35; at most 0.9) */
+  float tree_theta;           /* opening angle of that bound (0 = 0.45; at most 0.9) */
   int32_t surrogate_gate;     /* 0: the error in the gate is the held-out maximum error of the
                                  training (rs_mlp_set_err_max); 1: per node, calibrated on 64
                                  members evaluated exactly, floored at err_max / 8 */

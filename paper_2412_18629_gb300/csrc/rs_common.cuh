@@ -69,7 +69,7 @@ constexpr int64_t kSurrogateMinMembers = 1024;
 // Default smallest node unbound through the certified tree bound (batched form) and its
 // opening angle (a cell is expanded when its radius bound is at most theta times the distance).
 constexpr int64_t kTreeMinDefault = 16384;
-constexpr float kTreeThetaDefault = 0.35f;
+constexpr float kTreeThetaDefault = 0.45f;
 
 struct Buffer {
   void* ptr = nullptr;
