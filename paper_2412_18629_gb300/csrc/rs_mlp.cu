@@ -402,10 +402,10 @@ __global__ void k_mlp_reduce(int nblk, const float* __restrict__ part, float* __
   grad[p] = s;
 }
 
-// Adam step on the float32 masters, then refresh the bf16 device weights.
-// Adam step number k = *step (0-based); corr[2k], corr[2k + 1] = 1 - b1^(k+1), 1 - b2^(k+1)
-// (the bias corrections, rounded on the host). The step counter lives on the device so that
-// one captured epoch replays with the right corrections.
+// Adam step on the float32 masters (k_pack_weights then refreshes the bf16 device weights).
+// Step number k = *step (0-based); corr[2k], corr[2k + 1] = 1 - b1^(k+1), 1 - b2^(k+1) (the
+// bias corrections, rounded on the host). The step counter lives on the device so that one
+// captured epoch replays with the right corrections.
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ grad, float lr, float b1, float b2, float eps,
                        const float* __restrict__ corr, const int64_t* __restrict__ step) {
