@@ -259,7 +259,10 @@ def kernel_work(r):
     if r.get("sort_keypasses"):
         out["k_sort"] = ("hbm", r["sort_keypasses"] * SORT_BYTES_PER_KEY_PASS, "B",
                          "24 B per key and 8-bit pass (k_sort_hist + k_sort_scatter)")
-    for k in ("k_nn6d_pruned", "k_link6d_pruned", "k_nn6d", "k_link6d"):
+    # the batched forms run the brute-force pair kernels only on small levels (a few thousand
+    # members), which the per-member figure does not separate: they get no stage entry there
+    six = ("k_nn6d", "k_link6d") if r.get("form") == "plain" else ("k_nn6d_pruned", "k_link6d_pruned")
+    for k in six:
         out[k] = ("hbm", r["members"] * NODE_BYTES_PER_MEMBER, "B", "40 B per member and level")
     w = r.get("pairs", {})
     out["k_potential"] = ("alu", w.get("pairs_small", 0.0) * OPS_PAIR, "ops", "7 per ordered pair")

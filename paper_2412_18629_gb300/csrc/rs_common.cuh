@@ -114,6 +114,7 @@ struct rs_ctx {
   int64_t pot_pairs[2] = {0, 0};  // ordered pairs the direct sums evaluated (last rs_unbind)
   float nn_bound_margin = 1.f;    // scale of the sampled nearest-neighbour bounds' margin
   int64_t nn_bound_min = 0;       // smallest node searched with sampled bounds (0: default)
+  bool nn_bounded_level = false;  // the last level's searches used sampled bounds
   // optional per-kernel CUDA-event timing of the dominant kernels (rs_profile)
   bool profile = false;
   bool count_work = false;  // counting variants of the pruned 6D kernels (rs_count_work)

@@ -348,6 +348,7 @@ k_nn6d(int64_t nb, int64_t nn, const int64_t* __restrict__ tile_off, const int64
 // select on the (non-negative) float bit patterns. Nodes up to kSelectWarpMax members take one
 // warp each (k_select_l2_warp), larger ones a block (k_select_l2).
 constexpr int64_t kSelectWarpMax = 4096;
+constexpr int64_t kPrunedMinMembers = 4096;
 
 __global__ void __launch_bounds__(kT)
 k_select_l2_warp(int64_t nb, int64_t nn, const int64_t* __restrict__ node_off,
@@ -856,7 +857,9 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     int64_t* cidx = scratch_t<int64_t>(ctx, S_CHILD_IDX, size_t(m) + 1);
     int64_t* mpos = scratch_t<int64_t>(ctx, S_GKEY_A, size_t(m) + 1);
     if (!tile_off || !nn2 || !uf || !cnt || !cflag || !cidx || !mpos) return RS_ERR_OOM;
-    const bool batched = ctx->cfg.batched != 0;
+    // batched form: pruned searches, except on levels of at most kPrunedMinMembers members,
+    // where the brute-force pair kernels (identical results) cost less than the bucket set-up
+    const bool batched = ctx->cfg.batched != 0 && m > kPrunedMinMembers;
     const int64_t tiles_ub = nn + m / kTile6 + 1;
     if (batched) {
       RS_TRY(prune6d_prepare(ctx, nb, nn, mb, m, sums, st));
@@ -884,11 +887,13 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     if (batched) {  // bounded searches: nodes whose l2 fell outside their bounds, exactly again
       const int* failed = nullptr;
       RS_TRY(prune6d_check(ctx, nb, nn, m, nn2, &failed, st));
-      h = hier_of(ctx);
-      ProfScope prof_(ctx, "k_select_l2", st);
-      k_select_l2<<<unsigned(nn), kT, 0, st>>>(nb, h.node_off, h.node_size, nn2, mb, f_num, f_den, h.inv,
-                                               failed);
-      RS_LAUNCHED(ctx, "k_select_l2");
+      if (failed) {
+        h = hier_of(ctx);
+        ProfScope prof_(ctx, "k_select_l2", st);
+        k_select_l2<<<unsigned(nn), kT, 0, st>>>(nb, h.node_off, h.node_size, nn2, mb, f_num, f_den, h.inv,
+                                                 failed);
+        RS_LAUNCHED(ctx, "k_select_l2");
+      }
     }
     k_iota_u32<<<grid_for(m, kT), kT, 0, st>>>(m, uf);
     RS_LAUNCHED(ctx, "k_iota_u32");

@@ -932,6 +932,9 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
   Hier h = hier_of(ctx);
   NNArgs A = nn_args(ctx, nn);
   const int64_t nbk_ub = nn + m / 32 + 1;
+  const int64_t bmin = ctx->nn_bound_min > 0 ? ctx->nn_bound_min : kBoundMinDefault;
+  ctx->nn_bounded_level = m >= bmin;  // a node of bmin members needs that many at the level
+  if (!ctx->nn_bounded_level) return run_nn(ctx, A, A.order, A.nbuckets, nbk_ub, nn2, st);
   int64_t* fs = scratch_t<int64_t>(ctx, S_P_QFS, size_t(nbk_ub) + 1);
   int64_t* fr = scratch_t<int64_t>(ctx, S_P_QFR, size_t(nbk_ub) + 1);
   uint32_t* qs = scratch_t<uint32_t>(ctx, S_P_QS, size_t(nbk_ub));
@@ -939,7 +942,6 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
   int64_t* qcount = scratch_t<int64_t>(ctx, S_P_QCOUNT, 4);
   float2* bounds = scratch_t<float2>(ctx, S_P_BOUNDS, size_t(std::max<int64_t>(nn, 1)));
   if (!fs || !fr || !qs || !qr || !qcount || !bounds) return RS_ERR_OOM;
-  const int64_t bmin = ctx->nn_bound_min > 0 ? ctx->nn_bound_min : kBoundMinDefault;
   k_queue_flags<<<grid_for(nbk_ub, kT), kT, 0, st>>>(nbk_ub, A.nbuckets, A.order, A.bk, h.node_size, bmin, fs,
                                                      fr);
   RS_LAUNCHED(ctx, "k_queue_flags");
@@ -962,6 +964,8 @@ int rs::prune6d_nn(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t mb, int64_t m, f
 // exactly (*failed_out: int [nn], 1 for those nodes, for the selection to be repeated there).
 int rs::prune6d_check(rs_ctx* ctx, int64_t nb, int64_t nn, int64_t m, float* nn2, const int** failed_out,
                       cudaStream_t st) {
+  *failed_out = nullptr;
+  if (!ctx->nn_bounded_level) return RS_OK;  // every search of the level was exact
   Hier h = hier_of(ctx);
   NNArgs A = nn_args(ctx, nn);
   const int64_t nbk_ub = nn + m / 32 + 1;
