@@ -111,3 +111,26 @@ def test_oracle_sample_cubes_around_the_median_load():
     assert all(c not in [(i, i, i) for i in range(8)] for c in cubes)
     loads = {(i, i, i): (i + 1) ** 2 for i in range(8)}
     assert all(loads.get(c, 0) == 0 for c in cubes)
+
+
+def test_six_d_stages_follow_the_form(monkeypatch):
+    """The batched forms run the brute-force pair kernels only on their small levels: those get
+    no stage entry there (the per-member figure would not describe them); the plain form reports
+    them and no pruned kernel."""
+    monkeypatch.setattr(bench, "_measured_peaks", lambda: {"hbm_gbs": 6700.0})
+    prof = {"k_nn6d": (4.0, 5), "k_link6d": (2.0, 5), "k_nn6d_pruned": (13.0, 20),
+            "k_link6d_pruned": (7.0, 10)}
+    batched = bench.stages(_form(prof=prof, form="batched"))
+    assert "k_nn6d_pruned" in batched and "k_link6d_pruned" in batched
+    assert "k_nn6d" not in batched and "k_link6d" not in batched
+    plain = bench.stages(_form(prof=prof, form="plain"))
+    assert "k_nn6d" in plain and "k_link6d" in plain and "k_nn6d_pruned" not in plain
+
+
+def test_traffic_attached_to_stages(monkeypatch):
+    monkeypatch.setattr(bench, "_measured_peaks", lambda: {"hbm_gbs": 6700.0})
+    prof = {"k_fof_link": (6.0, 2), "k_tree_walk": (8.0, 3)}
+    st = bench.stages(_form(prof=prof), {"k_fof_link": 3.0e9, "k_tree_walk": 7.0e8})
+    assert st["k_fof_link"]["traffic"] == 3.0e9
+    assert st["k_fof_link"]["algorithmic_bytes_per_launch"] == pytest.approx((1 << 24) * 28.0 / 2)
+    assert st["k_tree_walk"]["traffic"] == 7.0e8 and "algorithmic_bytes_per_launch" not in st["k_tree_walk"]
