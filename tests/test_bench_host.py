@@ -134,3 +134,16 @@ def test_traffic_attached_to_stages(monkeypatch):
     assert st["k_fof_link"]["traffic"] == 3.0e9
     assert st["k_fof_link"]["algorithmic_bytes_per_launch"] == pytest.approx((1 << 24) * 28.0 / 2)
     assert st["k_tree_walk"]["traffic"] == 7.0e8 and "algorithmic_bytes_per_launch" not in st["k_tree_walk"]
+
+
+def test_stream_snapshots_follow_the_recipe():
+    """The batched stream's snapshot k has n = 2^(18 + k mod 5) particles at unit mean spacing
+    (box = n^(1/3)); the generator worker returns what the pipeline needs."""
+    from paper_2412_18629_gb300 import synth
+    for k in range(7):
+        spec = synth.stream_spec(k)
+        assert spec.n == 1 << (18 + k % 5)
+        assert spec.box == pytest.approx(spec.n ** (1.0 / 3.0), rel=1e-12)
+    s = bench._gen_stream(0)
+    assert set(s) == {"pos", "vel", "ids", "box", "link_length", "softening", "particle_mass"}
+    assert s["pos"].shape == (1 << 18, 3) and s["ids"].dtype.name == "int64"
