@@ -350,17 +350,18 @@ k_nn6d(int64_t nb, int64_t nn, const int64_t* __restrict__ tile_off, const int64
 constexpr int64_t kSelectWarpMax = 4096;
 constexpr int64_t kPrunedMinMembers = 4096;
 
+// only (if given): int [nn], the nodes to select for (the others keep their l2).
 __global__ void __launch_bounds__(kT)
 k_select_l2_warp(int64_t nb, int64_t nn, const int64_t* __restrict__ node_off,
                  const int64_t* __restrict__ node_size, const float* __restrict__ nn2, int64_t mb,
-                 int f_num, int f_den, float4* __restrict__ inv) {
+                 int f_num, int f_den, float4* __restrict__ inv, const int* __restrict__ only) {
   __shared__ uint32_t hist[kT / 32][256];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t k = int64_t(blockIdx.x) * (kT / 32) + w;
   if (k >= nn) return;
   const int64_t q = nb + k;
   const int64_t base = node_off[q] - mb, g = node_size[q];
-  if (g > kSelectWarpMax) return;
+  if (g > kSelectWarpMax || (only && !only[k])) return;
   uint32_t kk = uint32_t((int64_t(f_num) * g + f_den - 1) / f_den - 1);
   uint32_t prefix = 0, mask = 0;
   uint32_t* h = hist[w];
@@ -879,7 +880,7 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     {
       ProfScope prof_(ctx, "k_select_l2", st);
       k_select_l2_warp<<<grid_for(nn, kT / 32), kT, 0, st>>>(nb, nn, h.node_off, h.node_size, nn2, mb, f_num,
-                                                            f_den, h.inv);
+                                                            f_den, h.inv, nullptr);
       k_select_l2<<<unsigned(nn), kT, 0, st>>>(nb, h.node_off, h.node_size, nn2, mb, f_num, f_den, h.inv,
                                                nullptr);
     }
@@ -887,9 +888,11 @@ extern "C" int rs_fof6d(rs_ctx* ctx, int64_t n, const float* pos, const float* v
     if (batched) {  // bounded searches: nodes whose l2 fell outside their bounds, exactly again
       const int* failed = nullptr;
       RS_TRY(prune6d_check(ctx, nb, nn, m, nn2, &failed, st));
-      if (failed) {
+      if (failed) {  // bounded nodes can be small enough for the warp selection too
         h = hier_of(ctx);
         ProfScope prof_(ctx, "k_select_l2", st);
+        k_select_l2_warp<<<grid_for(nn, kT / 32), kT, 0, st>>>(nb, nn, h.node_off, h.node_size, nn2, mb, f_num,
+                                                              f_den, h.inv, failed);
         k_select_l2<<<unsigned(nn), kT, 0, st>>>(nb, h.node_off, h.node_size, nn2, mb, f_num, f_den, h.inv,
                                                  failed);
         RS_LAUNCHED(ctx, "k_select_l2");

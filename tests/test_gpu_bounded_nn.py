@@ -78,3 +78,15 @@ def test_smaller_bounded_nodes(snap, plain):
     _, hp, pp, _ = plain
     assert_hier_equal(h, hp)
     assert np.array_equal(params.view(np.uint32), pp.view(np.uint32))
+
+
+def test_forced_fallback_of_small_bounded_nodes(snap, plain):
+    """Bounded nodes of 2048-4096 members take the warp-level selection: when all of them fail
+    (empty bounds), that selection runs again on them and the hierarchy stays exact."""
+    lab, h, params, work = _hierarchy(snap, "batched", margin=-1.0, min_members=2048)
+    assert work["bounded_nodes"] > 10 and work["bound_failures"] == work["bounded_nodes"], work
+    sizes = np.diff(h["member_off"])
+    assert ((sizes >= 2048) & (sizes <= 4096)).sum() >= 1
+    _, hp, pp, _ = plain
+    assert_hier_equal(h, hp)
+    assert np.array_equal(params.view(np.uint32), pp.view(np.uint32))
